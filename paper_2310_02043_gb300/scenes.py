@@ -1,0 +1,330 @@
+"""Seeded synthetic inputs: scenes, luminaires and their perturbations.
+
+This module is the one place both the CUDA path and the CPU oracle take their
+inputs from. It builds geometry and parameter arrays only; it holds none of the
+light-transport arithmetic (no flux, no sampling, no intersection, no texel
+lookup), so that the two implementations stay independent.
+
+Scene layout (all arrays are C-contiguous numpy):
+
+* ``xyz``       float32 [n_tri, 3, 3]  triangle vertex positions, metres
+* ``uv``        float32 [n_tri, 3, 2]  per-vertex coordinates in the triangle's
+                                       tile chart, in [0, 1]^2
+* ``tile``      int32   [n_tri]        tile (texel chart) of each triangle
+* ``albedo``    float32 [n_tri]        Lambertian albedo rho in [0, 1]
+* ``tile_res``  int32   [n_tiles, 2]   texel resolution (res_u, res_v)
+* ``tile_area`` float64 [n_tiles]      surface area the tile covers, m^2
+
+A planar quad is one tile made of two triangles that share the quad's chart;
+a lone triangle is a 1x1 tile. Texels of a tile are numbered
+``u_index + res_u * v_index`` after all texels of the tiles before it.
+
+Luminaires are a float64 array [n_lights, 9] with columns ``LIGHT_FIELDS``:
+type (0 point, 1 spot), position x, y, z, yaw, pitch (radians; the spot axis
+is (cos p cos y, cos p sin y, sin p) with z up), p_int (the intensity
+parameter, I_e = p_int^2 / 2 as in Sec. 4.4.1 of the paper), theta_in and
+theta_out (spot cone half-angles, radians).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+LIGHT_FIELDS = ("type", "x", "y", "z", "yaw", "pitch", "p_int", "theta_in", "theta_out")
+POINT, SPOT = 0, 1
+GRAD_FIELDS = ("x", "y", "z", "yaw", "pitch", "p_int", "theta_in", "theta_out")
+
+
+@dataclass
+class Scene:
+    name: str
+    xyz: np.ndarray
+    uv: np.ndarray
+    tile: np.ndarray
+    albedo: np.ndarray
+    tile_res: np.ndarray
+    tile_area: np.ndarray
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_tri(self) -> int:
+        return int(self.xyz.shape[0])
+
+    @property
+    def n_tiles(self) -> int:
+        return int(self.tile_res.shape[0])
+
+    @property
+    def n_texels(self) -> int:
+        return int(np.sum(self.tile_res[:, 0].astype(np.int64) * self.tile_res[:, 1]))
+
+    def texel_offsets(self) -> np.ndarray:
+        """First texel index of every tile, plus the total at the end."""
+        counts = self.tile_res[:, 0].astype(np.int64) * self.tile_res[:, 1]
+        return np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+
+    def bbox_diagonal(self) -> float:
+        pts = self.xyz.reshape(-1, 3).astype(np.float64)
+        return float(np.linalg.norm(pts.max(0) - pts.min(0)))
+
+
+class _Builder:
+    """Accumulates quads and triangles into the flat scene arrays."""
+
+    def __init__(self):
+        self.xyz, self.uv, self.tile, self.albedo = [], [], [], []
+        self.res, self.area = [], []
+
+    def quad(self, corner, a, b, res_u, res_v, albedo):
+        """Parallelogram corner + s*a + t*b, s, t in [0, 1]; one tile."""
+        c = np.asarray(corner, np.float64)
+        a = np.asarray(a, np.float64)
+        b = np.asarray(b, np.float64)
+        t = len(self.res)
+        p00, p10, p11, p01 = c, c + a, c + a + b, c + b
+        self.xyz += [[p00, p10, p11], [p00, p11, p01]]
+        self.uv += [[[0, 0], [1, 0], [1, 1]], [[0, 0], [1, 1], [0, 1]]]
+        self.tile += [t, t]
+        self.albedo += [albedo, albedo]
+        self.res.append([int(res_u), int(res_v)])
+        self.area.append(float(np.linalg.norm(np.cross(a, b))))
+
+    def quad_pitch(self, corner, a, b, pitch, albedo):
+        """Quad whose texel count follows a target texel pitch (metres)."""
+        ru = max(1, int(np.ceil(np.linalg.norm(a) / pitch - 1e-9)))
+        rv = max(1, int(np.ceil(np.linalg.norm(b) / pitch - 1e-9)))
+        self.quad(corner, a, b, ru, rv, albedo)
+
+    def triangle(self, p0, p1, p2, albedo):
+        """A lone triangle is a 1x1 tile."""
+        p0, p1, p2 = (np.asarray(p, np.float64) for p in (p0, p1, p2))
+        t = len(self.res)
+        self.xyz.append([p0, p1, p2])
+        self.uv.append([[0, 0], [1, 0], [0, 1]])
+        self.tile.append(t)
+        self.albedo.append(albedo)
+        self.res.append([1, 1])
+        self.area.append(0.5 * float(np.linalg.norm(np.cross(p1 - p0, p2 - p0))))
+
+    def box(self, lo, hi, res_or_pitch, albedo, faces=("-x", "+x", "-y", "+y", "-z", "+z"), pitch=False):
+        lo = np.asarray(lo, np.float64)
+        hi = np.asarray(hi, np.float64)
+        dx, dy, dz = hi - lo
+        ex, ey, ez = np.array([dx, 0, 0]), np.array([0, dy, 0]), np.array([0, 0, dz])
+        spec = {
+            "-x": (lo, ey, ez),
+            "+x": (lo + ex, ey, ez),
+            "-y": (lo, ex, ez),
+            "+y": (lo + ey, ex, ez),
+            "-z": (lo, ex, ey),
+            "+z": (lo + ez, ex, ey),
+        }
+        for f in faces:
+            c, a, b = spec[f]
+            if pitch:
+                self.quad_pitch(c, a, b, res_or_pitch, albedo)
+            else:
+                self.quad(c, a, b, res_or_pitch, res_or_pitch, albedo)
+
+    def build(self, name, **meta) -> Scene:
+        return Scene(
+            name=name,
+            xyz=np.ascontiguousarray(np.asarray(self.xyz, np.float32)),
+            uv=np.ascontiguousarray(np.asarray(self.uv, np.float32)),
+            tile=np.ascontiguousarray(np.asarray(self.tile, np.int32)),
+            albedo=np.ascontiguousarray(np.asarray(self.albedo, np.float32)),
+            tile_res=np.ascontiguousarray(np.asarray(self.res, np.int32).reshape(-1, 2)),
+            tile_area=np.ascontiguousarray(np.asarray(self.area, np.float64)),
+            meta=dict(meta),
+        )
+
+
+def make_lights(rows) -> np.ndarray:
+    """Rows of (type, x, y, z, yaw, pitch, p_int, theta_in, theta_out)."""
+    arr = np.asarray(rows, np.float64).reshape(-1, len(LIGHT_FIELDS))
+    return np.ascontiguousarray(arr)
+
+
+def point_light(pos, intensity):
+    """Point light with I_e = intensity (p_int = sqrt(2 I_e))."""
+    return [POINT, *pos, 0.0, 0.0, float(np.sqrt(2.0 * intensity)), 0.0, 0.0]
+
+
+def spot_light(pos, yaw, pitch, intensity, theta_in, theta_out):
+    return [SPOT, *pos, yaw, pitch, float(np.sqrt(2.0 * intensity)), theta_in, theta_out]
+
+
+# --------------------------------------------------------------------------
+# Workload scenes
+# --------------------------------------------------------------------------
+
+def cornell_box(res: int = 32, albedo: float = 0.7) -> Scene:
+    """Cornell-box room: 1 m cube with the front (y = 0) open, 5 room quads,
+    a short 0.3 m box and a tall 0.3 x 0.3 x 0.6 m box without bottoms (they
+    rest on the floor). 15 quads = 30 triangles, res x res texels per face."""
+    b = _Builder()
+    one = 1.0
+    b.quad([0, 0, 0], [one, 0, 0], [0, one, 0], res, res, albedo)      # floor z = 0
+    b.quad([0, 0, one], [one, 0, 0], [0, one, 0], res, res, albedo)    # ceiling z = 1
+    b.quad([0, one, 0], [one, 0, 0], [0, 0, one], res, res, albedo)    # back wall y = 1
+    b.quad([0, 0, 0], [0, one, 0], [0, 0, one], res, res, albedo)      # left wall x = 0
+    b.quad([one, 0, 0], [0, one, 0], [0, 0, one], res, res, albedo)    # right wall x = 1
+    sides = ("-x", "+x", "-y", "+y", "+z")
+    b.box([0.2, 0.55, 0.0], [0.5, 0.85, 0.3], res, albedo, faces=sides)
+    b.box([0.55, 0.25, 0.0], [0.85, 0.55, 0.6], res, albedo, faces=sides)
+    return b.build("cornell", res=res, albedo=albedo)
+
+
+def cornell_lights() -> np.ndarray:
+    """One point light at (0.5, 0.5, 0.9), I_e = 1."""
+    return make_lights([point_light((0.5, 0.5, 0.9), 1.0)])
+
+
+def office(seed: int = 0, pitch: float = 0.02, n_boxes: int = 200) -> Scene:
+    """Procedural office, 20 x 10 x 3 m closed room with ``n_boxes`` desks and
+    cabinets (6 faces each, lifted 1 cm off the floor), texel pitch ``pitch``.
+
+    Boxes sit one per cell of a 20 x 10 grid of 1 m cells (cells drawn without
+    replacement when fewer than 200), jittered inside the cell: 60 % desks of
+    0.9 x 0.7 x 0.75 m, 40 % cabinets of 0.5 x 0.45 x U[1, 2] m, each turned by
+    0 or 90 degrees. Albedo is U[0.3, 0.8] per box and per room face."""
+    rng = np.random.default_rng(seed)
+    b = _Builder()
+    L, W, H = 20.0, 10.0, 3.0
+    room = [
+        ([0, 0, 0], [L, 0, 0], [0, W, 0]),   # floor
+        ([0, 0, H], [L, 0, 0], [0, W, 0]),   # ceiling
+        ([0, 0, 0], [L, 0, 0], [0, 0, H]),   # wall y = 0
+        ([0, W, 0], [L, 0, 0], [0, 0, H]),   # wall y = W
+        ([0, 0, 0], [0, W, 0], [0, 0, H]),   # wall x = 0
+        ([L, 0, 0], [0, W, 0], [0, 0, H]),   # wall x = L
+    ]
+    for c, a, bb in room:
+        b.quad_pitch(c, a, bb, pitch, float(rng.uniform(0.3, 0.8)))
+    cells = rng.permutation(200)[:n_boxes]
+    for cell in np.sort(cells):
+        cx, cy = float(cell % 20), float(cell // 20)
+        if rng.uniform() < 0.6:
+            sx, sy, sz = 0.9, 0.7, 0.75
+        else:
+            sx, sy, sz = 0.5, 0.45, float(rng.uniform(1.0, 2.0))
+        if rng.uniform() < 0.5:
+            sx, sy = sy, sx
+        margin = 0.05
+        x0 = cx + margin + rng.uniform(0.0, 1.0 - 2 * margin - sx)
+        y0 = cy + margin + rng.uniform(0.0, 1.0 - 2 * margin - sy)
+        z0 = 0.01
+        b.box([x0, y0, z0], [x0 + sx, y0 + sy, z0 + sz], pitch, float(rng.uniform(0.3, 0.8)), pitch=True)
+    return b.build("office", seed=seed, pitch=pitch, n_boxes=n_boxes)
+
+
+def office_lights(seed: int = 0, intensity: float = 50.0, theta_in_deg: float = 40.0,
+                  theta_out_deg: float = 60.0) -> np.ndarray:
+    """16 spots on a 4 x 4 grid at z = 2.8 m pointing down, pitch
+    -pi/2 + U(-0.2, 0.2), yaw U(0, 2 pi)."""
+    rng = np.random.default_rng(seed + 1000)
+    rows = []
+    for iy in range(4):
+        for ix in range(4):
+            x = 2.5 + 5.0 * ix
+            y = 1.25 + 2.5 * iy
+            yaw = float(rng.uniform(0.0, 2 * np.pi))
+            pitch = -np.pi / 2 + float(rng.uniform(-0.2, 0.2))
+            rows.append(spot_light((x, y, 2.8), yaw, pitch, intensity,
+                                   np.radians(theta_in_deg), np.radians(theta_out_deg)))
+    return make_lights(rows)
+
+
+def perturb_lights(lights: np.ndarray, seed: int, pos_sigma: float = 0.05, angle_sigma: float = 0.0,
+                   intensity_range=(0.8, 1.2), theta_in_delta: float = 0.0) -> np.ndarray:
+    """Seeded perturbation of a light array (the 'ground-truth' lights a target
+    is traced from). Intensity I_e is scaled by U[intensity_range]."""
+    rng = np.random.default_rng(seed)
+    out = np.array(lights, np.float64, copy=True)
+    n = out.shape[0]
+    out[:, 1:4] += rng.normal(0.0, pos_sigma, size=(n, 3))
+    if angle_sigma > 0:
+        out[:, 4:6] += rng.normal(0.0, angle_sigma, size=(n, 2))
+    scale = rng.uniform(intensity_range[0], intensity_range[1], size=n)
+    out[:, 6] *= np.sqrt(scale)          # I_e = p^2 / 2 scales by `scale`
+    if theta_in_delta > 0:
+        spot = out[:, 0] == SPOT
+        d = rng.uniform(-theta_in_delta, theta_in_delta, size=n)
+        out[spot, 7] = np.minimum(out[spot, 7] + d[spot], out[spot, 8] - 1e-3)
+    return np.ascontiguousarray(out)
+
+
+# --------------------------------------------------------------------------
+# Small scenes used to pin the oracle and to probe edge cases
+# --------------------------------------------------------------------------
+
+def plane(half: float = 1.0, res: int = 16, albedo: float = 0.5, z: float = 0.0) -> Scene:
+    """A single square quad [-half, half]^2 at height z, res x res texels."""
+    b = _Builder()
+    b.quad([-half, -half, z], [2 * half, 0, 0], [0, 2 * half, 0], res, res, albedo)
+    return b.build("plane", half=half, res=res)
+
+
+def closed_cube(size: float = 1.0, res: int = 8, albedo: float = 0.5) -> Scene:
+    """Closed cube [0, size]^3, 6 quads, uniform albedo (no ray escapes)."""
+    b = _Builder()
+    b.box([0, 0, 0], [size, size, size], res, albedo)
+    return b.build("cube", size=size, res=res, albedo=albedo)
+
+
+def icosphere(radius: float = 1.0, subdiv: int = 3, albedo: float = 0.5) -> Scene:
+    """Closed icosphere centred at the origin; each triangle is a 1x1 tile."""
+    t = (1.0 + 5 ** 0.5) / 2.0
+    verts = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0), (0, -1, t), (0, 1, t),
+             (0, -1, -t), (0, 1, -t), (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
+    faces = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4),
+             (11, 10, 2), (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8),
+             (3, 8, 9), (4, 9, 5), (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    v = [np.asarray(p, np.float64) / np.linalg.norm(p) for p in verts]
+    for _ in range(subdiv):
+        cache = {}
+
+        def mid(i, j):
+            key = (min(i, j), max(i, j))
+            if key not in cache:
+                m = v[i] + v[j]
+                v.append(m / np.linalg.norm(m))
+                cache[key] = len(v) - 1
+            return cache[key]
+
+        nf = []
+        for a, bb, c in faces:
+            ab, bc, ca = mid(a, bb), mid(bb, c), mid(c, a)
+            nf += [(a, ab, ca), (bb, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        faces = nf
+    b = _Builder()
+    for a, bb, c in faces:
+        b.triangle(radius * v[a], radius * v[bb], radius * v[c], albedo)
+    return b.build("icosphere", radius=radius, subdiv=subdiv, albedo=albedo)
+
+
+def random_triangles(n: int, seed: int, extent: float = 1.0, albedo: float = 0.5) -> Scene:
+    """n random triangles in [0, extent]^3 (a tiny scene for brute-force checks)."""
+    rng = np.random.default_rng(seed)
+    b = _Builder()
+    for _ in range(n):
+        c = rng.uniform(0.1, 0.9, size=3) * extent
+        p = [c + rng.normal(0, 0.2 * extent, size=3) for _ in range(3)]
+        b.triangle(p[0], p[1], p[2], albedo)
+    return b.build("random_triangles", seed=seed, n=n)
+
+
+def random_rays(n: int, seed: int, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
+    """n ray origins uniform in the box [lo, hi] and isotropic directions."""
+    rng = np.random.default_rng(seed)
+    o = rng.uniform(lo, hi, size=(n, 3))
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return o, d
+
+
+def random_weights(n_texels: int, seed: int, scale: float = 1.0) -> np.ndarray:
+    """Seeded per-texel adjoint weights (used to inject dO/dE directly)."""
+    rng = np.random.default_rng(seed)
+    return np.ascontiguousarray(rng.normal(0.0, scale, size=n_texels).astype(np.float32))

@@ -1,0 +1,178 @@
+"""Pins for the oracle's forward pass (Alg. 1, Eq. 7-8) against closed forms.
+
+* emission and bounce sampling distributions (uniform sphere, uniform cone,
+  cosine lobe) by Kolmogorov-Smirnov tests;
+* energy: in a closed scene nothing escapes, so sum_t A_t E_t equals the
+  emitted power times sum_{i<B} rho^i exactly;
+* inverse-square law: with one hit, a texel's irradiance is I Omega_t / A_t
+  (point light) or the quadrature of I a cos / r^2 (spot);
+* interior sphere: cosine-weighted reflection from any point of a sphere lands
+  uniformly on it, so the second-hit irradiance is uniform even for an
+  off-centre light."""
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+from paper_2310_02043_gb300 import scenes
+from tests import closed_forms as cf
+
+
+def test_point_emission_is_uniform_on_the_sphere():
+    light = scenes.make_lights([scenes.point_light((0, 0, 0), 2.0)])[0]
+    n = 4000
+    W = np.array([oracle.emit(light, n, 5, k)[0] for k in range(n)])
+    np.testing.assert_allclose(np.linalg.norm(W, axis=1), 1.0, atol=1e-12)
+    assert stats.kstest(W[:, 2], "uniform", args=(-1, 2)).pvalue > 1e-3
+    az = np.arctan2(W[:, 1], W[:, 0])
+    assert stats.kstest(az, "uniform", args=(-np.pi, 2 * np.pi)).pvalue > 1e-3
+    _, phi, a = oracle.emit(light, n, 5, 0)
+    assert phi == pytest.approx(2.0 * 4 * np.pi / n, rel=1e-14) and a == 1.0
+
+
+def test_spot_emission_is_uniform_in_the_outer_cone():
+    yaw, pitch, th_in, th_out = 0.7, -1.1, 0.3, 0.8
+    light = scenes.make_lights([scenes.spot_light((0, 0, 0), yaw, pitch, 3.0, th_in, th_out)])[0]
+    axis = cf.spot_axis(yaw, pitch)
+    n = 4000
+    rows = [oracle.emit(light, n, 8, k) for k in range(n)]
+    W = np.array([r[0] for r in rows])
+    c = W @ axis
+    co, ci = np.cos(th_out), np.cos(th_in)
+    assert c.min() >= co - 1e-12
+    assert stats.kstest(c, "uniform", args=(co, 1 - co)).pvalue > 1e-3
+    # azimuth about the axis is uniform
+    ref = np.cross(axis, [1.0, 0.0, 0.0]); ref /= np.linalg.norm(ref)
+    ref2 = np.cross(axis, ref)
+    az = np.arctan2(W @ ref2, W @ ref)
+    assert stats.kstest(az, "uniform", args=(-np.pi, 2 * np.pi)).pvalue > 1e-3
+    # flux: I * 2 pi (1 - cos th_out) * a(theta) / N with the falloff of Eq. S.11
+    phi = np.array([r[1] for r in rows])
+    a = cf.spot_quadratic_falloff(c, ci, co)
+    np.testing.assert_allclose(phi, 3.0 * 2 * np.pi * (1 - co) * a / n, rtol=1e-9, atol=1e-15)
+
+
+def test_cosine_directions_follow_the_cosine_lobe():
+    rng = np.random.default_rng(1)
+    for _ in range(4):
+        nrm = rng.normal(size=3); nrm /= np.linalg.norm(nrm)
+        if rng.uniform() < 0.3:
+            nrm = np.array([0.0, 0.0, -1.0]) if rng.uniform() < 0.5 else np.array([1.0, 0.0, 0.0])
+        u = rng.uniform(size=(3000, 2))
+        W = np.array([oracle.cosine_dir(nrm, a, b) for a, b in u])
+        np.testing.assert_allclose(np.linalg.norm(W, axis=1), 1.0, atol=1e-12)
+        c = W @ nrm
+        assert c.min() > 0
+        # cosine-weighted: cos^2(theta) is uniform on [0, 1]
+        assert stats.kstest(c * c, "uniform").pvalue > 1e-3
+
+
+def test_energy_closed_cube_point_light_is_exact():
+    rho, B, I = 0.6, 4, 1.7
+    sc = scenes.closed_cube(size=1.0, res=6, albedo=rho)
+    L = scenes.make_lights([scenes.point_light((0.31, 0.62, 0.44), I)])
+    r = oracle.forward(sc, L, seed=3, n_photons=20000, max_hits=B)
+    A = oracle.texel_areas(sc)
+    rho32 = float(np.float32(rho))        # albedo is stored as float32
+    expect = I * 4 * np.pi * sum(rho32 ** i for i in range(B))
+    assert np.sum(A * r["E"]) == pytest.approx(expect, rel=1e-12)
+    assert r["segments"] == 20000 * B and r["deposits"] == 20000 * B
+
+
+def test_bounce_flux_uses_the_albedo_of_the_surface_left():
+    # Eq. 7 with a Lambertian f and cosine sampling: Phi_{i+1} = rho(x_i) Phi_i.
+    # With per-face albedo, the second-hit energy equals sum_f rho_f times the
+    # first-hit energy landing on face f -- exactly, for the same seed.
+    sc = scenes.closed_cube(size=1.0, res=3, albedo=0.5)
+    rho_face = np.array([0.9, 0.1, 0.3, 0.6, 0.45, 0.75], np.float32)
+    sc.albedo = np.ascontiguousarray(rho_face[sc.tile])
+    L = scenes.make_lights([scenes.point_light((0.3, 0.6, 0.45), 1.0)])
+    n = 1 << 14
+    r1 = oracle.forward(sc, L, 6, n, 1)
+    r2 = oracle.forward(sc, L, 6, n, 2)
+    A = oracle.texel_areas(sc)
+    per_texel_tile = np.repeat(np.arange(6), 9)
+    e1_face = np.bincount(per_texel_tile, weights=A * r1["E"], minlength=6)
+    second = np.sum(A * (r2["E"] - r1["E"]))
+    assert second == pytest.approx(float(np.sum(rho_face.astype(np.float64) * e1_face)), rel=1e-11)
+
+
+def test_energy_closed_cube_spot_matches_cone_integral():
+    # E[sum_r Phi_r] = I * 2 pi * int_{co}^{1} a(c) dc = I 2 pi ((1 - ci) + (ci - co) / 3)
+    rho, B, I, th_in, th_out = 0.5, 2, 2.0, 0.35, 0.9
+    sc = scenes.closed_cube(size=1.0, res=4, albedo=rho)
+    L = scenes.make_lights([scenes.spot_light((0.5, 0.5, 0.8), 0.2, -1.3, I, th_in, th_out)])
+    n = 1 << 16
+    r = oracle.forward(sc, L, seed=4, n_photons=n, max_hits=B)
+    A = oracle.texel_areas(sc)
+    emitted = np.sum(A * r["E"]) / (1 + float(np.float32(rho)))
+    ci, co = np.cos(th_in), np.cos(th_out)
+    expect = I * 2 * np.pi * ((1 - ci) + (ci - co) / 3)
+    # per-ray flux I Omega a / N with a(c) of c ~ U[co, 1]: variance from E[a^2]
+    Ea2 = ((1 - ci) + (ci - co) / 5) / (1 - co)
+    Ea = ((1 - ci) + (ci - co) / 3) / (1 - co)
+    sigma = I * 2 * np.pi * (1 - co) * np.sqrt((Ea2 - Ea * Ea) / n)
+    assert abs(emitted - expect) < 5 * sigma
+
+
+def test_point_light_irradiance_on_plane_is_inverse_square():
+    half, res, I = 1.0, 12, 1.3
+    pos = (0.15, -0.1, 0.6)
+    sc = scenes.plane(half=half, res=res)
+    L = scenes.make_lights([scenes.point_light(pos, I)])
+    n = 1 << 20
+    r = oracle.forward(sc, L, seed=21, n_photons=n, max_hits=1, counts=True)
+    A = (2 * half / res) ** 2
+    omega = cf.plane_texel_solid_angles(half, res, np.array(pos))
+    expect = I * omega / A
+    phi = I * 4 * np.pi / n
+    p = omega / (4 * np.pi)
+    sigma = phi / A * np.sqrt(n * p * (1 - p))
+    z = (r["E"] - expect) / sigma
+    assert np.max(np.abs(z)) < 5.0
+    assert abs(np.mean(z * z) - 1.0) < 0.35          # chi-square / dof
+    # every deposit carries the same flux
+    np.testing.assert_allclose(r["E"] * A, r["count"] * phi, rtol=1e-12)
+
+
+def test_spot_irradiance_on_plane_matches_quadrature():
+    half, res = 1.5, 10
+    light = scenes.spot_light((0.1, 0.2, 1.0), 0.4, -np.pi / 2 + 0.25, 2.0, 0.25, 0.7)
+    sc = scenes.plane(half=half, res=res)
+    L = scenes.make_lights([light])
+    n = 1 << 20
+    r = oracle.forward(sc, L, seed=22, n_photons=n, max_hits=1)
+    A = (2 * half / res) ** 2
+    expect = cf.plane_texel_spot_flux(half, res, np.array(light), sub=8, order=6) / A
+    phi_max = 2.0 * 2 * np.pi * (1 - np.cos(0.7)) / n
+    sigma = np.sqrt(phi_max * np.maximum(expect, 1e-30) / A) + 1e-12
+    z = (r["E"] - expect) / sigma
+    assert np.max(np.abs(z)) < 5.0
+    assert np.sum(r["E"]) == pytest.approx(np.sum(expect), rel=5e-3)
+
+
+def test_sphere_direct_is_solid_angle_and_second_hit_is_uniform():
+    R, rho, I = 1.0, 0.5, 1.0
+    sc = scenes.icosphere(radius=R, subdiv=3, albedo=rho)
+    pos = np.array([0.3, 0.2, -0.35])
+    L = scenes.make_lights([scenes.point_light(pos, I)])
+    n = 1 << 21
+    r1 = oracle.forward(sc, L, seed=5, n_photons=n, max_hits=1, counts=True)
+    r2 = oracle.forward(sc, L, seed=5, n_photons=n, max_hits=2, counts=True)
+    A = sc.tile_area
+    phi = I * 4 * np.pi / n
+    # direct: E_f = I Omega_f / A_f, exact up to Monte Carlo noise
+    omega = np.array([cf.triangle_solid_angle(*sc.xyz[f].astype(np.float64), pos) for f in range(sc.n_tri)])
+    assert np.sum(omega) == pytest.approx(4 * np.pi, rel=1e-9)
+    p = omega / (4 * np.pi)
+    z1 = (r1["E"] - I * omega / A) / (phi / A * np.sqrt(n * p * (1 - p)))
+    assert np.max(np.abs(z1)) < 5.0 and abs(np.mean(z1 * z1) - 1) < 0.3
+    # second hit: same seed, so the difference is exactly the second deposits
+    E2 = r2["E"] - r1["E"]
+    c2 = r2["count"] - r1["count"]
+    total = I * 4 * np.pi * float(np.float32(rho))
+    assert np.sum(A * E2) == pytest.approx(total, rel=1e-10)
+    mean = total / np.sum(A)
+    sigma = rho * phi * np.sqrt(np.maximum(c2, 1)) / A
+    chi2 = np.mean(((E2 - mean) / sigma) ** 2)
+    assert 0.8 < chi2 < 1.3, chi2
