@@ -1,0 +1,188 @@
+/*
+ * lt.h -- C ABI of the GB300 light-tracing library (libltrace.so).
+ *
+ * View-independent adjoint light tracing (Lipp et al., "View-Independent
+ * Adjoint Light Tracing for Lighting Design Optimization", arXiv 2310.02043):
+ * a forward pass traces photons from parameterised luminaires and deposits
+ * irradiance into per-texel storage on the scene surfaces; an L2 objective
+ * compares it with a target; an adjoint pass replays the same photon paths
+ * and accumulates the objective's gradient with respect to every luminaire
+ * parameter.
+ *
+ * Conventions for every call:
+ *   - Returns LT_OK (0) or a negative lt_status. A failed call leaves a
+ *     message for lt_last_error(). No C++ exception crosses this interface.
+ *   - Work is queued on the context's CUDA stream (lt_create / lt_set_stream).
+ *     Calls that return a value in host memory synchronise that stream.
+ *   - Host input arrays are copied; the caller keeps ownership. Output
+ *     pointers are caller-owned and must hold the stated number of elements.
+ *   - "is_device" arguments say whether a pointer is device memory (1) or
+ *     host memory (0) of the context's device.
+ *   - Light parameter / gradient slot order is LT_GRAD_*:
+ *       [x, y, z, yaw, pitch, p_int, theta_in, theta_out].
+ */
+#ifndef LT_H
+#define LT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LT_OK = 0,
+    LT_ERR_ARG = -1,       /* invalid argument (sizes, ranges, null pointers) */
+    LT_ERR_CUDA = -2,      /* a CUDA runtime call failed */
+    LT_ERR_OOM = -3,       /* device allocation failed */
+    LT_ERR_STATE = -4,     /* call out of order (e.g. loss before a forward pass) */
+    LT_ERR_TIMEOUT = -5,   /* a kernel gave up after its iteration limit */
+    LT_ERR_OVERFLOW = -6,  /* fixed-point range exceeded */
+    LT_ERR_DEVICE = -7     /* a kernel reported an internal error (device error word) */
+} lt_status;
+
+enum { LT_POINT = 0, LT_SPOT = 1 };
+
+enum {
+    LT_GRAD_X = 0, LT_GRAD_Y = 1, LT_GRAD_Z = 2, LT_GRAD_YAW = 3, LT_GRAD_PITCH = 4,
+    LT_GRAD_P_INT = 5, LT_GRAD_THETA_IN = 6, LT_GRAD_THETA_OUT = 7, LT_GRAD_N = 8
+};
+
+/* One luminaire (Sec. 4.4 of the paper and the supplement's "Derivative
+ * terms for optimization parameters"):
+ *   type       LT_POINT or LT_SPOT
+ *   pos        position, metres
+ *   yaw,pitch  spot axis n = (cos p cos y, cos p sin y, sin p), z up (radians;
+ *              the paper rotates by a rotation vector, Eq. 15)
+ *   p_int      intensity parameter, I_e = p_int^2 / 2 (Sec. 4.4.1)
+ *   theta_in   inner cone half-angle: full intensity for theta <= theta_in
+ *   theta_out  outer cone half-angle: zero beyond; quadratic soft edge in
+ *              cos(theta) between the two (Eq. S.11). 0 <= theta_in < theta_out <= pi.
+ * Point lights ignore yaw, pitch and the cone angles. */
+typedef struct {
+    int32_t type;
+    float pos[3];
+    float yaw;
+    float pitch;
+    float p_int;
+    float theta_in;
+    float theta_out;
+} lt_light;
+
+/* Counters of the last passes and facts about the uploaded scene. */
+typedef struct {
+    uint64_t segments_forward;   /* traced segments (hit or miss) of the last forward pass */
+    uint64_t segments_adjoint;   /* same for the last adjoint pass */
+    uint64_t photons_forward;
+    uint64_t photons_adjoint;
+    int64_t n_texels;
+    int32_t n_triangles;
+    int32_t n_nodes;             /* wide-BVH nodes */
+    int32_t bvh_depth;           /* levels of wide nodes */
+    int32_t staged_nodes;        /* nodes held in shared memory per block */
+    double fixed_point_scale;    /* S: a texel accumulates round(Phi * S) */
+} lt_stats;
+
+/* Library ABI version (this header: 1). */
+int lt_version(void);
+
+/* Create a context on CUDA device `device`; work goes to `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream). */
+int lt_create(void **ctx_out, int device, void *cuda_stream);
+int lt_destroy(void *ctx);
+int lt_set_stream(void *ctx, void *cuda_stream);
+const char *lt_last_error(const void *ctx);
+
+/* Upload a triangle scene (host arrays, copied) and build its wide BVH.
+ *   tri_xyz    [n_tri][3][3] float   vertex positions
+ *   tri_uv     [n_tri][3][2] float   per-vertex chart coordinates in [0,1]^2
+ *   tri_tile   [n_tri] int32         tile (texel chart) of each triangle
+ *   tri_albedo [n_tri] float         Lambertian albedo in [0, 1]
+ *   tile_res   [n_tiles][2] int32    texel resolution (res_u, res_v) >= 1
+ *   tile_area  [n_tiles] double      area covered by the tile, m^2 (> 0)
+ * Texels are numbered tile by tile, u fastest. A texel's area is
+ * tile_area / (res_u res_v) (the box basis standing in for the per-vertex
+ * hat basis of Eq. 4; mass-lumped projection, Eq. S.6). Writes the texel
+ * count to *n_texels_out. Invalidates targets, weights and pass results. */
+int lt_upload_scene(void *ctx, const float *tri_xyz, const float *tri_uv, const int32_t *tri_tile,
+                    const float *tri_albedo, int32_t n_tri, const int32_t *tile_res, const double *tile_area,
+                    int32_t n_tiles, int64_t *n_texels_out);
+
+/* Target irradiance E*_t and weights alpha_t of the objective (Eq. 6),
+ * [n_texels] floats each; alpha may be NULL (all ones). */
+int lt_set_target(void *ctx, const float *E_target, const float *alpha, int is_device);
+
+/* Luminaires, host array of n_lights (1..LT_MAX_LIGHTS), copied. */
+#define LT_MAX_LIGHTS 1024
+int lt_set_lights(void *ctx, const lt_light *lights, int32_t n_lights);
+
+/* Forward pass (Alg. 1): photons [photon_begin, photon_end) of a budget of
+ * n_photons split evenly over the lights (light l owns a contiguous range;
+ * the first n_photons mod n_lights lights take one extra photon). Each photon
+ * is traced for up to max_hits surface hits (1..64): it deposits its flux
+ * Phi_i at every hit (Eq. 8, order 0) and continues in a cosine-weighted
+ * direction with Phi_{i+1} = rho Phi_i (Eq. 7). Random numbers are
+ * Philox4x32-10 with counter (photon lo, photon hi, segment, 0) and key
+ * (seed lo, seed hi). Clears and then fills the texel accumulator, a
+ * [n_texels] int64 fixed-point array (value round(Phi * S)); the result is
+ * bit-reproducible for any launch configuration. */
+int lt_trace_forward(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
+                     uint64_t photon_end);
+
+/* Device pointer of the int64 texel accumulator and its scale S (valid until
+ * the next lt_upload_scene). Ranks that split photons can sum these arrays
+ * (exact integer addition) before lt_loss. */
+int lt_texel_accumulator(void *ctx, int64_t **q_device, double *scale_out);
+
+/* Copy of the int64 texel accumulator ([n_texels]) into caller memory. */
+int lt_get_texel_sums(void *ctx, int64_t *q_out, int is_device);
+
+/* Objective (Eq. 6, order 0): O = 1/2 sum_t A_t alpha_t (E_t - E*_t)^2 with
+ * E_t = q_t / (S A_t). Also forms the adjoint weights
+ * w_t = alpha_t (E_t - E*_t) = dO/dPhi for a deposit into texel t, kept on the
+ * device for lt_trace_adjoint. Writes O (double) to loss_out. Deterministic. */
+int lt_loss(void *ctx, double *loss_out, int is_device);
+
+/* Irradiance E_t (float, [n_texels]) of the last forward pass. */
+int lt_get_irradiance(void *ctx, float *E_out, int is_device);
+
+/* Texel areas A_t (float, [n_texels]). */
+int lt_texel_areas(void *ctx, float *A_out, int is_device);
+
+/* Replace the adjoint weights w_t ([n_texels] floats) -- injects dO/dPhi
+ * directly (for gradient checks against closed forms). */
+int lt_set_adjoint_weights(void *ctx, const float *w, int is_device);
+
+/* Adjoint pass (Alg. 2, Eq. 11-12): replays photons [photon_begin,
+ * photon_end) of the budget n_photons from `seed` (the forward seed for a
+ * correlated estimate, another for a decorrelated one, Sec. 4.3). Per photon
+ * the adjoint state dO/dPhi_r = sum_i w_{t_i} prod_{j<i} rho_j is summed along
+ * the path and multiplied by dPhi_r/dp, taken at the first hit with that hit
+ * held fixed (Sec. 4.4.2: Eq. 14 for position, Eq. S.11-S.12 for the spot
+ * edge, Eq. 15 for orientation, I_e = p^2/2 for intensity). Writes dO/dp as
+ * double [n_lights][LT_GRAD_N] to grad_out. Needs weights from lt_loss or
+ * lt_set_adjoint_weights. Deterministic for a given launch configuration. */
+int lt_trace_adjoint(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
+                     uint64_t photon_end, double *grad_out, int is_device);
+
+/* Debug record of photons [photon_begin, photon_begin + count): original
+ * triangle index and texel of every hit, -1 after the path ends (host
+ * outputs [count][max_hits]). If grad_out is not NULL it receives every
+ * photon's own gradient term dO/dPhi_r * dPhi_r/dp (host [count][LT_GRAD_N],
+ * double; needs adjoint weights as lt_trace_adjoint does). */
+int lt_debug_paths(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
+                   uint64_t count, int32_t *tri_out, int64_t *texel_out, double *grad_out);
+
+int lt_get_stats(void *ctx, lt_stats *out);
+
+/* Launch shape of the tracing kernels: threads per block (multiple of 32,
+ * <= 1024), blocks per SM (>= 1) and the shared-memory budget for staged BVH
+ * nodes in bytes (0 = none). Zeros keep the current value. */
+int lt_set_launch(void *ctx, int32_t threads_per_block, int32_t blocks_per_sm, int32_t smem_node_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LT_H */

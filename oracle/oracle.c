@@ -591,12 +591,13 @@ int or_adjoint(const float *xyz, const float *uv, const int32_t *tile, const flo
 }
 
 /* Path record for photons [begin, begin + count): triangle and texel of every
- * hit (-1 after the path ends), plus the first-hit flux Phi_r. */
+ * hit (-1 after the path ends). With adjoint weights w (may be NULL),
+ * grad_out [count][8] receives each photon's own gradient term. */
 int or_paths(const float *xyz, const float *uv, const int32_t *tile, const float *albedo, int32_t n_tri,
              const int32_t *res, const double *tile_area, int32_t n_tiles,
              const double *light_params, int32_t n_lights,
              uint64_t seed, uint32_t design, uint64_t n_photons, uint64_t begin, uint64_t count, int32_t max_hits,
-             int32_t *tri_out, int64_t *texel_out, int n_threads)
+             int32_t *tri_out, int64_t *texel_out, const double *w, double *grad_out, int n_threads)
 {
     if (n_lights <= 0 || max_hits <= 0 || begin + count > n_photons) return -1;
     or_scene s;
@@ -611,7 +612,10 @@ int or_paths(const float *xyz, const float *uv, const int32_t *tile, const float
         io.rec_tri = tri_out + (size_t)k * max_hits;
         io.rec_texel = texel_out + (size_t)k * max_hits;
         for (int32_t i = 0; i < max_hits; ++i) { io.rec_tri[i] = -1; io.rec_texel[i] = -1; }
+        io.w = w;
         trace_photon(&s, L, n_lights, seed, design, begin + (uint64_t)k, max_hits, &io);
+        if (grad_out)
+            for (int j = 0; j < 8; ++j) grad_out[8 * (size_t)k + j] = io.has_grad ? io.grad[j] : 0.0;
     }
     free(L);
     scene_free(&s);

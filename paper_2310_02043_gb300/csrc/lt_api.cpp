@@ -1,0 +1,614 @@
+// lt_api.cpp -- the C ABI declared in include/lt.h: context, device buffers,
+// scene/BVH upload, light constants, launches and error reporting.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lt.h"
+#include "lt_internal.h"
+
+namespace {
+
+using namespace lt;
+
+constexpr double kPi = 3.14159265358979323846;
+
+struct Ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    std::string err;
+    // scene
+    Node *d_nodes = nullptr;
+    int32_t *d_parent = nullptr;
+    Tri *d_tris = nullptr;
+    TriHit *d_hits = nullptr;
+    float *d_area = nullptr;
+    int32_t n_nodes = 0, n_tri = 0, depth = 0;
+    int64_t n_texels = 0;
+    std::vector<float> tile_area_f;    // texel area per tile (float)
+    // objective
+    float *d_target = nullptr, *d_alpha = nullptr;
+    bool has_target = false, has_alpha = false;
+    // lights
+    std::vector<lt_light> lights;
+    LightDev *d_lights = nullptr;       // [LT_MAX_LIGHTS]
+    LightDev *h_lights = nullptr;       // pinned staging of the same size
+    cudaEvent_t lights_copied = nullptr;
+    uint64_t lights_for_n = 0;         // photon budget the device light table was built for
+    bool lights_dirty = true;
+    double power_bound = 0.0;          // sum_l I_l Omega_l
+    // pass state
+    unsigned long long *d_q = nullptr;
+    float *d_E = nullptr, *d_w = nullptr;
+    double scale = 1.0;
+    bool fwd_done = false, has_w = false;
+    double *d_loss = nullptr, *d_partial = nullptr, *d_grad = nullptr;
+    double *d_warp_acc = nullptr;
+    size_t warp_acc_bytes = 0;
+    unsigned long long *d_seg = nullptr;   // [2]: forward, adjoint
+    int32_t *d_err = nullptr;
+    double *h_pinned = nullptr;            // small pinned staging area
+    // launch
+    int threads = 256, blocks_per_sm = 0, smem_node_bytes = 48 * 1024;
+    lt_stats stats{};
+};
+
+int fail(Ctx *c, int code, const std::string &msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_fail(Ctx *c, cudaError_t e, const char *what) {
+    return fail(c, e == cudaErrorMemoryAllocation ? LT_ERR_OOM : LT_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define LT_CUDA(c, expr)                                   \
+    do {                                                   \
+        cudaError_t e_ = (expr);                           \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #expr); \
+    } while (0)
+
+template <class T>
+void dfree(T *&p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+template <class T>
+cudaError_t dalloc(T *&p, size_t n) {
+    dfree(p);
+    if (n == 0) n = 1;
+    return cudaMalloc(reinterpret_cast<void **>(&p), n * sizeof(T));
+}
+
+// Reads the device error word (synchronises the stream) and clears it.
+int check_device(Ctx *c) {
+    int32_t e = 0;
+    LT_CUDA(c, cudaMemcpyAsync(&e, c->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    LT_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (e) {
+        LT_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), c->stream));
+        if (e & kErrSteps) return fail(c, LT_ERR_TIMEOUT, "a ray exceeded its traversal step limit");
+        return fail(c, LT_ERR_DEVICE, "kernel error word " + std::to_string(e));
+    }
+    return LT_OK;
+}
+
+int copy_in(Ctx *c, void *dst, const void *src, size_t bytes, int is_device) {
+    LT_CUDA(c, cudaMemcpyAsync(dst, src, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                               c->stream));
+    return LT_OK;
+}
+
+int copy_out(Ctx *c, void *dst, const void *src, size_t bytes, int is_device) {
+    LT_CUDA(c, cudaMemcpyAsync(dst, src, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                               c->stream));
+    if (!is_device) LT_CUDA(c, cudaStreamSynchronize(c->stream));
+    return LT_OK;
+}
+
+// Per-light constants for a photon budget n (Sec. 4.4 and the supplement):
+// I_e = p^2 / 2; Phi_r = I_e Omega a / N_l with Omega = 4 pi (point) or
+// 2 pi (1 - cos theta_out) (spot).
+int upload_lights(Ctx *c, uint64_t n_photons) {
+    if (!c->lights_dirty && c->lights_for_n == n_photons) return LT_OK;
+    const int32_t L = (int32_t)c->lights.size();
+    // the previous copy out of the staging buffer must be done before reuse
+    LT_CUDA(c, cudaEventSynchronize(c->lights_copied));
+    LightDev *h = c->h_lights;
+    const uint64_t base = n_photons / (uint64_t)L, rem = n_photons % (uint64_t)L;
+    uint64_t first = 0;
+    double bound = 0.0;
+    for (int32_t l = 0; l < L; ++l) {
+        const lt_light &s = c->lights[l];
+        LightDev &d = h[l];
+        std::memset(&d, 0, sizeof(d));
+        const uint64_t nl = base + ((uint64_t)l < rem ? 1u : 0u);
+        const double I = 0.5 * (double)s.p_int * (double)s.p_int;
+        const double cy = std::cos((double)s.yaw), sy = std::sin((double)s.yaw);
+        const double cp = std::cos((double)s.pitch), sp = std::sin((double)s.pitch);
+        double omega = 4.0 * kPi;
+        d.type = s.type;
+        for (int k = 0; k < 3; ++k) d.pos[k] = s.pos[k];
+        d.ns[0] = (float)(cp * cy); d.ns[1] = (float)(cp * sy); d.ns[2] = (float)sp;
+        d.e1[0] = (float)(-sp * cy); d.e1[1] = (float)(-sp * sy); d.e1[2] = (float)cp;
+        d.e2[0] = (float)(-sy); d.e2[1] = (float)cy; d.e2[2] = 0.0f;
+        d.dn_dyaw[0] = (float)(-cp * sy); d.dn_dyaw[1] = (float)(cp * cy); d.dn_dyaw[2] = 0.0f;
+        d.dn_dpitch[0] = (float)(-sp * cy); d.dn_dpitch[1] = (float)(-sp * sy); d.dn_dpitch[2] = (float)cp;
+        if (s.type == LT_SPOT) {
+            const double co = std::cos((double)s.theta_out), ci = std::cos((double)s.theta_in);
+            omega = 2.0 * kPi * (1.0 - co);
+            d.co = (float)co;
+            d.ci = (float)ci;
+            d.inv_d = (float)(1.0 / (ci - co));
+            d.one_minus_co = (float)(1.0 - co);
+            d.sin_in = (float)std::sin((double)s.theta_in);
+            d.sin_out = (float)std::sin((double)s.theta_out);
+        }
+        d.flux_k = (float)(I * omega / (double)nl);
+        d.dflux_dp_k = (float)((double)s.p_int * omega / (double)nl);
+        d.first = first;
+        d.end = first + nl;
+        first += nl;
+        bound += I * omega;
+    }
+    LT_CUDA(c, cudaMemcpyAsync(c->d_lights, h, sizeof(LightDev) * (size_t)L, cudaMemcpyHostToDevice, c->stream));
+    LT_CUDA(c, cudaEventRecord(c->lights_copied, c->stream));
+    c->lights_for_n = n_photons;
+    c->lights_dirty = false;
+    c->power_bound = bound;
+    return LT_OK;
+}
+
+int launch_shape(Ctx *c, bool adjoint, int *grid, size_t *smem, int32_t *n_staged) {
+    const int32_t fit = c->smem_node_bytes / (int)sizeof(Node);
+    *n_staged = std::max(0, std::min(c->n_nodes, fit));
+    *smem = (size_t)(*n_staged) * sizeof(Node);
+    int bps = c->blocks_per_sm;
+    if (bps <= 0) {
+        cudaError_t e = trace_occupancy(adjoint, c->threads, *smem, &bps);
+        if (e != cudaSuccess) return cuda_fail(c, e, "occupancy query");
+        if (bps < 1) return fail(c, LT_ERR_ARG, "launch shape does not fit on an SM");
+    }
+    *grid = c->sm_count * bps;
+    return LT_OK;
+}
+
+TraceParams base_params(Ctx *c, uint64_t seed, int32_t max_hits, uint64_t begin, uint64_t end) {
+    TraceParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.nodes = c->d_nodes;
+    p.parent = c->d_parent;
+    p.n_nodes = c->n_nodes;
+    p.tris = c->d_tris;
+    p.hits = c->d_hits;
+    p.lights = c->d_lights;
+    p.n_lights = (int32_t)c->lights.size();
+    p.max_hits = max_hits;
+    p.max_steps = 16 * c->n_nodes + 64;
+    p.design = 0;
+    p.seed = seed;
+    p.photon_begin = begin;
+    p.photon_end = end;
+    p.n_texels = c->n_texels;
+    p.err = c->d_err;
+    return p;
+}
+
+int check_trace_args(Ctx *c, uint64_t n_photons, int32_t max_hits, uint64_t begin, uint64_t end) {
+    if (!c->d_nodes) return fail(c, LT_ERR_STATE, "no scene uploaded");
+    if (c->lights.empty()) return fail(c, LT_ERR_STATE, "no lights set");
+    if (n_photons == 0) return fail(c, LT_ERR_ARG, "n_photons must be positive");
+    if (max_hits < 1 || max_hits > 64) return fail(c, LT_ERR_ARG, "max_hits must be in [1, 64]");
+    if (begin > end || end > n_photons) return fail(c, LT_ERR_ARG, "photon range outside [0, n_photons]");
+    return LT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lt_version(void) { return 1; }
+
+int lt_create(void **ctx_out, int device, void *cuda_stream) {
+    if (!ctx_out) return LT_ERR_ARG;
+    *ctx_out = nullptr;
+    Ctx *c = new (std::nothrow) Ctx();
+    if (!c) return LT_ERR_OOM;
+    int n_dev = 0;
+    cudaError_t e = cudaGetDeviceCount(&n_dev);
+    if (e != cudaSuccess || device < 0 || device >= n_dev) {
+        delete c;
+        return e != cudaSuccess ? LT_ERR_CUDA : LT_ERR_ARG;
+    }
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaMalloc(&c->d_seg, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&c->d_err, sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&c->d_loss, sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->d_partial, kLossBlocks * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&c->h_pinned, 64 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->d_lights, LT_MAX_LIGHTS * sizeof(LightDev)) != cudaSuccess ||
+        cudaMallocHost(&c->h_lights, LT_MAX_LIGHTS * sizeof(LightDev)) != cudaSuccess ||
+        cudaMalloc(&c->d_grad, LT_MAX_LIGHTS * 8 * sizeof(double)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->lights_copied, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(c->lights_copied, c->stream) != cudaSuccess ||
+        cudaMemset(c->d_err, 0, sizeof(int32_t)) != cudaSuccess ||
+        cudaMemset(c->d_seg, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+        lt_destroy(c);
+        return LT_ERR_CUDA;
+    }
+    *ctx_out = c;
+    return LT_OK;
+}
+
+int lt_destroy(void *ctx) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return LT_OK;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
+    dfree(c->d_nodes); dfree(c->d_parent); dfree(c->d_tris); dfree(c->d_hits); dfree(c->d_area);
+    dfree(c->d_target); dfree(c->d_alpha); dfree(c->d_lights); dfree(c->d_q); dfree(c->d_E); dfree(c->d_w);
+    dfree(c->d_loss); dfree(c->d_partial); dfree(c->d_grad); dfree(c->d_warp_acc); dfree(c->d_seg);
+    dfree(c->d_err);
+    if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    if (c->h_lights) cudaFreeHost(c->h_lights);
+    if (c->lights_copied) cudaEventDestroy(c->lights_copied);
+    delete c;
+    return LT_OK;
+}
+
+int lt_set_stream(void *ctx, void *cuda_stream) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return LT_ERR_ARG;
+    c->stream = (cudaStream_t)cuda_stream;
+    return LT_OK;
+}
+
+const char *lt_last_error(const void *ctx) {
+    const Ctx *c = static_cast<const Ctx *>(ctx);
+    return c ? c->err.c_str() : "null context";
+}
+
+int lt_upload_scene(void *ctx, const float *tri_xyz, const float *tri_uv, const int32_t *tri_tile,
+                    const float *tri_albedo, int32_t n_tri, const int32_t *tile_res, const double *tile_area,
+                    int32_t n_tiles, int64_t *n_texels_out) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return LT_ERR_ARG;
+    if (!tri_xyz || !tri_uv || !tri_tile || !tri_albedo || !tile_res || !tile_area || n_tri <= 0 || n_tiles <= 0)
+        return fail(c, LT_ERR_ARG, "null scene array or empty scene");
+    LT_CUDA(c, cudaSetDevice(c->device));
+    std::vector<int64_t> off((size_t)n_tiles + 1, 0);
+    for (int32_t k = 0; k < n_tiles; ++k) {
+        const int32_t ru = tile_res[2 * k], rv = tile_res[2 * k + 1];
+        if (ru < 1 || rv < 1) return fail(c, LT_ERR_ARG, "tile resolution must be >= 1");
+        if (!(tile_area[k] > 0.0) || !std::isfinite(tile_area[k])) return fail(c, LT_ERR_ARG, "tile area must be > 0");
+        off[k + 1] = off[k] + (int64_t)ru * rv;
+    }
+    for (int32_t i = 0; i < n_tri; ++i) {
+        if (tri_tile[i] < 0 || tri_tile[i] >= n_tiles) return fail(c, LT_ERR_ARG, "triangle tile out of range");
+        if (!(tri_albedo[i] >= 0.0f && tri_albedo[i] <= 1.0f)) return fail(c, LT_ERR_ARG, "albedo must be in [0, 1]");
+        for (int k = 0; k < 9; ++k)
+            if (!std::isfinite(tri_xyz[9 * (size_t)i + k])) return fail(c, LT_ERR_ARG, "non-finite vertex");
+    }
+    BvhBuild bvh;
+    std::string berr;
+    if (!build_wide_bvh(tri_xyz, n_tri, &bvh, &berr)) return fail(c, LT_ERR_ARG, berr);
+    std::vector<Tri> tris((size_t)n_tri);
+    std::vector<TriHit> hits((size_t)n_tri);
+    for (int32_t j = 0; j < n_tri; ++j) {
+        const int32_t i = bvh.order[j];
+        Tri &t = tris[j];
+        const float *v = tri_xyz + 9 * (size_t)i;
+        for (int k = 0; k < 3; ++k) { t.v0[k] = v[k]; t.v1[k] = v[3 + k]; t.v2[k] = v[6 + k]; }
+        t.prim = i;
+        t.tile = tri_tile[i];
+        t.albedo = tri_albedo[i];
+        TriHit &h = hits[j];
+        for (int k = 0; k < 6; ++k) h.uv[k] = tri_uv[6 * (size_t)i + k];
+        h.res_u = tile_res[2 * tri_tile[i]];
+        h.res_v = tile_res[2 * tri_tile[i] + 1];
+        h.texel_off = off[tri_tile[i]];
+        h.pad = 0;
+    }
+    const int64_t T = off[n_tiles];
+    std::vector<float> area((size_t)T);
+    for (int32_t k = 0; k < n_tiles; ++k) {
+        const float a = (float)(tile_area[k] / ((double)tile_res[2 * k] * (double)tile_res[2 * k + 1]));
+        std::fill(area.begin() + off[k], area.begin() + off[k + 1], a);
+    }
+    LT_CUDA(c, cudaStreamSynchronize(c->stream));
+    LT_CUDA(c, dalloc(c->d_nodes, bvh.nodes.size()));
+    LT_CUDA(c, dalloc(c->d_parent, bvh.parent.size()));
+    LT_CUDA(c, dalloc(c->d_tris, (size_t)n_tri));
+    LT_CUDA(c, dalloc(c->d_hits, (size_t)n_tri));
+    LT_CUDA(c, dalloc(c->d_area, (size_t)T));
+    LT_CUDA(c, dalloc(c->d_q, (size_t)T));
+    LT_CUDA(c, dalloc(c->d_E, (size_t)T));
+    LT_CUDA(c, dalloc(c->d_w, (size_t)T));
+    LT_CUDA(c, dalloc(c->d_target, (size_t)T));
+    dfree(c->d_alpha);
+    LT_CUDA(c, cudaMemcpy(c->d_nodes, bvh.nodes.data(), bvh.nodes.size() * sizeof(Node), cudaMemcpyHostToDevice));
+    LT_CUDA(c, cudaMemcpy(c->d_parent, bvh.parent.data(), bvh.parent.size() * sizeof(int32_t),
+                          cudaMemcpyHostToDevice));
+    LT_CUDA(c, cudaMemcpy(c->d_tris, tris.data(), tris.size() * sizeof(Tri), cudaMemcpyHostToDevice));
+    LT_CUDA(c, cudaMemcpy(c->d_hits, hits.data(), hits.size() * sizeof(TriHit), cudaMemcpyHostToDevice));
+    LT_CUDA(c, cudaMemcpy(c->d_area, area.data(), area.size() * sizeof(float), cudaMemcpyHostToDevice));
+    LT_CUDA(c, cudaMemset(c->d_target, 0, (size_t)T * sizeof(float)));
+    c->n_nodes = (int32_t)bvh.nodes.size();
+    c->n_tri = n_tri;
+    c->depth = bvh.depth;
+    c->n_texels = T;
+    c->fwd_done = c->has_w = c->has_target = c->has_alpha = false;
+    c->stats = lt_stats{};
+    c->stats.n_texels = T;
+    c->stats.n_triangles = n_tri;
+    c->stats.n_nodes = c->n_nodes;
+    c->stats.bvh_depth = c->depth;
+    if (n_texels_out) *n_texels_out = T;
+    return LT_OK;
+}
+
+int lt_set_target(void *ctx, const float *E_target, const float *alpha, int is_device) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return LT_ERR_ARG;
+    if (!c->d_nodes) return fail(c, LT_ERR_STATE, "no scene uploaded");
+    if (!E_target) return fail(c, LT_ERR_ARG, "null target");
+    int rc = copy_in(c, c->d_target, E_target, (size_t)c->n_texels * sizeof(float), is_device);
+    if (rc) return rc;
+    if (alpha) {
+        if (!c->d_alpha) LT_CUDA(c, dalloc(c->d_alpha, (size_t)c->n_texels));
+        rc = copy_in(c, c->d_alpha, alpha, (size_t)c->n_texels * sizeof(float), is_device);
+        if (rc) return rc;
+        c->has_alpha = true;
+    } else {
+        c->has_alpha = false;
+    }
+    if (!is_device) LT_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->has_target = true;
+    return LT_OK;
+}
+
+int lt_set_lights(void *ctx, const lt_light *lights, int32_t n_lights) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return LT_ERR_ARG;
+    if (!lights || n_lights < 1 || n_lights > LT_MAX_LIGHTS) return fail(c, LT_ERR_ARG, "n_lights out of range");
+    for (int32_t l = 0; l < n_lights; ++l) {
+        const lt_light &s = lights[l];
+        if (s.type != LT_POINT && s.type != LT_SPOT) return fail(c, LT_ERR_ARG, "unknown light type");
+        bool finite = std::isfinite(s.p_int) && std::isfinite(s.yaw) && std::isfinite(s.pitch);
+        for (int k = 0; k < 3; ++k) finite = finite && std::isfinite(s.pos[k]);
+        if (!finite) return fail(c, LT_ERR_ARG, "non-finite light parameter");
+        if (s.type == LT_SPOT && !(s.theta_in >= 0.0f && s.theta_in < s.theta_out && s.theta_out <= (float)kPi))
+            return fail(c, LT_ERR_ARG, "spot cone needs 0 <= theta_in < theta_out <= pi");
+    }
+    c->lights.assign(lights, lights + n_lights);
+    c->lights_dirty = true;
+    return LT_OK;
+}
+
+int lt_trace_forward(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
+                     uint64_t photon_end) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return LT_ERR_ARG;
+    int rc = check_trace_args(c, n_photons, max_hits, photon_begin, photon_end);
+    if (rc) return rc;
+    LT_CUDA(c, cudaSetDevice(c->device));
+    if ((rc = upload_lights(c, n_photons))) return rc;
+    // Fixed point: S = 2^k with S * (total power bound) * max_hits < 2^62, so
+    // no texel (nor the sum of all texels) can overflow int64.
+    double S = std::ldexp(1.0, 40);
+    if (c->power_bound > 0.0) {
+        const int k = (int)std::floor(std::log2(std::ldexp(1.0, 62) / (c->power_bound * (double)max_hits)));
+        S = std::ldexp(1.0, std::max(-120, std::min(120, k)));
+    }
+    c->scale = S;
+    TraceParams p = base_params(c, seed, max_hits, photon_begin, photon_end);
+    p.q = c->d_q;
+    p.scale = (float)S;
+    p.segments = c->d_seg;
+    int grid;
+    size_t smem;
+    if ((rc = launch_shape(c, false, &grid, &smem, &p.n_staged))) return rc;
+    LT_CUDA(c, cudaMemsetAsync(c->d_q, 0, (size_t)c->n_texels * sizeof(unsigned long long), c->stream));
+    LT_CUDA(c, cudaMemsetAsync(c->d_seg, 0, sizeof(unsigned long long), c->stream));
+    LT_CUDA(c, launch_forward(p, grid, c->threads, smem, c->stream));
+    c->fwd_done = true;
+    c->has_w = false;
+    c->stats.photons_forward = photon_end - photon_begin;
+    c->stats.staged_nodes = p.n_staged;
+    c->stats.fixed_point_scale = S;
+    return LT_OK;
+}
+
+int lt_texel_accumulator(void *ctx, int64_t **q_device, double *scale_out) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c || !q_device) return LT_ERR_ARG;
+    if (!c->d_q) return fail(c, LT_ERR_STATE, "no scene uploaded");
+    *q_device = reinterpret_cast<int64_t *>(c->d_q);
+    if (scale_out) *scale_out = c->scale;
+    return LT_OK;
+}
+
+int lt_get_texel_sums(void *ctx, int64_t *q_out, int is_device) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c || !q_out) return LT_ERR_ARG;
+    if (!c->fwd_done) return fail(c, LT_ERR_STATE, "no forward pass");
+    LT_CUDA(c, cudaSetDevice(c->device));
+    return copy_out(c, q_out, c->d_q, (size_t)c->n_texels * sizeof(int64_t), is_device);
+}
+
+int lt_loss(void *ctx, double *loss_out, int is_device) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return LT_ERR_ARG;
+    if (!c->fwd_done) return fail(c, LT_ERR_STATE, "lt_loss needs a forward pass");
+    if (!c->has_target) return fail(c, LT_ERR_STATE, "lt_loss needs a target (lt_set_target)");
+    LT_CUDA(c, cudaSetDevice(c->device));
+    LossParams p;
+    p.q = c->d_q;
+    p.E_target = c->d_target;
+    p.alpha = c->has_alpha ? c->d_alpha : nullptr;
+    p.area = c->d_area;
+    p.inv_scale = 1.0 / c->scale;
+    p.n_texels = c->n_texels;
+    p.E_out = c->d_E;
+    p.w_out = c->d_w;
+    p.partial = c->d_partial;
+    p.loss_out = c->d_loss;
+    LT_CUDA(c, launch_loss(p, c->stream));
+    c->has_w = true;
+    if (loss_out) {
+        int rc = copy_out(c, loss_out, c->d_loss, sizeof(double), is_device);
+        if (rc) return rc;
+        if (!is_device) return check_device(c);
+    }
+    return LT_OK;
+}
+
+int lt_get_irradiance(void *ctx, float *E_out, int is_device) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c || !E_out) return LT_ERR_ARG;
+    if (!c->fwd_done) return fail(c, LT_ERR_STATE, "no forward pass");
+    LT_CUDA(c, cudaSetDevice(c->device));
+    LT_CUDA(c, launch_resolve(c->d_q, c->d_area, 1.0 / c->scale, c->n_texels, c->d_E, c->stream));
+    return copy_out(c, E_out, c->d_E, (size_t)c->n_texels * sizeof(float), is_device);
+}
+
+int lt_texel_areas(void *ctx, float *A_out, int is_device) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c || !A_out) return LT_ERR_ARG;
+    if (!c->d_area) return fail(c, LT_ERR_STATE, "no scene uploaded");
+    LT_CUDA(c, cudaSetDevice(c->device));
+    return copy_out(c, A_out, c->d_area, (size_t)c->n_texels * sizeof(float), is_device);
+}
+
+int lt_set_adjoint_weights(void *ctx, const float *w, int is_device) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c || !w) return LT_ERR_ARG;
+    if (!c->d_w) return fail(c, LT_ERR_STATE, "no scene uploaded");
+    LT_CUDA(c, cudaSetDevice(c->device));
+    int rc = copy_in(c, c->d_w, w, (size_t)c->n_texels * sizeof(float), is_device);
+    if (rc) return rc;
+    if (!is_device) LT_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->has_w = true;
+    return LT_OK;
+}
+
+int lt_trace_adjoint(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
+                     uint64_t photon_end, double *grad_out, int is_device) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return LT_ERR_ARG;
+    if (!grad_out) return fail(c, LT_ERR_ARG, "null gradient output");
+    int rc = check_trace_args(c, n_photons, max_hits, photon_begin, photon_end);
+    if (rc) return rc;
+    if (!c->has_w) return fail(c, LT_ERR_STATE, "lt_trace_adjoint needs weights (lt_loss or lt_set_adjoint_weights)");
+    LT_CUDA(c, cudaSetDevice(c->device));
+    if ((rc = upload_lights(c, n_photons))) return rc;
+    const int32_t L = (int32_t)c->lights.size();
+    TraceParams p = base_params(c, seed, max_hits, photon_begin, photon_end);
+    p.w = c->d_w;
+    p.segments = c->d_seg + 1;
+    int grid;
+    size_t smem;
+    if ((rc = launch_shape(c, true, &grid, &smem, &p.n_staged))) return rc;
+    // per-warp accumulators: cap their size by shrinking the grid
+    const size_t per_warp = (size_t)L * 8 * sizeof(double);
+    const size_t warps_per_block = (size_t)c->threads / 32;
+    const size_t cap = (size_t)512 << 20;
+    while (grid > c->sm_count && (size_t)grid * warps_per_block * per_warp > cap) grid -= c->sm_count;
+    const size_t n_warps = (size_t)grid * warps_per_block;
+    const size_t need = n_warps * per_warp;
+    if (need > c->warp_acc_bytes) {
+        LT_CUDA(c, cudaStreamSynchronize(c->stream));
+        dfree(c->d_warp_acc);
+        LT_CUDA(c, cudaMalloc(&c->d_warp_acc, need));
+        c->warp_acc_bytes = need;
+    }
+    p.warp_acc = c->d_warp_acc;
+    LT_CUDA(c, cudaMemsetAsync(c->d_warp_acc, 0, need, c->stream));
+    LT_CUDA(c, cudaMemsetAsync(c->d_seg + 1, 0, sizeof(unsigned long long), c->stream));
+    LT_CUDA(c, launch_adjoint(p, grid, c->threads, smem, c->stream));
+    LT_CUDA(c, launch_grad_finalize(c->d_warp_acc, (int64_t)n_warps, L, c->d_grad, c->stream));
+    c->stats.photons_adjoint = photon_end - photon_begin;
+    rc = copy_out(c, grad_out, c->d_grad, (size_t)L * 8 * sizeof(double), is_device);
+    if (rc) return rc;
+    if (!is_device) return check_device(c);
+    return LT_OK;
+}
+
+int lt_debug_paths(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
+                   uint64_t count, int32_t *tri_out, int64_t *texel_out, double *grad_out) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return LT_ERR_ARG;
+    if (!tri_out || !texel_out) return fail(c, LT_ERR_ARG, "null output");
+    int rc = check_trace_args(c, n_photons, max_hits, photon_begin, photon_begin + count);
+    if (rc) return rc;
+    if (grad_out && !c->has_w) return fail(c, LT_ERR_STATE, "per-photon gradients need adjoint weights");
+    if (count == 0) return LT_OK;
+    LT_CUDA(c, cudaSetDevice(c->device));
+    if ((rc = upload_lights(c, n_photons))) return rc;
+    const size_t n = (size_t)count * (size_t)max_hits;
+    int32_t *d_tri = nullptr;
+    int64_t *d_tex = nullptr;
+    double *d_grad = nullptr;
+    cudaError_t e = cudaMalloc(&d_tri, n * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&d_tex, n * sizeof(int64_t));
+    if (e == cudaSuccess && grad_out) e = cudaMalloc(&d_grad, (size_t)count * 8 * sizeof(double));
+    if (e == cudaSuccess) {
+        TraceParams p = base_params(c, seed, max_hits, photon_begin, photon_begin + count);
+        p.rec_tri = d_tri;
+        p.rec_texel = d_tex;
+        p.rec_grad = d_grad;
+        p.w = c->d_w;
+        e = launch_paths(p, count, c->stream);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tri_out, d_tri, n * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(texel_out, d_tex, n * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && grad_out)
+        e = cudaMemcpyAsync(grad_out, d_grad, (size_t)count * 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d_tri);
+    cudaFree(d_tex);
+    cudaFree(d_grad);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lt_debug_paths");
+    return check_device(c);
+}
+
+int lt_get_stats(void *ctx, lt_stats *out) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c || !out) return LT_ERR_ARG;
+    LT_CUDA(c, cudaSetDevice(c->device));
+    unsigned long long seg[2] = {0, 0};
+    LT_CUDA(c, cudaMemcpyAsync(seg, c->d_seg, sizeof(seg), cudaMemcpyDeviceToHost, c->stream));
+    LT_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->stats.segments_forward = seg[0];
+    c->stats.segments_adjoint = seg[1];
+    *out = c->stats;
+    return check_device(c);
+}
+
+int lt_set_launch(void *ctx, int32_t threads_per_block, int32_t blocks_per_sm, int32_t smem_node_bytes) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return LT_ERR_ARG;
+    if (threads_per_block) {
+        if (threads_per_block % 32 || threads_per_block < 32 || threads_per_block > trace_kernel_max_threads())
+            return fail(c, LT_ERR_ARG, "threads_per_block must be a multiple of 32 within the kernel's bound");
+        c->threads = threads_per_block;
+    }
+    if (blocks_per_sm < 0) return fail(c, LT_ERR_ARG, "blocks_per_sm must be >= 0");
+    if (blocks_per_sm) c->blocks_per_sm = blocks_per_sm;
+    if (smem_node_bytes < 0 || smem_node_bytes > 200 * 1024)
+        return fail(c, LT_ERR_ARG, "smem_node_bytes must be in [0, 200 KiB]");
+    if (smem_node_bytes) c->smem_node_bytes = smem_node_bytes;
+    return LT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,225 @@
+// lt_bvh.cpp -- host builder of the 8-wide BVH the tracing kernels traverse.
+//
+// 1. A binary BVH by binned surface-area heuristic (16 bins along the largest
+//    centroid extent; leaves of at most kLeafMax triangles).
+// 2. Collapse to 8-wide nodes: a wide node starts from a binary inner node's
+//    two children and repeatedly opens the inner child with the largest
+//    surface area until it has 8 children or only leaves remain.
+// 3. Nodes are emitted breadth-first, so the top levels form a prefix of the
+//    node array (the part the kernels stage in shared memory), and leaf
+//    triangles are laid out contiguously in the order their leaves appear.
+// Child boxes are the exact float bounds of their triangles.
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <cstring>
+#include <deque>
+
+#include "lt_internal.h"
+
+namespace lt {
+namespace {
+
+struct Box {
+    float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX};
+    float hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    void grow(const float *p) {
+        for (int k = 0; k < 3; ++k) { lo[k] = std::min(lo[k], p[k]); hi[k] = std::max(hi[k], p[k]); }
+    }
+    void grow(const Box &b) {
+        for (int k = 0; k < 3; ++k) { lo[k] = std::min(lo[k], b.lo[k]); hi[k] = std::max(hi[k], b.hi[k]); }
+    }
+    double area() const {
+        if (hi[0] < lo[0]) return 0.0;
+        double dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
+        return 2.0 * (dx * dy + dy * dz + dz * dx);
+    }
+};
+
+struct BNode {
+    Box box;
+    int32_t left = -1, right = -1;   // inner node children
+    int32_t first = 0, count = 0;    // leaf triangle range in `idx`
+    bool leaf() const { return left < 0; }
+};
+
+struct Binary {
+    std::vector<BNode> nodes;
+    std::vector<int32_t> idx;
+};
+
+void build_binary(const float *xyz, int32_t n_tri, Binary *b) {
+    std::vector<Box> tbox(n_tri);
+    std::vector<float> cen(3 * (size_t)n_tri);
+    for (int32_t i = 0; i < n_tri; ++i) {
+        for (int v = 0; v < 3; ++v) tbox[i].grow(xyz + 9 * (size_t)i + 3 * v);
+        for (int k = 0; k < 3; ++k) cen[3 * (size_t)i + k] = 0.5f * (tbox[i].lo[k] + tbox[i].hi[k]);
+    }
+    b->idx.resize(n_tri);
+    for (int32_t i = 0; i < n_tri; ++i) b->idx[i] = i;
+    b->nodes.clear();
+    b->nodes.reserve(2 * (size_t)n_tri);
+    b->nodes.emplace_back();
+    struct Job { int32_t node, first, count; };
+    std::vector<Job> stack;
+    stack.push_back({0, 0, n_tri});
+    constexpr int kBins = 16;
+    while (!stack.empty()) {
+        Job j = stack.back();
+        stack.pop_back();
+        Box box, cbox;
+        for (int32_t i = j.first; i < j.first + j.count; ++i) {
+            box.grow(tbox[b->idx[i]]);
+            cbox.grow(&cen[3 * (size_t)b->idx[i]]);
+        }
+        b->nodes[j.node].box = box;
+        if (j.count <= kLeafMax) {
+            b->nodes[j.node].first = j.first;
+            b->nodes[j.node].count = j.count;
+            continue;
+        }
+        int axis = 0;
+        float ext[3];
+        for (int k = 0; k < 3; ++k) ext[k] = cbox.hi[k] - cbox.lo[k];
+        if (ext[1] > ext[axis]) axis = 1;
+        if (ext[2] > ext[axis]) axis = 2;
+        int32_t mid = j.first + j.count / 2;
+        int32_t *beg = b->idx.data() + j.first, *end = beg + j.count;
+        bool split_done = false;
+        if (ext[axis] > 0.0f) {
+            Box bin_box[kBins];
+            int32_t bin_cnt[kBins] = {0};
+            const float inv = (float)kBins / ext[axis];
+            auto bin_of = [&](int32_t t) {
+                int k = (int)((cen[3 * (size_t)t + axis] - cbox.lo[axis]) * inv);
+                return std::min(kBins - 1, std::max(0, k));
+            };
+            for (int32_t *p = beg; p < end; ++p) {
+                int k = bin_of(*p);
+                bin_box[k].grow(tbox[*p]);
+                bin_cnt[k] += 1;
+            }
+            double right_area[kBins];
+            int32_t right_cnt[kBins];
+            Box acc;
+            int32_t c = 0;
+            for (int k = kBins - 1; k > 0; --k) {
+                acc.grow(bin_box[k]);
+                c += bin_cnt[k];
+                right_area[k] = acc.area();
+                right_cnt[k] = c;
+            }
+            Box lacc;
+            int32_t lc = 0;
+            double best = 1e300;
+            int best_k = -1;
+            for (int k = 1; k < kBins; ++k) {
+                lacc.grow(bin_box[k - 1]);
+                lc += bin_cnt[k - 1];
+                if (lc == 0 || right_cnt[k] == 0) continue;
+                double cost = lacc.area() * lc + right_area[k] * right_cnt[k];
+                if (cost < best) { best = cost; best_k = k; }
+            }
+            if (best_k > 0) {
+                int32_t *m = std::partition(beg, end, [&](int32_t t) { return bin_of(t) < best_k; });
+                if (m != beg && m != end) { mid = (int32_t)(m - b->idx.data()); split_done = true; }
+            }
+        }
+        if (!split_done) {
+            // all centroids in one bin: split at the median along the axis
+            std::nth_element(beg, b->idx.data() + mid, end, [&](int32_t x, int32_t y) {
+                float cx = cen[3 * (size_t)x + axis], cy = cen[3 * (size_t)y + axis];
+                return cx < cy || (cx == cy && x < y);
+            });
+        }
+        int32_t l = (int32_t)b->nodes.size();
+        b->nodes.emplace_back();
+        b->nodes.emplace_back();
+        b->nodes[j.node].left = l;
+        b->nodes[j.node].right = l + 1;
+        stack.push_back({l + 1, mid, j.first + j.count - mid});
+        stack.push_back({l, j.first, mid - j.first});
+    }
+}
+
+}  // namespace
+
+bool build_wide_bvh(const float *xyz, int32_t n_tri, BvhBuild *out, std::string *err) {
+    if (n_tri <= 0 || n_tri >= (1 << 28)) {
+        *err = "triangle count must be in [1, 2^28)";
+        return false;
+    }
+    Binary b;
+    build_binary(xyz, n_tri, &b);
+    out->nodes.clear();
+    out->parent.clear();
+    out->order.clear();
+    out->order.reserve(n_tri);
+    out->depth = 0;
+
+    struct Item { int32_t bnode, wnode, depth; };
+    std::deque<Item> queue;
+    out->nodes.emplace_back();
+    out->parent.push_back(-1);
+    queue.push_back({0, 0, 0});
+    while (!queue.empty()) {
+        Item it = queue.front();
+        queue.pop_front();
+        out->depth = std::max(out->depth, it.depth + 1);
+        if (it.depth >= kMaxDepth) {
+            *err = "BVH deeper than the traversal trail supports";
+            return false;
+        }
+        std::vector<int32_t> kids;
+        const BNode &root = b.nodes[it.bnode];
+        if (root.leaf()) {
+            kids.push_back(it.bnode);
+        } else {
+            kids.push_back(root.left);
+            kids.push_back(root.right);
+            while ((int)kids.size() < kWide) {
+                int pick = -1;
+                double best = -1.0;
+                for (int k = 0; k < (int)kids.size(); ++k) {
+                    const BNode &c = b.nodes[kids[k]];
+                    if (!c.leaf() && c.box.area() > best) { best = c.box.area(); pick = k; }
+                }
+                if (pick < 0) break;
+                int32_t open = kids[pick];
+                kids[pick] = b.nodes[open].left;
+                kids.insert(kids.begin() + pick + 1, b.nodes[open].right);
+            }
+        }
+        Node node;
+        for (int k = 0; k < kWide; ++k) {
+            node.lox[k] = node.loy[k] = node.loz[k] = 0.0f;
+            node.hix[k] = node.hiy[k] = node.hiz[k] = 0.0f;
+            node.child[k] = kEmptyChild;
+        }
+        for (int k = 0; k < (int)kids.size(); ++k) {
+            const BNode &c = b.nodes[kids[k]];
+            node.lox[k] = c.box.lo[0]; node.hix[k] = c.box.hi[0];
+            node.loy[k] = c.box.lo[1]; node.hiy[k] = c.box.hi[1];
+            node.loz[k] = c.box.lo[2]; node.hiz[k] = c.box.hi[2];
+            if (c.leaf()) {
+                int32_t first = (int32_t)out->order.size();
+                for (int32_t i = c.first; i < c.first + c.count; ++i) out->order.push_back(b.idx[i]);
+                node.child[k] = -1 - ((first << 2) | (c.count - 1));
+            } else {
+                int32_t wn = (int32_t)out->nodes.size();
+                out->nodes.emplace_back();
+                out->parent.push_back(it.wnode);
+                node.child[k] = wn;
+                queue.push_back({kids[k], wn, it.depth + 1});
+            }
+        }
+        out->nodes[it.wnode] = node;
+    }
+    if ((int32_t)out->order.size() != n_tri) {
+        *err = "BVH builder lost triangles";
+        return false;
+    }
+    return true;
+}
+
+}  // namespace lt

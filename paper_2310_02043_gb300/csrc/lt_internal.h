@@ -1,0 +1,140 @@
+// lt_internal.h -- device data layouts and launch interfaces shared by the
+// library's own translation units (BVH builder, kernels, C ABI).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+namespace lt {
+
+constexpr int kWide = 8;                 // children per BVH node
+constexpr int kMaxDepth = 24;            // levels of wide nodes (3 x 8-bit pending masks per u64 word)
+constexpr int kLeafMax = 3;              // triangles per leaf child
+constexpr int32_t kEmptyChild = INT32_MIN;
+
+// 8-wide BVH node, 224 bytes: child boxes stored axis-major so a node is
+// fourteen 16-byte loads. child[k] >= 0 is an inner node index; a leaf is
+// -1 - ((first << 2) | (count - 1)) over the leaf-ordered triangle array;
+// kEmptyChild marks an unused slot.
+struct alignas(16) Node {
+    float lox[kWide], hix[kWide], loy[kWide], hiy[kWide], loz[kWide], hiz[kWide];
+    int32_t child[kWide];
+};
+static_assert(sizeof(Node) == 224, "node layout");
+
+// Triangle in leaf order, 48 bytes (three 16-byte loads).
+struct alignas(16) Tri {
+    float v0[3];
+    int32_t prim;     // index in the uploaded scene (ties in t go to the lower one)
+    float v1[3];
+    int32_t tile;
+    float v2[3];
+    float albedo;
+};
+static_assert(sizeof(Tri) == 48, "tri layout");
+
+// What a hit needs besides the vertices: chart coordinates and texel range.
+struct alignas(16) TriHit {
+    float uv[6];
+    int32_t res_u, res_v;
+    int64_t texel_off;
+    int64_t pad;
+};
+static_assert(sizeof(TriHit) == 48, "hit layout");
+
+// Per-light constants derived on the host (double, rounded to float).
+struct alignas(16) LightDev {
+    float pos[3];
+    int32_t type;
+    float ns[3];        // spot axis n(yaw, pitch)
+    float flux_k;       // I_e * Omega / N_l: Phi_r = flux_k * a(theta)
+    float e1[3];        // dn/dpitch
+    float dflux_dp_k;   // p_int * Omega / N_l: dPhi_r/dp_int = dflux_dp_k * a(theta)
+    float e2[3];        // dn/dyaw / cos(pitch)
+    float co;           // cos(theta_out)
+    float dn_dyaw[3];
+    float ci;           // cos(theta_in)
+    float dn_dpitch[3];
+    float inv_d;        // 1 / (ci - co)
+    float one_minus_co;
+    float sin_in;
+    float sin_out;
+    float pad0;
+    uint64_t first;     // photon range [first, end)
+    uint64_t end;
+};
+
+// Device error word bits.
+enum : int32_t { kErrSteps = 1, kErrTexel = 2, kErrDepth = 4 };
+
+struct TraceParams {
+    const Node *nodes;
+    const int32_t *parent;
+    int32_t n_nodes;
+    int32_t n_staged;           // nodes copied to shared memory by every block
+    const Tri *tris;
+    const TriHit *hits;
+    const LightDev *lights;
+    int32_t n_lights;
+    int32_t max_hits;
+    int32_t max_steps;          // node visits per ray before giving up (kErrSteps)
+    uint32_t design;
+    uint64_t seed;
+    uint64_t photon_begin, photon_end;
+    int64_t n_texels;
+    // forward
+    unsigned long long *q;      // [n_texels] fixed-point irradiance accumulator
+    float scale;                // S
+    // adjoint
+    const float *w;             // [n_texels] dO/dPhi per deposit
+    double *warp_acc;           // [n_warps][n_lights][8]
+    // debug record
+    int32_t *rec_tri;
+    int64_t *rec_texel;
+    double *rec_grad;           // [count][8] per-photon gradient terms, may be null
+    // counters
+    unsigned long long *segments;
+    int32_t *err;
+};
+
+struct LossParams {
+    const unsigned long long *q;
+    const float *E_target;
+    const float *alpha;
+    const float *area;
+    double inv_scale;
+    int64_t n_texels;
+    float *E_out;               // may be null
+    float *w_out;
+    double *partial;            // [kLossBlocks]
+    double *loss_out;           // device scalar
+};
+
+constexpr int kLossBlocks = 1024;
+constexpr int kLossThreads = 256;
+
+// Kernel launchers (lt_kernels.cu).
+cudaError_t launch_forward(const TraceParams &p, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t launch_adjoint(const TraceParams &p, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t launch_paths(const TraceParams &p, uint64_t count, cudaStream_t s);
+cudaError_t launch_loss(const LossParams &p, cudaStream_t s);
+cudaError_t launch_resolve(const unsigned long long *q, const float *area, double inv_scale, int64_t n,
+                           float *E_out, cudaStream_t s);
+cudaError_t launch_grad_finalize(const double *warp_acc, int64_t n_warps, int32_t n_lights, double *out,
+                                 cudaStream_t s);
+int trace_kernel_max_threads();
+cudaError_t trace_occupancy(bool adjoint, int block, size_t smem, int *blocks_per_sm);
+
+// Wide-BVH builder (lt_bvh.cpp).
+struct BvhBuild {
+    std::vector<Node> nodes;        // breadth-first: parents before children
+    std::vector<int32_t> parent;    // parent node of every node (-1 for the root)
+    std::vector<int32_t> order;     // leaf-ordered triangle -> uploaded triangle index
+    int depth = 0;
+};
+bool build_wide_bvh(const float *xyz, int32_t n_tri, BvhBuild *out, std::string *err);
+
+}  // namespace lt

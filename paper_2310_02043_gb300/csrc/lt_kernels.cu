@@ -1,0 +1,704 @@
+// lt_kernels.cu -- sm_103a kernels of view-independent adjoint light tracing
+// (Lipp et al., arXiv 2310.02043): forward tracing into texels (Alg. 1,
+// Eq. 7-8), the objective (Eq. 6), and the adjoint replay (Alg. 2,
+// Eq. 11-15, S.11-S.12).
+//
+// Precision: FP32 throughout the path; fixed-point int64 texel sums; FP64
+// gradient and loss reductions. The arithmetic that decides integers (which
+// triangle is hit, which texel) uses explicitly rounded operations
+// (__fmul_rn etc.) so the compiler cannot contract it into FMAs.
+#include <cfloat>
+#include <cstdint>
+
+#include "../../include/lt.h"
+#include "lt_internal.h"
+
+namespace lt {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kTraceThreads = 256;
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC 2011).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Two uniforms in [0, 1): 24 high bits of counter lanes 0 and 1.
+__device__ __forceinline__ float2 uniforms(uint64_t seed, uint64_t photon, uint32_t segment, uint32_t design) {
+    const uint4 r = philox(make_uint4((uint32_t)photon, (uint32_t)(photon >> 32), segment, design),
+                           make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    return make_float2((float)(r.x >> 8) * 0x1p-24f, (float)(r.y >> 8) * 0x1p-24f);
+}
+
+// ---------------------------------------------------------------------------
+// Rays
+// ---------------------------------------------------------------------------
+struct Ray {
+    float ox, oy, oz;
+    float dx, dy, dz;
+    float ix, iy, iz;        // 1 / d, zero components replaced by +-1e-30
+    int kx, ky, kz;          // watertight shear axes
+    float Sx, Sy, Sz;
+};
+
+__device__ __forceinline__ float sel3(float a, float b, float c, int k) { return k == 0 ? a : (k == 1 ? b : c); }
+
+__device__ __forceinline__ void ray_init(Ray &r, float ox, float oy, float oz, float dx, float dy, float dz) {
+    r.ox = ox; r.oy = oy; r.oz = oz;
+    r.dx = dx; r.dy = dy; r.dz = dz;
+    const float gx = fabsf(dx) < 1e-30f ? copysignf(1e-30f, dx) : dx;
+    const float gy = fabsf(dy) < 1e-30f ? copysignf(1e-30f, dy) : dy;
+    const float gz = fabsf(dz) < 1e-30f ? copysignf(1e-30f, dz) : dz;
+    r.ix = __fdiv_rn(1.0f, gx);
+    r.iy = __fdiv_rn(1.0f, gy);
+    r.iz = __fdiv_rn(1.0f, gz);
+    int kz = 0;
+    if (fabsf(dy) > fabsf(dx)) kz = 1;
+    if (fabsf(dz) > fabsf(sel3(dx, dy, dz, kz))) kz = 2;
+    int kx = kz + 1 == 3 ? 0 : kz + 1;
+    int ky = kx + 1 == 3 ? 0 : kx + 1;
+    const float dkz = sel3(dx, dy, dz, kz);
+    if (dkz < 0.0f) { const int t = kx; kx = ky; ky = t; }
+    r.kx = kx; r.ky = ky; r.kz = kz;
+    r.Sx = __fdiv_rn(sel3(dx, dy, dz, kx), dkz);
+    r.Sy = __fdiv_rn(sel3(dx, dy, dz, ky), dkz);
+    r.Sz = __fdiv_rn(1.0f, dkz);
+}
+
+// Watertight ray/triangle test (Woop, Benthin, Wald, JCGT 2013). Returns the
+// unnormalised edge functions and determinant (det > 0) on a hit with t > 0.
+struct TriTest {
+    float t, U, V, W, det;
+};
+
+__device__ __forceinline__ bool tri_intersect(const Ray &r, const float4 a, const float4 b, const float4 c,
+                                              TriTest &out) {
+    const float Ax0 = __fsub_rn(a.x, r.ox), Ay0 = __fsub_rn(a.y, r.oy), Az0 = __fsub_rn(a.z, r.oz);
+    const float Bx0 = __fsub_rn(b.x, r.ox), By0 = __fsub_rn(b.y, r.oy), Bz0 = __fsub_rn(b.z, r.oz);
+    const float Cx0 = __fsub_rn(c.x, r.ox), Cy0 = __fsub_rn(c.y, r.oy), Cz0 = __fsub_rn(c.z, r.oz);
+    const float Akx = sel3(Ax0, Ay0, Az0, r.kx), Aky = sel3(Ax0, Ay0, Az0, r.ky), Akz = sel3(Ax0, Ay0, Az0, r.kz);
+    const float Bkx = sel3(Bx0, By0, Bz0, r.kx), Bky = sel3(Bx0, By0, Bz0, r.ky), Bkz = sel3(Bx0, By0, Bz0, r.kz);
+    const float Ckx = sel3(Cx0, Cy0, Cz0, r.kx), Cky = sel3(Cx0, Cy0, Cz0, r.ky), Ckz = sel3(Cx0, Cy0, Cz0, r.kz);
+    const float Ax = __fsub_rn(Akx, __fmul_rn(r.Sx, Akz)), Ay = __fsub_rn(Aky, __fmul_rn(r.Sy, Akz));
+    const float Bx = __fsub_rn(Bkx, __fmul_rn(r.Sx, Bkz)), By = __fsub_rn(Bky, __fmul_rn(r.Sy, Bkz));
+    const float Cx = __fsub_rn(Ckx, __fmul_rn(r.Sx, Ckz)), Cy = __fsub_rn(Cky, __fmul_rn(r.Sy, Ckz));
+    float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+    float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+    float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+    if (U == 0.0f || V == 0.0f || W == 0.0f) {
+        U = (float)__dsub_rn(__dmul_rn((double)Cx, (double)By), __dmul_rn((double)Cy, (double)Bx));
+        V = (float)__dsub_rn(__dmul_rn((double)Ax, (double)Cy), __dmul_rn((double)Ay, (double)Cx));
+        W = (float)__dsub_rn(__dmul_rn((double)Bx, (double)Ay), __dmul_rn((double)By, (double)Ax));
+    }
+    if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return false;
+    float det = __fadd_rn(__fadd_rn(U, V), W);
+    if (det == 0.0f) return false;
+    const float Az = __fmul_rn(r.Sz, Akz), Bz = __fmul_rn(r.Sz, Bkz), Cz = __fmul_rn(r.Sz, Ckz);
+    float T = __fadd_rn(__fadd_rn(__fmul_rn(U, Az), __fmul_rn(V, Bz)), __fmul_rn(W, Cz));
+    if (det < 0.0f) { det = -det; T = -T; U = -U; V = -V; W = -W; }
+    if (!(T > 0.0f)) return false;
+    out.t = __fdiv_rn(T, det);
+    out.U = U; out.V = V; out.W = W; out.det = det;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Wide-BVH traversal without a stack: the pending children of every level
+// are an 8-bit mask packed into three 64-bit registers; returning to a level
+// follows the parent link and re-tests that node's pending children against
+// the current closest hit.
+// ---------------------------------------------------------------------------
+struct Trail {
+    uint64_t w0 = 0, w1 = 0, w2 = 0;
+    __device__ __forceinline__ uint32_t get(int lvl) const {
+        const uint64_t w = lvl < 8 ? w0 : (lvl < 16 ? w1 : w2);
+        return (uint32_t)(w >> ((lvl & 7) * 8)) & 0xffu;
+    }
+    __device__ __forceinline__ void set(int lvl, uint32_t m) {
+        const int sh = (lvl & 7) * 8;
+        const uint64_t clear = ~(0xffull << sh), put = (uint64_t)m << sh;
+        if (lvl < 8) w0 = (w0 & clear) | put;
+        else if (lvl < 16) w1 = (w1 & clear) | put;
+        else w2 = (w2 & clear) | put;
+    }
+};
+
+struct Hit {
+    int32_t tri;       // leaf-order index, -1 on a miss
+    int32_t prim;      // uploaded index (tie-break)
+    float t, U, V, W, det;
+};
+
+__device__ __forceinline__ const float4 *node_ptr(const TraceParams &P, const float4 *smem, int32_t n) {
+    return n < P.n_staged ? smem + (size_t)n * (sizeof(Node) / 16)
+                          : reinterpret_cast<const float4 *>(P.nodes + n);
+}
+
+__device__ __forceinline__ float4 ld4(const float4 *p, bool shared) {
+    return shared ? *p : __ldg(p);
+}
+
+// Ize, "Robust BVH ray traversal" (JCGT 2013): scale the exit distance by
+// 1 + 2 gamma_3 so float rounding never rejects a box the ray touches.
+constexpr float kFarScale = 1.0f + 2.0f * (3.0f * 0x1p-24f) / (1.0f - 3.0f * 0x1p-24f);
+
+// Tests the children in `mask` of node n; returns the hit mask and entry
+// distances. Also returns the child words.
+__device__ __forceinline__ uint32_t test_node(const TraceParams &P, const float4 *smem, int32_t n, const Ray &r,
+                                              float tbest, uint32_t mask, float tnear[kWide],
+                                              int32_t child[kWide]) {
+    const float4 *p = node_ptr(P, smem, n);
+    const bool sh = n < P.n_staged;
+    float lox[8], hix[8], loy[8], hiy[8], loz[8], hiz[8];
+    {
+        const float4 a0 = ld4(p + 0, sh), a1 = ld4(p + 1, sh), b0 = ld4(p + 2, sh), b1 = ld4(p + 3, sh);
+        lox[0] = a0.x; lox[1] = a0.y; lox[2] = a0.z; lox[3] = a0.w; lox[4] = a1.x; lox[5] = a1.y; lox[6] = a1.z; lox[7] = a1.w;
+        hix[0] = b0.x; hix[1] = b0.y; hix[2] = b0.z; hix[3] = b0.w; hix[4] = b1.x; hix[5] = b1.y; hix[6] = b1.z; hix[7] = b1.w;
+    }
+    {
+        const float4 a0 = ld4(p + 4, sh), a1 = ld4(p + 5, sh), b0 = ld4(p + 6, sh), b1 = ld4(p + 7, sh);
+        loy[0] = a0.x; loy[1] = a0.y; loy[2] = a0.z; loy[3] = a0.w; loy[4] = a1.x; loy[5] = a1.y; loy[6] = a1.z; loy[7] = a1.w;
+        hiy[0] = b0.x; hiy[1] = b0.y; hiy[2] = b0.z; hiy[3] = b0.w; hiy[4] = b1.x; hiy[5] = b1.y; hiy[6] = b1.z; hiy[7] = b1.w;
+    }
+    {
+        const float4 a0 = ld4(p + 8, sh), a1 = ld4(p + 9, sh), b0 = ld4(p + 10, sh), b1 = ld4(p + 11, sh);
+        loz[0] = a0.x; loz[1] = a0.y; loz[2] = a0.z; loz[3] = a0.w; loz[4] = a1.x; loz[5] = a1.y; loz[6] = a1.z; loz[7] = a1.w;
+        hiz[0] = b0.x; hiz[1] = b0.y; hiz[2] = b0.z; hiz[3] = b0.w; hiz[4] = b1.x; hiz[5] = b1.y; hiz[6] = b1.z; hiz[7] = b1.w;
+    }
+    {
+        const int4 *cp = reinterpret_cast<const int4 *>(p + 12);
+        const int4 c0 = sh ? cp[0] : __ldg(cp), c1 = sh ? cp[1] : __ldg(cp + 1);
+        child[0] = c0.x; child[1] = c0.y; child[2] = c0.z; child[3] = c0.w;
+        child[4] = c1.x; child[5] = c1.y; child[6] = c1.z; child[7] = c1.w;
+    }
+    uint32_t hit = 0;
+#pragma unroll
+    for (int k = 0; k < kWide; ++k) {
+        const float t0x = (lox[k] - r.ox) * r.ix, t1x = (hix[k] - r.ox) * r.ix;
+        const float t0y = (loy[k] - r.oy) * r.iy, t1y = (hiy[k] - r.oy) * r.iy;
+        const float t0z = (loz[k] - r.oz) * r.iz, t1z = (hiz[k] - r.oz) * r.iz;
+        const float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), 0.0f));
+        const float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fmaxf(t0z, t1z)) * kFarScale;
+        tnear[k] = tn;
+        const bool h = ((mask >> k) & 1u) && child[k] != kEmptyChild && tn <= tf && tn <= tbest;
+        hit |= (h ? 1u : 0u) << k;
+    }
+    return hit;
+}
+
+__device__ __forceinline__ int pick_nearest(uint32_t m, const float tnear[kWide]) {
+    int best = -1;
+    float bt = FLT_MAX;
+#pragma unroll
+    for (int k = 0; k < kWide; ++k) {
+        if (((m >> k) & 1u) && (best < 0 || tnear[k] < bt)) { best = k; bt = tnear[k]; }
+    }
+    return best;
+}
+
+__device__ __forceinline__ int32_t pick_child(const int32_t child[kWide], int k) {
+    int32_t c = child[0];
+#pragma unroll
+    for (int j = 1; j < kWide; ++j) c = (j == k) ? child[j] : c;
+    return c;
+}
+
+// Closest hit excluding triangles of tile `skip_tile`. Ties in t go to the
+// lower uploaded triangle index.
+__device__ __forceinline__ Hit closest_hit(const TraceParams &P, const float4 *smem, const Ray &r, int32_t skip_tile) {
+    Hit h;
+    h.tri = -1; h.prim = INT32_MAX; h.t = FLT_MAX; h.U = h.V = h.W = 0.0f; h.det = 1.0f;
+    Trail trail;
+    int32_t node = 0;
+    int lvl = 0;
+    int steps = 0;
+    float tnear[kWide];
+    int32_t child[kWide];
+    while (true) {
+        if (++steps > P.max_steps) { atomicOr(P.err, kErrSteps); h.tri = -1; return h; }
+        uint32_t m = test_node(P, smem, node, r, h.t, 0xffu, tnear, child);
+        // leaves of this node first
+#pragma unroll
+        for (int k = 0; k < kWide; ++k) {
+            if (((m >> k) & 1u) && child[k] < 0) {
+                const int32_t code = -1 - child[k];
+                const int32_t first = code >> 2, count = (code & 3) + 1;
+                for (int32_t i = first; i < first + count; ++i) {
+                    const float4 *tp = reinterpret_cast<const float4 *>(P.tris + i);
+                    const float4 a = __ldg(tp), b = __ldg(tp + 1), c = __ldg(tp + 2);
+                    const int32_t tile = __float_as_int(b.w);
+                    if (tile == skip_tile) continue;
+                    TriTest tt;
+                    if (!tri_intersect(r, a, b, c, tt)) continue;
+                    const int32_t prim = __float_as_int(a.w);
+                    if (tt.t < h.t || (tt.t == h.t && prim < h.prim)) {
+                        h.tri = i; h.prim = prim; h.t = tt.t;
+                        h.U = tt.U; h.V = tt.V; h.W = tt.W; h.det = tt.det;
+                    }
+                }
+            }
+        }
+        uint32_t inner = 0;
+#pragma unroll
+        for (int k = 0; k < kWide; ++k)
+            inner |= (((m >> k) & 1u) && child[k] >= 0 && tnear[k] <= h.t ? 1u : 0u) << k;
+        if (inner) {
+            const int k = pick_nearest(inner, tnear);
+            trail.set(lvl, inner & ~(1u << k));
+            node = pick_child(child, k);
+            ++lvl;
+            if (lvl >= kMaxDepth) { atomicOr(P.err, kErrDepth); h.tri = -1; return h; }
+            continue;
+        }
+        // backtrack to the nearest level with pending children
+        bool found = false;
+        while (lvl > 0) {
+            --lvl;
+            node = P.parent[node];
+            const uint32_t pend = trail.get(lvl);
+            if (pend == 0) continue;
+            if (++steps > P.max_steps) { atomicOr(P.err, kErrSteps); h.tri = -1; return h; }
+            const uint32_t again = test_node(P, smem, node, r, h.t, pend, tnear, child);
+            uint32_t live = 0;
+#pragma unroll
+            for (int k = 0; k < kWide; ++k) live |= (((again >> k) & 1u) && child[k] >= 0 ? 1u : 0u) << k;
+            if (!live) { trail.set(lvl, 0); continue; }
+            const int k = pick_nearest(live, tnear);
+            trail.set(lvl, live & ~(1u << k));
+            node = pick_child(child, k);
+            ++lvl;
+            found = true;
+            break;
+        }
+        if (!found) return h;
+    }
+}
+
+// Texel of a hit: barycentric chart coordinates in float, clamped,
+// min(floor(u res), res - 1).
+__device__ __forceinline__ int64_t texel_of(const TraceParams &P, const Hit &h) {
+    const TriHit &th = P.hits[h.tri];
+    const float b0 = __fdiv_rn(h.U, h.det), b1 = __fdiv_rn(h.V, h.det), b2 = __fdiv_rn(h.W, h.det);
+    float u = __fadd_rn(__fadd_rn(__fmul_rn(b0, th.uv[0]), __fmul_rn(b1, th.uv[2])), __fmul_rn(b2, th.uv[4]));
+    float v = __fadd_rn(__fadd_rn(__fmul_rn(b0, th.uv[1]), __fmul_rn(b1, th.uv[3])), __fmul_rn(b2, th.uv[5]));
+    u = u < 0.0f ? 0.0f : (u > 1.0f ? 1.0f : u);
+    v = v < 0.0f ? 0.0f : (v > 1.0f ? 1.0f : v);
+    int32_t iu = (int32_t)floorf(__fmul_rn(u, (float)th.res_u));
+    int32_t iv = (int32_t)floorf(__fmul_rn(v, (float)th.res_v));
+    iu = min(max(iu, 0), th.res_u - 1);
+    iv = min(max(iv, 0), th.res_v - 1);
+    return th.texel_off + (int64_t)iu + (int64_t)th.res_u * (int64_t)iv;
+}
+
+// Unit geometric normal of triangle `tri`, turned to face against w.
+__device__ __forceinline__ float3 facing_normal(const TraceParams &P, int32_t tri, float wx, float wy, float wz) {
+    const float4 *tp = reinterpret_cast<const float4 *>(P.tris + tri);
+    const float4 a = __ldg(tp), b = __ldg(tp + 1), c = __ldg(tp + 2);
+    const float e1x = b.x - a.x, e1y = b.y - a.y, e1z = b.z - a.z;
+    const float e2x = c.x - a.x, e2y = c.y - a.y, e2z = c.z - a.z;
+    float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+    const float inv = rsqrtf(nx * nx + ny * ny + nz * nz);
+    nx *= inv; ny *= inv; nz *= inv;
+    if (nx * wx + ny * wy + nz * wz > 0.0f) { nx = -nx; ny = -ny; nz = -nz; }
+    return make_float3(nx, ny, nz);
+}
+
+__device__ __forceinline__ float albedo_of(const TraceParams &P, int32_t tri) {
+    return __ldg(reinterpret_cast<const float *>(P.tris + tri) + 11);
+}
+
+// Quadratic spot soft edge in cos(theta) (Eq. S.11).
+__device__ __forceinline__ float falloff(const LightDev &L, float c) {
+    if (c >= L.ci) return 1.0f;
+    if (c <= L.co) return 0.0f;
+    const float s = (c - L.co) * L.inv_d;
+    return s * s;
+}
+
+__device__ __forceinline__ int32_t light_of(const TraceParams &P, uint64_t photon) {
+    int32_t lo = 0, hi = P.n_lights - 1;
+    while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (photon < P.lights[mid].end) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+// Exitant ray of light L: uniform sphere (point) or uniform outer cone (spot).
+__device__ __forceinline__ float emit(const LightDev &L, float u1, float u2, float &wx, float &wy, float &wz,
+                                      float &a) {
+    float sp, cp;
+    sincospif(2.0f * u2, &sp, &cp);
+    if (L.type == LT_SPOT) {
+        const float c = 1.0f - u1 * L.one_minus_co;
+        const float s = sqrtf(fmaxf(0.0f, 1.0f - c * c));
+        wx = s * cp * L.e1[0] + s * sp * L.e2[0] + c * L.ns[0];
+        wy = s * cp * L.e1[1] + s * sp * L.e2[1] + c * L.ns[1];
+        wz = s * cp * L.e1[2] + s * sp * L.e2[2] + c * L.ns[2];
+        a = falloff(L, c);
+        return L.flux_k * a;
+    }
+    const float c = 1.0f - 2.0f * u1;
+    const float s = sqrtf(fmaxf(0.0f, 1.0f - c * c));
+    wx = s * cp; wy = s * sp; wz = c;
+    a = 1.0f;
+    return L.flux_k;
+}
+
+// Cosine-weighted direction about unit n (branchless orthonormal basis of
+// Duff et al., JCGT 2017).
+__device__ __forceinline__ void cosine_dir(float3 n, float u1, float u2, float &wx, float &wy, float &wz) {
+    const float sgn = n.z >= 0.0f ? 1.0f : -1.0f;
+    const float a = -1.0f / (sgn + n.z);
+    const float b = n.x * n.y * a;
+    const float t1x = 1.0f + sgn * n.x * n.x * a, t1y = sgn * b, t1z = -sgn * n.x;
+    const float t2x = b, t2y = sgn + n.y * n.y * a, t2z = -n.y;
+    float sp, cp;
+    sincospif(2.0f * u2, &sp, &cp);
+    const float r = sqrtf(u1), z = sqrtf(1.0f - u1);
+    const float lx = r * cp, ly = r * sp;
+    wx = lx * t1x + ly * t2x + z * n.x;
+    wy = lx * t1y + ly * t2y + z * n.y;
+    wz = lx * t1z + ly * t2z + z * n.z;
+}
+
+// dPhi_r/dp at the first hit x1 (normal n1 facing the light), the hit held
+// fixed (Sec. 4.4.2). Order [x, y, z, yaw, pitch, p_int, theta_in, theta_out].
+__device__ __forceinline__ void dflux(const LightDev &L, float phi_r, float a_emit, float x1x, float x1y, float x1z,
+                                      float3 n1, float out[8]) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) out[k] = 0.0f;
+    const float dx = L.pos[0] - x1x, dy = L.pos[1] - x1y, dz = L.pos[2] - x1z;
+    const float ell = sqrtf(dx * dx + dy * dy + dz * dz);
+    const float il = 1.0f / ell;
+    const float ux = dx * il, uy = dy * il, uz = dz * il;
+    const float c1 = n1.x * ux + n1.y * uy + n1.z * uz;
+    if (c1 > 0.0f) {
+        // Eq. 14: virtual intensity Phi_r r^2 / cos times grad(cos / r^2)
+        const float k = phi_r * il;
+        const float ic1 = 1.0f / c1;
+        out[0] = k * (n1.x * ic1 - 3.0f * ux);
+        out[1] = k * (n1.y * ic1 - 3.0f * uy);
+        out[2] = k * (n1.z * ic1 - 3.0f * uz);
+    }
+    out[5] = L.dflux_dp_k * a_emit;         // I_e = p^2 / 2
+    if (L.type != LT_SPOT) return;
+    const float wx = -ux, wy = -uy, wz = -uz;
+    const float c = L.ns[0] * wx + L.ns[1] * wy + L.ns[2] * wz;
+    if (!(c > L.co && c < L.ci)) return;
+    const float scale = L.flux_k;            // I_e Omega / N_l
+    const float s = (c - L.co) * L.inv_d;
+    const float da_dc = 2.0f * s * L.inv_d;
+    // Eq. S.12: d cos(theta)/dx = -(n - cos(theta) w) / r
+    out[0] += scale * da_dc * (-(L.ns[0] - c * wx) * il);
+    out[1] += scale * da_dc * (-(L.ns[1] - c * wy) * il);
+    out[2] += scale * da_dc * (-(L.ns[2] - c * wz) * il);
+    // Eq. 15 with n(yaw, pitch): d cos(theta)/dn = w
+    out[3] = scale * da_dc * (wx * L.dn_dyaw[0] + wy * L.dn_dyaw[1] + wz * L.dn_dyaw[2]);
+    out[4] = scale * da_dc * (wx * L.dn_dpitch[0] + wy * L.dn_dpitch[1] + wz * L.dn_dpitch[2]);
+    const float id3 = L.inv_d * L.inv_d * L.inv_d;
+    out[6] = scale * 2.0f * (c - L.co) * (c - L.co) * L.sin_in * id3;
+    out[7] = scale * (-2.0f) * (c - L.co) * (c - L.ci) * L.sin_out * id3;
+}
+
+// Warp-aggregated fixed-point deposit: lanes depositing into the same texel
+// sum their values with shuffles; one 64-bit atomic per distinct texel.
+__device__ __forceinline__ void deposit(unsigned long long *q, bool dep, int64_t texel, unsigned long long val) {
+    const unsigned m = __ballot_sync(kFull, dep);
+    if (!dep) return;
+    const unsigned peers = __match_any_sync(m, (unsigned long long)texel);
+    unsigned long long tot = 0;
+    unsigned rest = peers;
+    while (rest) {
+        const int src = __ffs(rest) - 1;
+        tot += __shfl_sync(peers, val, src);
+        rest &= rest - 1;
+    }
+    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(q + texel, tot);
+}
+
+__device__ __forceinline__ void stage_nodes(const TraceParams &P, float4 *smem) {
+    const int n = P.n_staged * (int)(sizeof(Node) / 16);
+    const float4 *src = reinterpret_cast<const float4 *>(P.nodes);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) smem[i] = __ldg(src + i);
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Forward / adjoint tracing. A warp takes 32 consecutive photons per
+// iteration and walks their paths segment by segment in lock step.
+// ---------------------------------------------------------------------------
+template <bool kAdjoint>
+__global__ void __launch_bounds__(kTraceThreads) trace_kernel(const TraceParams P) {
+    extern __shared__ float4 smem[];
+    stage_nodes(P, smem);
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (uint64_t)(blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t n_warps = (uint64_t)(gridDim.x * blockDim.x) >> 5;
+    unsigned long long segs = 0;
+    double acc = 0.0;          // adjoint: lane k < 8 holds parameter k of light `cur`
+    int32_t cur = -1;
+
+    for (uint64_t base = P.photon_begin + warp * 32; base < P.photon_end; base += n_warps * 32) {
+        const uint64_t photon = base + lane;
+        const bool valid = photon < P.photon_end;
+        const int32_t l = valid ? light_of(P, photon) : 0;
+        const LightDev &L = P.lights[l];
+        float wx = 0.0f, wy = 0.0f, wz = 1.0f, a_emit = 0.0f, phi = 0.0f;
+        if (valid) {
+            const float2 u = uniforms(P.seed, photon, 0u, P.design);
+            phi = emit(L, u.x, u.y, wx, wy, wz, a_emit);
+        }
+        const float phi_r = phi;
+        float ox = L.pos[0], oy = L.pos[1], oz = L.pos[2];
+        int32_t skip = -1;
+        bool alive = valid;
+        float g = 0.0f, beta = 1.0f;
+        float dp[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) dp[k] = 0.0f;
+
+        for (int i = 1; i <= P.max_hits; ++i) {
+            const unsigned am = __ballot_sync(kFull, alive);
+            if (am == 0) break;
+            if (lane == 0) segs += __popc(am);
+            Hit h;
+            h.tri = -1;
+            if (alive) {
+                Ray r;
+                ray_init(r, ox, oy, oz, wx, wy, wz);
+                h = closest_hit(P, smem, r, skip);
+            }
+            const bool hit = alive && h.tri >= 0;
+            int64_t texel = 0;
+            float x1x = 0.0f, x1y = 0.0f, x1z = 0.0f;
+            float3 n = make_float3(0.0f, 0.0f, 1.0f);
+            if (hit) {
+                texel = texel_of(P, h);
+                x1x = fmaf(h.t, wx, ox); x1y = fmaf(h.t, wy, oy); x1z = fmaf(h.t, wz, oz);
+                n = facing_normal(P, h.tri, wx, wy, wz);
+            }
+            if (!kAdjoint) {
+                const unsigned long long v = hit ? (unsigned long long)__float2ll_rn(phi * P.scale) : 0ull;
+                deposit(P.q, hit, texel, v);
+            } else if (hit) {
+                if (i == 1) dflux(L, phi_r, a_emit, x1x, x1y, x1z, n, dp);
+                g += __ldg(P.w + texel) * beta;        // Eq. 12
+            }
+            if (!hit || i == P.max_hits) { alive = false; continue; }
+            const float rho = albedo_of(P, h.tri);
+            const float2 u = uniforms(P.seed, photon, (uint32_t)i, P.design);
+            cosine_dir(n, u.x, u.y, wx, wy, wz);
+            phi *= rho;                                  // Eq. 7
+            beta *= rho;
+            ox = x1x; oy = x1y; oz = x1z;
+            skip = __ldg(reinterpret_cast<const int32_t *>(P.tris + h.tri) + 7);
+        }
+
+        if (kAdjoint) {
+            // Eq. 11: sum_r dO/dPhi_r dPhi_r/dp, reduced per light in a fixed
+            // lane order and added to this warp's FP64 accumulator.
+            unsigned pending = __ballot_sync(kFull, valid);
+            while (pending) {
+                const int src = __ffs(pending) - 1;
+                const int32_t L0 = __shfl_sync(kFull, l, src);
+                const bool mine = valid && l == L0;
+                const unsigned grp = __ballot_sync(kFull, mine);
+                double v[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) v[k] = mine ? (double)(g * dp[k]) : 0.0;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) v[k] += __shfl_xor_sync(kFull, v[k], off);
+                }
+                if (L0 != cur) {
+                    if (cur >= 0 && lane < 8) P.warp_acc[(warp * P.n_lights + cur) * 8 + lane] = acc;
+                    acc = 0.0;
+                    cur = L0;
+                }
+                double mine_v = v[0];
+#pragma unroll
+                for (int k = 1; k < 8; ++k) mine_v = (lane == k) ? v[k] : mine_v;
+                acc += mine_v;
+                pending &= ~grp;
+            }
+        }
+    }
+    if (kAdjoint && cur >= 0 && lane < 8) P.warp_acc[(warp * P.n_lights + cur) * 8 + lane] = acc;
+    if (lane == 0 && segs) atomicAdd(P.segments, segs);
+}
+
+// Path record for debugging: one thread per photon.
+__global__ void __launch_bounds__(128) paths_kernel(const TraceParams P, uint64_t count) {
+    const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    const uint64_t photon = P.photon_begin + k;
+    const int32_t l = light_of(P, photon);
+    const LightDev &L = P.lights[l];
+    float wx, wy, wz, a_emit;
+    const float2 u0 = uniforms(P.seed, photon, 0u, P.design);
+    const float phi_r = emit(L, u0.x, u0.y, wx, wy, wz, a_emit);
+    float ox = L.pos[0], oy = L.pos[1], oz = L.pos[2];
+    int32_t skip = -1;
+    int32_t *rt = P.rec_tri + k * P.max_hits;
+    int64_t *rx = P.rec_texel + k * P.max_hits;
+    for (int i = 0; i < P.max_hits; ++i) { rt[i] = -1; rx[i] = -1; }
+    float g = 0.0f, beta = 1.0f, dp[8];
+    for (int j = 0; j < 8; ++j) dp[j] = 0.0f;
+    for (int i = 1; i <= P.max_hits; ++i) {
+        Ray r;
+        ray_init(r, ox, oy, oz, wx, wy, wz);
+        const Hit h = closest_hit(P, nullptr, r, skip);
+        if (h.tri < 0) break;
+        const int64_t texel = texel_of(P, h);
+        rt[i - 1] = h.prim;
+        rx[i - 1] = texel;
+        const float x1x = fmaf(h.t, wx, ox), x1y = fmaf(h.t, wy, oy), x1z = fmaf(h.t, wz, oz);
+        const float3 n = facing_normal(P, h.tri, wx, wy, wz);
+        if (P.rec_grad) {
+            if (i == 1) dflux(L, phi_r, a_emit, x1x, x1y, x1z, n, dp);
+            g += __ldg(P.w + texel) * beta;
+        }
+        if (i == P.max_hits) break;
+        const float2 u = uniforms(P.seed, photon, (uint32_t)i, P.design);
+        cosine_dir(n, u.x, u.y, wx, wy, wz);
+        beta *= albedo_of(P, h.tri);
+        ox = x1x; oy = x1y; oz = x1z;
+        skip = __ldg(reinterpret_cast<const int32_t *>(P.tris + h.tri) + 7);
+    }
+    if (P.rec_grad)
+        for (int j = 0; j < 8; ++j) P.rec_grad[k * 8 + j] = (double)(g * dp[j]);
+}
+
+// ---------------------------------------------------------------------------
+// Objective (Eq. 6) and adjoint weights; fixed grid and fixed reduction order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
+    }
+    __syncthreads();
+    return t;
+}
+
+__global__ void __launch_bounds__(kLossThreads) loss_kernel(const LossParams P) {
+    __shared__ double sh[kLossThreads / 32];
+    double part = 0.0;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < P.n_texels;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const double A = (double)P.area[t];
+        const double E = (double)(long long)P.q[t] * P.inv_scale / A;
+        const double r = E - (double)P.E_target[t];
+        const double a = P.alpha ? (double)P.alpha[t] : 1.0;
+        if (P.E_out) P.E_out[t] = (float)E;
+        P.w_out[t] = (float)(a * r);
+        part += 0.5 * A * a * r * r;
+    }
+    const double s = block_sum(part, sh);
+    if (threadIdx.x == 0) P.partial[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kLossThreads) loss_final_kernel(const double *partial, int n, double *out) {
+    __shared__ double sh[kLossThreads / 32];
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v += partial[i];
+    const double s = block_sum(v, sh);
+    if (threadIdx.x == 0) *out = s;
+}
+
+__global__ void resolve_kernel(const unsigned long long *q, const float *area, double inv_scale, int64_t n,
+                               float *E) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        E[t] = (float)((double)(long long)q[t] * inv_scale / (double)area[t]);
+}
+
+// Sum of the per-warp gradient accumulators: one block per light, fixed order.
+__global__ void __launch_bounds__(256) grad_finalize_kernel(const double *acc, int64_t n_warps, int32_t n_lights,
+                                                            double *out) {
+    __shared__ double sh[256 / 32];
+    const int32_t l = blockIdx.x;
+    for (int k = 0; k < 8; ++k) {
+        double v = 0.0;
+        for (int64_t w = threadIdx.x; w < n_warps; w += blockDim.x) v += acc[(w * n_lights + l) * 8 + k];
+        const double s = block_sum(v, sh);
+        if (threadIdx.x == 0) out[l * 8 + k] = s;
+    }
+}
+
+}  // namespace
+
+int trace_kernel_max_threads() { return kTraceThreads; }
+
+cudaError_t trace_occupancy(bool adjoint, int block, size_t smem, int *blocks_per_sm) {
+    auto fn = adjoint ? trace_kernel<true> : trace_kernel<false>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem);
+}
+
+cudaError_t launch_forward(const TraceParams &p, int grid, int block, size_t smem, cudaStream_t s) {
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(trace_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    trace_kernel<false><<<grid, block, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint(const TraceParams &p, int grid, int block, size_t smem, cudaStream_t s) {
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(trace_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    trace_kernel<true><<<grid, block, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_paths(const TraceParams &p, uint64_t count, cudaStream_t s) {
+    TraceParams q = p;
+    q.n_staged = 0;
+    const unsigned blocks = (unsigned)((count + 127) / 128);
+    paths_kernel<<<blocks, 128, 0, s>>>(q, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loss(const LossParams &p, cudaStream_t s) {
+    loss_kernel<<<kLossBlocks, kLossThreads, 0, s>>>(p);
+    loss_final_kernel<<<1, kLossThreads, 0, s>>>(p.partial, kLossBlocks, p.loss_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resolve(const unsigned long long *q, const float *area, double inv_scale, int64_t n, float *E,
+                           cudaStream_t s) {
+    resolve_kernel<<<1024, 256, 0, s>>>(q, area, inv_scale, n, E);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_finalize(const double *acc, int64_t n_warps, int32_t n_lights, double *out, cudaStream_t s) {
+    grad_finalize_kernel<<<n_lights, 256, 0, s>>>(acc, n_warps, n_lights, out);
+    return cudaGetLastError();
+}
+
+}  // namespace lt

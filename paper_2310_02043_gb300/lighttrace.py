@@ -1,0 +1,261 @@
+"""Python binding of the C ABI in include/lt.h (argument marshalling only).
+
+Every step of the light-tracing path runs in the CUDA library
+``_lib/libltrace.so``; this module converts numpy arrays / torch tensors to
+pointers and raises on error statuses. There is no fallback: if the library
+is missing, importing works but creating a ``Tracer`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libltrace.so")
+
+LT_OK, LT_ERR_ARG, LT_ERR_CUDA, LT_ERR_OOM, LT_ERR_STATE, LT_ERR_TIMEOUT, LT_ERR_OVERFLOW, LT_ERR_DEVICE = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+STATUS_NAMES = {0: "LT_OK", -1: "LT_ERR_ARG", -2: "LT_ERR_CUDA", -3: "LT_ERR_OOM", -4: "LT_ERR_STATE",
+                -5: "LT_ERR_TIMEOUT", -6: "LT_ERR_OVERFLOW", -7: "LT_ERR_DEVICE"}
+MAX_LIGHTS = 1024
+GRAD_N = 8
+
+# Every symbol the header declares (checked by the test suite).
+EXPORTED = ("lt_version", "lt_create", "lt_destroy", "lt_set_stream", "lt_last_error", "lt_upload_scene",
+            "lt_set_target", "lt_set_lights", "lt_trace_forward", "lt_texel_accumulator", "lt_get_texel_sums", "lt_loss",
+            "lt_get_irradiance", "lt_texel_areas", "lt_set_adjoint_weights", "lt_trace_adjoint", "lt_debug_paths",
+            "lt_get_stats", "lt_set_launch")
+
+
+class LtError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class lt_light(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("pos", ctypes.c_float * 3), ("yaw", ctypes.c_float),
+                ("pitch", ctypes.c_float), ("p_int", ctypes.c_float), ("theta_in", ctypes.c_float),
+                ("theta_out", ctypes.c_float)]
+
+
+class lt_stats(ctypes.Structure):
+    _fields_ = [("segments_forward", ctypes.c_uint64), ("segments_adjoint", ctypes.c_uint64),
+                ("photons_forward", ctypes.c_uint64), ("photons_adjoint", ctypes.c_uint64),
+                ("n_texels", ctypes.c_int64), ("n_triangles", ctypes.c_int32), ("n_nodes", ctypes.c_int32),
+                ("bvh_depth", ctypes.c_int32), ("staged_nodes", ctypes.c_int32),
+                ("fixed_point_scale", ctypes.c_double)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libltrace.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA light-tracing library not built: {path} is missing "
+                                   "(run __graft_entry__.build())")
+            lib = ctypes.CDLL(path)
+            _declare(lib)
+            _lib = lib
+    return _lib
+
+
+def _declare(lib):
+    vp, i32, i64, u64, ci = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int
+    sig = {
+        "lt_version": [],
+        "lt_create": [ctypes.POINTER(vp), ci, vp],
+        "lt_destroy": [vp],
+        "lt_set_stream": [vp, vp],
+        "lt_upload_scene": [vp, vp, vp, vp, vp, i32, vp, vp, i32, ctypes.POINTER(i64)],
+        "lt_set_target": [vp, vp, vp, ci],
+        "lt_set_lights": [vp, vp, i32],
+        "lt_trace_forward": [vp, u64, u64, i32, u64, u64],
+        "lt_texel_accumulator": [vp, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double)],
+        "lt_get_texel_sums": [vp, vp, ci],
+        "lt_loss": [vp, vp, ci],
+        "lt_get_irradiance": [vp, vp, ci],
+        "lt_texel_areas": [vp, vp, ci],
+        "lt_set_adjoint_weights": [vp, vp, ci],
+        "lt_trace_adjoint": [vp, u64, u64, i32, u64, u64, vp, ci],
+        "lt_debug_paths": [vp, u64, u64, i32, u64, u64, vp, vp, vp],
+        "lt_get_stats": [vp, ctypes.POINTER(lt_stats)],
+        "lt_set_launch": [vp, i32, i32, i32],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.lt_last_error.argtypes = [vp]
+    lib.lt_last_error.restype = ctypes.c_char_p
+
+
+def _ptr(x):
+    """Pointer and is_device flag of a numpy array or torch tensor."""
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data_as(ctypes.c_void_p), 0
+    import torch
+    if isinstance(x, torch.Tensor):
+        assert x.is_contiguous()
+        return ctypes.c_void_p(x.data_ptr()), (1 if x.is_cuda else 0)
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def lights_to_struct(lights: np.ndarray):
+    """[n, 9] rows (type, x, y, z, yaw, pitch, p_int, theta_in, theta_out) -> lt_light array."""
+    arr = np.asarray(lights, np.float64).reshape(-1, 9)
+    out = (lt_light * arr.shape[0])()
+    for i, row in enumerate(arr):
+        out[i].type = int(row[0])
+        out[i].pos[0], out[i].pos[1], out[i].pos[2] = float(row[1]), float(row[2]), float(row[3])
+        out[i].yaw, out[i].pitch, out[i].p_int = float(row[4]), float(row[5]), float(row[6])
+        out[i].theta_in, out[i].theta_out = float(row[7]), float(row[8])
+    return out
+
+
+class Tracer:
+    """One library context on one CUDA device and stream.
+
+    Methods map one to one onto the C ABI; see include/lt.h for semantics."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.lib = load_library()
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream(device).cuda_stream
+        h = ctypes.c_void_p()
+        rc = self.lib.lt_create(ctypes.byref(h), device, ctypes.c_void_p(stream))
+        if rc != LT_OK:
+            raise LtError(rc, "lt_create failed")
+        self.h = h
+        self.device = device
+        self.n_texels = 0
+        self.n_lights = 0
+
+    def _check(self, rc):
+        if rc != LT_OK:
+            msg = self.lib.lt_last_error(self.h)
+            raise LtError(rc, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.lt_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        self._check(self.lib.lt_set_stream(self.h, ctypes.c_void_p(stream)))
+
+    def upload_scene(self, scene) -> int:
+        xyz = np.ascontiguousarray(scene.xyz, np.float32)
+        uv = np.ascontiguousarray(scene.uv, np.float32)
+        tile = np.ascontiguousarray(scene.tile, np.int32)
+        alb = np.ascontiguousarray(scene.albedo, np.float32)
+        res = np.ascontiguousarray(scene.tile_res, np.int32)
+        area = np.ascontiguousarray(scene.tile_area, np.float64)
+        n = ctypes.c_int64()
+        self._check(self.lib.lt_upload_scene(self.h, _ptr(xyz)[0], _ptr(uv)[0], _ptr(tile)[0], _ptr(alb)[0],
+                                             xyz.shape[0], _ptr(res)[0], _ptr(area)[0], res.shape[0],
+                                             ctypes.byref(n)))
+        self.n_texels = int(n.value)
+        return self.n_texels
+
+    def set_target(self, E_target, alpha=None):
+        e, dev = _ptr(E_target)
+        a = _ptr(alpha)[0] if alpha is not None else None
+        self._check(self.lib.lt_set_target(self.h, e, a, dev))
+
+    def set_lights(self, lights):
+        arr = lights_to_struct(lights)
+        self._check(self.lib.lt_set_lights(self.h, arr, len(arr)))
+        self.n_lights = len(arr)
+
+    def trace_forward(self, seed: int, n_photons: int, max_hits: int, begin: int = 0, end: int | None = None):
+        end = n_photons if end is None else end
+        self._check(self.lib.lt_trace_forward(self.h, seed, n_photons, max_hits, begin, end))
+
+    def texel_accumulator(self):
+        """(device pointer, scale) of the int64 texel accumulator."""
+        p = ctypes.c_void_p()
+        s = ctypes.c_double()
+        self._check(self.lib.lt_texel_accumulator(self.h, ctypes.byref(p), ctypes.byref(s)))
+        return p.value, s.value
+
+    def texel_sums(self, out=None):
+        """The int64 fixed-point texel accumulator (numpy, or into `out`)."""
+        if out is None:
+            out = np.empty(self.n_texels, np.int64)
+        p, dev = _ptr(out)
+        self._check(self.lib.lt_get_texel_sums(self.h, p, dev))
+        return out
+
+    def loss(self, out=None) -> float | None:
+        """Eq. 6 objective. Returns it as a float, or writes it into `out` (a
+        1-element float64 device tensor) without synchronising."""
+        if out is None:
+            v = ctypes.c_double()
+            self._check(self.lib.lt_loss(self.h, ctypes.cast(ctypes.byref(v), ctypes.c_void_p), 0))
+            return v.value
+        p, dev = _ptr(out)
+        self._check(self.lib.lt_loss(self.h, p, dev))
+        return None
+
+    def irradiance(self, out=None):
+        if out is None:
+            out = np.empty(self.n_texels, np.float32)
+        p, dev = _ptr(out)
+        self._check(self.lib.lt_get_irradiance(self.h, p, dev))
+        return out
+
+    def texel_areas(self, out=None):
+        if out is None:
+            out = np.empty(self.n_texels, np.float32)
+        p, dev = _ptr(out)
+        self._check(self.lib.lt_texel_areas(self.h, p, dev))
+        return out
+
+    def set_adjoint_weights(self, w):
+        p, dev = _ptr(w)
+        self._check(self.lib.lt_set_adjoint_weights(self.h, p, dev))
+
+    def trace_adjoint(self, seed: int, n_photons: int, max_hits: int, begin: int = 0, end: int | None = None,
+                      out=None):
+        """dO/dp as float64 [n_lights, 8] (numpy, or into `out`)."""
+        end = n_photons if end is None else end
+        if out is None:
+            out = np.zeros((self.n_lights, GRAD_N), np.float64)
+        p, dev = _ptr(out)
+        self._check(self.lib.lt_trace_adjoint(self.h, seed, n_photons, max_hits, begin, end, p, dev))
+        return out
+
+    def debug_paths(self, seed: int, n_photons: int, max_hits: int, begin: int, count: int, grads: bool = False):
+        """Per-photon record: (triangle [count, hits], texel [count, hits]) and,
+        with grads=True, each photon's gradient term [count, 8]."""
+        tri = np.empty((count, max_hits), np.int32)
+        tex = np.empty((count, max_hits), np.int64)
+        g = np.empty((count, GRAD_N), np.float64) if grads else None
+        self._check(self.lib.lt_debug_paths(self.h, seed, n_photons, max_hits, begin, count, _ptr(tri)[0],
+                                            _ptr(tex)[0], _ptr(g)[0] if grads else None))
+        return (tri, tex, g) if grads else (tri, tex)
+
+    def stats(self) -> dict:
+        s = lt_stats()
+        self._check(self.lib.lt_get_stats(self.h, ctypes.byref(s)))
+        return {name: getattr(s, name) for name, _ in s._fields_}
+
+    def set_launch(self, threads_per_block: int = 0, blocks_per_sm: int = 0, smem_node_bytes: int = 0):
+        self._check(self.lib.lt_set_launch(self.h, threads_per_block, blocks_per_sm, smem_node_bytes))

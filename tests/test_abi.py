@@ -1,0 +1,43 @@
+"""The C-ABI library builds, loads and exports every function include/lt.h
+declares (no compute calls: this runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2310_02043_gb300 import _build, lighttrace
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared(header):
+    src = open(os.path.join(ROOT, "include", header)).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lt_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return lighttrace.load_library()
+
+
+def test_every_declared_function_is_exported(lib):
+    names = _declared("lt.h")
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(lighttrace.EXPORTED) <= set(names)
+
+
+def test_version_and_argument_checks(lib):
+    assert lib.lt_version() == 1
+    assert lib.lt_create(None, 0, None) == lighttrace.LT_ERR_ARG
+    assert lib.lt_destroy(None) == lighttrace.LT_OK
+    assert lib.lt_last_error(None) == b"null context"
+
+
+def test_struct_layouts_match_the_header():
+    assert ctypes.sizeof(lighttrace.lt_light) == 36
+    assert ctypes.sizeof(lighttrace.lt_stats) == 8 * 5 + 4 * 4 + 8

@@ -1,0 +1,85 @@
+"""The full-size office workload (2^24 photons, 5 hits, 16 spots, 2 cm texels)
+in the launch shape the benchmark uses.
+
+The oracle cannot trace 84M segments by brute force in a test, so:
+  * properties that hold at any size: the closed room makes exactly
+    n_photons * hits segments; the integer texel sums of the full range equal
+    the sum of the sums of any partition of it, bit for bit; the gradient of
+    the full range equals the sum over the partition;
+  * photon ranges the oracle can trace, sampled across the whole budget
+    (irradiance aggregate, gradient from injected weights, per-photon paths).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_02043_gb300 import _build, scenes
+from paper_2310_02043_gb300.lighttrace import Tracer
+
+pytestmark = pytest.mark.gpu
+
+N, HITS, SEED = 1 << 24, 5, 2
+
+
+@pytest.fixture(scope="module")
+def office():
+    _build.build()
+    sc, L = scenes.office(seed=0, pitch=0.02), scenes.office_lights(0)
+    tr = Tracer(0)
+    tr.upload_scene(sc)
+    tr.set_lights(L)
+    yield tr, sc, L
+    tr.close()
+
+
+def test_full_range_segments_and_partition(office):
+    tr, sc, L = office
+    tr.trace_forward(SEED, N, HITS)
+    st = tr.stats()
+    assert st["segments_forward"] == N * HITS
+    q_full = tr.texel_sums()
+    cuts = [0, 1 << 20, 5_000_003, (1 << 24) - 777, N]
+    acc = np.zeros_like(q_full)
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        tr.trace_forward(SEED, N, HITS, a, b)
+        acc += tr.texel_sums()
+    assert np.array_equal(acc, q_full)
+
+
+@pytest.mark.parametrize("begin", [0, (1 << 23) + 12_345, N - 16_384])
+def test_sampled_ranges_match_oracle(office, begin):
+    tr, sc, L = office
+    count = 16_384
+    tr.trace_forward(SEED, N, HITS, begin, begin + count)
+    E = tr.irradiance().astype(np.float64)
+    ref = oracle.forward(sc, L, SEED, N, HITS, begin=begin, end=begin + count)
+    A = oracle.texel_areas(sc)
+    tot, tot_ref = np.sum(A * E), np.sum(A * ref["E"])
+    assert abs(tot - tot_ref) <= 1e-4 * tot_ref
+    tri, tex = tr.debug_paths(SEED, N, HITS, begin, 4096)
+    tri_o, tex_o = oracle.paths(sc, L, SEED, N, HITS, begin, 4096)
+    same = np.all(tri == tri_o, axis=1) & np.all(tex == tex_o, axis=1)
+    assert same.mean() >= 0.999
+
+
+def test_gradient_partition_and_sampled_range(office):
+    tr, sc, L = office
+    w = scenes.random_weights(sc.n_texels, seed=11, scale=1e-3)
+    tr.set_adjoint_weights(w)
+    g_full = tr.trace_adjoint(SEED, N, HITS)
+    cuts = [0, 3_000_001, 9_999_999, N]
+    g_sum = sum(tr.trace_adjoint(SEED, N, HITS, a, b) for a, b in zip(cuts[:-1], cuts[1:]))
+    assert np.allclose(g_sum, g_full, rtol=1e-9, atol=1e-9 * np.abs(g_full).max())
+    begin, count = (1 << 22) + 99, 8192
+    g = tr.trace_adjoint(SEED, N, HITS, begin, begin + count)
+    g_ref, _ = oracle.adjoint(sc, L, SEED, N, HITS, w.astype(np.float64), begin=begin, end=begin + count)
+    tri, tex, c = tr.debug_paths(SEED, N, HITS, begin, count, grads=True)
+    tri_o, tex_o, c_o = oracle.paths(sc, L, SEED, N, HITS, begin, count, w=w.astype(np.float64))
+    same = np.all(tri == tri_o, axis=1) & np.all(tex == tex_o, axis=1)
+    assert same.mean() >= 0.999
+    sizes = np.full(L.shape[0], N // L.shape[0])
+    lights = np.searchsorted(np.cumsum(sizes), np.arange(begin, begin + count), side="right")
+    corr = np.zeros_like(g)
+    np.add.at(corr, lights[~same], c[~same] - c_o[~same])
+    den = np.maximum(np.abs(g_ref), 1e-3 * np.abs(g_ref).max())
+    assert np.all(np.abs(g - corr - g_ref) / den <= 1e-3)

@@ -1,0 +1,262 @@
+"""GPU path vs the CPU oracle on the same seeded inputs (calls go through the C ABI).
+
+Tolerances (the path computes in FP32, the oracle in FP64; both take the
+hit/texel decisions in float, so a small fraction of paths can still part
+ways near triangle or texel edges):
+  * irradiance: sum_t A_t E_t to 1e-4 relative; E_t to 1e-3 relative on every
+    texel that received at least 1e3 deposits;
+  * objective O to 1e-4 relative;
+  * gradients: every component to 1e-3 relative, against
+    max(|g_oracle|, 1e-3 max|g_oracle|);
+  * fixed-point texel sums are bit-identical across launch shapes and reruns.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_02043_gb300 import _build, scenes
+from paper_2310_02043_gb300.lighttrace import LtError, Tracer
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tr():
+    _build.build()
+    t = Tracer(0)
+    yield t
+    t.close()
+
+
+def _forward(tr, sc, lights, seed, n, hits, begin=0, end=None):
+    tr.upload_scene(sc)
+    tr.set_lights(lights)
+    tr.trace_forward(seed, n, hits, begin, n if end is None else end)
+    return tr.irradiance().astype(np.float64), tr.stats()
+
+
+def _check_irradiance(sc, E, ref, min_count=1000):
+    A = oracle.texel_areas(sc)
+    tot, tot_ref = np.sum(A * E), np.sum(A * ref["E"])
+    assert abs(tot - tot_ref) <= 1e-4 * tot_ref, (tot, tot_ref)
+    m = ref["count"] >= min_count
+    rel = np.abs(E[m] - ref["E"][m]) / ref["E"][m]
+    bad = np.nonzero(rel > 1e-3)[0]
+    assert len(bad) == 0, f"{len(bad)} of {m.sum()} texels beyond 1e-3 (worst {rel.max():.3g})"
+    return int(m.sum())
+
+
+def _light_of_photons(n, n_lights, begin, count):
+    """Light of each photon: the budget is split evenly, the first n mod L
+    lights taking one extra photon (the contract of lt_trace_forward)."""
+    sizes = np.full(n_lights, n // n_lights) + (np.arange(n_lights) < n % n_lights)
+    ends = np.cumsum(sizes)
+    return np.searchsorted(ends, np.arange(begin, begin + count), side="right")
+
+
+def _check_grad(tr, sc, L, seed, n, hits, w, g, g_ref, rtol=1e-3, max_diverged=1e-3):
+    """Gradients agree to rtol (per component, against max(|g_ref|, rtol *
+    max|g_ref|)) once the photons whose paths parted ways between the float
+    GPU path and the double oracle are set aside; those must be rare and the
+    paths that agree must carry the same per-photon terms."""
+    tri, tex, c = tr.debug_paths(seed, n, hits, 0, n, grads=True)
+    tri_o, tex_o, c_o = oracle.paths(sc, L, seed, n, hits, 0, n, w=w)
+    same = np.all(tri == tri_o, axis=1) & np.all(tex == tex_o, axis=1)
+    assert 1.0 - same.mean() <= max_diverged, 1.0 - same.mean()
+    # Per-photon terms on agreeing paths: float rounding is amplified where
+    # the first hit is grazing (the 1/cos of Eq. 14), so single terms get 1e-2
+    # and the bulk (99.9 %) must sit within 1e-3.
+    col = np.maximum(np.abs(c_o).max(axis=0), 1e-300)
+    diff = np.abs(c[same] - c_o[same]) / np.maximum(np.abs(c_o[same]), 1e-4 * col)
+    assert np.all(diff <= 1e-2), f"per-photon terms differ: worst {diff.max():.3g}"
+    assert np.quantile(diff.max(axis=1), 0.999) <= 1e-3
+    lights = _light_of_photons(n, L.shape[0], 0, n)
+    # the aggregate kernel sums the same per-photon terms
+    g_sum = np.zeros_like(g)
+    np.add.at(g_sum, lights, c)
+    assert np.all(np.abs(g - g_sum) <= 1e-6 * np.maximum(np.abs(g_sum), np.abs(g_sum).max()))
+    corr = np.zeros_like(g)
+    np.add.at(corr, lights[~same], c[~same] - c_o[~same])
+    g, g_ref = np.asarray(g), np.asarray(g_ref)
+    den = np.maximum(np.abs(g_ref), rtol * np.max(np.abs(g_ref)))
+    rel = np.abs(g - corr - g_ref) / den
+    assert np.all(rel <= rtol), f"worst {rel.max():.3g} at {np.unravel_index(np.argmax(rel), rel.shape)}"
+    return 1.0 - same.mean()
+
+
+def test_cornell_forward_matches_oracle(tr):
+    sc, L = scenes.cornell_box(res=32), scenes.cornell_lights()
+    n, hits, seed = 1 << 20, 3, 2
+    E, st = _forward(tr, sc, L, seed, n, hits)
+    ref = oracle.forward(sc, L, seed, n, hits, counts=True)
+    assert _check_irradiance(sc, E, ref) > 100
+    assert abs(st["segments_forward"] - ref["segments"]) <= 1e-4 * ref["segments"]
+
+
+def test_cornell_paths_match_oracle(tr):
+    sc, L = scenes.cornell_box(res=32), scenes.cornell_lights()
+    n, hits, seed = 1 << 20, 3, 2
+    tr.upload_scene(sc)
+    tr.set_lights(L)
+    tri, tex = tr.debug_paths(seed, n, hits, 1000, 20000)
+    tri_o, tex_o = oracle.paths(sc, L, seed, n, hits, 1000, 20000)
+    same = np.all(tri == tri_o, axis=1) & np.all(tex == tex_o, axis=1)
+    assert same.mean() >= 0.999, same.mean()
+
+
+def test_office_forward_matches_oracle(tr):
+    sc, L = scenes.office(seed=0, pitch=0.1), scenes.office_lights(0)
+    n, hits, seed = 1 << 17, 5, 3
+    E, st = _forward(tr, sc, L, seed, n, hits)
+    ref = oracle.forward(sc, L, seed, n, hits, counts=True)
+    _check_irradiance(sc, E, ref, min_count=1000)
+    # closed room: every photon makes exactly `hits` segments
+    assert st["segments_forward"] == n * hits == ref["segments"]
+
+
+def test_ragged_range_and_mixed_lights(tr):
+    sc = scenes.cornell_box(res=16)
+    L = scenes.make_lights([scenes.point_light((0.5, 0.5, 0.9), 1.0),
+                            scenes.spot_light((0.3, 0.3, 0.95), 0.3, -1.4, 2.0, 0.0, 0.7),
+                            scenes.spot_light((0.7, 0.6, 0.9), 2.0, -1.2, 1.5, 0.3, 0.5)])
+    n, hits, seed, b, e = 100_003, 2, 7, 37, 90_001
+    E, st = _forward(tr, sc, L, seed, n, hits, b, e)
+    ref = oracle.forward(sc, L, seed, n, hits, begin=b, end=e, counts=True)
+    _check_irradiance(sc, E, ref, min_count=1000)
+    assert st["photons_forward"] == e - b
+
+
+def test_empty_range_and_dark_light(tr):
+    sc = scenes.cornell_box(res=8)
+    L = scenes.make_lights([scenes.point_light((0.5, 0.5, 0.9), 1.0), scenes.point_light((0.2, 0.2, 0.5), 0.0)])
+    E, st = _forward(tr, sc, L, 1, 5000, 3, 2000, 2000)
+    assert np.all(E == 0) and st["segments_forward"] == 0
+    # the dark light (p_int = 0) deposits nothing; the other light is unchanged
+    E, st = _forward(tr, sc, L, 1, 5000, 3)
+    ref = oracle.forward(sc, L, 1, 5000, 3, counts=True)
+    A = oracle.texel_areas(sc)
+    assert abs(np.sum(A * E) - np.sum(A * ref["E"])) <= 1e-4 * np.sum(A * ref["E"])
+
+
+def test_all_photons_escape(tr):
+    sc = scenes.plane(half=1.0, res=4)
+    L = scenes.make_lights([scenes.spot_light((0.0, 0.0, 1.0), 0.0, 1.2, 1.0, 0.2, 0.4)])  # points up
+    E, st = _forward(tr, sc, L, 1, 4096, 3)
+    assert np.all(E == 0) and st["segments_forward"] == 4096
+
+
+def test_fixed_point_sums_identical_across_launch_shapes(tr):
+    sc, L = scenes.office(seed=0, pitch=0.1), scenes.office_lights(0)
+    tr.upload_scene(sc)
+    tr.set_lights(L)
+    ref = None
+    for threads, bps, smem in [(256, 0, 48 * 1024), (128, 0, 224), (64, 1, 16 * 1024), (256, 2, 100 * 1024),
+                               (32, 3, 224 * 7)]:
+        tr.set_launch(threads, bps, smem)
+        tr.trace_forward(5, 1 << 16, 5)
+        q = tr.texel_sums()
+        if ref is None:
+            ref = q
+            assert q.sum() > 0
+        else:
+            assert np.array_equal(q, ref), (threads, bps, smem)
+    tr.set_launch(256, 0, 48 * 1024)
+    tr.trace_forward(5, 1 << 16, 5)
+    assert np.array_equal(tr.texel_sums(), ref)
+
+
+def _cornell_target(sc, lights):
+    Lt = scenes.perturb_lights(lights, seed=1, pos_sigma=0.05)
+    return oracle.forward(sc, Lt, 101, 1 << 16, 3)["E"].astype(np.float32)
+
+
+def test_loss_matches_oracle(tr):
+    sc, L = scenes.cornell_box(res=32), scenes.cornell_lights()
+    target = _cornell_target(sc, L)
+    alpha = np.random.default_rng(3).uniform(0.5, 1.5, sc.n_texels).astype(np.float32)
+    n, hits, seed = 1 << 20, 3, 2
+    tr.upload_scene(sc)
+    tr.set_lights(L)
+    tr.set_target(target, alpha)
+    tr.trace_forward(seed, n, hits)
+    O = tr.loss()
+    ref = oracle.forward(sc, L, seed, n, hits)
+    O_ref, _ = oracle.loss(sc, ref["E"], target, alpha)
+    assert abs(O - O_ref) <= 1e-4 * O_ref, (O, O_ref)
+
+
+def _adjoint_case(tr, sc, L, target, n, hits, seed):
+    """GPU forward + loss + adjoint as a user runs them, then the same adjoint
+    on both sides from identical weights (the oracle's, rounded to float)."""
+    tr.upload_scene(sc)
+    tr.set_lights(L)
+    tr.set_target(target)
+    tr.trace_forward(seed, n, hits)
+    tr.loss()
+    g_own = tr.trace_adjoint(seed, n, hits)
+    assert np.array_equal(g_own, tr.trace_adjoint(seed, n, hits))     # deterministic rerun
+    ref = oracle.forward(sc, L, seed, n, hits)
+    _, w = oracle.loss(sc, ref["E"], target, np.ones(sc.n_texels))
+    w32 = w.astype(np.float32)
+    tr.set_adjoint_weights(w32)
+    g = tr.trace_adjoint(seed, n, hits)
+    g_ref, _ = oracle.adjoint(sc, L, seed, n, hits, w32.astype(np.float64))
+    _check_grad(tr, sc, L, seed, n, hits, w32.astype(np.float64), g, g_ref)
+    # with its own weights the GPU gradient still tracks the oracle's
+    assert np.abs(g_own - g_ref).max() <= 1e-2 * np.abs(g_ref).max()
+    return g
+
+
+def test_adjoint_matches_oracle_cornell_point(tr):
+    sc, L = scenes.cornell_box(res=32), scenes.cornell_lights()
+    g = _adjoint_case(tr, sc, L, _cornell_target(sc, L), 1 << 18, 3, 2)
+    assert np.all(g[:, [3, 4, 6, 7]] == 0)
+
+
+def test_adjoint_matches_oracle_office_spots(tr):
+    sc, L = scenes.office(seed=0, pitch=0.1), scenes.office_lights(0)
+    Lt = scenes.perturb_lights(L, seed=2, pos_sigma=0.3, angle_sigma=0.1, intensity_range=(0.7, 1.3),
+                               theta_in_delta=np.radians(5))
+    target = oracle.forward(sc, Lt, 77, 1 << 16, 5)["E"].astype(np.float32)
+    g = _adjoint_case(tr, sc, L, target, 1 << 16, 5, 4)
+    assert np.all(np.abs(g) > 0)
+
+
+def test_adjoint_with_injected_weights(tr):
+    sc = scenes.cornell_box(res=16)
+    L = scenes.make_lights([scenes.spot_light((0.45, 0.5, 0.92), 0.3, -1.35, 1.0, 0.45, 0.9),
+                            scenes.point_light((0.2, 0.7, 0.5), 0.5)])
+    w = scenes.random_weights(sc.n_texels, seed=5)
+    n, hits, seed = 100_000, 3, 9
+    tr.upload_scene(sc)
+    tr.set_lights(L)
+    tr.set_adjoint_weights(w)
+    g = tr.trace_adjoint(seed, n, hits)
+    g_ref, _ = oracle.adjoint(sc, L, seed, n, hits, w.astype(np.float64))
+    _check_grad(tr, sc, L, seed, n, hits, w.astype(np.float64), g, g_ref)
+
+
+def test_call_order_and_argument_errors():
+    t = Tracer(0)
+    try:
+        with pytest.raises(LtError):
+            t.trace_forward(1, 100, 3)               # no scene
+        t.upload_scene(scenes.cornell_box(res=4))
+        with pytest.raises(LtError):
+            t.trace_forward(1, 100, 3)               # no lights
+        t.set_lights(scenes.cornell_lights())
+        with pytest.raises(LtError):
+            t.trace_forward(1, 100, 0)               # max_hits out of range
+        with pytest.raises(LtError):
+            t.trace_forward(1, 100, 3, 50, 101)      # range beyond the budget
+        with pytest.raises(LtError):
+            t.loss()                                 # no forward pass
+        t.trace_forward(1, 100, 3)
+        with pytest.raises(LtError):
+            t.loss()                                 # no target
+        with pytest.raises(LtError):
+            t.trace_adjoint(1, 100, 3)               # no weights
+        with pytest.raises(LtError):
+            t.set_lights(scenes.make_lights([scenes.spot_light((0, 0, 0), 0, 0, 1, 0.5, 0.5)]))  # empty soft edge
+    finally:
+        t.close()
