@@ -1,0 +1,466 @@
+"""Benchmark of forward + adjoint light tracing on the procedural office.
+
+One step = one optimisation iteration's hot path: upload the 16 spot lights,
+forward pass (2^24 photons, 5 hits), objective + adjoint weights, adjoint
+pass (decorrelated seed), gradient. Metric: Msegments/s of forward + adjoint
+(a segment is one traced ray, emission or bounce, hit or miss).
+
+  value   device time (CUDA events on the library's stream) of the step's
+          kernels with every input already resident in HBM; the L2 cache is
+          flushed (256 MiB write) between steps, outside the timed events.
+  e2e     the same metric through the C ABI with host buffers: per step the
+          light parameters go host->device, the loss and gradient come back
+          device->host, and an Adam update runs on the host.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun): each rank traces its own 2^24 photons (weak scaling); the
+integer texel sums and the gradients are summed across ranks with NCCL.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2310_02043_gb300 import scenes  # noqa: E402
+
+METRIC = "Msegments/s fwd+adjoint"
+PHOTONS, HITS = 1 << 24, 5
+TARGET_PHOTONS = 1 << 26
+KERNELS_PER_STEP = 5          # forward, loss, loss reduction, adjoint, gradient reduction
+LIGHT_DEV_BYTES = 112         # device light record the library uploads per light
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "trace_kernel_traffic.json")
+
+
+def workload():
+    sc = scenes.office(seed=0, pitch=0.02)
+    lights = scenes.office_lights(0)
+    truth = scenes.perturb_lights(lights, seed=1, pos_sigma=0.3, angle_sigma=0.1, intensity_range=(0.7, 1.3),
+                                  theta_in_delta=np.radians(5.0))
+    return sc, lights, truth
+
+
+def config_of(sc, lights, n_gpus):
+    return {"workload": f"procedural office 20x10x3 m, 200 desks/cabinets ({sc.n_tri} tris), {sc.n_texels} texels "
+                        f"at 2 cm, {lights.shape[0]} spots, 2^24 photons/GPU, 5 hits, target traced at 2^26",
+            "triangles": sc.n_tri, "texels": sc.n_texels, "lights": int(lights.shape[0]), "photons_per_gpu": PHOTONS,
+            "hits": HITS, "l2": "flushed between steps (256 MiB write outside the timed events)",
+            "parallelism": f"photon shards x{n_gpus}" if n_gpus > 1 else "single GPU"}
+
+
+# ---------------------------------------------------------------------------
+# Clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device_index = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device_index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# Roofline helpers
+# ---------------------------------------------------------------------------
+# Algorithmic FP32 operations of the traversal (counted from the method, not
+# from the compiled code): a node visit tests 8 child boxes, each 6 plane
+# subtractions, 6 multiplications by the inverse direction, 10 min/max to
+# form and combine the slab intervals, 1 scale and 2 comparisons (25 ops);
+# a watertight ray/triangle test is 9 subtractions, 12 shear operations,
+# 9 edge-function operations, 2 additions for the determinant, 8 for the
+# distance and 6 sign tests (46 ops); every segment also samples a direction
+# and a flux (about 40 ops) and computes the hit's texel and normal (about 40).
+OPS_PER_NODE = 8 * 25
+OPS_PER_TRI = 46
+OPS_PER_SEGMENT = 80
+
+
+def alu_peak_tflops(sm_mhz):
+    """FP32 issue peak: 152 SMs x 128 FP32 lanes x one operation per lane per
+    clock (an FMA counts as one operation, as in OPS_PER_*)."""
+    return 152 * 128 * sm_mhz * 1e6 / 1e12
+
+
+def kernel_hash():
+    src = os.path.join(ROOT, "paper_2310_02043_gb300", "csrc", "lt_kernels.cu")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def stored_traffic(kernel):
+    """DRAM bytes per segment from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    try:
+        d = json.load(open(TRAFFIC_FILE))
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_source_sha256_16") != kernel_hash():
+        return None
+    return d.get(kernel, {}).get("dram_bytes_per_segment")
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle on the host cores, a bounded sample of the workload
+# ---------------------------------------------------------------------------
+def cpu_baseline(sc, lights, truth, budget_s=15.0):
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    small = 1 << 12
+    target = oracle.forward(sc, truth, 77, small * 4, HITS)["E"]
+    t0 = time.perf_counter()
+    oracle.forward(sc, lights, 2, PHOTONS, HITS, begin=0, end=small)
+    probe = time.perf_counter() - t0
+    n = int(min(1 << 20, max(small, small * budget_s / 2.0 / max(probe, 1e-3))))
+    n = max(small, (n // 4096) * 4096)
+    t0 = time.perf_counter()
+    f = oracle.forward(sc, lights, 2, PHOTONS, HITS, begin=0, end=n)
+    t1 = time.perf_counter()
+    _, w = oracle.loss(sc, f["E"], target, np.ones(sc.n_texels))
+    t2 = time.perf_counter()
+    _, seg_adj = oracle.adjoint(sc, lights, 3, PHOTONS, HITS, w, begin=0, end=n)
+    t3 = time.perf_counter()
+    segs = f["segments"] + seg_adj
+    return {"value": segs / (t3 - t0) / 1e6, "unit": "Msegments/s", "cores": cores, "kind": "oracle",
+            "sample": f"photons [0, {n}) of the 2^24 budget, forward + loss + adjoint, brute-force FP64 oracle "
+                      f"({segs} segments in {t3 - t0:.1f} s: forward {t1 - t0:.1f} s, adjoint {t3 - t2:.1f} s)"}
+
+
+def run_reference(args):
+    """Reference arm: the oracle as it stands on the host cores, same metric."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sc, lights, truth = workload()
+    import oracle
+    oracle.build()
+    small = 1 << 12
+    target = oracle.forward(sc, truth, 77, small * 4, HITS)["E"]
+    n = 1 << 13
+    for _ in range(args.warmup):
+        oracle.forward(sc, lights, 2, PHOTONS, HITS, begin=0, end=small)
+    times, segs = [], 0
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        f = oracle.forward(sc, lights, 2 + k, PHOTONS, HITS, begin=0, end=n)
+        _, w = oracle.loss(sc, f["E"], target, np.ones(sc.n_texels))
+        _, sa = oracle.adjoint(sc, lights, 3 + k, PHOTONS, HITS, w, begin=0, end=n)
+        times.append(time.perf_counter() - t0)
+        segs += f["segments"] + sa
+    value = segs / sum(times) / 1e6
+    cores = os.cpu_count() or 1
+    line = {"metric": METRIC, "value": value, "unit": "Msegments/s", "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(sc, lights, args.gpus),
+            "cpu_baseline": {"value": value, "unit": "Msegments/s", "cores": cores, "kind": "oracle",
+                             "sample": f"each step: photons [0, {n}) of the 2^24 budget, forward + loss + adjoint"},
+            "e2e": {"value": value, "unit": "Msegments/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+class Adam:
+    """Adam (Kingma and Ba; beta1 0.9, beta2 0.999) on the light parameters."""
+
+    def __init__(self, lr, b1=0.9, b2=0.999, eps=1e-8):
+        self.lr, self.b1, self.b2, self.eps = lr, b1, b2, eps
+        self.m = self.v = None
+        self.t = 0
+
+    def step(self, x, g):
+        if self.m is None:
+            self.m, self.v = np.zeros_like(g), np.zeros_like(g)
+        self.t += 1
+        self.m = self.b1 * self.m + (1 - self.b1) * g
+        self.v = self.b2 * self.v + (1 - self.b2) * g * g
+        mh = self.m / (1 - self.b1 ** self.t)
+        vh = self.v / (1 - self.b2 ** self.t)
+        return x - self.lr * mh / (np.sqrt(vh) + self.eps)
+
+
+def apply_update(lights, grad, opt):
+    """Adam step on [x, y, z, yaw, pitch, p_int, theta_in] of every spot
+    (theta_out stays fixed); keeps 0 <= theta_in < theta_out."""
+    x = lights[:, 1:8].copy()
+    x = opt.step(x, grad[:, 0:7])
+    out = lights.copy()
+    out[:, 1:8] = x
+    out[:, 7] = np.clip(out[:, 7], 0.0, out[:, 8] - 1e-3)
+    return out
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2310_02043_gb300.lighttrace import Tracer
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    sc, lights, truth = workload()
+    tr = Tracer(local, stream.cuda_stream)
+    T = tr.upload_scene(sc)
+
+    # Target: traced from the perturbed ("ground-truth") lights at 2^26 photons.
+    tr.set_lights(truth)
+    tr.trace_forward(77, TARGET_PHOTONS, HITS)
+    target = torch.empty(T, dtype=torch.float32, device="cuda")
+    tr.irradiance(out=target)
+    tr.set_target(target)
+    tr.set_lights(lights)
+
+    # Work accounting (untimed): node visits and triangle tests per segment.
+    work = tr.count_work(5, PHOTONS, HITS)
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    grad_dev = torch.zeros((lights.shape[0], 8), dtype=torch.float64, device="cuda")
+    loss_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+    q_view = None
+    if world > 1:
+        ptr, _ = tr.texel_accumulator()
+
+        class _View:
+            __cuda_array_interface__ = {"shape": (T,), "typestr": "<i8", "data": (ptr, False), "version": 3}
+
+        q_view = torch.as_tensor(_View(), device="cuda")
+
+    def step(k, grad_out, loss_out):
+        # Every rank traces its own photon budget; with several ranks the
+        # integer texel sums are added across ranks before the objective.
+        seed = 1000 + 7919 * k + 104729 * rank
+        tr.trace_forward(seed, PHOTONS, HITS)
+        if q_view is not None:
+            dist.all_reduce(q_view)
+        tr.loss(out=loss_out)
+        tr.trace_adjoint(seed + 1, PHOTONS, HITS, out=grad_out)
+        if world > 1:
+            dist.all_reduce(grad_out)
+
+    for k in range(args.warmup):
+        step(k, grad_dev, loss_dev)
+    torch.cuda.synchronize()
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    props = torch.cuda.get_device_properties(local)
+    uuid = getattr(props, "uuid", None)
+    sampler = ClockSampler(f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else (uuid or local))
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    seg_f = seg_a = 0
+    for k in range(args.steps):
+        flush.zero_()
+        e = ev[k]
+        e[0].record(stream)
+        tr.trace_forward(1000 + 7919 * (k + 50) + 104729 * rank, PHOTONS, HITS)
+        e[1].record(stream)
+        if q_view is not None:
+            dist.all_reduce(q_view)
+        tr.loss(out=loss_dev)
+        e[2].record(stream)
+        tr.trace_adjoint(1 + 1000 + 7919 * (k + 50) + 104729 * rank, PHOTONS, HITS, out=grad_dev)
+        if world > 1:
+            dist.all_reduce(grad_dev)
+        e[3].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    st = tr.stats()
+    seg_f, seg_a = st["segments_forward"], st["segments_adjoint"]
+    t_step = [ev[k][0].elapsed_time(ev[k][3]) for k in range(args.steps)]
+    t_fwd = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
+    t_adj = [ev[k][2].elapsed_time(ev[k][3]) for k in range(args.steps)]
+    total_ms = sum(t_step)
+    if world > 1:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    segs_per_step_all = (seg_f + seg_a) * world
+    value = segs_per_step_all * args.steps / (total_ms / 1e3) / 1e6
+
+    # End to end through the C ABI with host buffers and a host Adam update.
+    pinned = torch.empty((lights.shape[0], 9), dtype=torch.float64).pin_memory()
+    pinned.copy_(torch.from_numpy(lights))
+    grad_host = np.zeros((lights.shape[0], 8), np.float64)
+    opt = Adam(lr=0.01)
+    cur = lights.copy()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        tr.set_lights(pinned.numpy())
+        seed = 5000 + 7919 * k + 104729 * rank
+        tr.trace_forward(seed, PHOTONS, HITS)
+        if q_view is not None:
+            dist.all_reduce(q_view)
+        loss_host = tr.loss()
+        tr.trace_adjoint(seed + 1, PHOTONS, HITS, out=grad_host)
+        if world > 1:
+            gd = torch.from_numpy(grad_host).cuda()
+            dist.all_reduce(gd)
+            grad_host[:] = gd.cpu().numpy()
+        cur = apply_update(cur, grad_host, opt)
+        pinned.copy_(torch.from_numpy(cur))
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e_value = segs_per_step_all * args.steps / e2e_s / 1e6
+    h2d = LIGHT_DEV_BYTES * lights.shape[0]
+    d2h = 8 + 8 * 8 * lights.shape[0]
+
+    if rank != 0:
+        tr.close()
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # Roofline of the dominant kernel (forward and adjoint trace kernels take
+    # about equal time; the forward one is reported, its work counted exactly).
+    fwd_ms = statistics.mean(t_fwd)
+    adj_ms = statistics.mean(t_adj)
+    dom_ms, dom = (fwd_ms, "forward") if fwd_ms >= adj_ms else (adj_ms, "adjoint")
+    segs = work["segments"]
+    ops = work["node_visits"] * OPS_PER_NODE + work["tri_tests"] * OPS_PER_TRI + segs * OPS_PER_SEGMENT
+    achieved = ops / (dom_ms / 1e3) / 1e12
+    sm_mhz = clocks["sm_mhz"] if clocks else 1477.0
+    peak_clock = clocks["sm_max_mhz"] if clocks and clocks.get("sm_max_mhz") else 2070.0
+    peak = alu_peak_tflops(peak_clock)
+    traffic = stored_traffic(f"trace_kernel_{dom}")
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic * segs if traffic is not None else None,
+                "kernel": f"trace_kernel ({dom})",
+                "peak_basis": f"FP32 issue peak 152 SMs x 128 lanes x {peak_clock:.0f} MHz (derived, not measured)",
+                "work_per_segment": {"node_visits": work["node_visits"] / segs, "tri_tests": work["tri_tests"] / segs,
+                                     "fp32_ops": ops / segs},
+                "frac_at_sampled_clock": achieved / alu_peak_tflops(sm_mhz)}
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(sc, lights, truth)
+    line = {"metric": METRIC, "value": value, "unit": "Msegments/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_of(sc, lights, world),
+            "e2e": {"value": e2e_value, "unit": "Msegments/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_opt_iter": 1e3 * e2e_s / args.steps},
+            "gpu_launches": KERNELS_PER_STEP * args.steps,
+            "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+            "kernel_ms": {"forward": fwd_ms, "adjoint": adj_ms,
+                          "loss": statistics.mean(ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps))},
+            "segments_per_step": {"forward": seg_f, "adjoint": seg_a}}
+    print(json.dumps(line), flush=True)
+    tr.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_profile_case(args):
+    """One forward + loss + adjoint of the office at --photons (for ncu)."""
+    import torch
+    from paper_2310_02043_gb300.lighttrace import Tracer
+    torch.cuda.set_device(0)
+    sc, lights, _ = workload()
+    tr = Tracer(0)
+    T = tr.upload_scene(sc)
+    tr.set_target(np.zeros(T, np.float32))
+    tr.set_lights(lights)
+    tr.trace_forward(2, args.photons, HITS)
+    tr.loss()
+    tr.trace_adjoint(3, args.photons, HITS)
+    st = tr.stats()
+    tr.close()
+    print(json.dumps({"profile_case": True, "photons": args.photons, "segments_forward": st["segments_forward"],
+                      "segments_adjoint": st["segments_adjoint"]}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-only", action="store_true",
+                    help="run one forward + loss + adjoint at --photons and exit (for profilers)")
+    ap.add_argument("--photons", type=int, default=1 << 20)
+    args = ap.parse_args()
+    if args.profile_only:
+        run_profile_case(args)
+        return
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -27,6 +27,12 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#if defined(__GNUC__)
+#define LT_API __attribute__((visibility("default")))
+#else
+#define LT_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -85,14 +91,14 @@ typedef struct {
 } lt_stats;
 
 /* Library ABI version (this header: 1). */
-int lt_version(void);
+LT_API int lt_version(void);
 
 /* Create a context on CUDA device `device`; work goes to `cuda_stream`
  * (a cudaStream_t; NULL = the legacy default stream). */
-int lt_create(void **ctx_out, int device, void *cuda_stream);
-int lt_destroy(void *ctx);
-int lt_set_stream(void *ctx, void *cuda_stream);
-const char *lt_last_error(const void *ctx);
+LT_API int lt_create(void **ctx_out, int device, void *cuda_stream);
+LT_API int lt_destroy(void *ctx);
+LT_API int lt_set_stream(void *ctx, void *cuda_stream);
+LT_API const char *lt_last_error(const void *ctx);
 
 /* Upload a triangle scene (host arrays, copied) and build its wide BVH.
  *   tri_xyz    [n_tri][3][3] float   vertex positions
@@ -105,17 +111,17 @@ const char *lt_last_error(const void *ctx);
  * tile_area / (res_u res_v) (the box basis standing in for the per-vertex
  * hat basis of Eq. 4; mass-lumped projection, Eq. S.6). Writes the texel
  * count to *n_texels_out. Invalidates targets, weights and pass results. */
-int lt_upload_scene(void *ctx, const float *tri_xyz, const float *tri_uv, const int32_t *tri_tile,
+LT_API int lt_upload_scene(void *ctx, const float *tri_xyz, const float *tri_uv, const int32_t *tri_tile,
                     const float *tri_albedo, int32_t n_tri, const int32_t *tile_res, const double *tile_area,
                     int32_t n_tiles, int64_t *n_texels_out);
 
 /* Target irradiance E*_t and weights alpha_t of the objective (Eq. 6),
  * [n_texels] floats each; alpha may be NULL (all ones). */
-int lt_set_target(void *ctx, const float *E_target, const float *alpha, int is_device);
+LT_API int lt_set_target(void *ctx, const float *E_target, const float *alpha, int is_device);
 
 /* Luminaires, host array of n_lights (1..LT_MAX_LIGHTS), copied. */
 #define LT_MAX_LIGHTS 1024
-int lt_set_lights(void *ctx, const lt_light *lights, int32_t n_lights);
+LT_API int lt_set_lights(void *ctx, const lt_light *lights, int32_t n_lights);
 
 /* Forward pass (Alg. 1): photons [photon_begin, photon_end) of a budget of
  * n_photons split evenly over the lights (light l owns a contiguous range;
@@ -127,32 +133,32 @@ int lt_set_lights(void *ctx, const lt_light *lights, int32_t n_lights);
  * (seed lo, seed hi). Clears and then fills the texel accumulator, a
  * [n_texels] int64 fixed-point array (value round(Phi * S)); the result is
  * bit-reproducible for any launch configuration. */
-int lt_trace_forward(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
+LT_API int lt_trace_forward(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
                      uint64_t photon_end);
 
 /* Device pointer of the int64 texel accumulator and its scale S (valid until
  * the next lt_upload_scene). Ranks that split photons can sum these arrays
  * (exact integer addition) before lt_loss. */
-int lt_texel_accumulator(void *ctx, int64_t **q_device, double *scale_out);
+LT_API int lt_texel_accumulator(void *ctx, int64_t **q_device, double *scale_out);
 
 /* Copy of the int64 texel accumulator ([n_texels]) into caller memory. */
-int lt_get_texel_sums(void *ctx, int64_t *q_out, int is_device);
+LT_API int lt_get_texel_sums(void *ctx, int64_t *q_out, int is_device);
 
 /* Objective (Eq. 6, order 0): O = 1/2 sum_t A_t alpha_t (E_t - E*_t)^2 with
  * E_t = q_t / (S A_t). Also forms the adjoint weights
  * w_t = alpha_t (E_t - E*_t) = dO/dPhi for a deposit into texel t, kept on the
  * device for lt_trace_adjoint. Writes O (double) to loss_out. Deterministic. */
-int lt_loss(void *ctx, double *loss_out, int is_device);
+LT_API int lt_loss(void *ctx, double *loss_out, int is_device);
 
 /* Irradiance E_t (float, [n_texels]) of the last forward pass. */
-int lt_get_irradiance(void *ctx, float *E_out, int is_device);
+LT_API int lt_get_irradiance(void *ctx, float *E_out, int is_device);
 
 /* Texel areas A_t (float, [n_texels]). */
-int lt_texel_areas(void *ctx, float *A_out, int is_device);
+LT_API int lt_texel_areas(void *ctx, float *A_out, int is_device);
 
 /* Replace the adjoint weights w_t ([n_texels] floats) -- injects dO/dPhi
  * directly (for gradient checks against closed forms). */
-int lt_set_adjoint_weights(void *ctx, const float *w, int is_device);
+LT_API int lt_set_adjoint_weights(void *ctx, const float *w, int is_device);
 
 /* Adjoint pass (Alg. 2, Eq. 11-12): replays photons [photon_begin,
  * photon_end) of the budget n_photons from `seed` (the forward seed for a
@@ -163,7 +169,7 @@ int lt_set_adjoint_weights(void *ctx, const float *w, int is_device);
  * edge, Eq. 15 for orientation, I_e = p^2/2 for intensity). Writes dO/dp as
  * double [n_lights][LT_GRAD_N] to grad_out. Needs weights from lt_loss or
  * lt_set_adjoint_weights. Deterministic for a given launch configuration. */
-int lt_trace_adjoint(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
+LT_API int lt_trace_adjoint(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
                      uint64_t photon_end, double *grad_out, int is_device);
 
 /* Debug record of photons [photon_begin, photon_begin + count): original
@@ -171,15 +177,22 @@ int lt_trace_adjoint(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_h
  * outputs [count][max_hits]). If grad_out is not NULL it receives every
  * photon's own gradient term dO/dPhi_r * dPhi_r/dp (host [count][LT_GRAD_N],
  * double; needs adjoint weights as lt_trace_adjoint does). */
-int lt_debug_paths(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
+LT_API int lt_debug_paths(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
                    uint64_t count, int32_t *tri_out, int64_t *texel_out, double *grad_out);
 
-int lt_get_stats(void *ctx, lt_stats *out);
+LT_API int lt_get_stats(void *ctx, lt_stats *out);
+
+/* Forward pass exactly as lt_trace_forward (same texel sums) through a
+ * counting variant of the kernel, for work accounting: writes
+ * counts_out[0] = segments traced, [1] = BVH node visits (including the
+ * re-tests on the way back up), [2] = ray/triangle tests, [3] = photons. */
+LT_API int lt_count_work(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
+                  uint64_t photon_end, uint64_t *counts_out);
 
 /* Launch shape of the tracing kernels: threads per block (multiple of 32,
  * <= 1024), blocks per SM (>= 1) and the shared-memory budget for staged BVH
  * nodes in bytes (0 = none). Zeros keep the current value. */
-int lt_set_launch(void *ctx, int32_t threads_per_block, int32_t blocks_per_sm, int32_t smem_node_bytes);
+LT_API int lt_set_launch(void *ctx, int32_t threads_per_block, int32_t blocks_per_sm, int32_t smem_node_bytes);
 
 #ifdef __cplusplus
 }

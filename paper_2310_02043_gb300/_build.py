@@ -26,28 +26,34 @@ def _nvcc() -> str:
 
 def _common(extra=()):
     return ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
+            "-Xcompiler", "-fvisibility=hidden",
             "-I", os.path.join(ROOT, "include"), *extra]
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "lt.h"), __file__]
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compile and link the library; returns its path."""
-    if not force and not _stale():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, out_dir: str = OUT_DIR,
+          defines: tuple = ()) -> str:
+    """Compile and link the library into out_dir; returns its path.
+
+    `defines` are extra -D macros (tuning knobs such as LT_MIN_BLOCKS)."""
+    lib_path = os.path.join(out_dir, "libltrace.so")
+    if not force and not defines and not _stale(lib_path):
+        return lib_path
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
     procs, objs = [], []
     for src in SOURCES:
-        obj = os.path.join(OUT_DIR, src.rsplit(".", 1)[0] + ".o")
+        obj = os.path.join(out_dir, src.rsplit(".", 1)[0] + ".o")
         objs.append(obj)
         extra = ["-Xptxas", "-v"] if (ptxas_info and src.endswith(".cu")) else []
+        extra += [f"-D{d}" for d in defines]
         cmd = [nvcc, *ARCH, *_common(extra), "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
@@ -61,11 +67,11 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             failed.append(src)
     if failed:
         raise RuntimeError(f"nvcc failed for {failed}")
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     link = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
     subprocess.run(link, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

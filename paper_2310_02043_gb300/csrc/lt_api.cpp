@@ -48,8 +48,8 @@ struct Ctx {
     double scale = 1.0;
     bool fwd_done = false, has_w = false;
     double *d_loss = nullptr, *d_partial = nullptr, *d_grad = nullptr;
-    double *d_warp_acc = nullptr;
-    size_t warp_acc_bytes = 0;
+    double *d_slots = nullptr;             // per-thread adjoint gradient sums
+    size_t slots_bytes = 0;
     unsigned long long *d_seg = nullptr;   // [2]: forward, adjoint
     int32_t *d_err = nullptr;
     double *h_pinned = nullptr;            // small pinned staging area
@@ -180,6 +180,11 @@ int launch_shape(Ctx *c, bool adjoint, int *grid, size_t *smem, int32_t *n_stage
     return LT_OK;
 }
 
+uint64_t photon_chunk(uint64_t n, int grid, int threads) {
+    const uint64_t T = (uint64_t)grid * (uint64_t)threads;
+    return std::max<uint64_t>(1, (n + T - 1) / T);
+}
+
 TraceParams base_params(Ctx *c, uint64_t seed, int32_t max_hits, uint64_t begin, uint64_t end) {
     TraceParams p;
     std::memset(&p, 0, sizeof(p));
@@ -257,7 +262,7 @@ int lt_destroy(void *ctx) {
     if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
     dfree(c->d_nodes); dfree(c->d_parent); dfree(c->d_tris); dfree(c->d_hits); dfree(c->d_area);
     dfree(c->d_target); dfree(c->d_alpha); dfree(c->d_lights); dfree(c->d_q); dfree(c->d_E); dfree(c->d_w);
-    dfree(c->d_loss); dfree(c->d_partial); dfree(c->d_grad); dfree(c->d_warp_acc); dfree(c->d_seg);
+    dfree(c->d_loss); dfree(c->d_partial); dfree(c->d_grad); dfree(c->d_slots); dfree(c->d_seg);
     dfree(c->d_err);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     if (c->h_lights) cudaFreeHost(c->h_lights);
@@ -395,10 +400,8 @@ int lt_set_lights(void *ctx, const lt_light *lights, int32_t n_lights) {
     return LT_OK;
 }
 
-int lt_trace_forward(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
-                     uint64_t photon_end) {
-    Ctx *c = static_cast<Ctx *>(ctx);
-    if (!c) return LT_ERR_ARG;
+static int forward_pass(Ctx *c, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
+                 uint64_t photon_end, unsigned long long *d_work) {
     int rc = check_trace_args(c, n_photons, max_hits, photon_begin, photon_end);
     if (rc) return rc;
     LT_CUDA(c, cudaSetDevice(c->device));
@@ -418,15 +421,56 @@ int lt_trace_forward(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_h
     int grid;
     size_t smem;
     if ((rc = launch_shape(c, false, &grid, &smem, &p.n_staged))) return rc;
+    p.chunk = photon_chunk(photon_end - photon_begin, grid, c->threads);
     LT_CUDA(c, cudaMemsetAsync(c->d_q, 0, (size_t)c->n_texels * sizeof(unsigned long long), c->stream));
     LT_CUDA(c, cudaMemsetAsync(c->d_seg, 0, sizeof(unsigned long long), c->stream));
-    LT_CUDA(c, launch_forward(p, grid, c->threads, smem, c->stream));
+    if (d_work) {
+        p.work = d_work;
+        LT_CUDA(c, launch_forward_counted(p, grid, c->threads, smem, c->stream));
+    } else {
+        LT_CUDA(c, launch_forward(p, grid, c->threads, smem, c->stream));
+    }
     c->fwd_done = true;
     c->has_w = false;
     c->stats.photons_forward = photon_end - photon_begin;
     c->stats.staged_nodes = p.n_staged;
     c->stats.fixed_point_scale = S;
     return LT_OK;
+}
+
+int lt_trace_forward(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
+                     uint64_t photon_end) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return LT_ERR_ARG;
+    return forward_pass(c, seed, n_photons, max_hits, photon_begin, photon_end, nullptr);
+}
+
+int lt_count_work(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
+                  uint64_t photon_end, uint64_t *counts_out) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return LT_ERR_ARG;
+    if (!counts_out) return fail(c, LT_ERR_ARG, "null counts output");
+    unsigned long long *d_work = nullptr;
+    LT_CUDA(c, cudaSetDevice(c->device));
+    LT_CUDA(c, cudaMalloc(&d_work, 2 * sizeof(unsigned long long)));
+    cudaError_t e = cudaMemsetAsync(d_work, 0, 2 * sizeof(unsigned long long), c->stream);
+    int rc = e == cudaSuccess ? forward_pass(c, seed, n_photons, max_hits, photon_begin, photon_end, d_work)
+                              : cuda_fail(c, e, "cudaMemsetAsync");
+    unsigned long long h[3] = {0, 0, 0};
+    if (rc == LT_OK) {
+        e = cudaMemcpyAsync(h, d_work, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h + 2, c->d_seg, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                                  c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) rc = cuda_fail(c, e, "lt_count_work");
+    }
+    cudaFree(d_work);
+    if (rc) return rc;
+    counts_out[0] = h[2];
+    counts_out[1] = h[0];
+    counts_out[2] = h[1];
+    counts_out[3] = photon_end - photon_begin;
+    return check_device(c);
 }
 
 int lt_texel_accumulator(void *ctx, int64_t **q_device, double *scale_out) {
@@ -519,24 +563,22 @@ int lt_trace_adjoint(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_h
     int grid;
     size_t smem;
     if ((rc = launch_shape(c, true, &grid, &smem, &p.n_staged))) return rc;
-    // per-warp accumulators: cap their size by shrinking the grid
-    const size_t per_warp = (size_t)L * 8 * sizeof(double);
-    const size_t warps_per_block = (size_t)c->threads / 32;
-    const size_t cap = (size_t)512 << 20;
-    while (grid > c->sm_count && (size_t)grid * warps_per_block * per_warp > cap) grid -= c->sm_count;
-    const size_t n_warps = (size_t)grid * warps_per_block;
-    const size_t need = n_warps * per_warp;
-    if (need > c->warp_acc_bytes) {
+    // Per-thread gradient slots: a thread's contiguous photon chunk touches at
+    // most chunk / (fewest photons of a light) + 2 lights.
+    p.chunk = photon_chunk(photon_end - photon_begin, grid, c->threads);
+    const uint64_t min_nl = n_photons / (uint64_t)L;
+    p.n_slots = min_nl == 0 ? L : (int32_t)std::min<uint64_t>((uint64_t)L, p.chunk / min_nl + 2);
+    const size_t need = (size_t)grid * (size_t)c->threads * (size_t)p.n_slots * 8 * sizeof(double);
+    if (need > c->slots_bytes) {
         LT_CUDA(c, cudaStreamSynchronize(c->stream));
-        dfree(c->d_warp_acc);
-        LT_CUDA(c, cudaMalloc(&c->d_warp_acc, need));
-        c->warp_acc_bytes = need;
+        dfree(c->d_slots);
+        LT_CUDA(c, cudaMalloc(&c->d_slots, need));
+        c->slots_bytes = need;
     }
-    p.warp_acc = c->d_warp_acc;
-    LT_CUDA(c, cudaMemsetAsync(c->d_warp_acc, 0, need, c->stream));
+    p.slots = c->d_slots;
     LT_CUDA(c, cudaMemsetAsync(c->d_seg + 1, 0, sizeof(unsigned long long), c->stream));
     LT_CUDA(c, launch_adjoint(p, grid, c->threads, smem, c->stream));
-    LT_CUDA(c, launch_grad_finalize(c->d_warp_acc, (int64_t)n_warps, L, c->d_grad, c->stream));
+    LT_CUDA(c, launch_grad_finalize(p, c->d_grad, c->stream));
     c->stats.photons_adjoint = photon_end - photon_begin;
     rc = copy_out(c, grad_out, c->d_grad, (size_t)L * 8 * sizeof(double), is_device);
     if (rc) return rc;

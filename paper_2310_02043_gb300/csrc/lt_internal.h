@@ -11,7 +11,7 @@
 namespace lt {
 
 constexpr int kWide = 8;                 // children per BVH node
-constexpr int kMaxDepth = 24;            // levels of wide nodes (3 x 8-bit pending masks per u64 word)
+constexpr int kMaxDepth = 16;            // levels of wide nodes (8-bit pending masks in two u64 words)
 constexpr int kLeafMax = 3;              // triangles per leaf child
 constexpr int32_t kEmptyChild = INT32_MIN;
 
@@ -88,15 +88,18 @@ struct TraceParams {
     // forward
     unsigned long long *q;      // [n_texels] fixed-point irradiance accumulator
     float scale;                // S
+    uint64_t chunk;             // photons per thread (contiguous)
     // adjoint
     const float *w;             // [n_texels] dO/dPhi per deposit
-    double *warp_acc;           // [n_warps][n_lights][8]
+    double *slots;              // [threads][n_slots][8] per-thread gradient sums
+    int32_t n_slots;            // lights a thread's chunk can touch
     // debug record
     int32_t *rec_tri;
     int64_t *rec_texel;
     double *rec_grad;           // [count][8] per-photon gradient terms, may be null
     // counters
     unsigned long long *segments;
+    unsigned long long *work;   // [2] node visits, triangle tests (counting kernel only)
     int32_t *err;
 };
 
@@ -118,13 +121,13 @@ constexpr int kLossThreads = 256;
 
 // Kernel launchers (lt_kernels.cu).
 cudaError_t launch_forward(const TraceParams &p, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t launch_forward_counted(const TraceParams &p, int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t launch_adjoint(const TraceParams &p, int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t launch_paths(const TraceParams &p, uint64_t count, cudaStream_t s);
 cudaError_t launch_loss(const LossParams &p, cudaStream_t s);
 cudaError_t launch_resolve(const unsigned long long *q, const float *area, double inv_scale, int64_t n,
                            float *E_out, cudaStream_t s);
-cudaError_t launch_grad_finalize(const double *warp_acc, int64_t n_warps, int32_t n_lights, double *out,
-                                 cudaStream_t s);
+cudaError_t launch_grad_finalize(const TraceParams &p, double *out, cudaStream_t s);
 int trace_kernel_max_threads();
 cudaError_t trace_occupancy(bool adjoint, int block, size_t smem, int *blocks_per_sm);
 

@@ -18,6 +18,10 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kTraceThreads = 256;
+#ifndef LT_MIN_BLOCKS
+#define LT_MIN_BLOCKS 3
+#endif
+constexpr int kTraceMinBlocks = LT_MIN_BLOCKS;   // resident blocks per SM the register budget targets
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC 2011).
@@ -48,7 +52,7 @@ struct Ray {
     float ox, oy, oz;
     float dx, dy, dz;
     float ix, iy, iz;        // 1 / d, zero components replaced by +-1e-30
-    int kx, ky, kz;          // watertight shear axes
+    int axes;                // watertight shear axes kx | ky << 2 | kz << 4
     float Sx, Sy, Sz;
 };
 
@@ -70,7 +74,7 @@ __device__ __forceinline__ void ray_init(Ray &r, float ox, float oy, float oz, f
     int ky = kx + 1 == 3 ? 0 : kx + 1;
     const float dkz = sel3(dx, dy, dz, kz);
     if (dkz < 0.0f) { const int t = kx; kx = ky; ky = t; }
-    r.kx = kx; r.ky = ky; r.kz = kz;
+    r.axes = kx | (ky << 2) | (kz << 4);
     r.Sx = __fdiv_rn(sel3(dx, dy, dz, kx), dkz);
     r.Sy = __fdiv_rn(sel3(dx, dy, dz, ky), dkz);
     r.Sz = __fdiv_rn(1.0f, dkz);
@@ -87,9 +91,10 @@ __device__ __forceinline__ bool tri_intersect(const Ray &r, const float4 a, cons
     const float Ax0 = __fsub_rn(a.x, r.ox), Ay0 = __fsub_rn(a.y, r.oy), Az0 = __fsub_rn(a.z, r.oz);
     const float Bx0 = __fsub_rn(b.x, r.ox), By0 = __fsub_rn(b.y, r.oy), Bz0 = __fsub_rn(b.z, r.oz);
     const float Cx0 = __fsub_rn(c.x, r.ox), Cy0 = __fsub_rn(c.y, r.oy), Cz0 = __fsub_rn(c.z, r.oz);
-    const float Akx = sel3(Ax0, Ay0, Az0, r.kx), Aky = sel3(Ax0, Ay0, Az0, r.ky), Akz = sel3(Ax0, Ay0, Az0, r.kz);
-    const float Bkx = sel3(Bx0, By0, Bz0, r.kx), Bky = sel3(Bx0, By0, Bz0, r.ky), Bkz = sel3(Bx0, By0, Bz0, r.kz);
-    const float Ckx = sel3(Cx0, Cy0, Cz0, r.kx), Cky = sel3(Cx0, Cy0, Cz0, r.ky), Ckz = sel3(Cx0, Cy0, Cz0, r.kz);
+    const int kx = r.axes & 3, ky = (r.axes >> 2) & 3, kz = r.axes >> 4;
+    const float Akx = sel3(Ax0, Ay0, Az0, kx), Aky = sel3(Ax0, Ay0, Az0, ky), Akz = sel3(Ax0, Ay0, Az0, kz);
+    const float Bkx = sel3(Bx0, By0, Bz0, kx), Bky = sel3(Bx0, By0, Bz0, ky), Bkz = sel3(Bx0, By0, Bz0, kz);
+    const float Ckx = sel3(Cx0, Cy0, Cz0, kx), Cky = sel3(Cx0, Cy0, Cz0, ky), Ckz = sel3(Cx0, Cy0, Cz0, kz);
     const float Ax = __fsub_rn(Akx, __fmul_rn(r.Sx, Akz)), Ay = __fsub_rn(Aky, __fmul_rn(r.Sy, Akz));
     const float Bx = __fsub_rn(Bkx, __fmul_rn(r.Sx, Bkz)), By = __fsub_rn(Bky, __fmul_rn(r.Sy, Bkz));
     const float Cx = __fsub_rn(Ckx, __fmul_rn(r.Sx, Ckz)), Cy = __fsub_rn(Cky, __fmul_rn(r.Sy, Ckz));
@@ -120,25 +125,31 @@ __device__ __forceinline__ bool tri_intersect(const Ray &r, const float4 a, cons
 // the current closest hit.
 // ---------------------------------------------------------------------------
 struct Trail {
-    uint64_t w0 = 0, w1 = 0, w2 = 0;
+    uint64_t w0 = 0, w1 = 0;
     __device__ __forceinline__ uint32_t get(int lvl) const {
-        const uint64_t w = lvl < 8 ? w0 : (lvl < 16 ? w1 : w2);
+        const uint64_t w = lvl < 8 ? w0 : w1;
         return (uint32_t)(w >> ((lvl & 7) * 8)) & 0xffu;
     }
     __device__ __forceinline__ void set(int lvl, uint32_t m) {
         const int sh = (lvl & 7) * 8;
         const uint64_t clear = ~(0xffull << sh), put = (uint64_t)m << sh;
         if (lvl < 8) w0 = (w0 & clear) | put;
-        else if (lvl < 16) w1 = (w1 & clear) | put;
-        else w2 = (w2 & clear) | put;
+        else w1 = (w1 & clear) | put;
     }
 };
 
 struct Hit {
     int32_t tri;       // leaf-order index, -1 on a miss
     int32_t prim;      // uploaded index (tie-break)
-    float t, U, V, W, det;
+    float t, b0, b1, b2;   // distance and barycentric weights of the three vertices
 };
+
+__device__ __forceinline__ void take_hit(Hit &h, int32_t tri, int32_t prim, const TriTest &tt) {
+    h.tri = tri; h.prim = prim; h.t = tt.t;
+    h.b0 = __fdiv_rn(tt.U, tt.det);
+    h.b1 = __fdiv_rn(tt.V, tt.det);
+    h.b2 = __fdiv_rn(tt.W, tt.det);
+}
 
 __device__ __forceinline__ const float4 *node_ptr(const TraceParams &P, const float4 *smem, int32_t n) {
     return n < P.n_staged ? smem + (size_t)n * (sizeof(Node) / 16)
@@ -216,9 +227,15 @@ __device__ __forceinline__ int32_t pick_child(const int32_t child[kWide], int k)
 
 // Closest hit excluding triangles of tile `skip_tile`. Ties in t go to the
 // lower uploaded triangle index.
-__device__ __forceinline__ Hit closest_hit(const TraceParams &P, const float4 *smem, const Ray &r, int32_t skip_tile) {
+struct Work {
+    uint32_t nodes = 0, tris = 0;   // node visits (including re-tests) and triangle tests
+};
+
+template <bool kCount = false>
+__device__ __forceinline__ Hit closest_hit(const TraceParams &P, const float4 *smem, const Ray &r, int32_t skip_tile,
+                                           Work *work = nullptr) {
     Hit h;
-    h.tri = -1; h.prim = INT32_MAX; h.t = FLT_MAX; h.U = h.V = h.W = 0.0f; h.det = 1.0f;
+    h.tri = -1; h.prim = INT32_MAX; h.t = FLT_MAX; h.b0 = h.b1 = h.b2 = 0.0f;
     Trail trail;
     int32_t node = 0;
     int lvl = 0;
@@ -227,6 +244,7 @@ __device__ __forceinline__ Hit closest_hit(const TraceParams &P, const float4 *s
     int32_t child[kWide];
     while (true) {
         if (++steps > P.max_steps) { atomicOr(P.err, kErrSteps); h.tri = -1; return h; }
+        if (kCount) work->nodes += 1;
         uint32_t m = test_node(P, smem, node, r, h.t, 0xffu, tnear, child);
         // leaves of this node first
 #pragma unroll
@@ -240,12 +258,10 @@ __device__ __forceinline__ Hit closest_hit(const TraceParams &P, const float4 *s
                     const int32_t tile = __float_as_int(b.w);
                     if (tile == skip_tile) continue;
                     TriTest tt;
+                    if (kCount) work->tris += 1;
                     if (!tri_intersect(r, a, b, c, tt)) continue;
                     const int32_t prim = __float_as_int(a.w);
-                    if (tt.t < h.t || (tt.t == h.t && prim < h.prim)) {
-                        h.tri = i; h.prim = prim; h.t = tt.t;
-                        h.U = tt.U; h.V = tt.V; h.W = tt.W; h.det = tt.det;
-                    }
+                    if (tt.t < h.t || (tt.t == h.t && prim < h.prim)) take_hit(h, i, prim, tt);
                 }
             }
         }
@@ -269,6 +285,7 @@ __device__ __forceinline__ Hit closest_hit(const TraceParams &P, const float4 *s
             const uint32_t pend = trail.get(lvl);
             if (pend == 0) continue;
             if (++steps > P.max_steps) { atomicOr(P.err, kErrSteps); h.tri = -1; return h; }
+            if (kCount) work->nodes += 1;
             const uint32_t again = test_node(P, smem, node, r, h.t, pend, tnear, child);
             uint32_t live = 0;
 #pragma unroll
@@ -289,7 +306,7 @@ __device__ __forceinline__ Hit closest_hit(const TraceParams &P, const float4 *s
 // min(floor(u res), res - 1).
 __device__ __forceinline__ int64_t texel_of(const TraceParams &P, const Hit &h) {
     const TriHit &th = P.hits[h.tri];
-    const float b0 = __fdiv_rn(h.U, h.det), b1 = __fdiv_rn(h.V, h.det), b2 = __fdiv_rn(h.W, h.det);
+    const float b0 = h.b0, b1 = h.b1, b2 = h.b2;
     float u = __fadd_rn(__fadd_rn(__fmul_rn(b0, th.uv[0]), __fmul_rn(b1, th.uv[2])), __fmul_rn(b2, th.uv[4]));
     float v = __fadd_rn(__fadd_rn(__fmul_rn(b0, th.uv[1]), __fmul_rn(b1, th.uv[3])), __fmul_rn(b2, th.uv[5]));
     u = u < 0.0f ? 0.0f : (u > 1.0f ? 1.0f : u);
@@ -435,109 +452,232 @@ __device__ __forceinline__ void stage_nodes(const TraceParams &P, float4 *smem) 
     __syncthreads();
 }
 
+// Deposit from the lanes of the warp that are depositing in this step: lanes
+// that hit the same texel add their values with shuffles and one of them does
+// the 64-bit atomic.
+__device__ __forceinline__ void deposit_active(unsigned long long *q, int64_t texel, unsigned long long val) {
+    const unsigned m = __activemask();
+    const unsigned peers = __match_any_sync(m, (unsigned long long)texel);
+    unsigned long long tot = 0;
+    unsigned rest = peers;
+    while (rest) {
+        const int src = __ffs(rest) - 1;
+        tot += __shfl_sync(peers, val, src);
+        rest &= rest - 1;
+    }
+    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(q + texel, tot);
+}
+
 // ---------------------------------------------------------------------------
-// Forward / adjoint tracing. A warp takes 32 consecutive photons per
-// iteration and walks their paths segment by segment in lock step.
+// Forward / adjoint tracing. Every thread owns a contiguous chunk of photons
+// and advances its own path through a small state machine, one unit of work
+// per loop iteration: test one BVH node, test the triangles of one leaf, or
+// finish a segment (deposit / adjoint update, bounce, next photon). Each
+// iteration the warp votes and runs the kind of step most of its lanes are
+// waiting for, so lanes never idle until a neighbour's path ends.
 // ---------------------------------------------------------------------------
-template <bool kAdjoint>
-__global__ void __launch_bounds__(kTraceThreads) trace_kernel(const TraceParams P) {
+struct Trav {
+    int32_t node;       // node to test next, -1 when the traversal has no node left
+    uint32_t mask;      // children of `node` to test (all on a first visit)
+    int32_t lvl;
+    int32_t steps;
+    int32_t leaf_node;  // node whose hit leaf children are pending
+    uint32_t leaves;    // pending leaf children of leaf_node
+    Trail trail;
+};
+
+__device__ __forceinline__ void trav_init(Trav &s, Hit &h) {
+    s.node = 0; s.mask = 0xffu; s.lvl = 0; s.steps = 0; s.leaf_node = 0; s.leaves = 0;
+    s.trail = Trail();
+    h.tri = -1; h.prim = INT32_MAX; h.t = FLT_MAX; h.b0 = h.b1 = h.b2 = 0.0f;
+}
+
+__device__ __forceinline__ int32_t child_word(const TraceParams &P, const float4 *smem, int32_t n, int k) {
+    const int32_t *c = reinterpret_cast<const int32_t *>(node_ptr(P, smem, n) + 12) + k;
+    return n < P.n_staged ? *c : __ldg(c);
+}
+
+// Test the children of s.node selected by s.mask; note hit leaves; descend to
+// the nearest hit inner child or climb to the nearest level with pending ones.
+template <bool kCount>
+__device__ __forceinline__ void node_step(const TraceParams &P, const float4 *smem, const Ray &r, Trav &s, Hit &h,
+                                          Work &work) {
+    if (kCount) work.nodes += 1;
+    if (++s.steps > P.max_steps) {
+        atomicOr(P.err, kErrSteps);
+        s.node = -1; s.leaves = 0; h.tri = -1;
+        return;
+    }
+    float tnear[kWide];
+    int32_t child[kWide];
+    const uint32_t m = test_node(P, smem, s.node, r, h.t, s.mask, tnear, child);
+    uint32_t leaves = 0, inner = 0;
+#pragma unroll
+    for (int k = 0; k < kWide; ++k) {
+        const bool hit = (m >> k) & 1u;
+        leaves |= (hit && child[k] < 0 ? 1u : 0u) << k;
+        inner |= (hit && child[k] >= 0 && tnear[k] <= h.t ? 1u : 0u) << k;
+    }
+    if (leaves) { s.leaf_node = s.node; s.leaves = leaves; }
+    if (inner) {
+        const int k = pick_nearest(inner, tnear);
+        s.trail.set(s.lvl, inner & ~(1u << k));
+        s.node = pick_child(child, k);
+        s.mask = 0xffu;
+        if (++s.lvl >= kMaxDepth) {
+            atomicOr(P.err, kErrDepth);
+            s.node = -1; s.leaves = 0; h.tri = -1;
+        }
+        return;
+    }
+    while (s.lvl > 0) {
+        --s.lvl;
+        s.node = __ldg(P.parent + s.node);
+        const uint32_t pend = s.trail.get(s.lvl);
+        if (pend) {
+            s.trail.set(s.lvl, 0);
+            s.mask = pend;
+            return;
+        }
+    }
+    s.node = -1;
+}
+
+// Test the triangles of one pending leaf child.
+template <bool kCount>
+__device__ __forceinline__ void leaf_step(const TraceParams &P, const float4 *smem, const Ray &r, Trav &s, Hit &h,
+                                          int32_t skip_tile, Work &work) {
+    const int k = __ffs(s.leaves) - 1;
+    s.leaves &= s.leaves - 1;
+    const int32_t code = -1 - child_word(P, smem, s.leaf_node, k);
+    const int32_t first = code >> 2, count = (code & 3) + 1;
+    for (int32_t i = first; i < first + count; ++i) {
+        const float4 *tp = reinterpret_cast<const float4 *>(P.tris + i);
+        const float4 a = __ldg(tp), b = __ldg(tp + 1), c = __ldg(tp + 2);
+        if (__float_as_int(b.w) == skip_tile) continue;
+        if (kCount) work.tris += 1;
+        TriTest tt;
+        if (!tri_intersect(r, a, b, c, tt)) continue;
+        const int32_t prim = __float_as_int(a.w);
+        if (tt.t < h.t || (tt.t == h.t && prim < h.prim)) take_hit(h, i, prim, tt);
+    }
+}
+
+template <bool kAdjoint, bool kCount = false>
+__global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(const TraceParams P) {
     extern __shared__ float4 smem[];
     stage_nodes(P, smem);
-    const int lane = threadIdx.x & 31;
-    const uint64_t warp = (uint64_t)(blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t n_warps = (uint64_t)(gridDim.x * blockDim.x) >> 5;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t n = P.photon_end - P.photon_begin;
+    const uint64_t chunk = P.chunk;
+    uint64_t photon = P.photon_begin + min(tid * chunk, n);
+    const uint64_t p_end = P.photon_begin + min((tid + 1) * chunk, n);
+    int32_t first_light = 0;
+    if (kAdjoint)
+        for (int i = 0; i < P.n_slots * 8; ++i) P.slots[tid * (uint64_t)P.n_slots * 8 + i] = 0.0;
+
+    int32_t l = 0, seg = 0, skip = -1;
+    float phi = 0.0f, a_emit = 0.0f, g = 0.0f, beta = 1.0f;
+    float x1x = 0.0f, x1y = 0.0f, x1z = 0.0f;      // adjoint: first hit and its normal
+    float3 n1 = make_float3(0.0f, 0.0f, 0.0f);
+    bool hit1 = false;
+    Ray r;
+    Trav s;
+    Hit h;
+    Work work;
     unsigned long long segs = 0;
-    double acc = 0.0;          // adjoint: lane k < 8 holds parameter k of light `cur`
-    int32_t cur = -1;
+    bool active = photon < p_end;
 
-    for (uint64_t base = P.photon_begin + warp * 32; base < P.photon_end; base += n_warps * 32) {
-        const uint64_t photon = base + lane;
-        const bool valid = photon < P.photon_end;
-        const int32_t l = valid ? light_of(P, photon) : 0;
+    // Emission of the current photon (Alg. 1: exitant ray carrying Phi_r).
+    auto start_photon = [&]() {
+        while (photon >= P.lights[l].end) ++l;
         const LightDev &L = P.lights[l];
-        float wx = 0.0f, wy = 0.0f, wz = 1.0f, a_emit = 0.0f, phi = 0.0f;
-        if (valid) {
-            const float2 u = uniforms(P.seed, photon, 0u, P.design);
-            phi = emit(L, u.x, u.y, wx, wy, wz, a_emit);
-        }
-        const float phi_r = phi;
-        float ox = L.pos[0], oy = L.pos[1], oz = L.pos[2];
-        int32_t skip = -1;
-        bool alive = valid;
-        float g = 0.0f, beta = 1.0f;
-        float dp[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) dp[k] = 0.0f;
+        const float2 u = uniforms(P.seed, photon, 0u, P.design);
+        float wx, wy, wz;
+        phi = emit(L, u.x, u.y, wx, wy, wz, a_emit);
+        ray_init(r, L.pos[0], L.pos[1], L.pos[2], wx, wy, wz);
+        seg = 1;
+        skip = -1;
+        g = 0.0f;
+        beta = 1.0f;
+        hit1 = false;
+        trav_init(s, h);
+    };
+    if (active) {
+        l = light_of(P, photon);
+        first_light = l;
+        start_photon();
+    }
 
-        for (int i = 1; i <= P.max_hits; ++i) {
-            const unsigned am = __ballot_sync(kFull, alive);
-            if (am == 0) break;
-            if (lane == 0) segs += __popc(am);
-            Hit h;
-            h.tri = -1;
-            if (alive) {
-                Ray r;
-                ray_init(r, ox, oy, oz, wx, wy, wz);
-                h = closest_hit(P, smem, r, skip);
-            }
-            const bool hit = alive && h.tri >= 0;
-            int64_t texel = 0;
-            float x1x = 0.0f, x1y = 0.0f, x1z = 0.0f;
-            float3 n = make_float3(0.0f, 0.0f, 1.0f);
-            if (hit) {
-                texel = texel_of(P, h);
-                x1x = fmaf(h.t, wx, ox); x1y = fmaf(h.t, wy, oy); x1z = fmaf(h.t, wz, oz);
-                n = facing_normal(P, h.tri, wx, wy, wz);
-            }
-            if (!kAdjoint) {
-                const unsigned long long v = hit ? (unsigned long long)__float2ll_rn(phi * P.scale) : 0ull;
-                deposit(P.q, hit, texel, v);
-            } else if (hit) {
-                if (i == 1) dflux(L, phi_r, a_emit, x1x, x1y, x1z, n, dp);
-                g += __ldg(P.w + texel) * beta;        // Eq. 12
-            }
-            if (!hit || i == P.max_hits) { alive = false; continue; }
-            const float rho = albedo_of(P, h.tri);
-            const float2 u = uniforms(P.seed, photon, (uint32_t)i, P.design);
-            cosine_dir(n, u.x, u.y, wx, wy, wz);
-            phi *= rho;                                  // Eq. 7
-            beta *= rho;
-            ox = x1x; oy = x1y; oz = x1z;
-            skip = __ldg(reinterpret_cast<const int32_t *>(P.tris + h.tri) + 7);
-        }
-
-        if (kAdjoint) {
-            // Eq. 11: sum_r dO/dPhi_r dPhi_r/dp, reduced per light in a fixed
-            // lane order and added to this warp's FP64 accumulator.
-            unsigned pending = __ballot_sync(kFull, valid);
-            while (pending) {
-                const int src = __ffs(pending) - 1;
-                const int32_t L0 = __shfl_sync(kFull, l, src);
-                const bool mine = valid && l == L0;
-                const unsigned grp = __ballot_sync(kFull, mine);
-                double v[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) v[k] = mine ? (double)(g * dp[k]) : 0.0;
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) v[k] += __shfl_xor_sync(kFull, v[k], off);
+    while (true) {
+        const bool can_leaf = active && s.leaves != 0;
+        const bool can_node = active && !can_leaf && s.node >= 0;
+        const bool fin = active && !can_leaf && s.node < 0;
+        const unsigned bl = __ballot_sync(kFull, can_leaf);
+        const unsigned bn = __ballot_sync(kFull, can_node);
+        const unsigned bf = __ballot_sync(kFull, fin);
+        if ((bl | bn | bf) == 0u) break;
+        const int nl = __popc(bl), nn = __popc(bn), nf = __popc(bf);
+        if (nn >= nl && nn >= nf) {
+            if (can_node) node_step<kCount>(P, smem, r, s, h, work);
+        } else if (nl >= nf) {
+            if (can_leaf) leaf_step<kCount>(P, smem, r, s, h, skip, work);
+        } else if (fin) {
+            // Finish the segment: one traced ray, hit or miss.
+            segs += 1;
+            bool next_seg = false;
+            if (h.tri >= 0) {
+                const int64_t texel = texel_of(P, h);
+                const float xx = fmaf(h.t, r.dx, r.ox), xy = fmaf(h.t, r.dy, r.oy), xz = fmaf(h.t, r.dz, r.oz);
+                const float3 nrm = facing_normal(P, h.tri, r.dx, r.dy, r.dz);
+                if (!kAdjoint) {
+                    deposit_active(P.q, texel, (unsigned long long)__float2ll_rn(phi * P.scale));   // Eq. 8
+                } else {
+                    if (seg == 1) { x1x = xx; x1y = xy; x1z = xz; n1 = nrm; hit1 = true; }
+                    g += __ldg(P.w + texel) * beta;                                             // Eq. 12
                 }
-                if (L0 != cur) {
-                    if (cur >= 0 && lane < 8) P.warp_acc[(warp * P.n_lights + cur) * 8 + lane] = acc;
-                    acc = 0.0;
-                    cur = L0;
+                if (seg < P.max_hits) {
+                    const float rho = albedo_of(P, h.tri);
+                    const float2 u = uniforms(P.seed, photon, (uint32_t)seg, P.design);
+                    float wx, wy, wz;
+                    cosine_dir(nrm, u.x, u.y, wx, wy, wz);
+                    phi *= rho;                                                                 // Eq. 7
+                    beta *= rho;
+                    skip = __ldg(reinterpret_cast<const int32_t *>(P.tris + h.tri) + 7);
+                    ray_init(r, xx, xy, xz, wx, wy, wz);
+                    trav_init(s, h);
+                    ++seg;
+                    next_seg = true;
                 }
-                double mine_v = v[0];
+            }
+            if (!next_seg) {
+                if (kAdjoint && hit1) {
+                    // Eq. 11: this photon's dO/dPhi_r * dPhi_r/dp into its light's slot
+                    const LightDev &L = P.lights[l];
+                    float dp[8];
+                    dflux(L, L.flux_k * a_emit, a_emit, x1x, x1y, x1z, n1, dp);
+                    double *o = P.slots + (tid * (uint64_t)P.n_slots + (uint64_t)(l - first_light)) * 8;
 #pragma unroll
-                for (int k = 1; k < 8; ++k) mine_v = (lane == k) ? v[k] : mine_v;
-                acc += mine_v;
-                pending &= ~grp;
+                    for (int k = 0; k < 8; ++k) o[k] += (double)(g * dp[k]);
+                }
+                ++photon;
+                if (photon < p_end) start_photon(); else active = false;
             }
         }
     }
-    if (kAdjoint && cur >= 0 && lane < 8) P.warp_acc[(warp * P.n_lights + cur) * 8 + lane] = acc;
-    if (lane == 0 && segs) atomicAdd(P.segments, segs);
+    unsigned long long tot = segs;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) tot += __shfl_xor_sync(kFull, tot, off);
+    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(P.segments, tot);
+    if (kCount) {
+        unsigned long long nodes = work.nodes, tris = work.tris;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            nodes += __shfl_xor_sync(kFull, nodes, off);
+            tris += __shfl_xor_sync(kFull, tris, off);
+        }
+        if ((threadIdx.x & 31) == 0) { atomicAdd(P.work, nodes); atomicAdd(P.work + 1, tris); }
+    }
 }
 
 // Path record for debugging: one thread per photon.
@@ -630,16 +770,29 @@ __global__ void resolve_kernel(const unsigned long long *q, const float *area, d
         E[t] = (float)((double)(long long)q[t] * inv_scale / (double)area[t]);
 }
 
-// Sum of the per-warp gradient accumulators: one block per light, fixed order.
-__global__ void __launch_bounds__(256) grad_finalize_kernel(const double *acc, int64_t n_warps, int32_t n_lights,
-                                                            double *out) {
+// Sum of the per-thread gradient slots of every light in thread order: one
+// block per light; thread t's chunk of photons starts at begin + t * chunk and
+// its slot s holds light (light of its first photon) + s.
+__global__ void __launch_bounds__(256) grad_finalize_kernel(const TraceParams P, double *out) {
     __shared__ double sh[256 / 32];
     const int32_t l = blockIdx.x;
+    const uint64_t n = P.photon_end - P.photon_begin;
+    const uint64_t lo = max(P.lights[l].first, P.photon_begin), hi = min(P.lights[l].end, P.photon_end);
+    double v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = 0.0;
+    if (lo < hi && n > 0) {
+        const uint64_t t0 = (lo - P.photon_begin) / P.chunk, t1 = (hi - 1 - P.photon_begin) / P.chunk;
+        for (uint64_t t = t0 + threadIdx.x; t <= t1; t += blockDim.x) {
+            const int32_t s = l - light_of(P, P.photon_begin + t * P.chunk);
+            const double *src = P.slots + (t * (uint64_t)P.n_slots + (uint64_t)s) * 8;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] += src[k];
+        }
+    }
     for (int k = 0; k < 8; ++k) {
-        double v = 0.0;
-        for (int64_t w = threadIdx.x; w < n_warps; w += blockDim.x) v += acc[(w * n_lights + l) * 8 + k];
-        const double s = block_sum(v, sh);
-        if (threadIdx.x == 0) out[l * 8 + k] = s;
+        const double tot = block_sum(v[k], sh);
+        if (threadIdx.x == 0) out[l * 8 + k] = tot;
     }
 }
 
@@ -663,6 +816,16 @@ cudaError_t launch_forward(const TraceParams &p, int grid, int block, size_t sme
         if (e != cudaSuccess) return e;
     }
     trace_kernel<false><<<grid, block, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forward_counted(const TraceParams &p, int grid, int block, size_t smem, cudaStream_t s) {
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(trace_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    trace_kernel<false, true><<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -696,8 +859,8 @@ cudaError_t launch_resolve(const unsigned long long *q, const float *area, doubl
     return cudaGetLastError();
 }
 
-cudaError_t launch_grad_finalize(const double *acc, int64_t n_warps, int32_t n_lights, double *out, cudaStream_t s) {
-    grad_finalize_kernel<<<n_lights, 256, 0, s>>>(acc, n_warps, n_lights, out);
+cudaError_t launch_grad_finalize(const TraceParams &p, double *out, cudaStream_t s) {
+    grad_finalize_kernel<<<p.n_lights, 256, 0, s>>>(p, out);
     return cudaGetLastError();
 }
 

@@ -27,7 +27,7 @@ GRAD_N = 8
 EXPORTED = ("lt_version", "lt_create", "lt_destroy", "lt_set_stream", "lt_last_error", "lt_upload_scene",
             "lt_set_target", "lt_set_lights", "lt_trace_forward", "lt_texel_accumulator", "lt_get_texel_sums", "lt_loss",
             "lt_get_irradiance", "lt_texel_areas", "lt_set_adjoint_weights", "lt_trace_adjoint", "lt_debug_paths",
-            "lt_get_stats", "lt_set_launch")
+            "lt_get_stats", "lt_set_launch", "lt_count_work")
 
 
 class LtError(RuntimeError):
@@ -89,6 +89,7 @@ def _declare(lib):
         "lt_debug_paths": [vp, u64, u64, i32, u64, u64, vp, vp, vp],
         "lt_get_stats": [vp, ctypes.POINTER(lt_stats)],
         "lt_set_launch": [vp, i32, i32, i32],
+        "lt_count_work": [vp, u64, u64, i32, u64, u64, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -256,6 +257,14 @@ class Tracer:
         s = lt_stats()
         self._check(self.lib.lt_get_stats(self.h, ctypes.byref(s)))
         return {name: getattr(s, name) for name, _ in s._fields_}
+
+    def count_work(self, seed: int, n_photons: int, max_hits: int, begin: int = 0, end: int | None = None) -> dict:
+        """Forward pass through the counting kernel: segments, node visits,
+        triangle tests and photons."""
+        end = n_photons if end is None else end
+        out = np.zeros(4, np.uint64)
+        self._check(self.lib.lt_count_work(self.h, seed, n_photons, max_hits, begin, end, _ptr(out)[0]))
+        return dict(segments=int(out[0]), node_visits=int(out[1]), tri_tests=int(out[2]), photons=int(out[3]))
 
     def set_launch(self, threads_per_block: int = 0, blocks_per_sm: int = 0, smem_node_bytes: int = 0):
         self._check(self.lib.lt_set_launch(self.h, threads_per_block, blocks_per_sm, smem_node_bytes))
