@@ -161,8 +161,8 @@ def cpu_baseline(sc, lights, truth, budget_s=15.0):
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
-    small = 1 << 12
-    target = oracle.forward(sc, truth, 77, small * 4, HITS)["E"]
+    small = 1 << 14
+    target = oracle.forward(sc, truth, 77, small, HITS)["E"]
     t0 = time.perf_counter()
     oracle.forward(sc, lights, 2, PHOTONS, HITS, begin=0, end=small)
     probe = time.perf_counter() - t0

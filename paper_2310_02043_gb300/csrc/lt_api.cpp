@@ -167,7 +167,7 @@ int upload_lights(Ctx *c, uint64_t n_photons) {
 }
 
 int launch_shape(Ctx *c, bool adjoint, int *grid, size_t *smem, int32_t *n_staged) {
-    const int32_t fit = c->smem_node_bytes / (int)sizeof(Node);
+    const int32_t fit = c->smem_node_bytes / (int)sizeof(Node);   // whole nodes that fit the budget
     *n_staged = std::max(0, std::min(c->n_nodes, fit));
     *smem = (size_t)(*n_staged) * sizeof(Node);
     int bps = c->blocks_per_sm;
@@ -322,7 +322,15 @@ int lt_upload_scene(void *ctx, const float *tri_xyz, const float *tri_uv, const 
         h.res_u = tile_res[2 * tri_tile[i]];
         h.res_v = tile_res[2 * tri_tile[i] + 1];
         h.texel_off = off[tri_tile[i]];
-        h.pad = 0;
+        double e1[3], e2[3], nn[3];
+        for (int k = 0; k < 3; ++k) { e1[k] = (double)v[3 + k] - v[k]; e2[k] = (double)v[6 + k] - v[k]; }
+        nn[0] = e1[1] * e2[2] - e1[2] * e2[1];
+        nn[1] = e1[2] * e2[0] - e1[0] * e2[2];
+        nn[2] = e1[0] * e2[1] - e1[1] * e2[0];
+        const double ln = std::sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+        if (!(ln > 0.0)) return fail(c, LT_ERR_ARG, "degenerate triangle " + std::to_string(i));
+        for (int k = 0; k < 3; ++k) h.n[k] = (float)(nn[k] / ln);
+        for (int k = 0; k < 3; ++k) h.pad[k] = 0.0f;
     }
     const int64_t T = off[n_tiles];
     std::vector<float> area((size_t)T);

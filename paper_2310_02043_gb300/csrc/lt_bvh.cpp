@@ -142,6 +142,51 @@ void build_binary(const float *xyz, int32_t n_tri, Binary *b) {
     }
 }
 
+// Slot of every child: slot s stands for the direction whose component a is
+// + when bit a of s is set. A child goes to the slot that best matches where
+// it lies relative to the parent's centre; the assignment minimising the sum
+// of -dot(child centre - parent centre, slot direction) is found exactly by
+// dynamic programming over subsets of slots (8 slots, at most 8 children).
+std::vector<int> assign_slots(const Binary &b, const std::vector<int32_t> &kids, const Box &parent) {
+    const int n = (int)kids.size();
+    double pc[3];
+    for (int a = 0; a < 3; ++a) pc[a] = 0.5 * ((double)parent.lo[a] + parent.hi[a]);
+    double cost[kWide][kWide];
+    for (int j = 0; j < n; ++j) {
+        const Box &bx = b.nodes[kids[j]].box;
+        for (int s = 0; s < kWide; ++s) {
+            double c = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                const double v = 0.5 * ((double)bx.lo[a] + bx.hi[a]) - pc[a];
+                c -= ((s >> a) & 1 ? 1.0 : -1.0) * v;
+            }
+            cost[j][s] = c;
+        }
+    }
+    // dp[m] = best cost of giving children 0..popcount(m)-1 the slots in m
+    std::vector<double> dp(1 << kWide, 1e300);
+    std::vector<int> from(1 << kWide, -1);
+    dp[0] = 0.0;
+    for (int m = 0; m < (1 << kWide); ++m) {
+        const int j = __builtin_popcount(m);
+        if (j >= n || dp[m] >= 1e300) continue;
+        for (int s = 0; s < kWide; ++s) {
+            if (m & (1 << s)) continue;
+            const double c = dp[m] + cost[j][s];
+            if (c < dp[m | (1 << s)]) { dp[m | (1 << s)] = c; from[m | (1 << s)] = s; }
+        }
+    }
+    int best = -1;
+    for (int m = 0; m < (1 << kWide); ++m)
+        if (__builtin_popcount(m) == n && (best < 0 || dp[m] < dp[best])) best = m;
+    std::vector<int> slot(n);
+    for (int m = best, j = n - 1; j >= 0; --j) {
+        slot[j] = from[m];
+        m &= ~(1 << from[m]);
+    }
+    return slot;
+}
+
 }  // namespace
 
 bool build_wide_bvh(const float *xyz, int32_t n_tri, BvhBuild *out, std::string *err) {
@@ -191,13 +236,16 @@ bool build_wide_bvh(const float *xyz, int32_t n_tri, BvhBuild *out, std::string 
             }
         }
         Node node;
+        std::memset(&node, 0, sizeof(node));
         for (int k = 0; k < kWide; ++k) {
-            node.lox[k] = node.loy[k] = node.loz[k] = 0.0f;
-            node.hix[k] = node.hiy[k] = node.hiz[k] = 0.0f;
+            node.lox[k] = node.loy[k] = node.loz[k] = 3.0e38f;
+            node.hix[k] = node.hiy[k] = node.hiz[k] = -3.0e38f;
             node.child[k] = kEmptyChild;
         }
-        for (int k = 0; k < (int)kids.size(); ++k) {
-            const BNode &c = b.nodes[kids[k]];
+        const std::vector<int> slot_of = assign_slots(b, kids, root.box);
+        for (int j = 0; j < (int)kids.size(); ++j) {
+            const int k = slot_of[j];
+            const BNode &c = b.nodes[kids[j]];
             node.lox[k] = c.box.lo[0]; node.hix[k] = c.box.hi[0];
             node.loy[k] = c.box.lo[1]; node.hiy[k] = c.box.hi[1];
             node.loz[k] = c.box.lo[2]; node.hiz[k] = c.box.hi[2];
@@ -210,7 +258,8 @@ bool build_wide_bvh(const float *xyz, int32_t n_tri, BvhBuild *out, std::string 
                 out->nodes.emplace_back();
                 out->parent.push_back(it.wnode);
                 node.child[k] = wn;
-                queue.push_back({kids[k], wn, it.depth + 1});
+                node.inner_mask |= 1u << k;
+                queue.push_back({kids[j], wn, it.depth + 1});
             }
         }
         out->nodes[it.wnode] = node;

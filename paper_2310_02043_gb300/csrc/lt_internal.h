@@ -15,15 +15,22 @@ constexpr int kMaxDepth = 16;            // levels of wide nodes (8-bit pending 
 constexpr int kLeafMax = 3;              // triangles per leaf child
 constexpr int32_t kEmptyChild = INT32_MIN;
 
-// 8-wide BVH node, 224 bytes: child boxes stored axis-major so a node is
-// fourteen 16-byte loads. child[k] >= 0 is an inner node index; a leaf is
-// -1 - ((first << 2) | (count - 1)) over the leaf-ordered triangle array;
-// kEmptyChild marks an unused slot.
+// 8-wide BVH node, 240 bytes. Child boxes are stored axis-major (twelve
+// 16-byte vectors), lo and hi of an axis 32 bytes apart, so a ray picks its
+// near and far planes per axis by an address offset. child[k] >= 0 is an
+// inner node index; a leaf is -1 - ((first << 2) | (count - 1)) over the
+// leaf-ordered triangle array; kEmptyChild marks an unused slot, whose box is
+// inverted (lo = +big, hi = -big) so that no ray ever hits it. Children sit
+// in slots ordered by direction: bit a of the slot index is set when the
+// child lies on the + side of the parent along axis a.
 struct alignas(16) Node {
     float lox[kWide], hix[kWide], loy[kWide], hiy[kWide], loz[kWide], hiz[kWide];
     int32_t child[kWide];
+    uint32_t inner_mask;     // slots holding inner nodes
+    uint32_t pad[3];
 };
-static_assert(sizeof(Node) == 224, "node layout");
+static_assert(sizeof(Node) == 240, "node layout");
+constexpr int kNodeVec = (int)(sizeof(Node) / 16);
 
 // Triangle in leaf order, 48 bytes (three 16-byte loads).
 struct alignas(16) Tri {
@@ -41,9 +48,10 @@ struct alignas(16) TriHit {
     float uv[6];
     int32_t res_u, res_v;
     int64_t texel_off;
-    int64_t pad;
+    float n[3];              // unit geometric normal
+    float pad[3];
 };
-static_assert(sizeof(TriHit) == 48, "hit layout");
+static_assert(sizeof(TriHit) == 64, "hit layout");
 
 // Per-light constants derived on the host (double, rounded to float).
 struct alignas(16) LightDev {

@@ -45,6 +45,18 @@ __device__ __forceinline__ float2 uniforms(uint64_t seed, uint64_t photon, uint3
     return make_float2((float)(r.x >> 8) * 0x1p-24f, (float)(r.y >> 8) * 0x1p-24f);
 }
 
+// 3-input min / max (PTX ISA 8.8, sm_100 and later).
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 // ---------------------------------------------------------------------------
 // Rays
 // ---------------------------------------------------------------------------
@@ -53,6 +65,7 @@ struct Ray {
     float dx, dy, dz;
     float ix, iy, iz;        // 1 / d, zero components replaced by +-1e-30
     int axes;                // watertight shear axes kx | ky << 2 | kz << 4
+    int octant;              // bit a set when the ray runs towards -a
     float Sx, Sy, Sz;
 };
 
@@ -64,9 +77,10 @@ __device__ __forceinline__ void ray_init(Ray &r, float ox, float oy, float oz, f
     const float gx = fabsf(dx) < 1e-30f ? copysignf(1e-30f, dx) : dx;
     const float gy = fabsf(dy) < 1e-30f ? copysignf(1e-30f, dy) : dy;
     const float gz = fabsf(dz) < 1e-30f ? copysignf(1e-30f, dz) : dz;
-    r.ix = __fdiv_rn(1.0f, gx);
-    r.iy = __fdiv_rn(1.0f, gy);
-    r.iz = __fdiv_rn(1.0f, gz);
+    r.ix = __frcp_rn(gx);
+    r.iy = __frcp_rn(gy);
+    r.iz = __frcp_rn(gz);
+    r.octant = (r.ix < 0.0f ? 1 : 0) | (r.iy < 0.0f ? 2 : 0) | (r.iz < 0.0f ? 4 : 0);
     int kz = 0;
     if (fabsf(dy) > fabsf(dx)) kz = 1;
     if (fabsf(dz) > fabsf(sel3(dx, dy, dz, kz))) kz = 2;
@@ -77,7 +91,7 @@ __device__ __forceinline__ void ray_init(Ray &r, float ox, float oy, float oz, f
     r.axes = kx | (ky << 2) | (kz << 4);
     r.Sx = __fdiv_rn(sel3(dx, dy, dz, kx), dkz);
     r.Sy = __fdiv_rn(sel3(dx, dy, dz, ky), dkz);
-    r.Sz = __fdiv_rn(1.0f, dkz);
+    r.Sz = __frcp_rn(dkz);
 }
 
 // Watertight ray/triangle test (Woop, Benthin, Wald, JCGT 2013). Returns the
@@ -119,10 +133,10 @@ __device__ __forceinline__ bool tri_intersect(const Ray &r, const float4 a, cons
 }
 
 // ---------------------------------------------------------------------------
-// Wide-BVH traversal without a stack: the pending children of every level
-// are an 8-bit mask packed into three 64-bit registers; returning to a level
-// follows the parent link and re-tests that node's pending children against
-// the current closest hit.
+// Wide-BVH traversal without a stack. The pending children of every level
+// are an 8-bit mask packed into two 64-bit registers (in the ray's visiting
+// order, see order_mask); returning to a level follows the parent link and
+// re-tests that node's pending children against the current closest hit.
 // ---------------------------------------------------------------------------
 struct Trail {
     uint64_t w0 = 0, w1 = 0;
@@ -151,154 +165,160 @@ __device__ __forceinline__ void take_hit(Hit &h, int32_t tri, int32_t prim, cons
     h.b2 = __fdiv_rn(tt.W, tt.det);
 }
 
-__device__ __forceinline__ const float4 *node_ptr(const TraceParams &P, const float4 *smem, int32_t n) {
-    return n < P.n_staged ? smem + (size_t)n * (sizeof(Node) / 16)
-                          : reinterpret_cast<const float4 *>(P.nodes + n);
+struct Work {
+    uint32_t nodes = 0, tris = 0;   // node visits (including re-tests) and triangle tests
+};
+
+struct Trav {
+    int32_t node;       // node to test next, -1 when the traversal has no node left
+    uint32_t mask;      // pending children (visiting order) of `node`; kFresh on a first visit
+    int32_t lvl;
+    int32_t steps;
+    int32_t leaf_node;  // node whose hit leaf children are pending
+    uint32_t leaves;    // pending leaf children of leaf_node (slot order)
+    Trail trail;
+};
+constexpr uint32_t kFresh = 0x1ffu;
+
+__device__ __forceinline__ void trav_init(Trav &s, Hit &h) {
+    s.node = 0; s.mask = kFresh; s.lvl = 0; s.steps = 0; s.leaf_node = 0; s.leaves = 0;
+    s.trail = Trail();
+    h.tri = -1; h.prim = INT32_MAX; h.t = FLT_MAX; h.b0 = h.b1 = h.b2 = 0.0f;
 }
 
-__device__ __forceinline__ float4 ld4(const float4 *p, bool shared) {
-    return shared ? *p : __ldg(p);
+__device__ __forceinline__ const float4 *node_ptr(const TraceParams &P, const float4 *smem, int32_t n) {
+    return n < P.n_staged ? smem + (size_t)n * kNodeVec : reinterpret_cast<const float4 *>(P.nodes + n);
+}
+
+__device__ __forceinline__ float4 ld4(const float4 *p, bool shared) { return shared ? *p : __ldg(p); }
+
+__device__ __forceinline__ int32_t ld1(const int32_t *p, bool shared) { return shared ? *p : __ldg(p); }
+
+__device__ __forceinline__ int32_t child_word(const TraceParams &P, const float4 *smem, int32_t n, int k) {
+    return ld1(reinterpret_cast<const int32_t *>(node_ptr(P, smem, n) + 12) + k, n < P.n_staged);
 }
 
 // Ize, "Robust BVH ray traversal" (JCGT 2013): scale the exit distance by
 // 1 + 2 gamma_3 so float rounding never rejects a box the ray touches.
 constexpr float kFarScale = 1.0f + 2.0f * (3.0f * 0x1p-24f) / (1.0f - 3.0f * 0x1p-24f);
 
-// Tests the children in `mask` of node n; returns the hit mask and entry
-// distances. Also returns the child words.
-__device__ __forceinline__ uint32_t test_node(const TraceParams &P, const float4 *smem, int32_t n, const Ray &r,
-                                              float tbest, uint32_t mask, float tnear[kWide],
-                                              int32_t child[kWide]) {
-    const float4 *p = node_ptr(P, smem, n);
-    const bool sh = n < P.n_staged;
-    float lox[8], hix[8], loy[8], hiy[8], loz[8], hiz[8];
-    {
-        const float4 a0 = ld4(p + 0, sh), a1 = ld4(p + 1, sh), b0 = ld4(p + 2, sh), b1 = ld4(p + 3, sh);
-        lox[0] = a0.x; lox[1] = a0.y; lox[2] = a0.z; lox[3] = a0.w; lox[4] = a1.x; lox[5] = a1.y; lox[6] = a1.z; lox[7] = a1.w;
-        hix[0] = b0.x; hix[1] = b0.y; hix[2] = b0.z; hix[3] = b0.w; hix[4] = b1.x; hix[5] = b1.y; hix[6] = b1.z; hix[7] = b1.w;
-    }
-    {
-        const float4 a0 = ld4(p + 4, sh), a1 = ld4(p + 5, sh), b0 = ld4(p + 6, sh), b1 = ld4(p + 7, sh);
-        loy[0] = a0.x; loy[1] = a0.y; loy[2] = a0.z; loy[3] = a0.w; loy[4] = a1.x; loy[5] = a1.y; loy[6] = a1.z; loy[7] = a1.w;
-        hiy[0] = b0.x; hiy[1] = b0.y; hiy[2] = b0.z; hiy[3] = b0.w; hiy[4] = b1.x; hiy[5] = b1.y; hiy[6] = b1.z; hiy[7] = b1.w;
-    }
-    {
-        const float4 a0 = ld4(p + 8, sh), a1 = ld4(p + 9, sh), b0 = ld4(p + 10, sh), b1 = ld4(p + 11, sh);
-        loz[0] = a0.x; loz[1] = a0.y; loz[2] = a0.z; loz[3] = a0.w; loz[4] = a1.x; loz[5] = a1.y; loz[6] = a1.z; loz[7] = a1.w;
-        hiz[0] = b0.x; hiz[1] = b0.y; hiz[2] = b0.z; hiz[3] = b0.w; hiz[4] = b1.x; hiz[5] = b1.y; hiz[6] = b1.z; hiz[7] = b1.w;
-    }
-    {
-        const int4 *cp = reinterpret_cast<const int4 *>(p + 12);
-        const int4 c0 = sh ? cp[0] : __ldg(cp), c1 = sh ? cp[1] : __ldg(cp + 1);
-        child[0] = c0.x; child[1] = c0.y; child[2] = c0.z; child[3] = c0.w;
-        child[4] = c1.x; child[5] = c1.y; child[6] = c1.z; child[7] = c1.w;
-    }
+// Slab test of 4 children (slots 4h .. 4h+3). The ray's near plane along an
+// axis is lo when it runs towards +a and hi otherwise, so the entry and exit
+// distances need no per-axis min/max: near and far planes are picked by
+// address (lo and hi of an axis are two 16-byte vectors apart).
+__device__ __forceinline__ uint32_t test4(const float4 *p, bool sh, const Ray &r, float tbest, int half) {
+    const int xn = (r.octant & 1) << 1, yn = 4 + (r.octant & 2), zn = 8 + ((r.octant & 4) >> 1);
+    const float4 nx = ld4(p + xn + half, sh), fx = ld4(p + (xn ^ 2) + half, sh);
+    const float4 ny = ld4(p + yn + half, sh), fy = ld4(p + (yn ^ 2) + half, sh);
+    const float4 nz = ld4(p + zn + half, sh), fz = ld4(p + (zn ^ 2) + half, sh);
+    const float a_nx[4] = {nx.x, nx.y, nx.z, nx.w}, a_fx[4] = {fx.x, fx.y, fx.z, fx.w};
+    const float a_ny[4] = {ny.x, ny.y, ny.z, ny.w}, a_fy[4] = {fy.x, fy.y, fy.z, fy.w};
+    const float a_nz[4] = {nz.x, nz.y, nz.z, nz.w}, a_fz[4] = {fz.x, fz.y, fz.z, fz.w};
     uint32_t hit = 0;
 #pragma unroll
-    for (int k = 0; k < kWide; ++k) {
-        const float t0x = (lox[k] - r.ox) * r.ix, t1x = (hix[k] - r.ox) * r.ix;
-        const float t0y = (loy[k] - r.oy) * r.iy, t1y = (hiy[k] - r.oy) * r.iy;
-        const float t0z = (loz[k] - r.oz) * r.iz, t1z = (hiz[k] - r.oz) * r.iz;
-        const float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), 0.0f));
-        const float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fmaxf(t0z, t1z)) * kFarScale;
-        tnear[k] = tn;
-        const bool h = ((mask >> k) & 1u) && child[k] != kEmptyChild && tn <= tf && tn <= tbest;
-        hit |= (h ? 1u : 0u) << k;
+    for (int k = 0; k < 4; ++k) {
+        const float tn = max3f((a_nx[k] - r.ox) * r.ix, (a_ny[k] - r.oy) * r.iy,
+                               fmaxf((a_nz[k] - r.oz) * r.iz, 0.0f));
+        const float tf = min3f((a_fx[k] - r.ox) * r.ix, (a_fy[k] - r.oy) * r.iy, (a_fz[k] - r.oz) * r.iz) *
+                         kFarScale;
+        hit |= (tn <= tf && tn <= tbest ? 1u : 0u) << k;
     }
     return hit;
 }
 
-__device__ __forceinline__ int pick_nearest(uint32_t m, const float tnear[kWide]) {
-    int best = -1;
-    float bt = FLT_MAX;
-#pragma unroll
-    for (int k = 0; k < kWide; ++k) {
-        if (((m >> k) & 1u) && (best < 0 || tnear[k] < bt)) { best = k; bt = tnear[k]; }
+// Child boxes of node n the ray enters before tbest (slot order).
+__device__ __forceinline__ uint32_t test_node(const TraceParams &P, const float4 *smem, int32_t n, const Ray &r,
+                                              float tbest) {
+    const float4 *p = node_ptr(P, smem, n);
+    const bool sh = n < P.n_staged;
+    return test4(p, sh, r, tbest, 0) | (test4(p, sh, r, tbest, 1) << 4);
+}
+
+// Mask in the ray's visiting order: slot s becomes bit s ^ octant, so the
+// lowest set bit is the child on the side the ray comes from.
+__device__ __forceinline__ uint32_t order_mask(uint32_t m, int oct) {
+    if (oct & 1) m = ((m & 0x55u) << 1) | ((m >> 1) & 0x55u);
+    if (oct & 2) m = ((m & 0x33u) << 2) | ((m >> 2) & 0x33u);
+    if (oct & 4) m = ((m & 0x0fu) << 4) | ((m >> 4) & 0x0fu);
+    return m;
+}
+
+// Test the children of s.node (all on a first visit, the pending ones on a
+// return); note hit leaves; descend to the first hit inner child in visiting
+// order, or climb to the nearest level with pending children.
+template <bool kCount>
+__device__ __forceinline__ void node_step(const TraceParams &P, const float4 *smem, const Ray &r, Trav &s, Hit &h,
+                                          Work &work) {
+    if (kCount) work.nodes += 1;
+    if (++s.steps > P.max_steps) {
+        atomicOr(P.err, kErrSteps);
+        s.node = -1; s.leaves = 0; h.tri = -1;
+        return;
     }
-    return best;
+    const uint32_t hit = test_node(P, smem, s.node, r, h.t);
+    const bool sh = s.node < P.n_staged;
+    const uint32_t inner = (uint32_t)ld1(reinterpret_cast<const int32_t *>(node_ptr(P, smem, s.node) + 14), sh);
+    if (s.mask == kFresh) {
+        const uint32_t leaves = hit & ~inner;
+        if (leaves) { s.leaf_node = s.node; s.leaves = leaves; }
+    }
+    const uint32_t cand = order_mask(hit & inner, r.octant) & s.mask;
+    if (cand) {
+        const int j = __ffs(cand) - 1;
+        s.trail.set(s.lvl, cand & ~(1u << j));
+        s.node = child_word(P, smem, s.node, j ^ r.octant);
+        s.mask = kFresh;
+        if (++s.lvl >= kMaxDepth) {
+            atomicOr(P.err, kErrDepth);
+            s.node = -1; s.leaves = 0; h.tri = -1;
+        }
+        return;
+    }
+    while (s.lvl > 0) {
+        --s.lvl;
+        s.node = __ldg(P.parent + s.node);
+        const uint32_t pend = s.trail.get(s.lvl);
+        if (pend) {
+            s.trail.set(s.lvl, 0);
+            s.mask = pend;
+            return;
+        }
+    }
+    s.node = -1;
 }
 
-__device__ __forceinline__ int32_t pick_child(const int32_t child[kWide], int k) {
-    int32_t c = child[0];
-#pragma unroll
-    for (int j = 1; j < kWide; ++j) c = (j == k) ? child[j] : c;
-    return c;
+// Test the triangles of one pending leaf child. Ties in t go to the lower
+// uploaded triangle index.
+template <bool kCount>
+__device__ __forceinline__ void leaf_step(const TraceParams &P, const float4 *smem, const Ray &r, Trav &s, Hit &h,
+                                          int32_t skip_tile, Work &work) {
+    const int k = __ffs(s.leaves) - 1;
+    s.leaves &= s.leaves - 1;
+    const int32_t code = -1 - child_word(P, smem, s.leaf_node, k);
+    const int32_t first = code >> 2, count = (code & 3) + 1;
+    for (int32_t i = first; i < first + count; ++i) {
+        const float4 *tp = reinterpret_cast<const float4 *>(P.tris + i);
+        const float4 a = __ldg(tp), b = __ldg(tp + 1), c = __ldg(tp + 2);
+        if (__float_as_int(b.w) == skip_tile) continue;
+        if (kCount) work.tris += 1;
+        TriTest tt;
+        if (!tri_intersect(r, a, b, c, tt)) continue;
+        const int32_t prim = __float_as_int(a.w);
+        if (tt.t < h.t || (tt.t == h.t && prim < h.prim)) take_hit(h, i, prim, tt);
+    }
 }
 
-// Closest hit excluding triangles of tile `skip_tile`. Ties in t go to the
-// lower uploaded triangle index.
-struct Work {
-    uint32_t nodes = 0, tris = 0;   // node visits (including re-tests) and triangle tests
-};
-
-template <bool kCount = false>
-__device__ __forceinline__ Hit closest_hit(const TraceParams &P, const float4 *smem, const Ray &r, int32_t skip_tile,
-                                           Work *work = nullptr) {
+// Closest hit excluding triangles of tile `skip_tile`, one ray at a time
+// (path record); the same steps as the tracing kernels, so the same hits.
+__device__ Hit closest_hit(const TraceParams &P, const float4 *smem, const Ray &r, int32_t skip_tile) {
+    Trav s;
     Hit h;
-    h.tri = -1; h.prim = INT32_MAX; h.t = FLT_MAX; h.b0 = h.b1 = h.b2 = 0.0f;
-    Trail trail;
-    int32_t node = 0;
-    int lvl = 0;
-    int steps = 0;
-    float tnear[kWide];
-    int32_t child[kWide];
+    Work work;
+    trav_init(s, h);
     while (true) {
-        if (++steps > P.max_steps) { atomicOr(P.err, kErrSteps); h.tri = -1; return h; }
-        if (kCount) work->nodes += 1;
-        uint32_t m = test_node(P, smem, node, r, h.t, 0xffu, tnear, child);
-        // leaves of this node first
-#pragma unroll
-        for (int k = 0; k < kWide; ++k) {
-            if (((m >> k) & 1u) && child[k] < 0) {
-                const int32_t code = -1 - child[k];
-                const int32_t first = code >> 2, count = (code & 3) + 1;
-                for (int32_t i = first; i < first + count; ++i) {
-                    const float4 *tp = reinterpret_cast<const float4 *>(P.tris + i);
-                    const float4 a = __ldg(tp), b = __ldg(tp + 1), c = __ldg(tp + 2);
-                    const int32_t tile = __float_as_int(b.w);
-                    if (tile == skip_tile) continue;
-                    TriTest tt;
-                    if (kCount) work->tris += 1;
-                    if (!tri_intersect(r, a, b, c, tt)) continue;
-                    const int32_t prim = __float_as_int(a.w);
-                    if (tt.t < h.t || (tt.t == h.t && prim < h.prim)) take_hit(h, i, prim, tt);
-                }
-            }
-        }
-        uint32_t inner = 0;
-#pragma unroll
-        for (int k = 0; k < kWide; ++k)
-            inner |= (((m >> k) & 1u) && child[k] >= 0 && tnear[k] <= h.t ? 1u : 0u) << k;
-        if (inner) {
-            const int k = pick_nearest(inner, tnear);
-            trail.set(lvl, inner & ~(1u << k));
-            node = pick_child(child, k);
-            ++lvl;
-            if (lvl >= kMaxDepth) { atomicOr(P.err, kErrDepth); h.tri = -1; return h; }
-            continue;
-        }
-        // backtrack to the nearest level with pending children
-        bool found = false;
-        while (lvl > 0) {
-            --lvl;
-            node = P.parent[node];
-            const uint32_t pend = trail.get(lvl);
-            if (pend == 0) continue;
-            if (++steps > P.max_steps) { atomicOr(P.err, kErrSteps); h.tri = -1; return h; }
-            if (kCount) work->nodes += 1;
-            const uint32_t again = test_node(P, smem, node, r, h.t, pend, tnear, child);
-            uint32_t live = 0;
-#pragma unroll
-            for (int k = 0; k < kWide; ++k) live |= (((again >> k) & 1u) && child[k] >= 0 ? 1u : 0u) << k;
-            if (!live) { trail.set(lvl, 0); continue; }
-            const int k = pick_nearest(live, tnear);
-            trail.set(lvl, live & ~(1u << k));
-            node = pick_child(child, k);
-            ++lvl;
-            found = true;
-            break;
-        }
-        if (!found) return h;
+        if (s.leaves) leaf_step<false>(P, smem, r, s, h, skip_tile, work);
+        else if (s.node >= 0) node_step<false>(P, smem, r, s, h, work);
+        else return h;
     }
 }
 
@@ -306,9 +326,8 @@ __device__ __forceinline__ Hit closest_hit(const TraceParams &P, const float4 *s
 // min(floor(u res), res - 1).
 __device__ __forceinline__ int64_t texel_of(const TraceParams &P, const Hit &h) {
     const TriHit &th = P.hits[h.tri];
-    const float b0 = h.b0, b1 = h.b1, b2 = h.b2;
-    float u = __fadd_rn(__fadd_rn(__fmul_rn(b0, th.uv[0]), __fmul_rn(b1, th.uv[2])), __fmul_rn(b2, th.uv[4]));
-    float v = __fadd_rn(__fadd_rn(__fmul_rn(b0, th.uv[1]), __fmul_rn(b1, th.uv[3])), __fmul_rn(b2, th.uv[5]));
+    float u = __fadd_rn(__fadd_rn(__fmul_rn(h.b0, th.uv[0]), __fmul_rn(h.b1, th.uv[2])), __fmul_rn(h.b2, th.uv[4]));
+    float v = __fadd_rn(__fadd_rn(__fmul_rn(h.b0, th.uv[1]), __fmul_rn(h.b1, th.uv[3])), __fmul_rn(h.b2, th.uv[5]));
     u = u < 0.0f ? 0.0f : (u > 1.0f ? 1.0f : u);
     v = v < 0.0f ? 0.0f : (v > 1.0f ? 1.0f : v);
     int32_t iu = (int32_t)floorf(__fmul_rn(u, (float)th.res_u));
@@ -320,19 +339,18 @@ __device__ __forceinline__ int64_t texel_of(const TraceParams &P, const Hit &h) 
 
 // Unit geometric normal of triangle `tri`, turned to face against w.
 __device__ __forceinline__ float3 facing_normal(const TraceParams &P, int32_t tri, float wx, float wy, float wz) {
-    const float4 *tp = reinterpret_cast<const float4 *>(P.tris + tri);
-    const float4 a = __ldg(tp), b = __ldg(tp + 1), c = __ldg(tp + 2);
-    const float e1x = b.x - a.x, e1y = b.y - a.y, e1z = b.z - a.z;
-    const float e2x = c.x - a.x, e2y = c.y - a.y, e2z = c.z - a.z;
-    float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
-    const float inv = rsqrtf(nx * nx + ny * ny + nz * nz);
-    nx *= inv; ny *= inv; nz *= inv;
+    const float *n = P.hits[tri].n;
+    float nx = __ldg(n), ny = __ldg(n + 1), nz = __ldg(n + 2);
     if (nx * wx + ny * wy + nz * wz > 0.0f) { nx = -nx; ny = -ny; nz = -nz; }
     return make_float3(nx, ny, nz);
 }
 
 __device__ __forceinline__ float albedo_of(const TraceParams &P, int32_t tri) {
     return __ldg(reinterpret_cast<const float *>(P.tris + tri) + 11);
+}
+
+__device__ __forceinline__ int32_t tile_of(const TraceParams &P, int32_t tri) {
+    return __ldg(reinterpret_cast<const int32_t *>(P.tris + tri) + 7);
 }
 
 // Quadratic spot soft edge in cos(theta) (Eq. S.11).
@@ -429,29 +447,6 @@ __device__ __forceinline__ void dflux(const LightDev &L, float phi_r, float a_em
     out[7] = scale * (-2.0f) * (c - L.co) * (c - L.ci) * L.sin_out * id3;
 }
 
-// Warp-aggregated fixed-point deposit: lanes depositing into the same texel
-// sum their values with shuffles; one 64-bit atomic per distinct texel.
-__device__ __forceinline__ void deposit(unsigned long long *q, bool dep, int64_t texel, unsigned long long val) {
-    const unsigned m = __ballot_sync(kFull, dep);
-    if (!dep) return;
-    const unsigned peers = __match_any_sync(m, (unsigned long long)texel);
-    unsigned long long tot = 0;
-    unsigned rest = peers;
-    while (rest) {
-        const int src = __ffs(rest) - 1;
-        tot += __shfl_sync(peers, val, src);
-        rest &= rest - 1;
-    }
-    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(q + texel, tot);
-}
-
-__device__ __forceinline__ void stage_nodes(const TraceParams &P, float4 *smem) {
-    const int n = P.n_staged * (int)(sizeof(Node) / 16);
-    const float4 *src = reinterpret_cast<const float4 *>(P.nodes);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) smem[i] = __ldg(src + i);
-    __syncthreads();
-}
-
 // Deposit from the lanes of the warp that are depositing in this step: lanes
 // that hit the same texel add their values with shuffles and one of them does
 // the 64-bit atomic.
@@ -468,6 +463,13 @@ __device__ __forceinline__ void deposit_active(unsigned long long *q, int64_t te
     if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(q + texel, tot);
 }
 
+__device__ __forceinline__ void stage_nodes(const TraceParams &P, float4 *smem) {
+    const int n = P.n_staged * kNodeVec;
+    const float4 *src = reinterpret_cast<const float4 *>(P.nodes);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) smem[i] = __ldg(src + i);
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // Forward / adjoint tracing. Every thread owns a contiguous chunk of photons
 // and advances its own path through a small state machine, one unit of work
@@ -476,93 +478,6 @@ __device__ __forceinline__ void deposit_active(unsigned long long *q, int64_t te
 // iteration the warp votes and runs the kind of step most of its lanes are
 // waiting for, so lanes never idle until a neighbour's path ends.
 // ---------------------------------------------------------------------------
-struct Trav {
-    int32_t node;       // node to test next, -1 when the traversal has no node left
-    uint32_t mask;      // children of `node` to test (all on a first visit)
-    int32_t lvl;
-    int32_t steps;
-    int32_t leaf_node;  // node whose hit leaf children are pending
-    uint32_t leaves;    // pending leaf children of leaf_node
-    Trail trail;
-};
-
-__device__ __forceinline__ void trav_init(Trav &s, Hit &h) {
-    s.node = 0; s.mask = 0xffu; s.lvl = 0; s.steps = 0; s.leaf_node = 0; s.leaves = 0;
-    s.trail = Trail();
-    h.tri = -1; h.prim = INT32_MAX; h.t = FLT_MAX; h.b0 = h.b1 = h.b2 = 0.0f;
-}
-
-__device__ __forceinline__ int32_t child_word(const TraceParams &P, const float4 *smem, int32_t n, int k) {
-    const int32_t *c = reinterpret_cast<const int32_t *>(node_ptr(P, smem, n) + 12) + k;
-    return n < P.n_staged ? *c : __ldg(c);
-}
-
-// Test the children of s.node selected by s.mask; note hit leaves; descend to
-// the nearest hit inner child or climb to the nearest level with pending ones.
-template <bool kCount>
-__device__ __forceinline__ void node_step(const TraceParams &P, const float4 *smem, const Ray &r, Trav &s, Hit &h,
-                                          Work &work) {
-    if (kCount) work.nodes += 1;
-    if (++s.steps > P.max_steps) {
-        atomicOr(P.err, kErrSteps);
-        s.node = -1; s.leaves = 0; h.tri = -1;
-        return;
-    }
-    float tnear[kWide];
-    int32_t child[kWide];
-    const uint32_t m = test_node(P, smem, s.node, r, h.t, s.mask, tnear, child);
-    uint32_t leaves = 0, inner = 0;
-#pragma unroll
-    for (int k = 0; k < kWide; ++k) {
-        const bool hit = (m >> k) & 1u;
-        leaves |= (hit && child[k] < 0 ? 1u : 0u) << k;
-        inner |= (hit && child[k] >= 0 && tnear[k] <= h.t ? 1u : 0u) << k;
-    }
-    if (leaves) { s.leaf_node = s.node; s.leaves = leaves; }
-    if (inner) {
-        const int k = pick_nearest(inner, tnear);
-        s.trail.set(s.lvl, inner & ~(1u << k));
-        s.node = pick_child(child, k);
-        s.mask = 0xffu;
-        if (++s.lvl >= kMaxDepth) {
-            atomicOr(P.err, kErrDepth);
-            s.node = -1; s.leaves = 0; h.tri = -1;
-        }
-        return;
-    }
-    while (s.lvl > 0) {
-        --s.lvl;
-        s.node = __ldg(P.parent + s.node);
-        const uint32_t pend = s.trail.get(s.lvl);
-        if (pend) {
-            s.trail.set(s.lvl, 0);
-            s.mask = pend;
-            return;
-        }
-    }
-    s.node = -1;
-}
-
-// Test the triangles of one pending leaf child.
-template <bool kCount>
-__device__ __forceinline__ void leaf_step(const TraceParams &P, const float4 *smem, const Ray &r, Trav &s, Hit &h,
-                                          int32_t skip_tile, Work &work) {
-    const int k = __ffs(s.leaves) - 1;
-    s.leaves &= s.leaves - 1;
-    const int32_t code = -1 - child_word(P, smem, s.leaf_node, k);
-    const int32_t first = code >> 2, count = (code & 3) + 1;
-    for (int32_t i = first; i < first + count; ++i) {
-        const float4 *tp = reinterpret_cast<const float4 *>(P.tris + i);
-        const float4 a = __ldg(tp), b = __ldg(tp + 1), c = __ldg(tp + 2);
-        if (__float_as_int(b.w) == skip_tile) continue;
-        if (kCount) work.tris += 1;
-        TriTest tt;
-        if (!tri_intersect(r, a, b, c, tt)) continue;
-        const int32_t prim = __float_as_int(a.w);
-        if (tt.t < h.t || (tt.t == h.t && prim < h.prim)) take_hit(h, i, prim, tt);
-    }
-}
-
 template <bool kAdjoint, bool kCount = false>
 __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(const TraceParams P) {
     extern __shared__ float4 smem[];
@@ -643,7 +558,7 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
                     cosine_dir(nrm, u.x, u.y, wx, wy, wz);
                     phi *= rho;                                                                 // Eq. 7
                     beta *= rho;
-                    skip = __ldg(reinterpret_cast<const int32_t *>(P.tris + h.tri) + 7);
+                    skip = tile_of(P, h.tri);
                     ray_init(r, xx, xy, xz, wx, wy, wz);
                     trav_init(s, h);
                     ++seg;
@@ -680,7 +595,8 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
     }
 }
 
-// Path record for debugging: one thread per photon.
+// Path record for debugging: one thread per photon, the same per-segment
+// arithmetic as the tracing kernels.
 __global__ void __launch_bounds__(128) paths_kernel(const TraceParams P, uint64_t count) {
     const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= count) return;
@@ -689,37 +605,42 @@ __global__ void __launch_bounds__(128) paths_kernel(const TraceParams P, uint64_
     const LightDev &L = P.lights[l];
     float wx, wy, wz, a_emit;
     const float2 u0 = uniforms(P.seed, photon, 0u, P.design);
-    const float phi_r = emit(L, u0.x, u0.y, wx, wy, wz, a_emit);
-    float ox = L.pos[0], oy = L.pos[1], oz = L.pos[2];
+    emit(L, u0.x, u0.y, wx, wy, wz, a_emit);
     int32_t skip = -1;
     int32_t *rt = P.rec_tri + k * P.max_hits;
     int64_t *rx = P.rec_texel + k * P.max_hits;
     for (int i = 0; i < P.max_hits; ++i) { rt[i] = -1; rx[i] = -1; }
-    float g = 0.0f, beta = 1.0f, dp[8];
-    for (int j = 0; j < 8; ++j) dp[j] = 0.0f;
+    float g = 0.0f, beta = 1.0f;
+    float x1x = 0.0f, x1y = 0.0f, x1z = 0.0f;
+    float3 n1 = make_float3(0.0f, 0.0f, 0.0f);
+    bool hit1 = false;
+    Ray r;
+    ray_init(r, L.pos[0], L.pos[1], L.pos[2], wx, wy, wz);
     for (int i = 1; i <= P.max_hits; ++i) {
-        Ray r;
-        ray_init(r, ox, oy, oz, wx, wy, wz);
         const Hit h = closest_hit(P, nullptr, r, skip);
         if (h.tri < 0) break;
         const int64_t texel = texel_of(P, h);
         rt[i - 1] = h.prim;
         rx[i - 1] = texel;
-        const float x1x = fmaf(h.t, wx, ox), x1y = fmaf(h.t, wy, oy), x1z = fmaf(h.t, wz, oz);
-        const float3 n = facing_normal(P, h.tri, wx, wy, wz);
+        const float xx = fmaf(h.t, r.dx, r.ox), xy = fmaf(h.t, r.dy, r.oy), xz = fmaf(h.t, r.dz, r.oz);
+        const float3 nrm = facing_normal(P, h.tri, r.dx, r.dy, r.dz);
         if (P.rec_grad) {
-            if (i == 1) dflux(L, phi_r, a_emit, x1x, x1y, x1z, n, dp);
+            if (i == 1) { x1x = xx; x1y = xy; x1z = xz; n1 = nrm; hit1 = true; }
             g += __ldg(P.w + texel) * beta;
         }
         if (i == P.max_hits) break;
         const float2 u = uniforms(P.seed, photon, (uint32_t)i, P.design);
-        cosine_dir(n, u.x, u.y, wx, wy, wz);
+        cosine_dir(nrm, u.x, u.y, wx, wy, wz);
         beta *= albedo_of(P, h.tri);
-        ox = x1x; oy = x1y; oz = x1z;
-        skip = __ldg(reinterpret_cast<const int32_t *>(P.tris + h.tri) + 7);
+        skip = tile_of(P, h.tri);
+        ray_init(r, xx, xy, xz, wx, wy, wz);
     }
-    if (P.rec_grad)
+    if (P.rec_grad) {
+        float dp[8];
+        for (int j = 0; j < 8; ++j) dp[j] = 0.0f;
+        if (hit1) dflux(L, L.flux_k * a_emit, a_emit, x1x, x1y, x1z, n1, dp);
         for (int j = 0; j < 8; ++j) P.rec_grad[k * 8 + j] = (double)(g * dp[j]);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -796,45 +717,40 @@ __global__ void __launch_bounds__(256) grad_finalize_kernel(const TraceParams P,
     }
 }
 
+template <class K>
+cudaError_t allow_smem(K kernel, size_t smem) {
+    if (smem <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
 }  // namespace
 
 int trace_kernel_max_threads() { return kTraceThreads; }
 
 cudaError_t trace_occupancy(bool adjoint, int block, size_t smem, int *blocks_per_sm) {
     auto fn = adjoint ? trace_kernel<true> : trace_kernel<false>;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = allow_smem(fn, smem);
+    if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem);
 }
 
 cudaError_t launch_forward(const TraceParams &p, int grid, int block, size_t smem, cudaStream_t s) {
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(trace_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = allow_smem(trace_kernel<false>, smem);
+    if (e != cudaSuccess) return e;
     trace_kernel<false><<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
 }
 
 cudaError_t launch_forward_counted(const TraceParams &p, int grid, int block, size_t smem, cudaStream_t s) {
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(trace_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = allow_smem(trace_kernel<false, true>, smem);
+    if (e != cudaSuccess) return e;
     trace_kernel<false, true><<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint(const TraceParams &p, int grid, int block, size_t smem, cudaStream_t s) {
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(trace_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = allow_smem(trace_kernel<true>, smem);
+    if (e != cudaSuccess) return e;
     trace_kernel<true><<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
 }
