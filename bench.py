@@ -273,30 +273,35 @@ def run_ours(args):
 
     # Work accounting (untimed): node visits and triangle tests per segment.
     work = tr.count_work(5, PHOTONS, HITS)
+    from paper_2310_02043_gb300 import shard
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     grad_dev = torch.zeros((lights.shape[0], 8), dtype=torch.float64, device="cuda")
     loss_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+    # Every rank traces its own range of one common photon budget (weak
+    # scaling: 2^24 photons per GPU); the integer texel sums and the gradients
+    # are summed across ranks.
+    n_total, p_begin, p_end = shard.photon_range(rank, world, PHOTONS)
     q_view = None
     if world > 1:
         ptr, _ = tr.texel_accumulator()
+        q_view = shard.device_view(ptr, T)
 
-        class _View:
-            __cuda_array_interface__ = {"shape": (T,), "typestr": "<i8", "data": (ptr, False), "version": 3}
+    def forward(seed):
+        tr.trace_forward(seed, n_total, HITS, p_begin, p_end)
+        if q_view is not None:
+            shard.allreduce_sum(q_view)
 
-        q_view = torch.as_tensor(_View(), device="cuda")
+    def adjoint(seed, out):
+        tr.trace_adjoint(seed, n_total, HITS, p_begin, p_end, out=out)
+        if world > 1 and not isinstance(out, np.ndarray):
+            shard.allreduce_sum(out)
 
     def step(k, grad_out, loss_out):
-        # Every rank traces its own photon budget; with several ranks the
-        # integer texel sums are added across ranks before the objective.
-        seed = 1000 + 7919 * k + 104729 * rank
-        tr.trace_forward(seed, PHOTONS, HITS)
-        if q_view is not None:
-            dist.all_reduce(q_view)
+        seed = 1000 + 7919 * k
+        forward(seed)
         tr.loss(out=loss_out)
-        tr.trace_adjoint(seed + 1, PHOTONS, HITS, out=grad_out)
-        if world > 1:
-            dist.all_reduce(grad_out)
+        adjoint(seed + 1, grad_out)
 
     for k in range(args.warmup):
         step(k, grad_dev, loss_dev)
@@ -315,15 +320,11 @@ def run_ours(args):
         flush.zero_()
         e = ev[k]
         e[0].record(stream)
-        tr.trace_forward(1000 + 7919 * (k + 50) + 104729 * rank, PHOTONS, HITS)
+        forward(1000 + 7919 * (k + 50))
         e[1].record(stream)
-        if q_view is not None:
-            dist.all_reduce(q_view)
         tr.loss(out=loss_dev)
         e[2].record(stream)
-        tr.trace_adjoint(1 + 1000 + 7919 * (k + 50) + 104729 * rank, PHOTONS, HITS, out=grad_dev)
-        if world > 1:
-            dist.all_reduce(grad_dev)
+        adjoint(1001 + 7919 * (k + 50), grad_dev)
         e[3].record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -354,15 +355,13 @@ def run_ours(args):
     t0 = time.perf_counter()
     for k in range(args.steps):
         tr.set_lights(pinned.numpy())
-        seed = 5000 + 7919 * k + 104729 * rank
-        tr.trace_forward(seed, PHOTONS, HITS)
-        if q_view is not None:
-            dist.all_reduce(q_view)
-        loss_host = tr.loss()
-        tr.trace_adjoint(seed + 1, PHOTONS, HITS, out=grad_host)
+        seed = 5000 + 7919 * k
+        forward(seed)
+        tr.loss()
+        adjoint(seed + 1, grad_host)
         if world > 1:
             gd = torch.from_numpy(grad_host).cuda()
-            dist.all_reduce(gd)
+            shard.allreduce_sum(gd)
             grad_host[:] = gd.cpu().numpy()
         cur = apply_update(cur, grad_host, opt)
         pinned.copy_(torch.from_numpy(cur))
