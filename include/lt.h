@@ -189,6 +189,39 @@ LT_API int lt_get_stats(void *ctx, lt_stats *out);
 LT_API int lt_count_work(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
                   uint64_t photon_end, uint64_t *counts_out);
 
+/* Objective and adjoint weights for callers that cannot allocate device
+ * memory. The paper has no counterpart: this is a deployment variant of
+ * lt_loss.
+ *
+ * Some callers must not call cudaMalloc: code running inside a memory pool
+ * that another framework owns (its allocator would not see the block), code
+ * inside a CUDA-graph capture, or a device already at its memory budget.
+ * This call allocates nothing. The caller passes every input and output as
+ * device pointers on `device`; the only scratch, one double per block of
+ * 4096 texels, lives in a fixed 32 KiB array compiled into the library, which
+ * every device that loads the library holds until the process exits.
+ *   q         [n_texels] int64 fixed-point texel sums (lt_texel_accumulator)
+ *   scale     their scale S > 0: E_t = q_t / (S A_t)
+ *   area      [n_texels] texel areas A_t (lt_texel_areas)
+ *   E_target  [n_texels] target E*_t; alpha [n_texels] weights, or NULL (ones)
+ *   w_out     [n_texels] adjoint weights alpha_t (E_t - E*_t)
+ *   E_out     [n_texels] irradiance E_t, or NULL
+ *   loss_out  one device double: O = 1/2 sum_t A_t alpha_t (E_t - E*_t)^2
+ * n_texels must lie in [1, LT_LOSS_STATIC_MAX_TEXELS]; larger inputs return
+ * LT_ERR_ARG (use lt_loss). Work is queued on cuda_stream, nothing is
+ * synchronised; the calling thread's current device is restored. The first
+ * call on a device looks up the array's device address
+ * (cudaGetSymbolAddress): make that first call before any stream capture.
+ * All calls on a device share the array -- nothing in it needs clearing, each
+ * call writes every slot it reads -- so calls that overlap on the GPU (two
+ * streams, two threads) race: order them on one stream. Returns only a
+ * status (there is no context for lt_last_error). O equals lt_loss's up to
+ * the order of the floating-point sum; w_out and E_out are the same values. */
+#define LT_LOSS_STATIC_MAX_TEXELS 16777216
+LT_API int lt_loss_static(int device, void *cuda_stream, const int64_t *q, double scale, const float *area,
+                          const float *E_target, const float *alpha, int64_t n_texels, float *w_out,
+                          float *E_out, double *loss_out);
+
 /* Launch shape of the tracing kernels: threads per block (multiple of 32,
  * <= 1024), blocks per SM (>= 1) and the shared-memory budget for staged BVH
  * nodes in bytes (0 = none). Zeros keep the current value. */

@@ -27,7 +27,7 @@ GRAD_N = 8
 EXPORTED = ("lt_version", "lt_create", "lt_destroy", "lt_set_stream", "lt_last_error", "lt_upload_scene",
             "lt_set_target", "lt_set_lights", "lt_trace_forward", "lt_texel_accumulator", "lt_get_texel_sums", "lt_loss",
             "lt_get_irradiance", "lt_texel_areas", "lt_set_adjoint_weights", "lt_trace_adjoint", "lt_debug_paths",
-            "lt_get_stats", "lt_set_launch", "lt_count_work")
+            "lt_get_stats", "lt_set_launch", "lt_count_work", "lt_loss_static")
 
 
 class LtError(RuntimeError):
@@ -90,6 +90,7 @@ def _declare(lib):
         "lt_get_stats": [vp, ctypes.POINTER(lt_stats)],
         "lt_set_launch": [vp, i32, i32, i32],
         "lt_count_work": [vp, u64, u64, i32, u64, u64, vp],
+        "lt_loss_static": [ci, vp, vp, ctypes.c_double, vp, vp, vp, i64, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -121,6 +122,23 @@ def lights_to_struct(lights: np.ndarray):
         out[i].yaw, out[i].pitch, out[i].p_int = float(row[4]), float(row[5]), float(row[6])
         out[i].theta_in, out[i].theta_out = float(row[7]), float(row[8])
     return out
+
+
+LOSS_STATIC_MAX_TEXELS = 16777216
+
+
+def loss_static(device: int, stream: int, q_ptr: int, scale: float, area, E_target, w_out, loss_out, alpha=None,
+                E_out=None):
+    """lt_loss_static: the objective and adjoint weights without any device
+    allocation (for callers that cannot allocate). All buffers are device
+    tensors; q_ptr is the device address of the int64 texel sums."""
+    lib = load_library()
+    n = int(area.numel())
+    rc = lib.lt_loss_static(device, ctypes.c_void_p(stream), ctypes.c_void_p(q_ptr), float(scale), _ptr(area)[0],
+                            _ptr(E_target)[0], _ptr(alpha)[0] if alpha is not None else None, n, _ptr(w_out)[0],
+                            _ptr(E_out)[0] if E_out is not None else None, _ptr(loss_out)[0])
+    if rc != LT_OK:
+        raise LtError(rc, "lt_loss_static failed")
 
 
 class Tracer:
