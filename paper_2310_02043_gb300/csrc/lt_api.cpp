@@ -54,7 +54,7 @@ struct Ctx {
     int32_t *d_err = nullptr;
     double *h_pinned = nullptr;            // small pinned staging area
     // launch
-    int threads = 256, blocks_per_sm = 0, smem_node_bytes = 48 * 1024;
+    int threads = 256, blocks_per_sm = 0, smem_node_bytes = 72 * 1024;
     lt_stats stats{};
 };
 
@@ -147,9 +147,18 @@ int upload_lights(Ctx *c, uint64_t n_photons) {
             d.co = (float)co;
             d.ci = (float)ci;
             d.inv_d = (float)(1.0 / (ci - co));
-            d.one_minus_co = (float)(1.0 - co);
+            d.k_cos = (float)(1.0 - co);
             d.sin_in = (float)std::sin((double)s.theta_in);
             d.sin_out = (float)std::sin((double)s.theta_out);
+        } else {
+            // point light: the whole sphere about the world z axis, no falloff
+            d.e1[0] = 1.0f; d.e1[1] = 0.0f; d.e1[2] = 0.0f;
+            d.e2[0] = 0.0f; d.e2[1] = 1.0f; d.e2[2] = 0.0f;
+            d.ns[0] = 0.0f; d.ns[1] = 0.0f; d.ns[2] = 1.0f;
+            d.k_cos = 2.0f;
+            d.ci = -2.0f;
+            d.co = -3.0f;
+            d.inv_d = 1.0f;
         }
         d.flux_k = (float)(I * omega / (double)nl);
         d.dflux_dp_k = (float)((double)s.p_int * omega / (double)nl);
@@ -166,18 +175,28 @@ int upload_lights(Ctx *c, uint64_t n_photons) {
     return LT_OK;
 }
 
+// Launch shape of a tracing kernel. The whole BVH is staged in shared memory
+// when it fits the budget, otherwise no node is (nodes then come through L1).
 int launch_shape(Ctx *c, bool adjoint, int *grid, size_t *smem, int32_t *n_staged) {
-    const int32_t fit = c->smem_node_bytes / (int)sizeof(Node);   // whole nodes that fit the budget
-    *n_staged = std::max(0, std::min(c->n_nodes, fit));
+    const bool staged = (int64_t)c->n_nodes * (int64_t)sizeof(Node) <= (int64_t)c->smem_node_bytes;
+    *n_staged = staged ? c->n_nodes : 0;
     *smem = (size_t)(*n_staged) * sizeof(Node);
     int bps = c->blocks_per_sm;
     if (bps <= 0) {
-        cudaError_t e = trace_occupancy(adjoint, c->threads, *smem, &bps);
+        cudaError_t e = trace_occupancy(adjoint, staged, c->threads, *smem, &bps);
         if (e != cudaSuccess) return cuda_fail(c, e, "occupancy query");
         if (bps < 1) return fail(c, LT_ERR_ARG, "launch shape does not fit on an SM");
     }
     *grid = c->sm_count * bps;
     return LT_OK;
+}
+
+// Upper bound on the step-loop iterations of a warp: every iteration
+// advances at least one of its 32 lanes by one step, and a lane needs at most
+// max_hits segments per photon, each at most max_steps node tests, 8 leaf
+// tests and one finish.
+uint64_t step_limit(const TraceParams &p) {
+    return 32ull * ((uint64_t)p.chunk * (uint64_t)p.max_hits * ((uint64_t)p.max_steps + kWide + 2) + 1);
 }
 
 uint64_t photon_chunk(uint64_t n, int grid, int threads) {
@@ -430,6 +449,7 @@ static int forward_pass(Ctx *c, uint64_t seed, uint64_t n_photons, int32_t max_h
     size_t smem;
     if ((rc = launch_shape(c, false, &grid, &smem, &p.n_staged))) return rc;
     p.chunk = photon_chunk(photon_end - photon_begin, grid, c->threads);
+    p.max_iters = step_limit(p);
     LT_CUDA(c, cudaMemsetAsync(c->d_q, 0, (size_t)c->n_texels * sizeof(unsigned long long), c->stream));
     LT_CUDA(c, cudaMemsetAsync(c->d_seg, 0, sizeof(unsigned long long), c->stream));
     if (d_work) {
@@ -574,6 +594,7 @@ int lt_trace_adjoint(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_h
     // Per-thread gradient slots: a thread's contiguous photon chunk touches at
     // most chunk / (fewest photons of a light) + 2 lights.
     p.chunk = photon_chunk(photon_end - photon_begin, grid, c->threads);
+    p.max_iters = step_limit(p);
     const uint64_t min_nl = n_photons / (uint64_t)L;
     p.n_slots = min_nl == 0 ? L : (int32_t)std::min<uint64_t>((uint64_t)L, p.chunk / min_nl + 2);
     const size_t need = (size_t)grid * (size_t)c->threads * (size_t)p.n_slots * 8 * sizeof(double);

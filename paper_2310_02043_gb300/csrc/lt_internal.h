@@ -12,7 +12,11 @@ namespace lt {
 
 constexpr int kWide = 8;                 // children per BVH node
 constexpr int kMaxDepth = 16;            // levels of wide nodes (8-bit pending masks in two u64 words)
-constexpr int kLeafMax = 3;              // triangles per leaf child
+#ifndef LT_LEAF_MAX
+#define LT_LEAF_MAX 3
+#endif
+constexpr int kLeafMax = LT_LEAF_MAX;    // triangles per leaf child (1..4)
+static_assert(kLeafMax >= 1 && kLeafMax <= 4, "leaf encoding holds 1..4 triangles");
 constexpr int32_t kEmptyChild = INT32_MIN;
 
 // 8-wide BVH node, 240 bytes. Child boxes are stored axis-major (twelve
@@ -67,7 +71,7 @@ struct alignas(16) LightDev {
     float ci;           // cos(theta_in)
     float dn_dpitch[3];
     float inv_d;        // 1 / (ci - co)
-    float one_minus_co;
+    float k_cos;        // emission cos = 1 - u1 k_cos: 2 (point), 1 - cos(theta_out) (spot)
     float sin_in;
     float sin_out;
     float pad0;
@@ -89,6 +93,7 @@ struct TraceParams {
     int32_t n_lights;
     int32_t max_hits;
     int32_t max_steps;          // node visits per ray before giving up (kErrSteps)
+    uint64_t max_iters;         // step-loop iterations per thread before giving up (kErrSteps)
     uint32_t design;
     uint64_t seed;
     uint64_t photon_begin, photon_end;
@@ -137,7 +142,7 @@ cudaError_t launch_resolve(const unsigned long long *q, const float *area, doubl
                            float *E_out, cudaStream_t s);
 cudaError_t launch_grad_finalize(const TraceParams &p, double *out, cudaStream_t s);
 int trace_kernel_max_threads();
-cudaError_t trace_occupancy(bool adjoint, int block, size_t smem, int *blocks_per_sm);
+cudaError_t trace_occupancy(bool adjoint, bool staged, int block, size_t smem, int *blocks_per_sm);
 
 // Wide-BVH builder (lt_bvh.cpp).
 struct BvhBuild {

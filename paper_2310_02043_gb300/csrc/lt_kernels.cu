@@ -186,16 +186,24 @@ __device__ __forceinline__ void trav_init(Trav &s, Hit &h) {
     h.tri = -1; h.prim = INT32_MAX; h.t = FLT_MAX; h.b0 = h.b1 = h.b2 = 0.0f;
 }
 
-__device__ __forceinline__ const float4 *node_ptr(const TraceParams &P, const float4 *smem, int32_t n) {
-    return n < P.n_staged ? smem + (size_t)n * kNodeVec : reinterpret_cast<const float4 *>(P.nodes + n);
+// Node loads: with kSmem every node of the BVH sits in shared memory (the
+// whole array was staged by the block); otherwise every node comes from
+// global memory through the read-only L1 path.
+template <bool kSmem>
+__device__ __forceinline__ float4 node_vec(const TraceParams &P, const float4 *smem, int32_t n, int v) {
+    if (kSmem) return smem[n * kNodeVec + v];
+    return __ldg(reinterpret_cast<const float4 *>(P.nodes + n) + v);
 }
 
-__device__ __forceinline__ float4 ld4(const float4 *p, bool shared) { return shared ? *p : __ldg(p); }
+template <bool kSmem>
+__device__ __forceinline__ int32_t node_word(const TraceParams &P, const float4 *smem, int32_t n, int w) {
+    if (kSmem) return reinterpret_cast<const int32_t *>(smem + n * kNodeVec)[w];
+    return __ldg(reinterpret_cast<const int32_t *>(P.nodes + n) + w);
+}
 
-__device__ __forceinline__ int32_t ld1(const int32_t *p, bool shared) { return shared ? *p : __ldg(p); }
-
+template <bool kSmem>
 __device__ __forceinline__ int32_t child_word(const TraceParams &P, const float4 *smem, int32_t n, int k) {
-    return ld1(reinterpret_cast<const int32_t *>(node_ptr(P, smem, n) + 12) + k, n < P.n_staged);
+    return node_word<kSmem>(P, smem, n, 48 + k);
 }
 
 // Ize, "Robust BVH ray traversal" (JCGT 2013): scale the exit distance by
@@ -206,11 +214,13 @@ constexpr float kFarScale = 1.0f + 2.0f * (3.0f * 0x1p-24f) / (1.0f - 3.0f * 0x1
 // axis is lo when it runs towards +a and hi otherwise, so the entry and exit
 // distances need no per-axis min/max: near and far planes are picked by
 // address (lo and hi of an axis are two 16-byte vectors apart).
-__device__ __forceinline__ uint32_t test4(const float4 *p, bool sh, const Ray &r, float tbest, int half) {
+template <bool kSmem>
+__device__ __forceinline__ uint32_t test4(const TraceParams &P, const float4 *smem, int32_t n, const Ray &r,
+                                          float tbest, int half) {
     const int xn = (r.octant & 1) << 1, yn = 4 + (r.octant & 2), zn = 8 + ((r.octant & 4) >> 1);
-    const float4 nx = ld4(p + xn + half, sh), fx = ld4(p + (xn ^ 2) + half, sh);
-    const float4 ny = ld4(p + yn + half, sh), fy = ld4(p + (yn ^ 2) + half, sh);
-    const float4 nz = ld4(p + zn + half, sh), fz = ld4(p + (zn ^ 2) + half, sh);
+    const float4 nx = node_vec<kSmem>(P, smem, n, xn + half), fx = node_vec<kSmem>(P, smem, n, (xn ^ 2) + half);
+    const float4 ny = node_vec<kSmem>(P, smem, n, yn + half), fy = node_vec<kSmem>(P, smem, n, (yn ^ 2) + half);
+    const float4 nz = node_vec<kSmem>(P, smem, n, zn + half), fz = node_vec<kSmem>(P, smem, n, (zn ^ 2) + half);
     const float a_nx[4] = {nx.x, nx.y, nx.z, nx.w}, a_fx[4] = {fx.x, fx.y, fx.z, fx.w};
     const float a_ny[4] = {ny.x, ny.y, ny.z, ny.w}, a_fy[4] = {fy.x, fy.y, fy.z, fy.w};
     const float a_nz[4] = {nz.x, nz.y, nz.z, nz.w}, a_fz[4] = {fz.x, fz.y, fz.z, fz.w};
@@ -227,11 +237,10 @@ __device__ __forceinline__ uint32_t test4(const float4 *p, bool sh, const Ray &r
 }
 
 // Child boxes of node n the ray enters before tbest (slot order).
+template <bool kSmem>
 __device__ __forceinline__ uint32_t test_node(const TraceParams &P, const float4 *smem, int32_t n, const Ray &r,
                                               float tbest) {
-    const float4 *p = node_ptr(P, smem, n);
-    const bool sh = n < P.n_staged;
-    return test4(p, sh, r, tbest, 0) | (test4(p, sh, r, tbest, 1) << 4);
+    return test4<kSmem>(P, smem, n, r, tbest, 0) | (test4<kSmem>(P, smem, n, r, tbest, 1) << 4);
 }
 
 // Mask in the ray's visiting order: slot s becomes bit s ^ octant, so the
@@ -246,7 +255,7 @@ __device__ __forceinline__ uint32_t order_mask(uint32_t m, int oct) {
 // Test the children of s.node (all on a first visit, the pending ones on a
 // return); note hit leaves; descend to the first hit inner child in visiting
 // order, or climb to the nearest level with pending children.
-template <bool kCount>
+template <bool kCount, bool kSmem>
 __device__ __forceinline__ void node_step(const TraceParams &P, const float4 *smem, const Ray &r, Trav &s, Hit &h,
                                           Work &work) {
     if (kCount) work.nodes += 1;
@@ -255,9 +264,8 @@ __device__ __forceinline__ void node_step(const TraceParams &P, const float4 *sm
         s.node = -1; s.leaves = 0; h.tri = -1;
         return;
     }
-    const uint32_t hit = test_node(P, smem, s.node, r, h.t);
-    const bool sh = s.node < P.n_staged;
-    const uint32_t inner = (uint32_t)ld1(reinterpret_cast<const int32_t *>(node_ptr(P, smem, s.node) + 14), sh);
+    const uint32_t hit = test_node<kSmem>(P, smem, s.node, r, h.t);
+    const uint32_t inner = (uint32_t)node_word<kSmem>(P, smem, s.node, 56);
     if (s.mask == kFresh) {
         const uint32_t leaves = hit & ~inner;
         if (leaves) { s.leaf_node = s.node; s.leaves = leaves; }
@@ -266,7 +274,7 @@ __device__ __forceinline__ void node_step(const TraceParams &P, const float4 *sm
     if (cand) {
         const int j = __ffs(cand) - 1;
         s.trail.set(s.lvl, cand & ~(1u << j));
-        s.node = child_word(P, smem, s.node, j ^ r.octant);
+        s.node = child_word<kSmem>(P, smem, s.node, j ^ r.octant);
         s.mask = kFresh;
         if (++s.lvl >= kMaxDepth) {
             atomicOr(P.err, kErrDepth);
@@ -289,12 +297,12 @@ __device__ __forceinline__ void node_step(const TraceParams &P, const float4 *sm
 
 // Test the triangles of one pending leaf child. Ties in t go to the lower
 // uploaded triangle index.
-template <bool kCount>
+template <bool kCount, bool kSmem>
 __device__ __forceinline__ void leaf_step(const TraceParams &P, const float4 *smem, const Ray &r, Trav &s, Hit &h,
                                           int32_t skip_tile, Work &work) {
     const int k = __ffs(s.leaves) - 1;
     s.leaves &= s.leaves - 1;
-    const int32_t code = -1 - child_word(P, smem, s.leaf_node, k);
+    const int32_t code = -1 - child_word<kSmem>(P, smem, s.leaf_node, k);
     const int32_t first = code >> 2, count = (code & 3) + 1;
     for (int32_t i = first; i < first + count; ++i) {
         const float4 *tp = reinterpret_cast<const float4 *>(P.tris + i);
@@ -316,8 +324,8 @@ __device__ Hit closest_hit(const TraceParams &P, const float4 *smem, const Ray &
     Work work;
     trav_init(s, h);
     while (true) {
-        if (s.leaves) leaf_step<false>(P, smem, r, s, h, skip_tile, work);
-        else if (s.node >= 0) node_step<false>(P, smem, r, s, h, work);
+        if (s.leaves) leaf_step<false, false>(P, smem, r, s, h, skip_tile, work);
+        else if (s.node >= 0) node_step<false, false>(P, smem, r, s, h, work);
         else return h;
     }
 }
@@ -370,42 +378,61 @@ __device__ __forceinline__ int32_t light_of(const TraceParams &P, uint64_t photo
     return lo;
 }
 
-// Exitant ray of light L: uniform sphere (point) or uniform outer cone (spot).
-__device__ __forceinline__ float emit(const LightDev &L, float u1, float u2, float &wx, float &wy, float &wz,
-                                      float &a) {
+// Direction with polar cosine c and sine s about n, azimuth 2 pi u2 measured
+// from t1 towards t2. Emission and bounces share it; its operations are
+// explicitly rounded so every kernel computes the same direction.
+__device__ __forceinline__ float3 frame_dir(float c, float s, float u2, float3 t1, float3 t2, float3 n) {
     float sp, cp;
     sincospif(2.0f * u2, &sp, &cp);
-    if (L.type == LT_SPOT) {
-        const float c = 1.0f - u1 * L.one_minus_co;
-        const float s = sqrtf(fmaxf(0.0f, 1.0f - c * c));
-        wx = s * cp * L.e1[0] + s * sp * L.e2[0] + c * L.ns[0];
-        wy = s * cp * L.e1[1] + s * sp * L.e2[1] + c * L.ns[1];
-        wz = s * cp * L.e1[2] + s * sp * L.e2[2] + c * L.ns[2];
-        a = falloff(L, c);
-        return L.flux_k * a;
-    }
-    const float c = 1.0f - 2.0f * u1;
-    const float s = sqrtf(fmaxf(0.0f, 1.0f - c * c));
-    wx = s * cp; wy = s * sp; wz = c;
-    a = 1.0f;
-    return L.flux_k;
+    const float a = __fmul_rn(s, cp), b = __fmul_rn(s, sp);
+    return make_float3(__fmaf_rn(c, n.x, __fmaf_rn(b, t2.x, __fmul_rn(a, t1.x))),
+                       __fmaf_rn(c, n.y, __fmaf_rn(b, t2.y, __fmul_rn(a, t1.y))),
+                       __fmaf_rn(c, n.z, __fmaf_rn(b, t2.z, __fmul_rn(a, t1.z))));
 }
 
-// Cosine-weighted direction about unit n (branchless orthonormal basis of
-// Duff et al., JCGT 2017).
-__device__ __forceinline__ void cosine_dir(float3 n, float u1, float u2, float &wx, float &wy, float &wz) {
+// Emission frame and polar cosine of light L: uniform sphere (point: the
+// world frame, cos = 1 - 2 u1) or uniform outer cone (spot: the axis frame,
+// cos = 1 - u1 (1 - cos theta_out)); the host stores k_cos = 2 or
+// 1 - cos theta_out and the world frame for point lights.
+__device__ __forceinline__ void emit_frame(const LightDev &L, float u1, float &c, float &s, float3 &t1, float3 &t2,
+                                           float3 &n) {
+    c = 1.0f - u1 * L.k_cos;
+    s = sqrtf(fmaxf(0.0f, 1.0f - c * c));
+    t1 = make_float3(L.e1[0], L.e1[1], L.e1[2]);
+    t2 = make_float3(L.e2[0], L.e2[1], L.e2[2]);
+    n = make_float3(L.ns[0], L.ns[1], L.ns[2]);
+}
+
+// Cosine-weighted lobe about unit n: cos = sqrt(1 - u1), sin = sqrt(u1), with
+// the branchless orthonormal basis of Duff et al. (JCGT 2017).
+__device__ __forceinline__ void bounce_frame(float3 n, float u1, float &c, float &s, float3 &t1, float3 &t2) {
     const float sgn = n.z >= 0.0f ? 1.0f : -1.0f;
     const float a = -1.0f / (sgn + n.z);
     const float b = n.x * n.y * a;
-    const float t1x = 1.0f + sgn * n.x * n.x * a, t1y = sgn * b, t1z = -sgn * n.x;
-    const float t2x = b, t2y = sgn + n.y * n.y * a, t2z = -n.y;
-    float sp, cp;
-    sincospif(2.0f * u2, &sp, &cp);
-    const float r = sqrtf(u1), z = sqrtf(1.0f - u1);
-    const float lx = r * cp, ly = r * sp;
-    wx = lx * t1x + ly * t2x + z * n.x;
-    wy = lx * t1y + ly * t2y + z * n.y;
-    wz = lx * t1z + ly * t2z + z * n.z;
+    t1 = make_float3(1.0f + sgn * n.x * n.x * a, sgn * b, -sgn * n.x);
+    t2 = make_float3(b, sgn + n.y * n.y * a, -n.y);
+    c = sqrtf(1.0f - u1);
+    s = sqrtf(u1);
+}
+
+// Exitant ray of light L and its flux Phi_r = flux_k a(theta).
+__device__ __forceinline__ float emit(const LightDev &L, float u1, float u2, float &wx, float &wy, float &wz,
+                                      float &a) {
+    float c, s;
+    float3 t1, t2, n;
+    emit_frame(L, u1, c, s, t1, t2, n);
+    const float3 w = frame_dir(c, s, u2, t1, t2, n);
+    wx = w.x; wy = w.y; wz = w.z;
+    a = falloff(L, c);
+    return L.flux_k * a;
+}
+
+__device__ __forceinline__ void cosine_dir(float3 n, float u1, float u2, float &wx, float &wy, float &wz) {
+    float c, s;
+    float3 t1, t2;
+    bounce_frame(n, u1, c, s, t1, t2);
+    const float3 w = frame_dir(c, s, u2, t1, t2, n);
+    wx = w.x; wy = w.y; wz = w.z;
 }
 
 // dPhi_r/dp at the first hit x1 (normal n1 facing the light), the hit held
@@ -478,10 +505,10 @@ __device__ __forceinline__ void stage_nodes(const TraceParams &P, float4 *smem) 
 // iteration the warp votes and runs the kind of step most of its lanes are
 // waiting for, so lanes never idle until a neighbour's path ends.
 // ---------------------------------------------------------------------------
-template <bool kAdjoint, bool kCount = false>
+template <bool kAdjoint, bool kCount, bool kSmem>
 __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(const TraceParams P) {
     extern __shared__ float4 smem[];
-    stage_nodes(P, smem);
+    if (kSmem) stage_nodes(P, smem);
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t n = P.photon_end - P.photon_begin;
     const uint64_t chunk = P.chunk;
@@ -503,28 +530,27 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
     unsigned long long segs = 0;
     bool active = photon < p_end;
 
-    // Emission of the current photon (Alg. 1: exitant ray carrying Phi_r).
-    auto start_photon = [&]() {
-        while (photon >= P.lights[l].end) ++l;
+    // Emission of the first photon (Alg. 1: exitant ray carrying Phi_r).
+    if (active) {
+        l = light_of(P, photon);
+        first_light = l;
         const LightDev &L = P.lights[l];
         const float2 u = uniforms(P.seed, photon, 0u, P.design);
         float wx, wy, wz;
         phi = emit(L, u.x, u.y, wx, wy, wz, a_emit);
         ray_init(r, L.pos[0], L.pos[1], L.pos[2], wx, wy, wz);
         seg = 1;
-        skip = -1;
-        g = 0.0f;
-        beta = 1.0f;
-        hit1 = false;
         trav_init(s, h);
-    };
-    if (active) {
-        l = light_of(P, photon);
-        first_light = l;
-        start_photon();
     }
 
+    uint64_t iters = 0;
     while (true) {
+        // Every lane runs every iteration, so this count is warp-uniform; it
+        // only trips if the step logic stops making progress.
+        if (++iters > P.max_iters) {
+            if ((threadIdx.x & 31) == 0) atomicOr(P.err, kErrSteps);
+            break;
+        }
         const bool can_leaf = active && s.leaves != 0;
         const bool can_node = active && !can_leaf && s.node >= 0;
         const bool fin = active && !can_leaf && s.node < 0;
@@ -533,39 +559,37 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
         const unsigned bf = __ballot_sync(kFull, fin);
         if ((bl | bn | bf) == 0u) break;
         const int nl = __popc(bl), nn = __popc(bn), nf = __popc(bf);
+        // The step kind with the most waiting lanes runs; it always has at
+        // least one lane, so every iteration advances some lane.
         if (nn >= nl && nn >= nf) {
-            if (can_node) node_step<kCount>(P, smem, r, s, h, work);
+            if (can_node) node_step<kCount, kSmem>(P, smem, r, s, h, work);
         } else if (nl >= nf) {
-            if (can_leaf) leaf_step<kCount>(P, smem, r, s, h, skip, work);
+            if (can_leaf) leaf_step<kCount, kSmem>(P, smem, r, s, h, skip, work);
         } else if (fin) {
-            // Finish the segment: one traced ray, hit or miss.
+            // Finish the segment (one traced ray, hit or miss), then start the
+            // next ray: a bounce from the hit or the next photon's emission.
             segs += 1;
-            bool next_seg = false;
+            bool bounce = false;
+            float3 x = make_float3(0.0f, 0.0f, 0.0f), nrm = make_float3(0.0f, 0.0f, 1.0f);
             if (h.tri >= 0) {
                 const int64_t texel = texel_of(P, h);
-                const float xx = fmaf(h.t, r.dx, r.ox), xy = fmaf(h.t, r.dy, r.oy), xz = fmaf(h.t, r.dz, r.oz);
-                const float3 nrm = facing_normal(P, h.tri, r.dx, r.dy, r.dz);
+                x = make_float3(fmaf(h.t, r.dx, r.ox), fmaf(h.t, r.dy, r.oy), fmaf(h.t, r.dz, r.oz));
+                nrm = facing_normal(P, h.tri, r.dx, r.dy, r.dz);
                 if (!kAdjoint) {
                     deposit_active(P.q, texel, (unsigned long long)__float2ll_rn(phi * P.scale));   // Eq. 8
                 } else {
-                    if (seg == 1) { x1x = xx; x1y = xy; x1z = xz; n1 = nrm; hit1 = true; }
+                    if (seg == 1) { x1x = x.x; x1y = x.y; x1z = x.z; n1 = nrm; hit1 = true; }
                     g += __ldg(P.w + texel) * beta;                                             // Eq. 12
                 }
                 if (seg < P.max_hits) {
                     const float rho = albedo_of(P, h.tri);
-                    const float2 u = uniforms(P.seed, photon, (uint32_t)seg, P.design);
-                    float wx, wy, wz;
-                    cosine_dir(nrm, u.x, u.y, wx, wy, wz);
                     phi *= rho;                                                                 // Eq. 7
                     beta *= rho;
                     skip = tile_of(P, h.tri);
-                    ray_init(r, xx, xy, xz, wx, wy, wz);
-                    trav_init(s, h);
-                    ++seg;
-                    next_seg = true;
+                    bounce = true;
                 }
             }
-            if (!next_seg) {
+            if (!bounce) {
                 if (kAdjoint && hit1) {
                     // Eq. 11: this photon's dO/dPhi_r * dPhi_r/dp into its light's slot
                     const LightDev &L = P.lights[l];
@@ -576,7 +600,33 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
                     for (int k = 0; k < 8; ++k) o[k] += (double)(g * dp[k]);
                 }
                 ++photon;
-                if (photon < p_end) start_photon(); else active = false;
+                if (photon >= p_end) active = false;
+            }
+            if (active) {
+                float c, sn;
+                float3 t1, t2, axis, org;
+                const float2 u = uniforms(P.seed, photon, bounce ? (uint32_t)seg : 0u, P.design);
+                if (bounce) {
+                    bounce_frame(nrm, u.x, c, sn, t1, t2);
+                    axis = nrm;
+                    org = x;
+                    ++seg;
+                } else {
+                    while (photon >= P.lights[l].end) ++l;
+                    const LightDev &L = P.lights[l];
+                    emit_frame(L, u.x, c, sn, t1, t2, axis);
+                    org = make_float3(L.pos[0], L.pos[1], L.pos[2]);
+                    a_emit = falloff(L, c);
+                    phi = L.flux_k * a_emit;
+                    seg = 1;
+                    skip = -1;
+                    g = 0.0f;
+                    beta = 1.0f;
+                    hit1 = false;
+                }
+                const float3 w = frame_dir(c, sn, u.y, t1, t2, axis);
+                ray_init(r, org.x, org.y, org.z, w.x, w.y, w.z);
+                trav_init(s, h);
             }
         }
     }
@@ -727,32 +777,36 @@ cudaError_t allow_smem(K kernel, size_t smem) {
 
 int trace_kernel_max_threads() { return kTraceThreads; }
 
-cudaError_t trace_occupancy(bool adjoint, int block, size_t smem, int *blocks_per_sm) {
-    auto fn = adjoint ? trace_kernel<true> : trace_kernel<false>;
+// The kernel instantiation for a launch: all nodes in shared memory when the
+// launch stages the whole BVH, otherwise none.
+template <bool kAdjoint, bool kCount>
+cudaError_t launch_trace(const TraceParams &p, int grid, int block, size_t smem, cudaStream_t s) {
+    const bool staged = p.n_staged > 0;
+    auto fn = staged ? trace_kernel<kAdjoint, kCount, true> : trace_kernel<kAdjoint, kCount, false>;
+    cudaError_t e = allow_smem(fn, smem);
+    if (e != cudaSuccess) return e;
+    fn<<<grid, block, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t trace_occupancy(bool adjoint, bool staged, int block, size_t smem, int *blocks_per_sm) {
+    auto fn = adjoint ? (staged ? trace_kernel<true, false, true> : trace_kernel<true, false, false>)
+                      : (staged ? trace_kernel<false, false, true> : trace_kernel<false, false, false>);
     cudaError_t e = allow_smem(fn, smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem);
 }
 
 cudaError_t launch_forward(const TraceParams &p, int grid, int block, size_t smem, cudaStream_t s) {
-    cudaError_t e = allow_smem(trace_kernel<false>, smem);
-    if (e != cudaSuccess) return e;
-    trace_kernel<false><<<grid, block, smem, s>>>(p);
-    return cudaGetLastError();
+    return launch_trace<false, false>(p, grid, block, smem, s);
 }
 
 cudaError_t launch_forward_counted(const TraceParams &p, int grid, int block, size_t smem, cudaStream_t s) {
-    cudaError_t e = allow_smem(trace_kernel<false, true>, smem);
-    if (e != cudaSuccess) return e;
-    trace_kernel<false, true><<<grid, block, smem, s>>>(p);
-    return cudaGetLastError();
+    return launch_trace<false, true>(p, grid, block, smem, s);
 }
 
 cudaError_t launch_adjoint(const TraceParams &p, int grid, int block, size_t smem, cudaStream_t s) {
-    cudaError_t e = allow_smem(trace_kernel<true>, smem);
-    if (e != cudaSuccess) return e;
-    trace_kernel<true><<<grid, block, smem, s>>>(p);
-    return cudaGetLastError();
+    return launch_trace<true, false>(p, grid, block, smem, s);
 }
 
 cudaError_t launch_paths(const TraceParams &p, uint64_t count, cudaStream_t s) {
