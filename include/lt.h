@@ -189,6 +189,51 @@ LT_API int lt_get_stats(void *ctx, lt_stats *out);
 LT_API int lt_count_work(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
                   uint64_t photon_end, uint64_t *counts_out);
 
+/* Philox design word (counter word 3) of the single-design passes; default
+ * 0. A design traced in a batch (lt_batch_*) as design d follows the same
+ * photon paths as a single-design pass with design word d; its irradiance,
+ * objective and gradient agree with that pass up to the rounding of the
+ * fixed-point scale (a batch sizes one power-of-two scale for its brightest
+ * design). */
+LT_API int lt_set_design(void *ctx, uint32_t design);
+
+/* ---- Batched designs -----------------------------------------------------
+ * Many candidate lighting designs of one scene, with uneven light counts,
+ * traced in one launch per pass: design d owns photons [d N, (d + 1) N) of
+ * the launch (N photons per design, split evenly over its lights) and its
+ * own texel sums, irradiance, weights and objective against the shared
+ * target (lt_set_target). The Philox design word of design d is d. A step
+ * uploads the lights and seeds, runs the forward pass, the per-design
+ * objective and the adjoint pass, and returns the objectives and gradients.
+ * It can run as a captured CUDA graph, instantiated on the first such step
+ * and replayed afterwards (seeds and the fixed-point scale are read from
+ * device memory the graph refreshes, so one graph serves every step; it is
+ * rebuilt after lt_set_launch or lt_batch_setup). Batch work runs on the
+ * context's own non-blocking stream and every step synchronises it; do not
+ * overlap batch steps with single-design passes of the same context. */
+#define LT_MAX_BATCH_LIGHTS 65536
+
+/* Allocate a batch: n_designs designs with lights_per_design[d] >= 1 lights
+ * each (at most LT_MAX_BATCH_LIGHTS in total), photons_per_design photons and
+ * max_hits hits per photon. Needs an uploaded scene; replaces a previous
+ * batch. Device memory: n_designs x n_texels x 16 bytes plus small buffers. */
+LT_API int lt_batch_setup(void *ctx, int32_t n_designs, const int32_t *lights_per_design,
+                          uint64_t photons_per_design, int32_t max_hits);
+
+/* Lights of every design, concatenated in design order (host, copied). */
+LT_API int lt_batch_set_lights(void *ctx, const lt_light *lights);
+
+/* One step: forward (seed_fwd), objective, adjoint (seed_adj). Writes the
+ * objective of every design to loss_out [n_designs] and dO/dp of every light
+ * to grad_out [total lights][LT_GRAD_N] (host, either may be NULL).
+ * use_graph = 1 replays a captured CUDA graph of the step. */
+LT_API int lt_batch_step(void *ctx, uint64_t seed_fwd, uint64_t seed_adj, double *loss_out, double *grad_out,
+                         int use_graph);
+
+/* Texel sums (int64) and irradiance (float) of one design after a step. */
+LT_API int lt_batch_texel_sums(void *ctx, int32_t design, int64_t *q_out, int is_device);
+LT_API int lt_batch_irradiance(void *ctx, int32_t design, float *E_out, int is_device);
+
 /* Objective and adjoint weights for callers that cannot allocate device
  * memory. The paper has no counterpart: this is a deployment variant of
  * lt_loss.

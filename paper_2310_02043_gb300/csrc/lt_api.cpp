@@ -36,6 +36,7 @@ struct Ctx {
     bool has_target = false, has_alpha = false;
     // lights
     std::vector<lt_light> lights;
+    uint32_t design_word = 0;          // Philox counter word 3 of the single-design passes
     LightDev *d_lights = nullptr;       // [LT_MAX_LIGHTS]
     LightDev *h_lights = nullptr;       // pinned staging of the same size
     cudaEvent_t lights_copied = nullptr;
@@ -56,6 +57,26 @@ struct Ctx {
     // launch
     int threads = 256, blocks_per_sm = 0, smem_node_bytes = 72 * 1024;
     lt_stats stats{};
+    bool seg_single = true;                // segment counters in d_seg belong to the last pass
+    // batched designs (lt_batch_*)
+    struct Batch {
+        int32_t n_designs = 0, n_lights = 0, max_hits = 0;
+        uint64_t photons = 0;                 // per design
+        std::vector<int32_t> counts;          // lights per design
+        std::vector<lt_light> lights;         // concatenated
+        bool has_lights = false;
+        cudaStream_t stream = nullptr;        // private, capturable
+        unsigned char *d_in = nullptr;        // StepHeader + LightDev[n_lights]
+        unsigned char *h_in = nullptr;        // pinned copy the step uploads
+        double *h_out = nullptr;              // pinned: loss[n_designs], grad[n_lights][8]
+        unsigned long long *d_q = nullptr;
+        float *d_E = nullptr, *d_w = nullptr;
+        double *d_partial = nullptr, *d_loss = nullptr, *d_grad = nullptr, *d_slots = nullptr;
+        size_t in_bytes = 0, slots_bytes = 0;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        uint64_t segments = 0;
+    } batch;
 };
 
 int fail(Ctx *c, int code, const std::string &msg) {
@@ -113,21 +134,20 @@ int copy_out(Ctx *c, void *dst, const void *src, size_t bytes, int is_device) {
     return LT_OK;
 }
 
-// Per-light constants for a photon budget n (Sec. 4.4 and the supplement):
-// I_e = p^2 / 2; Phi_r = I_e Omega a / N_l with Omega = 4 pi (point) or
-// 2 pi (1 - cos theta_out) (spot).
-int upload_lights(Ctx *c, uint64_t n_photons) {
-    if (!c->lights_dirty && c->lights_for_n == n_photons) return LT_OK;
-    const int32_t L = (int32_t)c->lights.size();
-    // the previous copy out of the staging buffer must be done before reuse
-    LT_CUDA(c, cudaEventSynchronize(c->lights_copied));
-    LightDev *h = c->h_lights;
+// Per-light constants of one design whose photon budget n is split evenly
+// over its L lights (Sec. 4.4 and the supplement): I_e = p^2 / 2,
+// Phi_r = I_e Omega a / N_l with Omega = 4 pi (point) or 2 pi (1 - cos
+// theta_out) (spot). The design's photons are global indices
+// [photon_base, photon_base + n); its texel arrays start at texel_base.
+// Returns the design's power bound sum_l I_l Omega_l.
+double derive_lights(const lt_light *in, int32_t L, uint64_t n_photons, uint64_t photon_base, uint64_t texel_base,
+                     uint32_t design, LightDev *out) {
     const uint64_t base = n_photons / (uint64_t)L, rem = n_photons % (uint64_t)L;
-    uint64_t first = 0;
+    uint64_t first = photon_base;
     double bound = 0.0;
     for (int32_t l = 0; l < L; ++l) {
-        const lt_light &s = c->lights[l];
-        LightDev &d = h[l];
+        const lt_light &s = in[l];
+        LightDev &d = out[l];
         std::memset(&d, 0, sizeof(d));
         const uint64_t nl = base + ((uint64_t)l < rem ? 1u : 0u);
         const double I = 0.5 * (double)s.p_int * (double)s.p_int;
@@ -160,13 +180,26 @@ int upload_lights(Ctx *c, uint64_t n_photons) {
             d.co = -3.0f;
             d.inv_d = 1.0f;
         }
-        d.flux_k = (float)(I * omega / (double)nl);
-        d.dflux_dp_k = (float)((double)s.p_int * omega / (double)nl);
+        d.flux_k = nl ? (float)(I * omega / (double)nl) : 0.0f;
+        d.dflux_dp_k = nl ? (float)((double)s.p_int * omega / (double)nl) : 0.0f;
         d.first = first;
         d.end = first + nl;
+        d.design = design;
+        d.photon_base = photon_base;
+        d.texel_base = texel_base;
         first += nl;
         bound += I * omega;
     }
+    return bound;
+}
+
+int upload_lights(Ctx *c, uint64_t n_photons) {
+    if (!c->lights_dirty && c->lights_for_n == n_photons) return LT_OK;
+    const int32_t L = (int32_t)c->lights.size();
+    // the previous copy out of the staging buffer must be done before reuse
+    LT_CUDA(c, cudaEventSynchronize(c->lights_copied));
+    LightDev *h = c->h_lights;
+    const double bound = derive_lights(c->lights.data(), L, n_photons, 0, 0, c->design_word, h);
     LT_CUDA(c, cudaMemcpyAsync(c->d_lights, h, sizeof(LightDev) * (size_t)L, cudaMemcpyHostToDevice, c->stream));
     LT_CUDA(c, cudaEventRecord(c->lights_copied, c->stream));
     c->lights_for_n = n_photons;
@@ -216,7 +249,7 @@ TraceParams base_params(Ctx *c, uint64_t seed, int32_t max_hits, uint64_t begin,
     p.n_lights = (int32_t)c->lights.size();
     p.max_hits = max_hits;
     p.max_steps = 16 * c->n_nodes + 64;
-    p.design = 0;
+    p.hdr = nullptr;
     p.seed = seed;
     p.photon_begin = begin;
     p.photon_end = end;
@@ -231,6 +264,122 @@ int check_trace_args(Ctx *c, uint64_t n_photons, int32_t max_hits, uint64_t begi
     if (n_photons == 0) return fail(c, LT_ERR_ARG, "n_photons must be positive");
     if (max_hits < 1 || max_hits > 64) return fail(c, LT_ERR_ARG, "max_hits must be in [1, 64]");
     if (begin > end || end > n_photons) return fail(c, LT_ERR_ARG, "photon range outside [0, n_photons]");
+    return LT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched designs
+// ---------------------------------------------------------------------------
+constexpr size_t kHdrBytes = 256;   // StepHeader, then the light records
+
+void batch_drop_graph(Ctx *c) {
+    if (c->batch.exec) cudaGraphExecDestroy(c->batch.exec);
+    if (c->batch.graph) cudaGraphDestroy(c->batch.graph);
+    c->batch.exec = nullptr;
+    c->batch.graph = nullptr;
+}
+
+void batch_free(Ctx *c) {
+    Ctx::Batch &b = c->batch;
+    if (b.stream) cudaStreamSynchronize(b.stream);
+    batch_drop_graph(c);
+    dfree(b.d_in); dfree(b.d_q); dfree(b.d_E); dfree(b.d_w); dfree(b.d_partial); dfree(b.d_loss); dfree(b.d_grad);
+    dfree(b.d_slots);
+    if (b.h_in) cudaFreeHost(b.h_in);
+    if (b.h_out) cudaFreeHost(b.h_out);
+    if (b.stream) cudaStreamDestroy(b.stream);
+    b = Ctx::Batch();
+}
+
+struct BatchLaunch {
+    TraceParams fwd, adj;
+    LossParams loss;
+    int grid_f, grid_a;
+    size_t smem_f, smem_a;
+};
+
+// Launch parameters of a batch step; grows the gradient slots if needed.
+// Runs before any stream capture (it may allocate).
+int batch_prepare(Ctx *c, BatchLaunch *bl) {
+    Ctx::Batch &b = c->batch;
+    const uint64_t n_total = b.photons * (uint64_t)b.n_designs;
+    const StepHeader *hdr = reinterpret_cast<const StepHeader *>(b.d_in);
+    const LightDev *lights = reinterpret_cast<const LightDev *>(b.d_in + kHdrBytes);
+    int rc;
+    bl->fwd = base_params(c, 0, b.max_hits, 0, n_total);
+    bl->fwd.lights = lights;
+    bl->fwd.n_lights = b.n_lights;
+    bl->fwd.hdr = hdr;
+    bl->fwd.q = b.d_q;
+    bl->fwd.segments = reinterpret_cast<unsigned long long *>(b.d_grad + (size_t)b.n_lights * 8);
+    if ((rc = launch_shape(c, false, &bl->grid_f, &bl->smem_f, &bl->fwd.n_staged))) return rc;
+    bl->fwd.chunk = photon_chunk(n_total, bl->grid_f, c->threads);
+    bl->fwd.max_iters = step_limit(bl->fwd);
+    bl->adj = bl->fwd;
+    bl->adj.q = nullptr;
+    bl->adj.w = b.d_w;
+    bl->adj.segments = bl->fwd.segments + 1;
+    if ((rc = launch_shape(c, true, &bl->grid_a, &bl->smem_a, &bl->adj.n_staged))) return rc;
+    bl->adj.chunk = photon_chunk(n_total, bl->grid_a, c->threads);
+    bl->adj.max_iters = step_limit(bl->adj);
+    int32_t max_count = 1;
+    for (int32_t n : b.counts) max_count = std::max(max_count, n);
+    const uint64_t min_nl = b.photons / (uint64_t)max_count;
+    bl->adj.n_slots = min_nl == 0 ? b.n_lights
+                                  : (int32_t)std::min<uint64_t>((uint64_t)b.n_lights, bl->adj.chunk / min_nl + 2);
+    const size_t need = (size_t)bl->grid_a * (size_t)c->threads * (size_t)bl->adj.n_slots * 8 * sizeof(double);
+    if (need > b.slots_bytes) {
+        LT_CUDA(c, cudaStreamSynchronize(b.stream));
+        dfree(b.d_slots);
+        LT_CUDA(c, cudaMalloc(&b.d_slots, need));
+        b.slots_bytes = need;
+        batch_drop_graph(c);
+    }
+    bl->adj.slots = b.d_slots;
+    LossParams &lp = bl->loss;
+    lp.q = b.d_q;
+    lp.E_target = c->d_target;
+    lp.alpha = c->has_alpha ? c->d_alpha : nullptr;
+    lp.area = c->d_area;
+    lp.inv_scale = 0.0;
+    lp.hdr = hdr;
+    lp.n_texels = c->n_texels;
+    lp.n_designs = b.n_designs;
+    lp.E_out = b.d_E;
+    lp.w_out = b.d_w;
+    lp.partial = b.d_partial;
+    lp.loss_out = b.d_loss;
+    return LT_OK;
+}
+
+// The work of one step, in stream order: lights and header in, forward,
+// objective per design, adjoint, gradient sums, results out to pinned memory.
+int batch_issue(Ctx *c, const BatchLaunch &bl) {
+    Ctx::Batch &b = c->batch;
+    const cudaStream_t s = b.stream;
+    const size_t T = (size_t)c->n_texels, D = (size_t)b.n_designs, L = (size_t)b.n_lights;
+    LT_CUDA(c, cudaMemcpyAsync(b.d_in, b.h_in, b.in_bytes, cudaMemcpyHostToDevice, s));
+    LT_CUDA(c, cudaMemsetAsync(b.d_q, 0, D * T * sizeof(unsigned long long), s));
+    LT_CUDA(c, cudaMemsetAsync(bl.fwd.segments, 0, 2 * sizeof(unsigned long long), s));
+    LT_CUDA(c, launch_forward(bl.fwd, bl.grid_f, c->threads, bl.smem_f, s));
+    LT_CUDA(c, launch_loss(bl.loss, s));
+    LT_CUDA(c, launch_adjoint(bl.adj, bl.grid_a, c->threads, bl.smem_a, s));
+    LT_CUDA(c, launch_grad_finalize(bl.adj, b.d_grad, s));
+    LT_CUDA(c, cudaMemcpyAsync(b.h_out, b.d_loss, D * sizeof(double), cudaMemcpyDeviceToHost, s));
+    LT_CUDA(c, cudaMemcpyAsync(b.h_out + D, b.d_grad, (L * 8 + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    return LT_OK;
+}
+
+int batch_check_device(Ctx *c) {
+    int32_t e = 0;
+    LT_CUDA(c, cudaMemcpyAsync(&e, c->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, c->batch.stream));
+    LT_CUDA(c, cudaStreamSynchronize(c->batch.stream));
+    if (e) {
+        LT_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), c->batch.stream));
+        LT_CUDA(c, cudaStreamSynchronize(c->batch.stream));
+        if (e & kErrSteps) return fail(c, LT_ERR_TIMEOUT, "a ray exceeded its traversal step limit");
+        return fail(c, LT_ERR_DEVICE, "kernel error word " + std::to_string(e));
+    }
     return LT_OK;
 }
 
@@ -283,6 +432,7 @@ int lt_destroy(void *ctx) {
     dfree(c->d_target); dfree(c->d_alpha); dfree(c->d_lights); dfree(c->d_q); dfree(c->d_E); dfree(c->d_w);
     dfree(c->d_loss); dfree(c->d_partial); dfree(c->d_grad); dfree(c->d_slots); dfree(c->d_seg);
     dfree(c->d_err);
+    batch_free(c);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     if (c->h_lights) cudaFreeHost(c->h_lights);
     if (c->lights_copied) cudaEventDestroy(c->lights_copied);
@@ -358,6 +508,7 @@ int lt_upload_scene(void *ctx, const float *tri_xyz, const float *tri_uv, const 
         std::fill(area.begin() + off[k], area.begin() + off[k + 1], a);
     }
     LT_CUDA(c, cudaStreamSynchronize(c->stream));
+    batch_free(c);     // batch buffers are sized by the old texel count
     LT_CUDA(c, dalloc(c->d_nodes, bvh.nodes.size()));
     LT_CUDA(c, dalloc(c->d_parent, bvh.parent.size()));
     LT_CUDA(c, dalloc(c->d_tris, (size_t)n_tri));
@@ -460,6 +611,7 @@ static int forward_pass(Ctx *c, uint64_t seed, uint64_t n_photons, int32_t max_h
     }
     c->fwd_done = true;
     c->has_w = false;
+    c->seg_single = true;
     c->stats.photons_forward = photon_end - photon_begin;
     c->stats.staged_nodes = p.n_staged;
     c->stats.fixed_point_scale = S;
@@ -530,7 +682,9 @@ int lt_loss(void *ctx, double *loss_out, int is_device) {
     p.alpha = c->has_alpha ? c->d_alpha : nullptr;
     p.area = c->d_area;
     p.inv_scale = 1.0 / c->scale;
+    p.hdr = nullptr;
     p.n_texels = c->n_texels;
+    p.n_designs = 1;
     p.E_out = c->d_E;
     p.w_out = c->d_w;
     p.partial = c->d_partial;
@@ -609,6 +763,7 @@ int lt_trace_adjoint(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_h
     LT_CUDA(c, launch_adjoint(p, grid, c->threads, smem, c->stream));
     LT_CUDA(c, launch_grad_finalize(p, c->d_grad, c->stream));
     c->stats.photons_adjoint = photon_end - photon_begin;
+    c->seg_single = true;
     rc = copy_out(c, grad_out, c->d_grad, (size_t)L * 8 * sizeof(double), is_device);
     if (rc) return rc;
     if (!is_device) return check_device(c);
@@ -657,13 +812,175 @@ int lt_get_stats(void *ctx, lt_stats *out) {
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c || !out) return LT_ERR_ARG;
     LT_CUDA(c, cudaSetDevice(c->device));
-    unsigned long long seg[2] = {0, 0};
-    LT_CUDA(c, cudaMemcpyAsync(seg, c->d_seg, sizeof(seg), cudaMemcpyDeviceToHost, c->stream));
-    LT_CUDA(c, cudaStreamSynchronize(c->stream));
-    c->stats.segments_forward = seg[0];
-    c->stats.segments_adjoint = seg[1];
+    if (c->seg_single) {   // a batch step stores its counts when it returns
+        unsigned long long seg[2] = {0, 0};
+        LT_CUDA(c, cudaMemcpyAsync(seg, c->d_seg, sizeof(seg), cudaMemcpyDeviceToHost, c->stream));
+        LT_CUDA(c, cudaStreamSynchronize(c->stream));
+        c->stats.segments_forward = seg[0];
+        c->stats.segments_adjoint = seg[1];
+    }
     *out = c->stats;
     return check_device(c);
+}
+
+int lt_set_design(void *ctx, uint32_t design) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return LT_ERR_ARG;
+    c->design_word = design;
+    c->lights_dirty = true;
+    return LT_OK;
+}
+
+int lt_batch_setup(void *ctx, int32_t n_designs, const int32_t *lights_per_design, uint64_t photons_per_design,
+                   int32_t max_hits) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return LT_ERR_ARG;
+    if (!c->d_nodes) return fail(c, LT_ERR_STATE, "no scene uploaded");
+    if (n_designs < 1 || !lights_per_design) return fail(c, LT_ERR_ARG, "need at least one design");
+    if (photons_per_design == 0) return fail(c, LT_ERR_ARG, "photons_per_design must be positive");
+    if (max_hits < 1 || max_hits > 64) return fail(c, LT_ERR_ARG, "max_hits must be in [1, 64]");
+    int64_t total = 0;
+    for (int32_t d = 0; d < n_designs; ++d) {
+        if (lights_per_design[d] < 1) return fail(c, LT_ERR_ARG, "every design needs at least one light");
+        total += lights_per_design[d];
+    }
+    if (total > LT_MAX_BATCH_LIGHTS) return fail(c, LT_ERR_ARG, "more lights than LT_MAX_BATCH_LIGHTS");
+    LT_CUDA(c, cudaSetDevice(c->device));
+    batch_free(c);
+    Ctx::Batch &b = c->batch;
+    b.n_designs = n_designs;
+    b.n_lights = (int32_t)total;
+    b.max_hits = max_hits;
+    b.photons = photons_per_design;
+    b.counts.assign(lights_per_design, lights_per_design + n_designs);
+    b.in_bytes = kHdrBytes + sizeof(LightDev) * (size_t)total;
+    const size_t DT = (size_t)n_designs * (size_t)c->n_texels;
+    cudaError_t e = cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&b.d_in, b.in_bytes);
+    if (e == cudaSuccess) e = cudaMallocHost(&b.h_in, b.in_bytes);
+    if (e == cudaSuccess) e = cudaMallocHost(&b.h_out, ((size_t)n_designs + (size_t)total * 8 + 2) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&b.d_q, DT * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&b.d_E, DT * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&b.d_w, DT * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&b.d_partial, (size_t)n_designs * kLossBlocksBatch * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&b.d_loss, (size_t)n_designs * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&b.d_grad, ((size_t)total * 8 + 2) * sizeof(double));
+    if (e != cudaSuccess) {
+        batch_free(c);
+        return cuda_fail(c, e, "lt_batch_setup");
+    }
+    std::memset(b.h_in, 0, b.in_bytes);
+    return LT_OK;
+}
+
+int lt_batch_set_lights(void *ctx, const lt_light *lights) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return LT_ERR_ARG;
+    Ctx::Batch &b = c->batch;
+    if (!b.n_designs) return fail(c, LT_ERR_STATE, "lt_batch_setup first");
+    if (!lights) return fail(c, LT_ERR_ARG, "null lights");
+    for (int32_t l = 0; l < b.n_lights; ++l) {
+        const lt_light &s = lights[l];
+        if (s.type != LT_POINT && s.type != LT_SPOT) return fail(c, LT_ERR_ARG, "unknown light type");
+        if (s.type == LT_SPOT && !(s.theta_in >= 0.0f && s.theta_in < s.theta_out && s.theta_out <= (float)kPi))
+            return fail(c, LT_ERR_ARG, "spot cone needs 0 <= theta_in < theta_out <= pi");
+    }
+    b.lights.assign(lights, lights + b.n_lights);
+    LightDev *out = reinterpret_cast<LightDev *>(b.h_in + kHdrBytes);
+    double bound = 0.0;
+    int32_t off = 0;
+    for (int32_t d = 0; d < b.n_designs; ++d) {
+        bound = std::max(bound, derive_lights(lights + off, b.counts[d], b.photons, (uint64_t)d * b.photons,
+                                              (uint64_t)d * (uint64_t)c->n_texels, (uint32_t)d, out + off));
+        off += b.counts[d];
+    }
+    // one fixed-point scale for the batch, safe for its brightest design
+    double S = std::ldexp(1.0, 40);
+    if (bound > 0.0) {
+        const int k = (int)std::floor(std::log2(std::ldexp(1.0, 62) / (bound * (double)b.max_hits)));
+        S = std::ldexp(1.0, std::max(-120, std::min(120, k)));
+    }
+    StepHeader *h = reinterpret_cast<StepHeader *>(b.h_in);
+    h->scale = S;
+    h->inv_scale = 1.0 / S;
+    b.has_lights = true;
+    return LT_OK;
+}
+
+int lt_batch_step(void *ctx, uint64_t seed_fwd, uint64_t seed_adj, double *loss_out, double *grad_out,
+                  int use_graph) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return LT_ERR_ARG;
+    Ctx::Batch &b = c->batch;
+    if (!b.n_designs || !b.has_lights) return fail(c, LT_ERR_STATE, "lt_batch_setup and lt_batch_set_lights first");
+    if (!c->has_target) return fail(c, LT_ERR_STATE, "no target (lt_set_target)");
+    LT_CUDA(c, cudaSetDevice(c->device));
+    StepHeader *h = reinterpret_cast<StepHeader *>(b.h_in);
+    h->seed_fwd = seed_fwd;
+    h->seed_adj = seed_adj;
+    BatchLaunch bl;
+    int rc = batch_prepare(c, &bl);
+    if (rc) return rc;
+    if (use_graph) {
+        if (!b.exec) {
+            LT_CUDA(c, cudaStreamBeginCapture(b.stream, cudaStreamCaptureModeRelaxed));
+            rc = batch_issue(c, bl);
+            cudaGraph_t g = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(b.stream, &g);
+            if (rc || e != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return rc ? rc : cuda_fail(c, e, "cudaStreamEndCapture");
+            }
+            b.graph = g;
+            const cudaError_t ei = cudaGraphInstantiate(&b.exec, b.graph, 0);
+            if (ei != cudaSuccess) {
+                batch_drop_graph(c);
+                return cuda_fail(c, ei, "cudaGraphInstantiate");
+            }
+        }
+        LT_CUDA(c, cudaGraphLaunch(b.exec, b.stream));
+    } else {
+        if ((rc = batch_issue(c, bl))) return rc;
+    }
+    LT_CUDA(c, cudaStreamSynchronize(b.stream));
+    if ((rc = batch_check_device(c))) return rc;
+    const size_t D = (size_t)b.n_designs, L = (size_t)b.n_lights;
+    if (loss_out) std::memcpy(loss_out, b.h_out, D * sizeof(double));
+    if (grad_out) std::memcpy(grad_out, b.h_out + D, L * 8 * sizeof(double));
+    uint64_t seg[2];
+    std::memcpy(seg, b.h_out + D + L * 8, sizeof(seg));
+    b.segments = seg[0] + seg[1];
+    c->stats.segments_forward = seg[0];
+    c->stats.segments_adjoint = seg[1];
+    c->stats.photons_forward = c->stats.photons_adjoint = b.photons * D;
+    c->seg_single = false;
+    return LT_OK;
+}
+
+int lt_batch_texel_sums(void *ctx, int32_t design, int64_t *q_out, int is_device) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c || !q_out) return LT_ERR_ARG;
+    Ctx::Batch &b = c->batch;
+    if (design < 0 || design >= b.n_designs) return fail(c, LT_ERR_ARG, "design out of range");
+    LT_CUDA(c, cudaSetDevice(c->device));
+    const size_t T = (size_t)c->n_texels;
+    LT_CUDA(c, cudaMemcpyAsync(q_out, b.d_q + (size_t)design * T, T * sizeof(int64_t),
+                               is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b.stream));
+    LT_CUDA(c, cudaStreamSynchronize(b.stream));
+    return LT_OK;
+}
+
+int lt_batch_irradiance(void *ctx, int32_t design, float *E_out, int is_device) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c || !E_out) return LT_ERR_ARG;
+    Ctx::Batch &b = c->batch;
+    if (design < 0 || design >= b.n_designs) return fail(c, LT_ERR_ARG, "design out of range");
+    LT_CUDA(c, cudaSetDevice(c->device));
+    const size_t T = (size_t)c->n_texels;
+    LT_CUDA(c, cudaMemcpyAsync(E_out, b.d_E + (size_t)design * T, T * sizeof(float),
+                               is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b.stream));
+    LT_CUDA(c, cudaStreamSynchronize(b.stream));
+    return LT_OK;
 }
 
 int lt_set_launch(void *ctx, int32_t threads_per_block, int32_t blocks_per_sm, int32_t smem_node_bytes) {
@@ -679,6 +996,7 @@ int lt_set_launch(void *ctx, int32_t threads_per_block, int32_t blocks_per_sm, i
     if (smem_node_bytes < 0 || smem_node_bytes > 200 * 1024)
         return fail(c, LT_ERR_ARG, "smem_node_bytes must be in [0, 200 KiB]");
     if (smem_node_bytes) c->smem_node_bytes = smem_node_bytes;
+    batch_drop_graph(c);     // a captured batch step holds the old launch shape
     return LT_OK;
 }
 

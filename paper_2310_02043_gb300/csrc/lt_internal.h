@@ -74,9 +74,21 @@ struct alignas(16) LightDev {
     float k_cos;        // emission cos = 1 - u1 k_cos: 2 (point), 1 - cos(theta_out) (spot)
     float sin_in;
     float sin_out;
-    float pad0;
-    uint64_t first;     // photon range [first, end)
+    uint32_t design;    // design this light belongs to (Philox counter word 3, texel array)
+    uint64_t first;     // global photon range [first, end)
     uint64_t end;
+    uint64_t photon_base;   // first global photon of the light's design
+    uint64_t texel_base;    // offset of the design's texel sums and weights (design slot x n_texels)
+};
+static_assert(sizeof(LightDev) == 144, "light layout");
+
+// Values a captured step reads from device memory, so one instantiated graph
+// serves every step (written with the lights from pinned host memory).
+struct alignas(16) StepHeader {
+    uint64_t seed_fwd;
+    uint64_t seed_adj;
+    double scale;       // fixed-point scale S of the texel sums
+    double inv_scale;
 };
 
 // Device error word bits.
@@ -94,12 +106,12 @@ struct TraceParams {
     int32_t max_hits;
     int32_t max_steps;          // node visits per ray before giving up (kErrSteps)
     uint64_t max_iters;         // step-loop iterations per thread before giving up (kErrSteps)
-    uint32_t design;
     uint64_t seed;
+    const StepHeader *hdr;      // if set, seed and scale come from here (graph replay)
     uint64_t photon_begin, photon_end;
     int64_t n_texels;
     // forward
-    unsigned long long *q;      // [n_texels] fixed-point irradiance accumulator
+    unsigned long long *q;      // [designs][n_texels] fixed-point irradiance accumulator
     float scale;                // S
     uint64_t chunk;             // photons per thread (contiguous)
     // adjoint
@@ -117,19 +129,22 @@ struct TraceParams {
 };
 
 struct LossParams {
-    const unsigned long long *q;
-    const float *E_target;
+    const unsigned long long *q;    // [n_designs][n_texels]
+    const float *E_target;          // shared by all designs
     const float *alpha;
     const float *area;
     double inv_scale;
+    const StepHeader *hdr;          // if set, inv_scale comes from here
     int64_t n_texels;
-    float *E_out;               // may be null
-    float *w_out;
-    double *partial;            // [kLossBlocks]
-    double *loss_out;           // device scalar
+    int32_t n_designs;
+    float *E_out;                   // [n_designs][n_texels], may be null
+    float *w_out;                   // [n_designs][n_texels]
+    double *partial;                // [n_designs][kLossBlocks]
+    double *loss_out;               // [n_designs] device
 };
 
 constexpr int kLossBlocks = 1024;
+constexpr int kLossBlocksBatch = 128;   // blocks per design when several designs share a launch
 constexpr int kLossThreads = 256;
 
 // Kernel launchers (lt_kernels.cu).

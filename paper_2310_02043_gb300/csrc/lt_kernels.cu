@@ -517,6 +517,8 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
     int32_t first_light = 0;
     if (kAdjoint)
         for (int i = 0; i < P.n_slots * 8; ++i) P.slots[tid * (uint64_t)P.n_slots * 8 + i] = 0.0;
+    const uint64_t seed = P.hdr ? (kAdjoint ? P.hdr->seed_adj : P.hdr->seed_fwd) : P.seed;
+    const float scale = P.hdr ? (float)P.hdr->scale : P.scale;
 
     int32_t l = 0, seg = 0, skip = -1;
     float phi = 0.0f, a_emit = 0.0f, g = 0.0f, beta = 1.0f;
@@ -535,7 +537,7 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
         l = light_of(P, photon);
         first_light = l;
         const LightDev &L = P.lights[l];
-        const float2 u = uniforms(P.seed, photon, 0u, P.design);
+        const float2 u = uniforms(seed, photon - L.photon_base, 0u, L.design);
         float wx, wy, wz;
         phi = emit(L, u.x, u.y, wx, wy, wz, a_emit);
         ray_init(r, L.pos[0], L.pos[1], L.pos[2], wx, wy, wz);
@@ -575,11 +577,12 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
                 const int64_t texel = texel_of(P, h);
                 x = make_float3(fmaf(h.t, r.dx, r.ox), fmaf(h.t, r.dy, r.oy), fmaf(h.t, r.dz, r.oz));
                 nrm = facing_normal(P, h.tri, r.dx, r.dy, r.dz);
+                const uint64_t tb = P.lights[l].texel_base;
                 if (!kAdjoint) {
-                    deposit_active(P.q, texel, (unsigned long long)__float2ll_rn(phi * P.scale));   // Eq. 8
+                    deposit_active(P.q + tb, texel, (unsigned long long)__float2ll_rn(phi * scale));   // Eq. 8
                 } else {
                     if (seg == 1) { x1x = x.x; x1y = x.y; x1z = x.z; n1 = nrm; hit1 = true; }
-                    g += __ldg(P.w + texel) * beta;                                             // Eq. 12
+                    g += __ldg(P.w + tb + texel) * beta;                                          // Eq. 12
                 }
                 if (seg < P.max_hits) {
                     const float rho = albedo_of(P, h.tri);
@@ -605,19 +608,19 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
             if (active) {
                 float c, sn;
                 float3 t1, t2, axis, org;
-                const float2 u = uniforms(P.seed, photon, bounce ? (uint32_t)seg : 0u, P.design);
+                if (!bounce) while (photon >= P.lights[l].end) ++l;
+                const LightDev &Ln = P.lights[l];
+                const float2 u = uniforms(seed, photon - Ln.photon_base, bounce ? (uint32_t)seg : 0u, Ln.design);
                 if (bounce) {
                     bounce_frame(nrm, u.x, c, sn, t1, t2);
                     axis = nrm;
                     org = x;
                     ++seg;
                 } else {
-                    while (photon >= P.lights[l].end) ++l;
-                    const LightDev &L = P.lights[l];
-                    emit_frame(L, u.x, c, sn, t1, t2, axis);
-                    org = make_float3(L.pos[0], L.pos[1], L.pos[2]);
-                    a_emit = falloff(L, c);
-                    phi = L.flux_k * a_emit;
+                    emit_frame(Ln, u.x, c, sn, t1, t2, axis);
+                    org = make_float3(Ln.pos[0], Ln.pos[1], Ln.pos[2]);
+                    a_emit = falloff(Ln, c);
+                    phi = Ln.flux_k * a_emit;
                     seg = 1;
                     skip = -1;
                     g = 0.0f;
@@ -654,7 +657,8 @@ __global__ void __launch_bounds__(128) paths_kernel(const TraceParams P, uint64_
     const int32_t l = light_of(P, photon);
     const LightDev &L = P.lights[l];
     float wx, wy, wz, a_emit;
-    const float2 u0 = uniforms(P.seed, photon, 0u, P.design);
+    const uint64_t local = photon - L.photon_base;
+    const float2 u0 = uniforms(P.seed, local, 0u, L.design);
     emit(L, u0.x, u0.y, wx, wy, wz, a_emit);
     int32_t skip = -1;
     int32_t *rt = P.rec_tri + k * P.max_hits;
@@ -676,10 +680,10 @@ __global__ void __launch_bounds__(128) paths_kernel(const TraceParams P, uint64_
         const float3 nrm = facing_normal(P, h.tri, r.dx, r.dy, r.dz);
         if (P.rec_grad) {
             if (i == 1) { x1x = xx; x1y = xy; x1z = xz; n1 = nrm; hit1 = true; }
-            g += __ldg(P.w + texel) * beta;
+            g += __ldg(P.w + L.texel_base + texel) * beta;
         }
         if (i == P.max_hits) break;
-        const float2 u = uniforms(P.seed, photon, (uint32_t)i, P.design);
+        const float2 u = uniforms(P.seed, local, (uint32_t)i, L.design);
         cosine_dir(nrm, u.x, u.y, wx, wy, wz);
         beta *= albedo_of(P, h.tri);
         skip = tile_of(P, h.tri);
@@ -710,29 +714,33 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return t;
 }
 
+// blockIdx.y is the design; its texels are reduced by gridDim.x blocks.
 __global__ void __launch_bounds__(kLossThreads) loss_kernel(const LossParams P) {
     __shared__ double sh[kLossThreads / 32];
+    const int64_t base = (int64_t)blockIdx.y * P.n_texels;
+    const double inv_scale = P.hdr ? P.hdr->inv_scale : P.inv_scale;
     double part = 0.0;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < P.n_texels;
          t += (int64_t)gridDim.x * blockDim.x) {
         const double A = (double)P.area[t];
-        const double E = (double)(long long)P.q[t] * P.inv_scale / A;
+        const double E = (double)(long long)P.q[base + t] * inv_scale / A;
         const double r = E - (double)P.E_target[t];
         const double a = P.alpha ? (double)P.alpha[t] : 1.0;
-        if (P.E_out) P.E_out[t] = (float)E;
-        P.w_out[t] = (float)(a * r);
+        if (P.E_out) P.E_out[base + t] = (float)E;
+        P.w_out[base + t] = (float)(a * r);
         part += 0.5 * A * a * r * r;
     }
     const double s = block_sum(part, sh);
-    if (threadIdx.x == 0) P.partial[blockIdx.x] = s;
+    if (threadIdx.x == 0) P.partial[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
 }
 
+// One block per design: the design's n block partials in order.
 __global__ void __launch_bounds__(kLossThreads) loss_final_kernel(const double *partial, int n, double *out) {
     __shared__ double sh[kLossThreads / 32];
     double v = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) v += partial[i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v += partial[(int64_t)blockIdx.x * n + i];
     const double s = block_sum(v, sh);
-    if (threadIdx.x == 0) *out = s;
+    if (threadIdx.x == 0) out[blockIdx.x] = s;
 }
 
 __global__ void resolve_kernel(const unsigned long long *q, const float *area, double inv_scale, int64_t n,
@@ -818,8 +826,9 @@ cudaError_t launch_paths(const TraceParams &p, uint64_t count, cudaStream_t s) {
 }
 
 cudaError_t launch_loss(const LossParams &p, cudaStream_t s) {
-    loss_kernel<<<kLossBlocks, kLossThreads, 0, s>>>(p);
-    loss_final_kernel<<<1, kLossThreads, 0, s>>>(p.partial, kLossBlocks, p.loss_out);
+    const int blocks = p.n_designs > 1 ? kLossBlocksBatch : kLossBlocks;
+    loss_kernel<<<dim3(blocks, p.n_designs), kLossThreads, 0, s>>>(p);
+    loss_final_kernel<<<p.n_designs, kLossThreads, 0, s>>>(p.partial, blocks, p.loss_out);
     return cudaGetLastError();
 }
 

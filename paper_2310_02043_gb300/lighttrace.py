@@ -27,7 +27,8 @@ GRAD_N = 8
 EXPORTED = ("lt_version", "lt_create", "lt_destroy", "lt_set_stream", "lt_last_error", "lt_upload_scene",
             "lt_set_target", "lt_set_lights", "lt_trace_forward", "lt_texel_accumulator", "lt_get_texel_sums", "lt_loss",
             "lt_get_irradiance", "lt_texel_areas", "lt_set_adjoint_weights", "lt_trace_adjoint", "lt_debug_paths",
-            "lt_get_stats", "lt_set_launch", "lt_count_work", "lt_loss_static")
+            "lt_get_stats", "lt_set_launch", "lt_count_work", "lt_loss_static", "lt_set_design", "lt_batch_setup",
+            "lt_batch_set_lights", "lt_batch_step", "lt_batch_texel_sums", "lt_batch_irradiance")
 
 
 class LtError(RuntimeError):
@@ -91,6 +92,12 @@ def _declare(lib):
         "lt_set_launch": [vp, i32, i32, i32],
         "lt_count_work": [vp, u64, u64, i32, u64, u64, vp],
         "lt_loss_static": [ci, vp, vp, ctypes.c_double, vp, vp, vp, i64, vp, vp, vp],
+        "lt_set_design": [vp, ctypes.c_uint32],
+        "lt_batch_setup": [vp, i32, vp, u64, i32],
+        "lt_batch_set_lights": [vp, vp],
+        "lt_batch_step": [vp, u64, u64, vp, vp, ci],
+        "lt_batch_texel_sums": [vp, i32, vp, ci],
+        "lt_batch_irradiance": [vp, i32, vp, ci],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -283,6 +290,40 @@ class Tracer:
         out = np.zeros(4, np.uint64)
         self._check(self.lib.lt_count_work(self.h, seed, n_photons, max_hits, begin, end, _ptr(out)[0]))
         return dict(segments=int(out[0]), node_visits=int(out[1]), tri_tests=int(out[2]), photons=int(out[3]))
+
+    def set_design(self, design: int):
+        """Philox design word of the single-design passes."""
+        self._check(self.lib.lt_set_design(self.h, design))
+
+    # ---- batched designs ----
+    def batch_setup(self, lights_per_design, photons_per_design: int, max_hits: int):
+        counts = np.ascontiguousarray(lights_per_design, np.int32)
+        self._check(self.lib.lt_batch_setup(self.h, counts.shape[0], _ptr(counts)[0], photons_per_design, max_hits))
+        self.batch_counts = counts
+
+    def batch_set_lights(self, lights):
+        """Lights of every design, concatenated in design order, rows as in set_lights."""
+        arr = lights_to_struct(lights)
+        assert len(arr) == int(self.batch_counts.sum())
+        self._check(self.lib.lt_batch_set_lights(self.h, arr))
+
+    def batch_step(self, seed_fwd: int, seed_adj: int, use_graph: bool = False):
+        """(objective per design [D], gradient per light [total lights, 8])."""
+        loss = np.empty(self.batch_counts.shape[0], np.float64)
+        grad = np.empty((int(self.batch_counts.sum()), GRAD_N), np.float64)
+        self._check(self.lib.lt_batch_step(self.h, seed_fwd, seed_adj, _ptr(loss)[0], _ptr(grad)[0],
+                                           1 if use_graph else 0))
+        return loss, grad
+
+    def batch_texel_sums(self, design: int):
+        out = np.empty(self.n_texels, np.int64)
+        self._check(self.lib.lt_batch_texel_sums(self.h, design, _ptr(out)[0], 0))
+        return out
+
+    def batch_irradiance(self, design: int):
+        out = np.empty(self.n_texels, np.float32)
+        self._check(self.lib.lt_batch_irradiance(self.h, design, _ptr(out)[0], 0))
+        return out
 
     def set_launch(self, threads_per_block: int = 0, blocks_per_sm: int = 0, smem_node_bytes: int = 0):
         self._check(self.lib.lt_set_launch(self.h, threads_per_block, blocks_per_sm, smem_node_bytes))
