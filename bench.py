@@ -115,6 +115,13 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def clock_sampler(local):
+    import torch
+    props = torch.cuda.get_device_properties(local)
+    uuid = getattr(props, "uuid", None)
+    return ClockSampler(f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else (uuid or local))
+
+
 # ---------------------------------------------------------------------------
 # Roofline helpers
 # ---------------------------------------------------------------------------
@@ -308,9 +315,7 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
-    props = torch.cuda.get_device_properties(local)
-    uuid = getattr(props, "uuid", None)
-    sampler = ClockSampler(f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else (uuid or local))
+    sampler = clock_sampler(local)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -420,6 +425,145 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# Batched designs: 64 candidate designs in one launch per pass
+# ---------------------------------------------------------------------------
+BATCH_DESIGNS, BATCH_PHOTONS = 64, 1 << 22
+BATCH_KERNELS_PER_STEP = 5    # forward, loss, loss reduction, adjoint, gradient reduction
+
+
+def batch_config(sc, counts, shape):
+    return {"workload": f"batched designs: {len(counts)} candidate lighting designs, U{{4..32}} spots each "
+                        f"({int(counts.sum())} spots), over the procedural office ({sc.n_tri} tris, {sc.n_texels} "
+                        f"texels), 2^22 photons per design, 5 hits, one forward + one adjoint launch per step "
+                        f"(CUDA graph)",
+            "designs": len(counts), "spots": int(counts.sum()), "photons_per_design": BATCH_PHOTONS, "hits": HITS,
+            "launch_shape": {"threads": shape[0], "blocks_per_sm": shape[1], "smem_node_bytes": shape[2]},
+            "l2": "flushed between steps (256 MiB write outside the timed events); per-design texel arrays "
+                  f"{len(counts)} x {sc.n_texels * 16 / 1e6:.0f} MB exceed L2",
+            "parallelism": "single GPU"}
+
+
+def run_batch(args):
+    """64 designs x U{4..32} spots x 2^22 photons, one batch step per
+    iteration (captured CUDA graph), against the same designs traced one
+    single-design pass at a time."""
+    import torch
+    from paper_2310_02043_gb300 import autotune
+    from paper_2310_02043_gb300.lighttrace import Tracer
+
+    torch.cuda.set_device(0)
+    sc, _, truth = workload()
+    counts, designs = scenes.office_designs(0, BATCH_DESIGNS)
+    tr = Tracer(0)
+    T = tr.upload_scene(sc)
+    tr.set_lights(truth)
+    tr.trace_forward(77, TARGET_PHOTONS, HITS)
+    target = torch.empty(T, dtype=torch.float32, device="cuda")
+    tr.irradiance(out=target)
+    tr.set_target(target)
+    tr.batch_setup(counts, BATCH_PHOTONS, HITS)
+    tr.batch_set_lights(designs)
+
+    key = autotune.workload_key(torch.cuda.get_device_name(0), sc.n_tri, T, BATCH_PHOTONS, HITS, len(counts))
+    shape, tuned = autotune.tune(tr, lambda: tr.batch_step(1, 2, use_graph=True), key, repeats=2)
+
+    stream = torch.cuda.ExternalStream(tr.batch_stream())
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for k in range(args.warmup):
+        tr.batch_step(10 + k, 20 + k, use_graph=True)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = clock_sampler(0)
+    sampler.start()
+    segs = 0
+    for k in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        ev[k][0].record(stream)
+        tr.batch_step(100 + 2 * k, 101 + 2 * k, use_graph=True)
+        ev[k][1].record(stream)
+        st = tr.stats()
+        segs += st["segments_forward"] + st["segments_adjoint"]
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    t_step = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(t_step)
+    value = segs / (total_ms / 1e3) / 1e6
+    seg_step = segs / args.steps
+
+    # The same designs, one single-design pass each (set_lights, forward,
+    # objective, adjoint), on the library's main stream.
+    offs = np.concatenate([[0], np.cumsum(counts)])
+    main = torch.cuda.current_stream()
+    seq_ms, seq_segs = [], 0
+    for k in range(max(1, min(args.steps, 3))):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        a.record(main)
+        for d in range(len(counts)):
+            tr.set_design(d)
+            tr.set_lights(designs[offs[d]:offs[d + 1]])
+            tr.trace_forward(200 + k, BATCH_PHOTONS, HITS)
+            tr.loss(out=torch.empty(1, dtype=torch.float64, device="cuda"))
+            tr.trace_adjoint(300 + k, BATCH_PHOTONS, HITS, out=torch.empty((counts[d], 8), dtype=torch.float64,
+                                                                           device="cuda"))
+            st = tr.stats()
+            seq_segs += st["segments_forward"] + st["segments_adjoint"]
+        b.record(main)
+        torch.cuda.synchronize()
+        seq_ms.append(a.elapsed_time(b))
+    tr.set_design(0)
+    seq_value = seq_segs / (sum(seq_ms) / 1e3) / 1e6
+
+    # End to end: host lights in, objectives and gradients out, host Adam on
+    # every design's parameters.
+    opt = Adam(lr=0.01)
+    cur = designs.copy()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        tr.batch_set_lights(cur)
+        loss, grad = tr.batch_step(500 + 2 * k, 501 + 2 * k, use_graph=True)
+        cur = apply_update(cur, grad, opt)
+    e2e_s = time.perf_counter() - t0
+    e2e_value = seg_step * args.steps / e2e_s / 1e6
+    h2d = 256 + LIGHT_DEV_BYTES * int(counts.sum())
+    d2h = 8 * (len(counts) + 8 * int(counts.sum()) + 2)
+
+    # Roofline: FP32 work of the whole step from the counting kernel on a few
+    # designs (single-design passes with the same design words).
+    ops_seg = []
+    for d in range(0, len(counts), 16):
+        tr.set_design(d)
+        tr.set_lights(designs[offs[d]:offs[d + 1]])
+        w = tr.count_work(100, BATCH_PHOTONS, HITS)
+        ops_seg.append((w["node_visits"] * OPS_PER_NODE + w["tri_tests"] * OPS_PER_TRI
+                        + w["segments"] * OPS_PER_SEGMENT) / w["segments"])
+    tr.set_design(0)
+    ops = statistics.mean(ops_seg) * seg_step
+    step_ms = total_ms / args.steps
+    achieved = ops / (step_ms / 1e3) / 1e12
+    peak_clock = clocks["sm_max_mhz"] if clocks and clocks.get("sm_max_mhz") else 2070.0
+    peak = alu_peak_tflops(peak_clock)
+    line = {"metric": METRIC, "value": value, "unit": "Msegments/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": batch_config(sc, counts, shape),
+            "e2e": {"value": e2e_value, "unit": "Msegments/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_opt_iter": 1e3 * e2e_s / args.steps},
+            "gpu_launches": BATCH_KERNELS_PER_STEP * args.steps,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "trace_kernel forward + adjoint (whole batch step)",
+                         "peak_basis": f"FP32 issue peak 152 SMs x 128 lanes x {peak_clock:.0f} MHz (derived)",
+                         "fp32_ops_per_segment": statistics.mean(ops_seg)},
+            "sequential": {"value": seq_value, "unit": "Msegments/s", "ms_per_step": statistics.mean(seq_ms),
+                           "what": "the same designs as single-design passes, one after another"},
+            "autotune_ms": {json.dumps(list(k)): v for k, v in tuned.items()},
+            "cpu_baseline": None, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    tr.close()
+
+
 def run_profile_case(args):
     """One forward + loss + adjoint of the office at --photons (for ncu)."""
     import torch
@@ -449,7 +593,12 @@ def main():
     ap.add_argument("--profile-only", action="store_true",
                     help="run one forward + loss + adjoint at --photons and exit (for profilers)")
     ap.add_argument("--photons", type=int, default=1 << 20)
+    ap.add_argument("--workload", choices=["office", "batch"], default="office",
+                    help="office: one design, 16 spots (default); batch: 64 designs in one launch per pass")
     args = ap.parse_args()
+    if args.workload == "batch" and args.impl == "ours" and not args.profile_only:
+        run_batch(args)
+        return
     if args.profile_only:
         run_profile_case(args)
         return

@@ -88,6 +88,8 @@ typedef struct {
     int32_t bvh_depth;           /* levels of wide nodes */
     int32_t staged_nodes;        /* nodes held in shared memory per block */
     double fixed_point_scale;    /* S: a texel accumulates round(Phi * S) */
+    int32_t grid_blocks;         /* launch shape of the last forward pass (single or batch) */
+    int32_t block_threads;
 } lt_stats;
 
 /* Library ABI version (this header: 1). */
@@ -230,6 +232,12 @@ LT_API int lt_batch_set_lights(void *ctx, const lt_light *lights);
 LT_API int lt_batch_step(void *ctx, uint64_t seed_fwd, uint64_t seed_adj, double *loss_out, double *grad_out,
                          int use_graph);
 
+/* The context's batch stream (a cudaStream_t), valid from lt_batch_setup
+ * until the next lt_batch_setup or lt_destroy; NULL before the first setup.
+ * Callers order their own work after a step, or record CUDA events around
+ * one, on this stream. */
+LT_API int lt_batch_stream(void *ctx, void **stream_out);
+
 /* Texel sums (int64) and irradiance (float) of one design after a step. */
 LT_API int lt_batch_texel_sums(void *ctx, int32_t design, int64_t *q_out, int is_device);
 LT_API int lt_batch_irradiance(void *ctx, int32_t design, float *E_out, int is_device);
@@ -267,9 +275,12 @@ LT_API int lt_loss_static(int device, void *cuda_stream, const int64_t *q, doubl
                           const float *E_target, const float *alpha, int64_t n_texels, float *w_out,
                           float *E_out, double *loss_out);
 
-/* Launch shape of the tracing kernels: threads per block (multiple of 32,
- * <= 1024), blocks per SM (>= 1) and the shared-memory budget for staged BVH
- * nodes in bytes (0 = none). Zeros keep the current value. */
+/* Launch shape of the tracing kernels. threads_per_block: a multiple of 32
+ * within the kernel's bound, 0 = the default 256. blocks_per_sm: resident
+ * blocks per SM, 0 = as many as fit. smem_node_bytes: shared-memory budget
+ * for staged BVH nodes in [0, 200 KiB] (the whole BVH is staged when it fits,
+ * else none), 0 = stage nothing. A negative argument keeps the current
+ * value. The defaults are 256 threads, as many blocks as fit, 72 KiB. */
 LT_API int lt_set_launch(void *ctx, int32_t threads_per_block, int32_t blocks_per_sm, int32_t smem_node_bytes);
 
 #ifdef __cplusplus

@@ -12,12 +12,13 @@ import json
 import os
 import statistics
 
-# (threads per block, blocks per SM (0: occupancy), shared-memory node budget in bytes (1: none))
+# (threads per block, blocks per SM (0: as many as fit), shared-memory node
+# budget in bytes (0: nodes through L1)); every field is set explicitly.
 CANDIDATES = (
-    (256, 0, 200 * 1024), (256, 0, 1),
-    (128, 0, 200 * 1024), (128, 0, 1),
-    (192, 0, 200 * 1024), (192, 0, 1),
-    (256, 2, 200 * 1024), (256, 2, 1),
+    (256, 0, 200 * 1024), (256, 0, 0),
+    (128, 0, 200 * 1024), (128, 0, 0),
+    (192, 0, 200 * 1024), (192, 0, 0),
+    (256, 2, 200 * 1024), (256, 2, 0),
 )
 
 

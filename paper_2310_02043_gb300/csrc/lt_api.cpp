@@ -615,6 +615,8 @@ static int forward_pass(Ctx *c, uint64_t seed, uint64_t n_photons, int32_t max_h
     c->stats.photons_forward = photon_end - photon_begin;
     c->stats.staged_nodes = p.n_staged;
     c->stats.fixed_point_scale = S;
+    c->stats.grid_blocks = grid;
+    c->stats.block_threads = c->threads;
     return LT_OK;
 }
 
@@ -953,7 +955,17 @@ int lt_batch_step(void *ctx, uint64_t seed_fwd, uint64_t seed_adj, double *loss_
     c->stats.segments_forward = seg[0];
     c->stats.segments_adjoint = seg[1];
     c->stats.photons_forward = c->stats.photons_adjoint = b.photons * D;
+    c->stats.grid_blocks = bl.grid_f;
+    c->stats.block_threads = c->threads;
+    c->stats.staged_nodes = bl.fwd.n_staged;
     c->seg_single = false;
+    return LT_OK;
+}
+
+int lt_batch_stream(void *ctx, void **stream_out) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c || !stream_out) return LT_ERR_ARG;
+    *stream_out = (void *)c->batch.stream;
     return LT_OK;
 }
 
@@ -986,16 +998,13 @@ int lt_batch_irradiance(void *ctx, int32_t design, float *E_out, int is_device) 
 int lt_set_launch(void *ctx, int32_t threads_per_block, int32_t blocks_per_sm, int32_t smem_node_bytes) {
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return LT_ERR_ARG;
-    if (threads_per_block) {
-        if (threads_per_block % 32 || threads_per_block < 32 || threads_per_block > trace_kernel_max_threads())
-            return fail(c, LT_ERR_ARG, "threads_per_block must be a multiple of 32 within the kernel's bound");
-        c->threads = threads_per_block;
-    }
-    if (blocks_per_sm < 0) return fail(c, LT_ERR_ARG, "blocks_per_sm must be >= 0");
-    if (blocks_per_sm) c->blocks_per_sm = blocks_per_sm;
-    if (smem_node_bytes < 0 || smem_node_bytes > 200 * 1024)
-        return fail(c, LT_ERR_ARG, "smem_node_bytes must be in [0, 200 KiB]");
-    if (smem_node_bytes) c->smem_node_bytes = smem_node_bytes;
+    if (threads_per_block > 0 &&
+        (threads_per_block % 32 || threads_per_block > trace_kernel_max_threads()))
+        return fail(c, LT_ERR_ARG, "threads_per_block must be a multiple of 32 within the kernel's bound");
+    if (smem_node_bytes > 200 * 1024) return fail(c, LT_ERR_ARG, "smem_node_bytes must be in [0, 200 KiB]");
+    if (threads_per_block >= 0) c->threads = threads_per_block ? threads_per_block : 256;
+    if (blocks_per_sm >= 0) c->blocks_per_sm = blocks_per_sm;
+    if (smem_node_bytes >= 0) c->smem_node_bytes = smem_node_bytes;
     batch_drop_graph(c);     // a captured batch step holds the old launch shape
     return LT_OK;
 }

@@ -28,7 +28,8 @@ EXPORTED = ("lt_version", "lt_create", "lt_destroy", "lt_set_stream", "lt_last_e
             "lt_set_target", "lt_set_lights", "lt_trace_forward", "lt_texel_accumulator", "lt_get_texel_sums", "lt_loss",
             "lt_get_irradiance", "lt_texel_areas", "lt_set_adjoint_weights", "lt_trace_adjoint", "lt_debug_paths",
             "lt_get_stats", "lt_set_launch", "lt_count_work", "lt_loss_static", "lt_set_design", "lt_batch_setup",
-            "lt_batch_set_lights", "lt_batch_step", "lt_batch_texel_sums", "lt_batch_irradiance")
+            "lt_batch_set_lights", "lt_batch_step", "lt_batch_texel_sums", "lt_batch_irradiance",
+            "lt_batch_stream")
 
 
 class LtError(RuntimeError):
@@ -48,7 +49,8 @@ class lt_stats(ctypes.Structure):
                 ("photons_forward", ctypes.c_uint64), ("photons_adjoint", ctypes.c_uint64),
                 ("n_texels", ctypes.c_int64), ("n_triangles", ctypes.c_int32), ("n_nodes", ctypes.c_int32),
                 ("bvh_depth", ctypes.c_int32), ("staged_nodes", ctypes.c_int32),
-                ("fixed_point_scale", ctypes.c_double)]
+                ("fixed_point_scale", ctypes.c_double), ("grid_blocks", ctypes.c_int32),
+                ("block_threads", ctypes.c_int32)]
 
 
 _lib = None
@@ -98,6 +100,7 @@ def _declare(lib):
         "lt_batch_step": [vp, u64, u64, vp, vp, ci],
         "lt_batch_texel_sums": [vp, i32, vp, ci],
         "lt_batch_irradiance": [vp, i32, vp, ci],
+        "lt_batch_stream": [vp, ctypes.POINTER(ctypes.c_void_p)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -315,6 +318,12 @@ class Tracer:
                                            1 if use_graph else 0))
         return loss, grad
 
+    def batch_stream(self) -> int:
+        """The batch stream handle (cudaStream_t as an int; 0 before batch_setup)."""
+        out = ctypes.c_void_p()
+        self._check(self.lib.lt_batch_stream(self.h, ctypes.byref(out)))
+        return int(out.value or 0)
+
     def batch_texel_sums(self, design: int):
         out = np.empty(self.n_texels, np.int64)
         self._check(self.lib.lt_batch_texel_sums(self.h, design, _ptr(out)[0], 0))
@@ -325,5 +334,7 @@ class Tracer:
         self._check(self.lib.lt_batch_irradiance(self.h, design, _ptr(out)[0], 0))
         return out
 
-    def set_launch(self, threads_per_block: int = 0, blocks_per_sm: int = 0, smem_node_bytes: int = 0):
+    def set_launch(self, threads_per_block: int = -1, blocks_per_sm: int = -1, smem_node_bytes: int = -1):
+        """Launch shape of the tracing kernels (0: default 256 threads / as
+        many blocks as fit / no staged nodes; negative: keep)."""
         self._check(self.lib.lt_set_launch(self.h, threads_per_block, blocks_per_sm, smem_node_bytes))

@@ -236,6 +236,28 @@ def office_lights(seed: int = 0, intensity: float = 50.0, theta_in_deg: float = 
     return make_lights(rows)
 
 
+def office_designs(seed: int = 0, n_designs: int = 64, min_spots: int = 4, max_spots: int = 32,
+                   total_intensity: float = 800.0, theta_in_deg: float = 40.0, theta_out_deg: float = 60.0):
+    """Candidate lighting designs for the office: design d has n_d ~ U{min_spots
+    .. max_spots} spots at z = 2.8 m, uniform over the 20 x 10 m ceiling (0.5 m
+    from the walls), pitch -pi/2 + U(-0.2, 0.2), yaw U(0, 2 pi), and I_e =
+    total_intensity / n_d each (every design emits the same power as the 16
+    spots of office_lights). Returns (counts int32 [D], lights [sum n_d, 9])
+    with the designs concatenated in order."""
+    rng = np.random.default_rng(seed + 5000)
+    counts = rng.integers(min_spots, max_spots + 1, size=n_designs).astype(np.int32)
+    rows = []
+    for n in counts:
+        for _ in range(int(n)):
+            x = float(rng.uniform(0.5, 19.5))
+            y = float(rng.uniform(0.5, 9.5))
+            yaw = float(rng.uniform(0.0, 2 * np.pi))
+            pitch = -np.pi / 2 + float(rng.uniform(-0.2, 0.2))
+            rows.append(spot_light((x, y, 2.8), yaw, pitch, total_intensity / int(n),
+                                   np.radians(theta_in_deg), np.radians(theta_out_deg)))
+    return counts, make_lights(rows)
+
+
 def perturb_lights(lights: np.ndarray, seed: int, pos_sigma: float = 0.05, angle_sigma: float = 0.0,
                    intensity_range=(0.8, 1.2), theta_in_delta: float = 0.0) -> np.ndarray:
     """Seeded perturbation of a light array (the 'ground-truth' lights a target

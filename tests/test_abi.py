@@ -40,4 +40,4 @@ def test_version_and_argument_checks(lib):
 
 def test_struct_layouts_match_the_header():
     assert ctypes.sizeof(lighttrace.lt_light) == 36
-    assert ctypes.sizeof(lighttrace.lt_stats) == 8 * 5 + 4 * 4 + 8
+    assert ctypes.sizeof(lighttrace.lt_stats) == 8 * 5 + 4 * 4 + 8 + 4 * 2

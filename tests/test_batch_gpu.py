@@ -76,6 +76,7 @@ def test_batch_designs_equal_single_design_passes(setup):
 def test_graph_replay_equals_eager(setup):
     tr, sc, target, designs = setup
     tr.batch_setup(COUNTS, N, HITS)
+    assert tr.batch_stream() != 0
     lights = np.concatenate(designs)
     for step, shift in enumerate([0.0, 0.05, -0.03]):
         L = lights.copy()

@@ -165,6 +165,32 @@ def test_fixed_point_sums_identical_across_launch_shapes(tr):
     assert np.array_equal(tr.texel_sums(), ref)
 
 
+def test_launch_shape_arguments(tr):
+    # 0 selects the default (256 threads / as many blocks as fit / no staged
+    # nodes), a negative argument keeps the current value
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    sc, L = scenes.office(seed=0, pitch=0.1), scenes.office_lights(0)
+    tr.upload_scene(sc)
+    tr.set_lights(L)
+
+    def shape():
+        tr.trace_forward(5, 1 << 14, 5)
+        st = tr.stats()
+        return st["grid_blocks"], st["block_threads"], st["staged_nodes"]
+
+    tr.set_launch(128, 2, 0)
+    assert shape() == (2 * sms, 128, 0)
+    tr.set_launch(-1, -1, 200 * 1024)
+    assert shape() == (2 * sms, 128, tr.stats()["n_nodes"])
+    tr.set_launch(0, 0, -1)
+    g, t, staged = shape()
+    assert t == 256 and g % sms == 0 and staged > 0
+    tr.set_launch(0, 0, 0)
+    assert shape()[2] == 0
+    tr.set_launch(256, 0, 48 * 1024)
+
+
 def _cornell_target(sc, lights):
     Lt = scenes.perturb_lights(lights, seed=1, pos_sigma=0.05)
     return oracle.forward(sc, Lt, 101, 1 << 16, 3)["E"].astype(np.float32)
