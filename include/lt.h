@@ -158,6 +158,15 @@ LT_API int lt_get_irradiance(void *ctx, float *E_out, int is_device);
 /* Texel areas A_t (float, [n_texels]). */
 LT_API int lt_texel_areas(void *ctx, float *A_out, int is_device);
 
+/* Centre of every texel in world space and the unit normal of its tile
+ * (host arrays [n_texels][3]): the point whose chart coordinates are
+ * ((i + 1/2) / res_u, (j + 1/2) / res_v) in texel (i, j) of its tile, mapped
+ * through the barycentric coordinates of the tile triangle that contains it
+ * in the chart (the one whose smallest barycentric coordinate is largest,
+ * clamped onto that triangle if none contains it). Inputs of the irradiance
+ * surrogate (sg.h); computed on the host from the uploaded scene. */
+LT_API int lt_texel_centres(void *ctx, float *pos_out, float *normal_out);
+
 /* Replace the adjoint weights w_t ([n_texels] floats) -- injects dO/dPhi
  * directly (for gradient checks against closed forms). */
 LT_API int lt_set_adjoint_weights(void *ctx, const float *w, int is_device);

@@ -1,7 +1,8 @@
 """Builds libltrace.so in-tree (paper_2310_02043_gb300/_lib/) with nvcc for sm_103a.
 
-The three translation units compile in parallel; the result is linked as a
-shared library exporting the C ABI of include/lt.h.
+The translation units compile in parallel; the result is linked as a shared
+library exporting the C ABIs of include/lt.h (light tracer) and include/sg.h
+(irradiance surrogate).
 """
 from __future__ import annotations
 
@@ -14,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libltrace.so")
-SOURCES = ["lt_kernels.cu", "lt_api.cpp", "lt_bvh.cpp", "lt_noalloc.cu"]
+SOURCES = ["lt_kernels.cu", "lt_api.cpp", "lt_bvh.cpp", "lt_noalloc.cu", "sg_kernels.cu", "sg_api.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -34,7 +35,8 @@ def _stale(lib: str = LIB) -> bool:
     if not os.path.exists(lib):
         return True
     t = os.path.getmtime(lib)
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "lt.h"), __file__]
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", h)
+                                                                 for h in ("lt.h", "sg.h")] + [__file__]
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 

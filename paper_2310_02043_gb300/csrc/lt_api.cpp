@@ -57,6 +57,10 @@ struct Ctx {
     // launch
     int threads = 256, blocks_per_sm = 0, smem_node_bytes = 72 * 1024;
     lt_stats stats{};
+    // host copy of the uploaded charts (texel centres)
+    std::vector<float> h_xyz, h_uv;
+    std::vector<int32_t> h_tile, h_res;
+    std::vector<int64_t> h_off;
     bool seg_single = true;                // segment counters in d_seg belong to the last pass
     // batched designs (lt_batch_*)
     struct Batch {
@@ -502,6 +506,11 @@ int lt_upload_scene(void *ctx, const float *tri_xyz, const float *tri_uv, const 
         for (int k = 0; k < 3; ++k) h.pad[k] = 0.0f;
     }
     const int64_t T = off[n_tiles];
+    c->h_xyz.assign(tri_xyz, tri_xyz + 9 * (size_t)n_tri);
+    c->h_uv.assign(tri_uv, tri_uv + 6 * (size_t)n_tri);
+    c->h_tile.assign(tri_tile, tri_tile + n_tri);
+    c->h_res.assign(tile_res, tile_res + 2 * (size_t)n_tiles);
+    c->h_off = off;
     std::vector<float> area((size_t)T);
     for (int32_t k = 0; k < n_tiles; ++k) {
         const float a = (float)(tile_area[k] / ((double)tile_res[2 * k] * (double)tile_res[2 * k + 1]));
@@ -959,6 +968,60 @@ int lt_batch_step(void *ctx, uint64_t seed_fwd, uint64_t seed_adj, double *loss_
     c->stats.block_threads = c->threads;
     c->stats.staged_nodes = bl.fwd.n_staged;
     c->seg_single = false;
+    return LT_OK;
+}
+
+int lt_texel_centres(void *ctx, float *pos_out, float *normal_out) {
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c || !pos_out || !normal_out) return LT_ERR_ARG;
+    if (c->h_off.empty()) return fail(c, LT_ERR_STATE, "no scene uploaded");
+    const int32_t n_tiles = (int32_t)c->h_res.size() / 2;
+    std::vector<std::vector<int32_t>> tris_of((size_t)n_tiles);
+    for (size_t i = 0; i < c->h_tile.size(); ++i) tris_of[(size_t)c->h_tile[i]].push_back((int32_t)i);
+    for (int32_t k = 0; k < n_tiles; ++k) {
+        const int32_t ru = c->h_res[2 * k], rv = c->h_res[2 * k + 1];
+        for (int32_t j = 0; j < rv; ++j)
+            for (int32_t i = 0; i < ru; ++i) {
+                const double qu = (i + 0.5) / ru, qv = (j + 0.5) / rv;
+                double best = -1e300, bp[3] = {0, 0, 0}, bn[3] = {0, 0, 1};
+                for (int32_t tri : tris_of[(size_t)k]) {
+                    const float *uv = c->h_uv.data() + 6 * (size_t)tri;
+                    const float *X = c->h_xyz.data() + 9 * (size_t)tri;
+                    // barycentric coordinates of (qu, qv) in the triangle's chart
+                    const double e1u = (double)uv[2] - uv[0], e1v = (double)uv[3] - uv[1];
+                    const double e2u = (double)uv[4] - uv[0], e2v = (double)uv[5] - uv[1];
+                    const double det = e1u * e2v - e1v * e2u;
+                    if (det == 0.0) continue;
+                    const double du = qu - uv[0], dv = qv - uv[1];
+                    double b1 = (du * e2v - dv * e2u) / det;
+                    double b2 = (e1u * dv - e1v * du) / det;
+                    double b0 = 1.0 - b1 - b2;
+                    const double score = std::min(b0, std::min(b1, b2));
+                    if (!(score > best)) continue;
+                    best = score;
+                    b0 = std::max(b0, 0.0);
+                    b1 = std::max(b1, 0.0);
+                    b2 = std::max(b2, 0.0);
+                    const double sb = b0 + b1 + b2;
+                    double e[2][3];
+                    for (int a = 0; a < 3; ++a) {
+                        bp[a] = (b0 * X[a] + b1 * X[3 + a] + b2 * X[6 + a]) / sb;
+                        e[0][a] = (double)X[3 + a] - X[a];
+                        e[1][a] = (double)X[6 + a] - X[a];
+                    }
+                    bn[0] = e[0][1] * e[1][2] - e[0][2] * e[1][1];
+                    bn[1] = e[0][2] * e[1][0] - e[0][0] * e[1][2];
+                    bn[2] = e[0][0] * e[1][1] - e[0][1] * e[1][0];
+                    const double ln = std::sqrt(bn[0] * bn[0] + bn[1] * bn[1] + bn[2] * bn[2]);
+                    for (int a = 0; a < 3; ++a) bn[a] /= ln;
+                }
+                const size_t t = (size_t)(c->h_off[k] + i + (int64_t)ru * j);
+                for (int a = 0; a < 3; ++a) {
+                    pos_out[3 * t + a] = (float)bp[a];
+                    normal_out[3 * t + a] = (float)bn[a];
+                }
+            }
+    }
     return LT_OK;
 }
 

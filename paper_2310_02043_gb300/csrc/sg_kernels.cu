@@ -1,0 +1,942 @@
+// sg_kernels.cu -- kernels of the irradiance surrogate: hash encoding, a fused
+// 4 x 64 network on the tensor cores (mma.sync m16n8k16, bf16 inputs, fp32
+// accumulation; each warp carries 16 rows through all layers in registers),
+// its weight gradient, Adam, and the design objective with its gradient with
+// respect to the luminaire parameters.
+#include <algorithm>
+
+#include <cuda_bf16.h>
+
+#include "sg_internal.h"
+
+namespace sg {
+namespace {
+
+__constant__ int c_res[kLevels] = {16, 20, 25, 32, 40, 50, 64, 80, 101, 128, 161, 203, 256, 322, 406, 512};
+constexpr int kDenseLevels = 7;            // levels whose (N+1)^3 grid fits 2^19 entries
+constexpr float kRScale = 0.01f;
+constexpr int LDW = 72;                    // row stride (elements) of 64-wide bf16 rows in shared memory
+constexpr int LDT3 = 24;                   // row stride of W3 transposed ([64][16])
+constexpr int S_W0 = 0, S_W1 = S_W0 + 64 * LDW, S_W2 = S_W1 + 64 * LDW, S_W3 = S_W2 + 64 * LDW;
+constexpr int S_T0 = S_W3 + 16 * LDW, S_T1 = S_T0 + 64 * LDW, S_T2 = S_T1 + 64 * LDW, S_T3 = S_T2 + 64 * LDW;
+constexpr int S_FWD_END = S_T0;            // forward-only kernels stop here
+constexpr int S_ALL_END = S_T3 + 64 * LDT3;
+
+// Per-warp scratch after the weights.
+struct alignas(16) WarpScratch {
+    uint16_t X[16 * LDW];     // bf16 input rows
+    float D[16];
+    float aux0[16];           // E_obs (train) or gD (design backward)
+    float aux1[16];           // loss weight (train) or A w K (design backward)
+    float xn[16][3];
+    int32_t sidx[16], tidx[16];
+    float gX[16][kGeom];
+};
+
+constexpr size_t smem_bytes(bool transposed) {
+    return (size_t)(transposed ? S_ALL_END : S_FWD_END) * 2 + (size_t)kMlpWarps * sizeof(WarpScratch);
+}
+
+// ---------------------------------------------------------------------------
+// tensor-core helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t ld32(const uint16_t *p) { return *reinterpret_cast<const uint32_t *>(p); }
+
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(float x) {
+    __nv_bfloat16 v = __float2bfloat16_rn(x);
+    return *reinterpret_cast<uint16_t *>(&v);
+}
+
+__device__ __forceinline__ float lo_f(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float hi_f(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
+
+__device__ __forceinline__ void mma(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3, const void *p) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(a));
+}
+
+// Weights into shared memory: W_k as [out][LDW] (forward operand) and, if
+// requested, transposed as [in][LDW] / [64][LDT3] (backward operand).
+__device__ void load_weights(uint16_t *s, const uint16_t *__restrict__ W, bool transposed) {
+    for (int i = threadIdx.x; i < kWeights; i += blockDim.x) {
+        const uint16_t v = W[i];
+        if (i < kOffW3) {
+            const int layer = i >> 12, r = i & 4095, n = r >> 6, m = r & 63;
+            s[S_W0 + layer * 64 * LDW + n * LDW + m] = v;
+            if (transposed) s[S_T0 + layer * 64 * LDW + m * LDW + n] = v;
+        } else {
+            const int r = i - kOffW3, n = r >> 6, m = r & 63;
+            s[S_W3 + n * LDW + m] = v;
+            if (transposed) s[S_T3 + m * LDT3 + n] = v;
+        }
+    }
+}
+
+// A fragments (16 x 64, four k-tiles) of the bf16 rows in X.
+__device__ __forceinline__ void load_rows(uint32_t (&A)[4][4], const uint16_t *X, int g, int c) {
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        A[kk][0] = ld32(X + g * LDW + 16 * kk + 2 * c);
+        A[kk][1] = ld32(X + (g + 8) * LDW + 16 * kk + 2 * c);
+        A[kk][2] = ld32(X + g * LDW + 16 * kk + 8 + 2 * c);
+        A[kk][3] = ld32(X + (g + 8) * LDW + 16 * kk + 8 + 2 * c);
+    }
+}
+
+// acc (16 x 64) = A (16 x 64) B, B[k][n] = M[n][k] with M in shared memory
+// as [64][LDW] rows.
+__device__ __forceinline__ void gemm64(float (&acc)[8][4], const uint32_t (&A)[4][4], const uint16_t *M, int g, int c) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            const uint16_t *w = M + (8 * j + g) * LDW + 16 * kk + 2 * c;
+            mma(acc[j], A[kk], ld32(w), ld32(w + 8));
+        }
+    }
+}
+
+// Accumulator tiles -> bf16 A fragments of relu(acc).
+__device__ __forceinline__ void relu_pack(const float (&acc)[8][4], uint32_t (&A)[4][4]) {
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float *t = acc[2 * kk + h];
+            A[kk][2 * h] = pack2(fmaxf(t[0], 0.0f), fmaxf(t[1], 0.0f));
+            A[kk][2 * h + 1] = pack2(fmaxf(t[2], 0.0f), fmaxf(t[3], 0.0f));
+        }
+}
+
+// Gradient tiles times the ReLU mask of the forward activations -> bf16 A
+// fragments (the gradient at the pre-activation, rounded for the next product).
+__device__ __forceinline__ void mask_pack(const float (&acc)[8][4], const uint32_t (&act)[4][4], uint32_t (&G)[4][4]) {
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float *t = acc[2 * kk + h];
+            const uint32_t a0 = act[kk][2 * h], a1 = act[kk][2 * h + 1];
+            G[kk][2 * h] = pack2(lo_f(a0) > 0.0f ? t[0] : 0.0f, hi_f(a0) > 0.0f ? t[1] : 0.0f);
+            G[kk][2 * h + 1] = pack2(lo_f(a1) > 0.0f ? t[2] : 0.0f, hi_f(a1) > 0.0f ? t[3] : 0.0f);
+        }
+}
+
+// Fragments -> rows [rows][64] bf16 in global memory.
+__device__ __forceinline__ void store_frags(uint16_t *base, int64_t row0, const uint32_t (&A)[4][4], int g, int c) {
+    uint32_t *b = reinterpret_cast<uint32_t *>(base);
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        b[(row0 + g) * 32 + 8 * kk + c] = A[kk][0];
+        b[(row0 + g + 8) * 32 + 8 * kk + c] = A[kk][1];
+        b[(row0 + g) * 32 + 8 * kk + 4 + c] = A[kk][2];
+        b[(row0 + g + 8) * 32 + 8 * kk + 4 + c] = A[kk][3];
+    }
+}
+
+__device__ __forceinline__ void store_dO(uint16_t *base, int64_t row0, const uint32_t (&a)[4], int g, int c) {
+    uint32_t *b = reinterpret_cast<uint32_t *>(base);
+    b[(row0 + g) * 8 + c] = a[0];
+    b[(row0 + g + 8) * 8 + c] = a[1];
+    b[(row0 + g) * 8 + 4 + c] = a[2];
+    b[(row0 + g + 8) * 8 + 4 + c] = a[3];
+}
+
+// Forward of 16 rows: act[k] = bf16 inputs of products 1..3, o = output tiles.
+__device__ __forceinline__ void forward(const uint16_t *sw, const uint16_t *X, uint32_t (&act)[3][4][4],
+                                        float (&o)[2][4], int g, int c) {
+    uint32_t A0[4][4];
+    load_rows(A0, X, g, c);
+    float acc[8][4];
+    gemm64(acc, A0, sw + S_W0, g, c);
+    relu_pack(acc, act[0]);
+    gemm64(acc, act[0], sw + S_W1, g, c);
+    relu_pack(acc, act[1]);
+    gemm64(acc, act[1], sw + S_W2, g, c);
+    relu_pack(acc, act[2]);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        o[j][0] = o[j][1] = o[j][2] = o[j][3] = 0.0f;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            const uint16_t *w = sw + S_W3 + (8 * j + g) * LDW + 16 * kk + 2 * c;
+            mma(o[j], act[2][kk], ld32(w), ld32(w + 8));
+        }
+    }
+}
+
+// Backward of 16 rows from the output gradient fragment dO (one k-tile of
+// the 16 outputs): dX = gradient at the input (fp32 tiles). If dz is set,
+// the bf16 gradients at z3, z2, z1 are stored as rows of dz[0..2].
+__device__ __forceinline__ void backward(const uint16_t *sw, const uint32_t (&act)[3][4][4], const uint32_t (&dO)[4],
+                                         float (&dX)[8][4], int g, int c, uint16_t *dz, int64_t rows_cap,
+                                         int64_t row0) {
+    float acc[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+        const uint16_t *w = sw + S_T3 + (8 * j + g) * LDT3 + 2 * c;
+        mma(acc[j], dO, ld32(w), ld32(w + 8));
+    }
+    uint32_t G[4][4];
+    mask_pack(acc, act[2], G);
+    if (dz) store_frags(dz + 2 * rows_cap * 64, row0, G, g, c);
+    gemm64(acc, G, sw + S_T2, g, c);
+    mask_pack(acc, act[1], G);
+    if (dz) store_frags(dz + 1 * rows_cap * 64, row0, G, g, c);
+    gemm64(acc, G, sw + S_T1, g, c);
+    mask_pack(acc, act[0], G);
+    if (dz) store_frags(dz, row0, G, g, c);
+    gemm64(dX, G, sw + S_T0, g, c);
+}
+
+// ---------------------------------------------------------------------------
+// hash encoding
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cell_of(const float (&xn)[3], int level, int (&i0)[3], float (&f)[3]) {
+    const float n = (float)c_res[level];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float pos = __fmul_rn(xn[a], n);
+        int ii = (int)floorf(pos);
+        ii = min(max(ii, 0), c_res[level] - 1);
+        f[a] = fminf(fmaxf(__fsub_rn(pos, (float)ii), 0.0f), 1.0f);
+        i0[a] = ii;
+    }
+}
+
+__device__ __forceinline__ uint32_t vertex_index(int level, int x, int y, int z) {
+    if (level < kDenseLevels) {
+        const uint32_t n = (uint32_t)c_res[level] + 1u;
+        return (uint32_t)x + n * ((uint32_t)y + n * (uint32_t)z);
+    }
+    return ((uint32_t)x ^ ((uint32_t)y * 2654435761u) ^ ((uint32_t)z * 805459861u)) & (uint32_t)(kTableSize - 1);
+}
+
+__device__ __forceinline__ float2 encode_level(const float (&xn)[3], int level, const float *__restrict__ table) {
+    int i0[3];
+    float f[3];
+    cell_of(xn, level, i0, f);
+    const float2 *tl = reinterpret_cast<const float2 *>(table) + (size_t)level * kTableSize;
+    float2 e = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int cn = 0; cn < 8; ++cn) {
+        const int bx = cn & 1, by = (cn >> 1) & 1, bz = (cn >> 2) & 1;
+        const float w = (bx ? f[0] : 1.0f - f[0]) * (by ? f[1] : 1.0f - f[1]) * (bz ? f[2] : 1.0f - f[2]);
+        const float2 v = __ldg(tl + vertex_index(level, i0[0] + bx, i0[1] + by, i0[2] + bz));
+        e.x += w * v.x;
+        e.y += w * v.y;
+    }
+    return e;
+}
+
+__device__ __forceinline__ void scatter_level(const float (&xn)[3], int level, float g0, float g1, float *dtable) {
+    if (g0 == 0.0f && g1 == 0.0f) return;
+    int i0[3];
+    float f[3];
+    cell_of(xn, level, i0, f);
+    float *tl = dtable + (size_t)level * kTableSize * 2;
+#pragma unroll
+    for (int cn = 0; cn < 8; ++cn) {
+        const int bx = cn & 1, by = (cn >> 1) & 1, bz = (cn >> 2) & 1;
+        const float w = (bx ? f[0] : 1.0f - f[0]) * (by ? f[1] : 1.0f - f[1]) * (bz ? f[2] : 1.0f - f[2]);
+        const uint32_t idx = vertex_index(level, i0[0] + bx, i0[1] + by, i0[2] + bz);
+        atomicAdd(tl + 2 * idx, w * g0);
+        atomicAdd(tl + 2 * idx + 1, w * g1);
+    }
+}
+
+__device__ __forceinline__ void normalised(const TexelView &tv, float4 P, float (&xn)[3]) {
+    xn[0] = __fmul_rn(__fsub_rn(P.x, tv.lo[0]), tv.inv_ext);
+    xn[1] = __fmul_rn(__fsub_rn(P.y, tv.lo[1]), tv.inv_ext);
+    xn[2] = __fmul_rn(__fsub_rn(P.z, tv.lo[2]), tv.inv_ext);
+}
+
+// ---------------------------------------------------------------------------
+// geometric light features (input entries 32..48) and their gradient
+// ---------------------------------------------------------------------------
+struct Geo {
+    float ux, uy, uz, r, r2, ir, cl, cr, acr, a, s;
+    bool soft;
+};
+
+__device__ __forceinline__ Geo geo_of(const LightC &L, float4 P, float4 N) {
+    Geo q;
+    const float dx = L.p[0] - P.x, dy = L.p[1] - P.y, dz = L.p[2] - P.z;
+    q.r2 = dx * dx + dy * dy + dz * dz;
+    q.r = sqrtf(q.r2);
+    q.ir = 1.0f / q.r;
+    q.ux = dx * q.ir;
+    q.uy = dy * q.ir;
+    q.uz = dz * q.ir;
+    q.cl = -(q.ux * L.nl[0] + q.uy * L.nl[1] + q.uz * L.nl[2]);
+    q.cr = N.x * q.ux + N.y * q.uy + N.z * q.uz;
+    q.acr = fabsf(q.cr);
+    q.s = (q.cl - L.co) * L.inv_dc;
+    q.soft = q.cl > L.co && q.cl < L.ci;
+    q.a = q.cl >= L.ci ? 1.0f : (q.soft ? q.s * q.s : 0.0f);
+    return q;
+}
+
+// Writes entries 32..63 of one input row (bf16) and returns D.
+__device__ __forceinline__ float geometry_row(const LightC &L, float4 P, float4 N, const TexelView &tv, uint16_t *row) {
+    const Geo q = geo_of(L, P, N);
+    float G[kGeom];
+    G[0] = q.ux;
+    G[1] = q.uy;
+    G[2] = q.uz;
+    G[3] = q.r * 0.1f;
+    G[4] = L.nl[0];
+    G[5] = L.nl[1];
+    G[6] = L.nl[2];
+    G[7] = q.cl;
+    G[8] = q.acr;
+    G[9] = q.a;
+    G[10] = L.ci;
+    G[11] = (L.p[0] - tv.lo[0]) * tv.inv_ext;
+    G[12] = (L.p[1] - tv.lo[1]) * tv.inv_ext;
+    G[13] = (L.p[2] - tv.lo[2]) * tv.inv_ext;
+    G[14] = N.x;
+    G[15] = N.y;
+    G[16] = N.z;
+#pragma unroll
+    for (int k = 0; k < kGeom; ++k) row[32 + k] = bf16_bits(G[k]);
+    row[49] = bf16_bits(1.0f);
+#pragma unroll
+    for (int k = 50; k < 64; ++k) row[k] = 0;
+    return q.a * q.acr / q.r2;
+}
+
+// dO/d(x, y, z, yaw, pitch, theta_in) of one row from the gradient at the
+// input entries 32..48 (gX) and at D (gD), by the chain rule through the
+// features.
+__device__ __forceinline__ void geometry_grad(const LightC &L, float4 P, float4 N, const TexelView &tv,
+                                              const float *gX, float gD, float (&g)[6]) {
+    const Geo q = geo_of(L, P, N);
+    const float da_dcos = q.soft ? 2.0f * q.s * L.inv_dc : 0.0f;
+    const float da_dthin = q.soft ? 2.0f * q.s * q.s * L.inv_dc * L.sin_in : 0.0f;
+    const float g_a = gX[9] + gD * q.acr / q.r2;
+    const float g_cl = gX[7] + g_a * da_dcos;
+    const float g_cr = gX[8] + gD * q.a / q.r2;
+    const float sg = q.cr > 0.0f ? 1.0f : (q.cr < 0.0f ? -1.0f : 0.0f);
+    const float vx = gX[0] - L.nl[0] * g_cl + sg * N.x * g_cr;
+    const float vy = gX[1] - L.nl[1] * g_cl + sg * N.y * g_cr;
+    const float vz = gX[2] - L.nl[2] * g_cl + sg * N.z * g_cr;
+    const float udv = q.ux * vx + q.uy * vy + q.uz * vz;
+    const float radial = gX[3] * 0.1f - 2.0f * gD * q.a * q.acr / (q.r2 * q.r);
+    g[0] = (vx - q.ux * udv) * q.ir + q.ux * radial + gX[11] * tv.inv_ext;
+    g[1] = (vy - q.uy * udv) * q.ir + q.uy * radial + gX[12] * tv.inv_ext;
+    g[2] = (vz - q.uz * udv) * q.ir + q.uz * radial + gX[13] * tv.inv_ext;
+    const float u_dny = q.ux * L.dny[0] + q.uy * L.dny[1] + q.uz * L.dny[2];
+    const float u_dnp = q.ux * L.dnp[0] + q.uy * L.dnp[1] + q.uz * L.dnp[2];
+    g[3] = gX[4] * L.dny[0] + gX[5] * L.dny[1] + gX[6] * L.dny[2] - g_cl * u_dny;
+    g[4] = gX[4] * L.dnp[0] + gX[5] * L.dnp[1] + gX[6] * L.dnp[2] - g_cl * u_dnp;
+    g[5] = g_a * da_dthin - gX[10] * L.sin_in;
+}
+
+__device__ __forceinline__ float sigmoidf_(float v) { return 1.0f / (1.0f + __expf(-v)); }
+__device__ __forceinline__ float softplusf_(float v) { return v > 20.0f ? v : log1pf(__expf(v)); }
+
+// splitmix64 (Steele, Lea and Flood 2014) for drawing training samples.
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// training
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kMlpWarps * 32, 2) train_kernel(const TrainArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint16_t *sw = reinterpret_cast<uint16_t *>(smem_raw);
+    __shared__ double red[kMlpWarps];
+    load_weights(sw, A.Wb, true);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+    WarpScratch *ws = reinterpret_cast<WarpScratch *>(smem_raw + (size_t)S_ALL_END * 2) + warp;
+    const int64_t n = A.tex.n;
+    const int64_t tiles = ((int64_t)A.batch + 15) / 16;
+    const int64_t cap = A.rb.rows;
+    const double inv_b = 1.0 / (double)A.batch;
+    double loss = 0.0;
+    for (int64_t tile = (int64_t)blockIdx.x * kMlpWarps + warp; tile < tiles; tile += (int64_t)gridDim.x * kMlpWarps) {
+        const int64_t row0 = tile * 16;
+        if (lane < 16) {
+            const int64_t i = row0 + lane;
+            const bool valid = i < A.batch;
+            int32_t s = 0, t = 0;
+            if (valid) {
+                if (A.samples) {
+                    s = A.samples[2 * i];
+                    t = A.samples[2 * i + 1];
+                } else {
+                    const uint64_t r = mix64(A.seed ^ mix64((A.step << 32) ^ (uint64_t)i));
+                    s = (int32_t)(((r >> 32) * (uint64_t)A.n_solves) >> 32);
+                    t = (int32_t)(((r & 0xFFFFFFFFull) * (uint64_t)n) >> 32);
+                }
+            }
+            const float4 P = A.tex.pos[t], N = A.tex.nrm[t];
+            uint16_t *row = ws->X + lane * LDW;
+            ws->D[lane] = geometry_row(A.lights[s], P, N, A.tex, row);
+            ws->aux0[lane] = valid ? __ldg(A.E_obs + (int64_t)s * n + t) : 0.0f;
+            ws->aux1[lane] = valid ? A.tex.area[t] * A.tex.inv_mean_area : 0.0f;
+            float xn[3];
+            normalised(A.tex, P, xn);
+            ws->xn[lane][0] = xn[0];
+            ws->xn[lane][1] = xn[1];
+            ws->xn[lane][2] = xn[2];
+            ws->sidx[lane] = s;
+            ws->tidx[lane] = valid ? t : -1;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+            const int r = lane & 15, level = (lane >> 4) + 2 * p;
+            const float xn[3] = {ws->xn[r][0], ws->xn[r][1], ws->xn[r][2]};
+            const float2 e = encode_level(xn, level, A.table);
+            *reinterpret_cast<uint32_t *>(ws->X + r * LDW + 2 * level) = pack2(e.x, e.y);
+        }
+        __syncwarp();
+        {   // rows of the first product's input
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(ws->X);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(A.rb.act);
+            for (int k = lane; k < 16 * 32; k += 32) dst[(row0 + (k >> 5)) * 32 + (k & 31)] = src[(k >> 5) * (LDW / 2) + (k & 31)];
+        }
+        uint32_t act[3][4][4];
+        float o[2][4];
+        forward(sw, ws->X, act, o, g, c);
+        store_frags(A.rb.act + 1 * cap * 64, row0, act[0], g, c);
+        store_frags(A.rb.act + 2 * cap * 64, row0, act[1], g, c);
+        store_frags(A.rb.act + 3 * cap * 64, row0, act[2], g, c);
+        uint32_t dO[4] = {0u, 0u, 0u, 0u};
+        if (c == 0) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = g + 8 * h;
+                const float o0 = o[0][2 * h], o1 = o[0][2 * h + 1];
+                const float v = sigmoidf_(o0), sp = softplusf_(o1);
+                const float D = ws->D[r];
+                const float K = v * D + kRScale * sp;
+                const float e = K - ws->aux0[r];
+                const float wgt = ws->aux1[r];
+                loss += 0.5 * (double)wgt * (double)e * (double)e * inv_b;
+                const float dK = (float)((double)(wgt * e) * inv_b);
+                dO[h] = pack2(dK * v * (1.0f - v) * D, dK * kRScale * sigmoidf_(o1));
+            }
+        }
+        store_dO(A.rb.dz + 3 * cap * 64, row0, dO, g, c);
+        float dX[8][4];
+        backward(sw, act, dO, dX, g, c, A.rb.dz, cap, row0);
+        // encoding gradient: tile j < 4 holds input entries 8j + 2c (+1) = level 4j + c
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = g + 8 * h;
+                if (ws->tidx[r] < 0) continue;
+                const float xn[3] = {ws->xn[r][0], ws->xn[r][1], ws->xn[r][2]};
+                scatter_level(xn, 4 * j + c, dX[j][2 * h], dX[j][2 * h + 1], A.dtable);
+            }
+        __syncwarp();
+    }
+    loss = warp_sum_d(loss);
+    if (lane == 0) red[warp] = loss;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kMlpWarps; ++w) s += red[w];
+        A.loss_part[blockIdx.x] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the network on given rows
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kMlpWarps * 32, 2) network_kernel(const NetworkArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint16_t *sw = reinterpret_cast<uint16_t *>(smem_raw);
+    load_weights(sw, A.Wb, A.dO != nullptr);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+    WarpScratch *ws = reinterpret_cast<WarpScratch *>(smem_raw + (size_t)S_ALL_END * 2) + warp;
+    const int64_t tiles = ((int64_t)A.rows + 15) / 16;
+    const int64_t cap = A.rb.rows;
+    for (int64_t tile = (int64_t)blockIdx.x * kMlpWarps + warp; tile < tiles; tile += (int64_t)gridDim.x * kMlpWarps) {
+        const int64_t row0 = tile * 16;
+        for (int k = lane; k < 16 * 64; k += 32) {
+            const int64_t r = row0 + (k >> 6);
+            ws->X[(k >> 6) * LDW + (k & 63)] = r < A.rows ? bf16_bits(A.X[r * 64 + (k & 63)]) : (uint16_t)0;
+        }
+        __syncwarp();
+        {
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(ws->X);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(A.rb.act);
+            for (int k = lane; k < 16 * 32; k += 32) dst[(row0 + (k >> 5)) * 32 + (k & 31)] = src[(k >> 5) * (LDW / 2) + (k & 31)];
+        }
+        uint32_t act[3][4][4];
+        float o[2][4];
+        forward(sw, ws->X, act, o, g, c);
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int64_t r = row0 + g + 8 * (e >> 1);
+                if (r < A.rows) A.O[r * 16 + 8 * j + 2 * c + (e & 1)] = o[j][e];
+            }
+        if (A.dO) {
+            store_frags(A.rb.act + 1 * cap * 64, row0, act[0], g, c);
+            store_frags(A.rb.act + 2 * cap * 64, row0, act[1], g, c);
+            store_frags(A.rb.act + 3 * cap * 64, row0, act[2], g, c);
+            auto dv = [&](int64_t r, int col) { return r < A.rows ? A.dO[r * 16 + col] : 0.0f; };
+            uint32_t dO[4];
+            dO[0] = pack2(dv(row0 + g, 2 * c), dv(row0 + g, 2 * c + 1));
+            dO[1] = pack2(dv(row0 + g + 8, 2 * c), dv(row0 + g + 8, 2 * c + 1));
+            dO[2] = pack2(dv(row0 + g, 8 + 2 * c), dv(row0 + g, 9 + 2 * c));
+            dO[3] = pack2(dv(row0 + g + 8, 8 + 2 * c), dv(row0 + g + 8, 9 + 2 * c));
+            store_dO(A.rb.dz + 3 * cap * 64, row0, dO, g, c);
+            float dX[8][4];
+            backward(sw, act, dO, dX, g, c, A.rb.dz, cap, row0);
+            if (A.dX)
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int64_t r = row0 + g + 8 * (e >> 1);
+                        if (r < A.rows) A.dX[r * 64 + 8 * j + 2 * c + (e & 1)] = dX[j][e];
+                    }
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// weight gradient: dW_k = sum over rows of dz_{k+1}^T a_k, per chunk of rows
+// ---------------------------------------------------------------------------
+struct alignas(16) WgradScratch {
+    uint16_t dzs[16 * 24];
+    uint16_t as[16 * LDW];
+};
+
+__global__ void __launch_bounds__(128) wgrad_kernel(const RowBuffers rb, int32_t rows, float *__restrict__ partial) {
+    __shared__ WgradScratch scr[4];
+    __shared__ float red[4][16 * 64];
+    const int item = blockIdx.y, chunk = blockIdx.x;
+    const int layer = item < 12 ? item >> 2 : 3, mt = item < 12 ? item & 3 : 0;
+    const int64_t cap = rb.rows;
+    const uint16_t *act = rb.act + (int64_t)layer * cap * 64;
+    const uint16_t *dz = rb.dz + (int64_t)layer * cap * 64;
+    const int ldz = layer < 3 ? 64 : 16;
+    const int n0 = 16 * mt;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+    WgradScratch &S = scr[warp];
+    float acc[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+    const int64_t begin = (int64_t)chunk * kWgradChunk;
+    const int64_t end = min((int64_t)rows, begin + kWgradChunk);
+    for (int64_t r0 = begin + 16 * warp; r0 < end; r0 += 64) {
+        {   // gradient tile: 16 rows x 16 columns
+            const int rr = lane >> 1, half = lane & 1;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (r0 + rr < end) v = *reinterpret_cast<const uint4 *>(dz + (r0 + rr) * ldz + n0 + 8 * half);
+            *reinterpret_cast<uint4 *>(S.dzs + rr * 24 + 8 * half) = v;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {   // activation tile: 16 rows x 64 columns
+            const int idx = lane + 32 * q, rr = idx >> 3, part = idx & 7;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (r0 + rr < end) v = *reinterpret_cast<const uint4 *>(act + (r0 + rr) * 64 + 8 * part);
+            *reinterpret_cast<uint4 *>(S.as + rr * LDW + 8 * part) = v;
+        }
+        __syncwarp();
+        uint32_t a[4];
+        {
+            const int q = lane >> 3;
+            ldsm_x4_trans(a[0], a[1], a[2], a[3], S.dzs + ((q >> 1) * 8 + (lane & 7)) * 24 + (q & 1) * 8);
+        }
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            const int q = lane >> 3;
+            uint32_t b0, b1, b2, b3;
+            ldsm_x4_trans(b0, b1, b2, b3, S.as + ((q & 1) * 8 + (lane & 7)) * LDW + 16 * jj + (q >> 1) * 8);
+            mma(acc[2 * jj], a, b0, b1);
+            mma(acc[2 * jj + 1], a, b2, b3);
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) red[warp][(g + 8 * (e >> 1)) * 64 + 8 * j + 2 * c + (e & 1)] = acc[j][e];
+    __syncthreads();
+    float *out = partial + ((int64_t)chunk * kWgradItems + item) * 1024;
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x) out[i] = red[0][i] + red[1][i] + red[2][i] + red[3][i];
+}
+
+__global__ void wgrad_reduce_kernel(const float *__restrict__ partial, int n_chunks, float *__restrict__ dW,
+                                    const double *__restrict__ loss_part, int n_loss, double *loss) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kWeights) {
+        int item, local;
+        if (i < kOffW3) {
+            const int layer = i >> 12, r = i & 4095, nn = r >> 6, m = r & 63;
+            item = layer * 4 + (nn >> 4);
+            local = (nn & 15) * 64 + m;
+        } else {
+            item = 12;
+            local = i - kOffW3;
+        }
+        float s = 0.0f;
+        for (int ch = 0; ch < n_chunks; ++ch) s += partial[((int64_t)ch * kWgradItems + item) * 1024 + local];
+        dW[i] = s;
+    }
+    if (i == 0 && loss) {
+        double s = 0.0;
+        for (int k = 0; k < n_loss; ++k) s += loss_part[k];
+        *loss = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Adam
+// ---------------------------------------------------------------------------
+__global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float bc1,
+                            float bc2, uint16_t *__restrict__ bf) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float pi = p[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+        p[i] = pi;
+        if (bf) bf[i] = bf16_bits(pi);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// encoding of points and texels
+// ---------------------------------------------------------------------------
+__global__ void encode_points_kernel(const float *__restrict__ xn, int32_t n, const float *__restrict__ table,
+                                     float *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n * kLevels) return;
+    const int64_t pt = i / kLevels;
+    const int level = (int)(i % kLevels);
+    const float x[3] = {xn[3 * pt], xn[3 * pt + 1], xn[3 * pt + 2]};
+    const float2 e = encode_level(x, level, table);
+    out[pt * 32 + 2 * level] = e.x;
+    out[pt * 32 + 2 * level + 1] = e.y;
+}
+
+__global__ void encode_texels_kernel(const TexelView tv, const float *__restrict__ table, uint16_t *__restrict__ enc) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= tv.n_pad * kLevels) return;
+    const int64_t t = i / kLevels;
+    const int level = (int)(i % kLevels);
+    float x[3];
+    normalised(tv, tv.pos[t], x);
+    const float2 e = encode_level(x, level, table);
+    *reinterpret_cast<uint32_t *>(enc + t * 32 + 2 * level) = pack2(e.x, e.y);
+}
+
+// ---------------------------------------------------------------------------
+// design objective
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void design_rows(const DesignArgs &A, WarpScratch *ws, int lane, int l, int64_t t0) {
+    if (lane < 16) {
+        const int64_t t = t0 + lane;
+        const float4 P = A.tex.pos[t], N = A.tex.nrm[t];
+        uint16_t *row = ws->X + lane * LDW;
+        ws->D[lane] = geometry_row(A.lights[l], P, N, A.tex, row);
+        const uint4 *src = reinterpret_cast<const uint4 *>(A.enc + t * 32);
+        uint4 *dst = reinterpret_cast<uint4 *>(row);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dst[k] = src[k];
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(kMlpWarps * 32, 2) design_forward_kernel(const DesignArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint16_t *sw = reinterpret_cast<uint16_t *>(smem_raw);
+    load_weights(sw, A.Wb, false);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+    WarpScratch *ws = reinterpret_cast<WarpScratch *>(smem_raw + (size_t)S_FWD_END * 2) + warp;
+    const int64_t tpl = A.tex.n_pad / 16;
+    const int64_t tiles = tpl * A.n_lights;
+    for (int64_t tile = (int64_t)blockIdx.x * kMlpWarps + warp; tile < tiles; tile += (int64_t)gridDim.x * kMlpWarps) {
+        const int l = (int)(tile / tpl);
+        const int64_t t0 = (tile % tpl) * 16;
+        design_rows(A, ws, lane, l, t0);
+        uint32_t act[3][4][4];
+        float o[2][4];
+        forward(sw, ws->X, act, o, g, c);
+        if (c == 0)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = g + 8 * h;
+                const float K = sigmoidf_(o[0][2 * h]) * ws->D[r] + kRScale * softplusf_(o[0][2 * h + 1]);
+                A.K[(int64_t)l * A.tex.n_pad + t0 + r] = K;
+            }
+        __syncwarp();
+    }
+}
+
+__global__ void design_reduce_kernel(const TexelView tv, const LightC *__restrict__ lights, int32_t n_lights,
+                                     const float *__restrict__ K, const float *__restrict__ target,
+                                     const float *__restrict__ alpha, float *__restrict__ E_out, float *__restrict__ up,
+                                     double *__restrict__ loss_part) {
+    __shared__ double red[256];
+    double loss = 0.0;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tv.n_pad; t += (int64_t)gridDim.x * blockDim.x) {
+        float E = 0.0f;
+        for (int l = 0; l < n_lights; ++l) E += lights[l].intensity * K[(int64_t)l * tv.n_pad + t];
+        float u = 0.0f;
+        if (t < tv.n) {
+            const float d = E - target[t];
+            const float w = (alpha ? alpha[t] : 1.0f) * d;
+            u = tv.area[t] * w;
+            loss += 0.5 * (double)u * (double)d;
+            if (E_out) E_out[t] = E;
+        }
+        up[t] = u;
+    }
+    red[threadIdx.x] = loss;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) loss_part[blockIdx.x] = red[0];
+}
+
+__global__ void __launch_bounds__(kMlpWarps * 32, 2) design_backward_kernel(const DesignArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint16_t *sw = reinterpret_cast<uint16_t *>(smem_raw);
+    load_weights(sw, A.Wb, true);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+    WarpScratch *ws = reinterpret_cast<WarpScratch *>(smem_raw + (size_t)S_ALL_END * 2) + warp;
+    const int64_t tpl = A.tex.n_pad / 16;
+    const int64_t tiles = tpl * A.n_lights;
+    for (int64_t tile = (int64_t)blockIdx.x * kMlpWarps + warp; tile < tiles; tile += (int64_t)gridDim.x * kMlpWarps) {
+        const int l = (int)(tile / tpl);
+        const int64_t t0 = (tile % tpl) * 16;
+        const LightC &L = A.lights[l];
+        design_rows(A, ws, lane, l, t0);
+        uint32_t act[3][4][4];
+        float o[2][4];
+        forward(sw, ws->X, act, o, g, c);
+        uint32_t dO[4] = {0u, 0u, 0u, 0u};
+        if (c == 0)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = g + 8 * h;
+                const float D = ws->D[r];
+                const float v = sigmoidf_(o[0][2 * h]);
+                const float K = v * D + kRScale * softplusf_(o[0][2 * h + 1]);
+                const float u = A.up[t0 + r];
+                const float ui = u * L.intensity;       // dO/dK
+                ws->aux0[r] = ui * v;                   // dO/dD
+                ws->aux1[r] = u * K;                    // dO/dI
+                dO[h] = pack2(ui * v * (1.0f - v) * D, ui * kRScale * sigmoidf_(o[0][2 * h + 1]));
+            }
+        float dX[8][4];
+        backward(sw, act, dO, dX, g, c, nullptr, 0, 0);
+        // input entries 32..48 sit in tiles 4..6
+#pragma unroll
+        for (int j = 4; j < 7; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int col = 8 * j + 2 * c + (e & 1) - 32;
+                if (col < kGeom) ws->gX[g + 8 * (e >> 1)][col] = dX[j][e];
+            }
+        __syncwarp();
+        float gs[7] = {0, 0, 0, 0, 0, 0, 0};
+        if (lane < 16) {
+            const int64_t t = t0 + lane;
+            float gr[6];
+            geometry_grad(L, A.tex.pos[t], A.tex.nrm[t], A.tex, ws->gX[lane], ws->aux0[lane], gr);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) gs[k] = gr[k];
+            gs[6] = ws->aux1[lane];
+        }
+#pragma unroll
+        for (int k = 0; k < 7; ++k)
+#pragma unroll
+            for (int off = 8; off > 0; off >>= 1) gs[k] += __shfl_xor_sync(0xffffffffu, gs[k], off);
+        if (lane == 0) {
+            float *out = A.gpart + tile * 8;
+#pragma unroll
+            for (int k = 0; k < 7; ++k) out[k] = gs[k];
+            out[7] = 0.0f;
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void design_final_kernel(const float *__restrict__ gpart, const LightC *__restrict__ lights,
+                                    int32_t n_lights, int64_t tpl, const double *__restrict__ loss_part,
+                                    double *__restrict__ out) {
+    __shared__ double red[7][256];
+    const int l = blockIdx.x;
+    if (l == n_lights) {   // the objective
+        double s = 0.0;
+        if (threadIdx.x == 0) {
+            for (int k = 0; k < kReduceBlocks; ++k) s += loss_part[k];
+            out[(int64_t)n_lights * 8] = s;
+        }
+        return;
+    }
+    double s[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int64_t i = threadIdx.x; i < tpl; i += blockDim.x) {
+        const float *p = gpart + ((int64_t)l * tpl + i) * 8;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) s[k] += (double)p[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 7; ++k) red[k][threadIdx.x] = s[k];
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st)
+#pragma unroll
+            for (int k = 0; k < 7; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double *o = out + (int64_t)l * 8;
+        o[0] = red[0][0];
+        o[1] = red[1][0];
+        o[2] = red[2][0];
+        o[3] = red[3][0];
+        o[4] = red[4][0];
+        o[5] = red[6][0] * (double)lights[l].p_int;   // dI/dp_int = p_int
+        o[6] = red[5][0];
+        o[7] = 0.0;
+    }
+}
+
+int g_sms = 0;
+
+}  // namespace
+
+int train_grid(int device) {
+    if (g_sms == 0) cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, device);
+    return 2 * (g_sms > 0 ? g_sms : 1);
+}
+
+static cudaError_t set_smem(const void *fn, size_t bytes) {
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+cudaError_t launch_train(const TrainArgs &a, int grid, cudaStream_t s) {
+    const size_t smem = smem_bytes(true);
+    cudaError_t e = set_smem((const void *)train_kernel, smem);
+    if (e != cudaSuccess) return e;
+    train_kernel<<<grid, kMlpWarps * 32, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_network(const NetworkArgs &a, cudaStream_t s) {
+    const size_t smem = smem_bytes(true);
+    cudaError_t e = set_smem((const void *)network_kernel, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t tiles = ((int64_t)a.rows + 15) / 16;
+    const int grid = (int)std::min<int64_t>((tiles + kMlpWarps - 1) / kMlpWarps, 4096);
+    network_kernel<<<grid, kMlpWarps * 32, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wgrad(const RowBuffers &rb, int32_t rows, float *partial, float *dW, const double *loss_part,
+                         int32_t n_loss_part, double *loss, cudaStream_t s) {
+    const int chunks = (rows + kWgradChunk - 1) / kWgradChunk;
+    wgrad_kernel<<<dim3(chunks, kWgradItems), 128, 0, s>>>(rb, rows, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    wgrad_reduce_kernel<<<(kWeights + 255) / 256, 256, 0, s>>>(partial, chunks, dW, loss_part, n_loss_part, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2,
+                        float eps, float bc1, float bc2, uint16_t *bf16_out, cudaStream_t s) {
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    adam_kernel<<<grid, 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, eps, bc1, bc2, bf16_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_encode_points(const float *xn, int32_t n, const float *table, float *enc_out, cudaStream_t s) {
+    const int64_t work = (int64_t)n * kLevels;
+    encode_points_kernel<<<(int)((work + 255) / 256), 256, 0, s>>>(xn, n, table, enc_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_encode_texels(const TexelView &t, const float *table, uint16_t *enc, cudaStream_t s) {
+    const int64_t work = t.n_pad * kLevels;
+    encode_texels_kernel<<<(int)((work + 255) / 256), 256, 0, s>>>(t, table, enc);
+    return cudaGetLastError();
+}
+
+static int design_grid(const DesignArgs &a) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int64_t tiles = a.tex.n_pad / 16 * a.n_lights;
+    return (int)std::min<int64_t>((tiles + kMlpWarps - 1) / kMlpWarps, (int64_t)train_grid(dev) * 4);
+}
+
+cudaError_t launch_design_forward(const DesignArgs &a, cudaStream_t s) {
+    const size_t smem = smem_bytes(false);
+    cudaError_t e = set_smem((const void *)design_forward_kernel, smem);
+    if (e != cudaSuccess) return e;
+    design_forward_kernel<<<design_grid(a), kMlpWarps * 32, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_design_reduce(const TexelView &t, const LightC *lights, int32_t n_lights, const float *K,
+                                 const float *E_target, const float *alpha, float *E_out, float *up,
+                                 double *loss_part, cudaStream_t s) {
+    design_reduce_kernel<<<kReduceBlocks, 256, 0, s>>>(t, lights, n_lights, K, E_target, alpha, E_out, up, loss_part);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_design_backward(const DesignArgs &a, cudaStream_t s) {
+    const size_t smem = smem_bytes(true);
+    cudaError_t e = set_smem((const void *)design_backward_kernel, smem);
+    if (e != cudaSuccess) return e;
+    design_backward_kernel<<<design_grid(a), kMlpWarps * 32, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_design_final(const float *gpart, const LightC *lights, int32_t n_lights, int64_t tiles_per_light,
+                                const double *loss_part, double *out, cudaStream_t s) {
+    design_final_kernel<<<n_lights + 1, 256, 0, s>>>(gpart, lights, n_lights, tiles_per_light, loss_part, out);
+    return cudaGetLastError();
+}
+
+}  // namespace sg

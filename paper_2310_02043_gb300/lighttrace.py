@@ -29,7 +29,7 @@ EXPORTED = ("lt_version", "lt_create", "lt_destroy", "lt_set_stream", "lt_last_e
             "lt_get_irradiance", "lt_texel_areas", "lt_set_adjoint_weights", "lt_trace_adjoint", "lt_debug_paths",
             "lt_get_stats", "lt_set_launch", "lt_count_work", "lt_loss_static", "lt_set_design", "lt_batch_setup",
             "lt_batch_set_lights", "lt_batch_step", "lt_batch_texel_sums", "lt_batch_irradiance",
-            "lt_batch_stream")
+            "lt_batch_stream", "lt_texel_centres")
 
 
 class LtError(RuntimeError):
@@ -101,6 +101,7 @@ def _declare(lib):
         "lt_batch_texel_sums": [vp, i32, vp, ci],
         "lt_batch_irradiance": [vp, i32, vp, ci],
         "lt_batch_stream": [vp, ctypes.POINTER(ctypes.c_void_p)],
+        "lt_texel_centres": [vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -317,6 +318,13 @@ class Tracer:
         self._check(self.lib.lt_batch_step(self.h, seed_fwd, seed_adj, _ptr(loss)[0], _ptr(grad)[0],
                                            1 if use_graph else 0))
         return loss, grad
+
+    def texel_centres(self):
+        """(pos [T, 3], normal [T, 3]) float32 of every texel centre."""
+        pos = np.empty((self.n_texels, 3), np.float32)
+        nrm = np.empty((self.n_texels, 3), np.float32)
+        self._check(self.lib.lt_texel_centres(self.h, _ptr(pos)[0], _ptr(nrm)[0]))
+        return pos, nrm
 
     def batch_stream(self) -> int:
         """The batch stream handle (cudaStream_t as an int; 0 before batch_setup)."""

@@ -350,3 +350,23 @@ def random_weights(n_texels: int, seed: int, scale: float = 1.0) -> np.ndarray:
     """Seeded per-texel adjoint weights (used to inject dO/dE directly)."""
     rng = np.random.default_rng(seed)
     return np.ascontiguousarray(rng.normal(0.0, scale, size=n_texels).astype(np.float32))
+
+
+# --------------------------------------------------------------------------
+# Initial parameters of the irradiance surrogate
+# --------------------------------------------------------------------------
+def surrogate_init(seed: int = 0):
+    """Seeded initial parameters of the irradiance surrogate: the four weight
+    matrices ([64, 64] x 3 and [16, 64], [out, in]) uniform in
+    +-sqrt(6 / fan_in) (He et al. 2015, uniform form), flattened in order, and
+    the hash table [16, 2^19, 2] uniform in +-1e-4 (the hash encoding's
+    initialisation). float32."""
+    rng = np.random.default_rng(seed + 7000)
+    parts = []
+    for out_dim, in_dim in ((64, 64), (64, 64), (64, 64), (16, 64)):
+        b = np.sqrt(6.0 / in_dim)
+        parts.append(rng.uniform(-b, b, size=(out_dim, in_dim)))
+    W = np.concatenate([p.ravel() for p in parts]).astype(np.float32)
+    table = rng.uniform(-1e-4, 1e-4, size=(16, 1 << 19, 2)).astype(np.float32)
+    return W, table
+

@@ -11,10 +11,10 @@ from paper_2310_02043_gb300 import _build, lighttrace
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared(header):
+def _declared(header, prefix="lt"):
     src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(lt_[a-z_0-9]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(" + prefix + r"_[a-z_0-9]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
@@ -29,6 +29,20 @@ def test_every_declared_function_is_exported(lib):
     for n in names:
         assert hasattr(lib, n), n
     assert set(lighttrace.EXPORTED) <= set(names)
+
+
+def test_every_surrogate_function_is_exported(lib):
+    from paper_2310_02043_gb300 import surrogate
+    names = _declared("sg.h", "sg")
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(surrogate.EXPORTED) == set(names)
+    assert lib.sg_create(None, 0, None) == lighttrace.LT_ERR_ARG
+
+
+def test_every_header_is_checked():
+    assert sorted(f for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")) == ["lt.h", "sg.h"]
 
 
 def test_version_and_argument_checks(lib):
