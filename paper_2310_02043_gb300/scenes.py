@@ -370,3 +370,33 @@ def surrogate_init(seed: int = 0):
     table = rng.uniform(-1e-4, 1e-4, size=(16, 1 << 19, 2)).astype(np.float32)
     return W, table
 
+
+def surrogate_training_lights(seed: int, n: int, theta_out_deg: float = 60.0) -> np.ndarray:
+    """Unit-intensity spots (I_e = 1) spread over the office ceiling for the
+    surrogate's training solves: position U[0.5, 19.5] x U[0.5, 9.5] x
+    U[2.5, 2.9] m, yaw U[0, 2 pi), pitch -pi/2 + U(-0.4, 0.4), theta_in
+    U[25, 55] deg, theta_out fixed."""
+    rng = np.random.default_rng(seed + 9000)
+    rows = []
+    for _ in range(n):
+        pos = (rng.uniform(0.5, 19.5), rng.uniform(0.5, 9.5), rng.uniform(2.5, 2.9))
+        rows.append(spot_light(pos, rng.uniform(0, 2 * np.pi), -np.pi / 2 + rng.uniform(-0.4, 0.4), 1.0,
+                               np.radians(rng.uniform(25.0, 55.0)), np.radians(theta_out_deg)))
+    return make_lights(rows)
+
+
+def perturb_lights_in_plane(lights: np.ndarray, seed: int, pos_sigma: float = 0.3, angle_sigma: float = 0.1,
+                            intensity_range=(0.7, 1.3), theta_in_deg: float = 5.0) -> np.ndarray:
+    """Seeded perturbation that keeps every light at its height (ceiling
+    spots stay in the room): x, y += N(0, pos_sigma), yaw, pitch +=
+    N(0, angle_sigma), I_e scaled by U[intensity_range], theta_in +=
+    U(-theta_in_deg, theta_in_deg) degrees (kept below theta_out)."""
+    rng = np.random.default_rng(seed)
+    out = np.array(lights, np.float64, copy=True)
+    n = out.shape[0]
+    out[:, 1:3] += rng.normal(0.0, pos_sigma, (n, 2))
+    out[:, 4:6] += rng.normal(0.0, angle_sigma, (n, 2))
+    out[:, 6] *= np.sqrt(rng.uniform(intensity_range[0], intensity_range[1], n))
+    out[:, 7] = np.clip(out[:, 7] + np.radians(rng.uniform(-theta_in_deg, theta_in_deg, n)), 0.0, out[:, 8] - 1e-3)
+    return out
+
