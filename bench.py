@@ -634,6 +634,14 @@ def run_surrogate(args):
     warm_s, warm_hist, _ = warmstart.time_to_loss(
         tr, sc, start, target, [("surrogate", prob, 400, 0.02), ("tracer", 1 << 22, 2000, 0.02)], SG_THRESHOLD,
         area, max_seconds=60)
+    # a tighter target: the surrogate's optimum no longer suffices and the
+    # tracer refines from it
+    tight = SG_THRESHOLD / 2
+    plain_t, plain_thist, _ = warmstart.time_to_loss(tr, sc, start, target, [("tracer", 1 << 22, 4000, 0.02)],
+                                                     tight, area, max_seconds=60)
+    warm_t, warm_thist, _ = warmstart.time_to_loss(
+        tr, sc, start, target, [("surrogate", prob, 200, 0.02), ("tracer", 1 << 22, 4000, 0.01)], tight, area,
+        max_seconds=60)
     clocks = clock.stop()
     fit_s = info["solve_s"] + info["train_s"]
     line = {"metric": "s to relative loss 1e-3 (surrogate warm start + tracer)", "value": warm_s,
@@ -655,10 +663,32 @@ def run_surrogate(args):
                          "unit": "TFLOP/s", "frac": design_flops / (design_ms / 1e3) / 1e12 / peak, "traffic": None,
                          "kernel": "sg_design (network forward + backward over 16 spots x all texels)",
                          "peak_basis": "measured bf16 burst (MEASURED_PEAKS.json), of measured"},
+            "tight": {"threshold": tight, "plain_s": plain_t, "warm_s": warm_t,
+                      "history": {"plain": plain_thist, "warm": warm_thist}},
             "history": {"plain": plain_hist, "warm": warm_hist}, "cpu_baseline": None, "clocks": clocks,
             "e2e": {"value": warm_s, "unit": "s", "h2d_bytes_per_step": 16 * 36, "d2h_bytes_per_step": 16 * 64 + 8},
             "gpu_launches": None}
     print(json.dumps(line), flush=True)
+    sg.close()
+    tr.close()
+
+
+def run_profile_surrogate(args):
+    """A small surrogate fit (64 solves at 2^18 photons), 5 training steps at
+    batch 2^18 and 3 design evaluations of the 16 office spots (for ncu)."""
+    import torch
+    from paper_2310_02043_gb300 import warmstart
+    from paper_2310_02043_gb300.lighttrace import Tracer
+    torch.cuda.set_device(0)
+    sc = scenes.office(seed=0, pitch=0.1)
+    tr = Tracer(0)
+    T = tr.upload_scene(sc)
+    sg, _ = warmstart.fit(tr, 64, 1 << 18, HITS, 5, SG_BATCH)
+    target = torch.zeros(T, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        sg.design(scenes.office_lights(0), target)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": "surrogate", "texels": T}))
     sg.close()
     tr.close()
 
@@ -699,8 +729,8 @@ def main():
     if args.workload == "batch" and args.impl == "ours" and not args.profile_only:
         run_batch(args)
         return
-    if args.workload == "surrogate" and args.impl == "ours" and not args.profile_only:
-        run_surrogate(args)
+    if args.workload == "surrogate" and args.impl == "ours":
+        run_profile_surrogate(args) if args.profile_only else run_surrogate(args)
         return
     if args.profile_only:
         run_profile_case(args)
