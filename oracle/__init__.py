@@ -62,8 +62,8 @@ def _declare(lib):
     lib.or_closest_hits.argtypes = [vp, i32, vp, vp, vp, i64, i32, vp, vp, vp]
     lib.or_philox4x32_10.argtypes = [vp, vp, vp]
     lib.or_philox4x32_10.restype = None
-    lib.or_dflux.argtypes = [vp, u64, vp, vp, f64, vp, vp]
-    lib.or_emit.argtypes = [vp, u64, u64, u32, u64, vp, vp, vp]
+    lib.or_dflux.argtypes = [vp, u64, vp, vp, f64, f64, f64, vp, vp]
+    lib.or_emit.argtypes = [vp, u64, u64, u32, u64, vp, vp, vp, vp]
     lib.or_cosine_dir.argtypes = [vp, f64, f64, vp]
     for name in ("or_forward", "or_adjoint", "or_paths", "or_closest_hits", "or_dflux", "or_emit",
                  "or_cosine_dir"):
@@ -178,25 +178,32 @@ def philox(ctr, key):
     return out
 
 
-def dflux(light_row, n_rays: int, x1, n1, a_emit: float = 1.0):
-    """(Phi_r, dPhi_r/dp[8]) for one light with its first hit held at x1."""
+def dflux(light_row, n_rays: int, x1, n1, a_emit: float = 1.0, u3: float = 0.5, u4: float = 0.5):
+    """(Phi_r, dPhi_r/dp[8]) for one light with its first hit held at x1.
+    For an area light the ray origin is given by the position uniforms (u3,
+    u4) and a_emit is the cosine towards x1 (computed)."""
     lib = _load()
     lp = np.ascontiguousarray(light_row, np.float64).reshape(9)
     x = np.ascontiguousarray(x1, np.float64)
     n = np.ascontiguousarray(n1, np.float64)
     phi = np.zeros(1)
     out = np.zeros(8)
-    lib.or_dflux(_p(lp), n_rays, _p(x), _p(n), a_emit, _p(phi), _p(out))
+    lib.or_dflux(_p(lp), n_rays, _p(x), _p(n), a_emit, u3, u4, _p(phi), _p(out))
     return float(phi[0]), out
 
 
-def emit(light_row, n_rays: int, seed: int, photon: int, design: int = 0):
+def emit(light_row, n_rays: int, seed: int, photon: int, design: int = 0, origin: bool = False):
+    """Emitted direction, flux and falloff (and with origin=True the ray
+    origin) of one photon of a single light."""
     lib = _load()
     lp = np.ascontiguousarray(light_row, np.float64).reshape(9)
     w = np.zeros(3)
     phi = np.zeros(1)
     a = np.zeros(1)
-    lib.or_emit(_p(lp), n_rays, seed, design, photon, _p(w), _p(phi), _p(a))
+    x0 = np.zeros(3)
+    lib.or_emit(_p(lp), n_rays, seed, design, photon, _p(w), _p(phi), _p(a), _p(x0))
+    if origin:
+        return w, float(phi[0]), float(a[0]), x0
     return w, float(phi[0]), float(a[0])
 
 

@@ -22,6 +22,12 @@
  *     gradient that Alg. S1 derives, regulariser 0), the spot soft edge a(theta)
  *     of Eq. S.11 and its position term (Eq. S.12), and the orientation chain
  *     rule (Eq. 15) with a yaw/pitch axis instead of a rotation vector.
+ *   - Rectangular area lights (supplement, Eq. S.15-S.16): a Lambertian
+ *     rectangle of total power P = p^2/2, rays sampled uniformly over its
+ *     surface and over the hemisphere about its normal, Phi_r = 2 P cos / N
+ *     (expected total P); dPhi_r/dp = Phi_r d log(cos_1 / r^2) + Phi_r
+ *     d log(cos theta), with the first hit fixed and the ray origin moving
+ *     rigidly with the light (translation, and rotation about the centroid).
  *
  * Precision: everything continuous (flux, hit points, directions, derivatives,
  * sums) is double. The two integer decisions of every segment -- which
@@ -33,7 +39,8 @@
  *
  * Random numbers: Philox4x32-10 (Salmon et al., SC 2011), counter =
  * (photon index low, photon index high, segment, design word), key = (seed
- * low, seed high); uniform u = (x >> 8) * 2^-24 from counter lanes 0 and 1.
+ * low, seed high); uniform u = (x >> 8) * 2^-24 from counter lanes 0 and 1
+ * (directions), and from lanes 2 and 3 for the position on an area light.
  *
  * Build: plain C99 with OpenMP; compile with -ffp-contract=off so float
  * arithmetic is the same on every host.
@@ -71,15 +78,23 @@ void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* Two uniforms in [0, 1) for (photon, segment, design) under `seed`. */
-static void draw2(uint64_t seed, uint64_t photon, uint32_t segment, uint32_t design, double *u1, double *u2)
+/* Four uniforms in [0, 1) for (photon, segment, design) under `seed`. */
+static void draw4(uint64_t seed, uint64_t photon, uint32_t segment, uint32_t design, double u[4])
 {
     uint32_t ctr[4] = {(uint32_t)photon, (uint32_t)(photon >> 32), segment, design};
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     uint32_t r[4];
     or_philox4x32_10(ctr, key, r);
-    *u1 = (double)(r[0] >> 8) * (1.0 / 16777216.0);
-    *u2 = (double)(r[1] >> 8) * (1.0 / 16777216.0);
+    for (int k = 0; k < 4; ++k) u[k] = (double)(r[k] >> 8) * (1.0 / 16777216.0);
+}
+
+/* The first two of them. */
+static void draw2(uint64_t seed, uint64_t photon, uint32_t segment, uint32_t design, double *u1, double *u2)
+{
+    double u[4];
+    draw4(seed, photon, segment, design, u);
+    *u1 = u[0];
+    *u2 = u[1];
 }
 
 /* ------------------------------------------------------------------------ */
@@ -257,7 +272,7 @@ static void tri_normal(const or_scene *s, int32_t tri, double n[3])
 /* Luminaires (Sec. 4.4, supplement "Derivative terms")                      */
 /* ------------------------------------------------------------------------ */
 typedef struct {
-    int type;               /* 0 point, 1 spot */
+    int type;               /* 0 point, 1 spot, 2 rectangular area light */
     double x[3];
     double yaw, pitch, p, th_in, th_out;
     double I;               /* I_e = p^2 / 2 (Sec. 4.4.1) */
@@ -265,7 +280,10 @@ typedef struct {
     double e1[3], e2[3];    /* dn/dpitch and dn/dyaw / cos(pitch): frame around n */
     double dn_dyaw[3], dn_dpitch[3];
     double co, ci;          /* cos(theta_out), cos(theta_in) */
-    double omega;           /* solid angle sampled: 4 pi (point) or 2 pi (1 - cos theta_out) (spot) */
+    double omega;           /* flux per ray = I omega a / N: 4 pi (point), 2 pi (1 - cos theta_out) (spot),
+                               2 (area: Phi_r = 2 P cos / N with a = cos) */
+    double t[3], b[3];      /* area: rectangle edges' directions, t = dn/dpitch, b = n x t */
+    double half_u, half_v;  /* area: half width along t, half height along b */
     uint64_t n_rays;        /* N_l */
     uint64_t first;         /* first global photon index of this light */
 } or_light;
@@ -294,6 +312,14 @@ static void lights_init(or_light *L, const double *params, int32_t n_lights, uin
             o->co = cos(o->th_out);
             o->ci = cos(o->th_in);
             o->omega = 2.0 * OR_PI * (1.0 - o->co);
+        } else if (o->type == 2) {
+            /* the theta_in / theta_out slots carry the width and height */
+            o->co = 0.0;
+            o->omega = 2.0;
+            o->half_u = 0.5 * o->th_in;
+            o->half_v = 0.5 * o->th_out;
+            for (int k = 0; k < 3; ++k) o->t[k] = o->e1[k];
+            o->b[0] = sy; o->b[1] = -cy; o->b[2] = 0.0;
         } else {
             o->omega = 4.0 * OR_PI;
         }
@@ -319,12 +345,28 @@ static double spot_falloff(const or_light *L, double c)
     return s * s;
 }
 
-/* Exitant ray of a light: direction w and flux Phi_r (Sec. 4.2 and the
- * supplement: point lights sample the sphere uniformly, Phi_r = I 4 pi / N;
- * spots sample the outer cone uniformly, Phi_r = I 2 pi (1 - cos theta_out) a / N). */
-static double emit(const or_light *L, double u1, double u2, double w[3], double *a_out)
+/* Exitant ray of a light: origin x0, direction w and flux Phi_r (Sec. 4.2
+ * and the supplement: point lights sample the sphere uniformly,
+ * Phi_r = I 4 pi / N; spots sample the outer cone uniformly,
+ * Phi_r = I 2 pi (1 - cos theta_out) a / N; area lights sample their
+ * rectangle (u3, u4) and the hemisphere about n uniformly, Phi_r =
+ * 2 P cos theta / N). */
+static double emit(const or_light *L, const double u[4], double x0[3], double w[3], double *a_out)
 {
+    double u1 = u[0], u2 = u[1];
     double phi = 2.0 * OR_PI * u2;
+    for (int k = 0; k < 3; ++k) x0[k] = L->x[k];
+    if (L->type == 2) {
+        double c = 1.0 - u1;
+        double s = sqrt(fmax(0.0, 1.0 - c * c));
+        double su = (2.0 * u[2] - 1.0) * L->half_u, sv = (2.0 * u[3] - 1.0) * L->half_v;
+        for (int k = 0; k < 3; ++k) {
+            w[k] = s * cos(phi) * L->e1[k] + s * sin(phi) * L->e2[k] + c * L->ns[k];
+            x0[k] = L->x[k] + su * L->t[k] + sv * L->b[k];
+        }
+        *a_out = c;
+        return L->I * L->omega * c / (double)L->n_rays;
+    }
     if (L->type == 1) {
         double c = 1.0 - u1 * (1.0 - L->co);
         double s = sqrt(fmax(0.0, 1.0 - c * c));
@@ -356,13 +398,21 @@ static void cosine_dir(const double n[3], double u1, double u2, double w[3])
     for (int k = 0; k < 3; ++k) w[k] = lx * t1[k] + ly * t2[k] + z * n[k];
 }
 
+static void area_dflux(const or_light *L, double phi_r, const double x0[3], double su, double sv,
+                       const double x1[3], const double n1[3], double out[8]);
+
 /* dPhi_r/dp at the first hit x1 with the first hit held fixed (Sec. 4.4.2).
- * n1 is the unit normal at x1 facing the light. Output order:
+ * n1 is the unit normal at x1 facing the light; x0 the ray origin and
+ * (su, sv) its coordinates on an area light. Output order:
  * [x, y, z, yaw, pitch, p_int, theta_in, theta_out]. */
-static void dflux_dp(const or_light *L, double phi_r, double a_emit, const double x1[3], const double n1[3],
-                     double out[8])
+static void dflux_dp(const or_light *L, double phi_r, double a_emit, const double x0[3], double su, double sv,
+                     const double x1[3], const double n1[3], double out[8])
 {
     for (int k = 0; k < 8; ++k) out[k] = 0.0;
+    if (L->type == 2) {
+        area_dflux(L, phi_r, x0, su, sv, x1, n1, out);
+        return;
+    }
     double d[3] = {L->x[0] - x1[0], L->x[1] - x1[1], L->x[2] - x1[2]};
     double ell = norm3(d);
     double u[3] = {d[0] / ell, d[1] / ell, d[2] / ell};
@@ -399,6 +449,43 @@ static void dflux_dp(const or_light *L, double phi_r, double a_emit, const doubl
     out[7] = scale * (-2.0) * (c - L->co) * (c - L->ci) * sin(L->th_out) / (D * D * D);
 }
 
+/* Area light (Eq. S.15-S.16): Phi_r = 2 P cos(theta) / N with cos(theta) =
+ * n . w, w the unit direction from the origin x0 to the fixed hit x1. With
+ * the sampling measure held fixed, dPhi_r/dq = I~ d(cos_1 / r^2)/dq +
+ * (2 P / N) d cos(theta)/dq. The origin moves rigidly with the light:
+ * dx0/dx = 1, dx0/dangle = su dt/dangle + sv db/dangle, and n turns with
+ * the angles. */
+static void area_dflux(const or_light *L, double phi_r, const double x0[3], double su, double sv,
+                       const double x1[3], const double n1[3], double out[8])
+{
+    double d[3] = {x0[0] - x1[0], x0[1] - x1[1], x0[2] - x1[2]};
+    double ell = norm3(d);
+    double u[3] = {d[0] / ell, d[1] / ell, d[2] / ell};       /* from x1 towards x0 */
+    double w[3] = {-u[0], -u[1], -u[2]};                         /* emitted direction */
+    double c1 = dot3(n1, u);
+    double ct = dot3(L->ns, w);
+    double k = L->I * L->omega / (double)L->n_rays;              /* 2 P / N */
+    double g0[3] = {0.0, 0.0, 0.0};                              /* dPhi_r / dx0 */
+    if (c1 > 0.0) {
+        double It = phi_r * ell * ell / c1;
+        for (int i = 0; i < 3; ++i) g0[i] = It * (n1[i] - 3.0 * c1 * u[i]) / (ell * ell * ell);
+    }
+    /* cos(theta) = -n . u: d/dx0 = -(n - (n . u) u) / r = -(n + ct u) / r */
+    for (int i = 0; i < 3; ++i) g0[i] += k * (-(L->ns[i] + ct * u[i]) / ell);
+    for (int i = 0; i < 3; ++i) out[i] = g0[i];
+    double cy = cos(L->yaw), sy = sin(L->yaw), cp = cos(L->pitch), sp = sin(L->pitch);
+    double dt_dyaw[3] = {sp * sy, -sp * cy, 0.0}, dt_dpitch[3] = {-cp * cy, -cp * sy, -sp};
+    double db_dyaw[3] = {cy, sy, 0.0};
+    double dx0_dyaw[3], dx0_dpitch[3];
+    for (int i = 0; i < 3; ++i) {
+        dx0_dyaw[i] = su * dt_dyaw[i] + sv * db_dyaw[i];
+        dx0_dpitch[i] = su * dt_dpitch[i];
+    }
+    out[3] = dot3(g0, dx0_dyaw) + k * dot3(w, L->dn_dyaw);
+    out[4] = dot3(g0, dx0_dpitch) + k * dot3(w, L->dn_dpitch);
+    out[5] = L->p * L->omega * ct / (double)L->n_rays;           /* P = p^2 / 2 */
+}
+
 /* ------------------------------------------------------------------------ */
 /* One photon path (Alg. 1 / Alg. 2)                                          */
 /* ------------------------------------------------------------------------ */
@@ -423,11 +510,12 @@ static void trace_photon(const or_scene *s, const or_light *L, int32_t n_lights,
 {
     int32_t l = light_of(L, n_lights, photon);
     const or_light *lt = &L[l];
-    double u1, u2, w[3], a_emit;
-    draw2(seed, photon, 0u, design, &u1, &u2);
-    double phi_r = emit(lt, u1, u2, w, &a_emit);
+    double u1, u2, w[3], a_emit, u0[4], o[3];
+    draw4(seed, photon, 0u, design, u0);
+    double phi_r = emit(lt, u0, o, w, &a_emit);
     double phi = phi_r;
-    double o[3] = {lt->x[0], lt->x[1], lt->x[2]};
+    double x0[3] = {o[0], o[1], o[2]};
+    double su = (2.0 * u0[2] - 1.0) * lt->half_u, sv = (2.0 * u0[3] - 1.0) * lt->half_v;
     int32_t skip_tile = -1;
     double g = 0.0, beta = 1.0, dphi[8];
     io->has_grad = 0;
@@ -448,7 +536,7 @@ static void trace_photon(const or_scene *s, const or_light *L, int32_t n_lights,
             io->n_dep += 1;
         }
         if (io->w) {
-            if (i == 1) { dflux_dp(lt, phi_r, a_emit, x, n, dphi); io->has_grad = 1; }
+            if (i == 1) { dflux_dp(lt, phi_r, a_emit, x0, su, sv, x, n, dphi); io->has_grad = 1; }
             g += io->w[t] * beta;                       /* Eq. 12 */
         }
         if (i == max_hits) break;
@@ -642,26 +730,36 @@ int or_closest_hits(const float *xyz, int32_t n_tri, const int32_t *tile, const 
 /* dPhi_r/dp for a given light, emitted-ray falloff and fixed first hit; used
  * by the tests to check the derivative formulas in isolation. */
 int or_dflux(const double *light_params, uint64_t n_rays, const double *x1, const double *n1, double a_emit,
-             double *phi_out, double *out)
+             double u3, double u4, double *phi_out, double *out)
 {
     or_light L;
     lights_init(&L, light_params, 1, n_rays);
+    double x0[3] = {L.x[0], L.x[1], L.x[2]}, su = 0.0, sv = 0.0;
+    if (L.type == 2) {    /* origin from the position uniforms; a = cos(theta) towards x1 */
+        su = (2.0 * u3 - 1.0) * L.half_u;
+        sv = (2.0 * u4 - 1.0) * L.half_v;
+        for (int k = 0; k < 3; ++k) x0[k] = L.x[k] + su * L.t[k] + sv * L.b[k];
+        double d[3] = {x1[0] - x0[0], x1[1] - x0[1], x1[2] - x0[2]};
+        a_emit = dot3(L.ns, d) / norm3(d);
+    }
     double phi_r = L.I * L.omega * a_emit / (double)L.n_rays;
     *phi_out = phi_r;
-    dflux_dp(&L, phi_r, a_emit, x1, n1, out);
+    dflux_dp(&L, phi_r, a_emit, x0, su, sv, x1, n1, out);
     return 0;
 }
 
 /* Emitted direction and falloff of photon `photon` under `seed` for a single
  * light with n_rays photons: used by the tests to check the sampling. */
 int or_emit(const double *light_params, uint64_t n_rays, uint64_t seed, uint32_t design, uint64_t photon,
-            double *w_out, double *phi_out, double *a_out)
+            double *w_out, double *phi_out, double *a_out, double *origin_out)
 {
     or_light L;
     lights_init(&L, light_params, 1, n_rays);
-    double u1, u2;
-    draw2(seed, photon, 0u, design, &u1, &u2);
-    *phi_out = emit(&L, u1, u2, w_out, a_out);
+    double u[4], x0[3];
+    draw4(seed, photon, 0u, design, u);
+    *phi_out = emit(&L, u, x0, w_out, a_out);
+    if (origin_out)
+        for (int k = 0; k < 3; ++k) origin_out[k] = x0[k];
     return 0;
 }
 

@@ -32,7 +32,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 LIGHT_FIELDS = ("type", "x", "y", "z", "yaw", "pitch", "p_int", "theta_in", "theta_out")
-POINT, SPOT = 0, 1
+POINT, SPOT, AREA = 0, 1, 2
 GRAD_FIELDS = ("x", "y", "z", "yaw", "pitch", "p_int", "theta_in", "theta_out")
 
 
@@ -153,6 +153,14 @@ def point_light(pos, intensity):
 
 def spot_light(pos, yaw, pitch, intensity, theta_in, theta_out):
     return [SPOT, *pos, yaw, pitch, float(np.sqrt(2.0 * intensity)), theta_in, theta_out]
+
+
+def area_light(pos, yaw, pitch, power, width, height):
+    """Rectangular Lambertian area light centred at pos, normal n(yaw, pitch),
+    edges along dn/dpitch (width) and n x dn/dpitch (height), total emitted
+    power P (p_int = sqrt(2 P)); the width and height take the theta_in and
+    theta_out slots of the row."""
+    return [AREA, *pos, yaw, pitch, float(np.sqrt(2.0 * power)), width, height]
 
 
 # --------------------------------------------------------------------------
