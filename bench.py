@@ -39,7 +39,7 @@ METRIC = "Msegments/s fwd+adjoint"
 PHOTONS, HITS = 1 << 24, 5
 TARGET_PHOTONS = 1 << 26
 KERNELS_PER_STEP = 5          # forward, loss, loss reduction, adjoint, gradient reduction
-LIGHT_DEV_BYTES = 144         # device light record the library uploads per light
+LIGHT_DEV_BYTES = 160         # device light record the library uploads per light
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "trace_kernel_traffic.json")
 

@@ -48,7 +48,7 @@ typedef enum {
     LT_ERR_DEVICE = -7     /* a kernel reported an internal error (device error word) */
 } lt_status;
 
-enum { LT_POINT = 0, LT_SPOT = 1 };
+enum { LT_POINT = 0, LT_SPOT = 1, LT_AREA = 2 };
 
 enum {
     LT_GRAD_X = 0, LT_GRAD_Y = 1, LT_GRAD_Z = 2, LT_GRAD_YAW = 3, LT_GRAD_PITCH = 4,
@@ -57,15 +57,21 @@ enum {
 
 /* One luminaire (Sec. 4.4 of the paper and the supplement's "Derivative
  * terms for optimization parameters"):
- *   type       LT_POINT or LT_SPOT
- *   pos        position, metres
- *   yaw,pitch  spot axis n = (cos p cos y, cos p sin y, sin p), z up (radians;
+ *   type       LT_POINT, LT_SPOT or LT_AREA
+ *   pos        position, metres (an area light's centroid)
+ *   yaw,pitch  axis n = (cos p cos y, cos p sin y, sin p), z up (radians;
  *              the paper rotates by a rotation vector, Eq. 15)
- *   p_int      intensity parameter, I_e = p_int^2 / 2 (Sec. 4.4.1)
- *   theta_in   inner cone half-angle: full intensity for theta <= theta_in
- *   theta_out  outer cone half-angle: zero beyond; quadratic soft edge in
- *              cos(theta) between the two (Eq. S.11). 0 <= theta_in < theta_out <= pi.
- * Point lights ignore yaw, pitch and the cone angles. */
+ *   p_int      intensity parameter, I_e = p_int^2 / 2 (Sec. 4.4.1); for an
+ *              area light the emitted power P = p_int^2 / 2
+ *   theta_in   spot: inner cone half-angle, full intensity for theta <= theta_in;
+ *              area: width (metres) along t = dn/dpitch
+ *   theta_out  spot: outer cone half-angle, zero beyond; quadratic soft edge in
+ *              cos(theta) between the two (Eq. S.11), 0 <= theta_in < theta_out <= pi;
+ *              area: height (metres) along b = n x t
+ * Point lights ignore yaw, pitch and the cone angles. An area light is a
+ * Lambertian rectangle (supplement, Eq. S.15-S.16): rays start uniformly on
+ * it and leave uniformly over the hemisphere about n with flux
+ * Phi_r = 2 P cos(theta) / N; its gradient slots 6 and 7 stay 0. */
 typedef struct {
     int32_t type;
     float pos[3];

@@ -140,8 +140,9 @@ int copy_out(Ctx *c, void *dst, const void *src, size_t bytes, int is_device) {
 
 // Per-light constants of one design whose photon budget n is split evenly
 // over its L lights (Sec. 4.4 and the supplement): I_e = p^2 / 2,
-// Phi_r = I_e Omega a / N_l with Omega = 4 pi (point) or 2 pi (1 - cos
-// theta_out) (spot). The design's photons are global indices
+// Phi_r = I_e Omega a / N_l with Omega = 4 pi (point), 2 pi (1 - cos
+// theta_out) (spot, a the soft edge) or 2 (area: P = p^2 / 2, a = cos theta,
+// Phi_r = 2 P cos / N_l). The design's photons are global indices
 // [photon_base, photon_base + n); its texel arrays start at texel_base.
 // Returns the design's power bound sum_l I_l Omega_l.
 double derive_lights(const lt_light *in, int32_t L, uint64_t n_photons, uint64_t photon_base, uint64_t texel_base,
@@ -174,6 +175,15 @@ double derive_lights(const lt_light *in, int32_t L, uint64_t n_photons, uint64_t
             d.k_cos = (float)(1.0 - co);
             d.sin_in = (float)std::sin((double)s.theta_in);
             d.sin_out = (float)std::sin((double)s.theta_out);
+        } else if (s.type == LT_AREA) {
+            // the hemisphere about n; the falloff is the emission cosine
+            omega = 2.0;
+            d.k_cos = 1.0f;
+            d.ci = 2.0f;
+            d.co = 0.0f;
+            d.inv_d = 1.0f;
+            d.half_u = 0.5f * s.theta_in;
+            d.half_v = 0.5f * s.theta_out;
         } else {
             // point light: the whole sphere about the world z axis, no falloff
             d.e1[0] = 1.0f; d.e1[1] = 0.0f; d.e1[2] = 0.0f;
@@ -569,19 +579,26 @@ int lt_set_target(void *ctx, const float *E_target, const float *alpha, int is_d
     return LT_OK;
 }
 
+// Argument checks of one luminaire; empty on success.
+static const char *light_error(const lt_light &s) {
+    if (s.type != LT_POINT && s.type != LT_SPOT && s.type != LT_AREA) return "unknown light type";
+    bool finite = std::isfinite(s.p_int) && std::isfinite(s.yaw) && std::isfinite(s.pitch);
+    for (int k = 0; k < 3; ++k) finite = finite && std::isfinite(s.pos[k]);
+    if (!finite) return "non-finite light parameter";
+    if (s.type == LT_SPOT && !(s.theta_in >= 0.0f && s.theta_in < s.theta_out && s.theta_out <= (float)kPi))
+        return "spot cone needs 0 <= theta_in < theta_out <= pi";
+    if (s.type == LT_AREA && !(s.theta_in > 0.0f && s.theta_out > 0.0f && std::isfinite(s.theta_in) &&
+                               std::isfinite(s.theta_out)))
+        return "area light needs a positive finite width and height";
+    return nullptr;
+}
+
 int lt_set_lights(void *ctx, const lt_light *lights, int32_t n_lights) {
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return LT_ERR_ARG;
     if (!lights || n_lights < 1 || n_lights > LT_MAX_LIGHTS) return fail(c, LT_ERR_ARG, "n_lights out of range");
-    for (int32_t l = 0; l < n_lights; ++l) {
-        const lt_light &s = lights[l];
-        if (s.type != LT_POINT && s.type != LT_SPOT) return fail(c, LT_ERR_ARG, "unknown light type");
-        bool finite = std::isfinite(s.p_int) && std::isfinite(s.yaw) && std::isfinite(s.pitch);
-        for (int k = 0; k < 3; ++k) finite = finite && std::isfinite(s.pos[k]);
-        if (!finite) return fail(c, LT_ERR_ARG, "non-finite light parameter");
-        if (s.type == LT_SPOT && !(s.theta_in >= 0.0f && s.theta_in < s.theta_out && s.theta_out <= (float)kPi))
-            return fail(c, LT_ERR_ARG, "spot cone needs 0 <= theta_in < theta_out <= pi");
-    }
+    for (int32_t l = 0; l < n_lights; ++l)
+        if (const char *e = light_error(lights[l])) return fail(c, LT_ERR_ARG, e);
     c->lights.assign(lights, lights + n_lights);
     c->lights_dirty = true;
     return LT_OK;
@@ -890,12 +907,8 @@ int lt_batch_set_lights(void *ctx, const lt_light *lights) {
     Ctx::Batch &b = c->batch;
     if (!b.n_designs) return fail(c, LT_ERR_STATE, "lt_batch_setup first");
     if (!lights) return fail(c, LT_ERR_ARG, "null lights");
-    for (int32_t l = 0; l < b.n_lights; ++l) {
-        const lt_light &s = lights[l];
-        if (s.type != LT_POINT && s.type != LT_SPOT) return fail(c, LT_ERR_ARG, "unknown light type");
-        if (s.type == LT_SPOT && !(s.theta_in >= 0.0f && s.theta_in < s.theta_out && s.theta_out <= (float)kPi))
-            return fail(c, LT_ERR_ARG, "spot cone needs 0 <= theta_in < theta_out <= pi");
-    }
+    for (int32_t l = 0; l < b.n_lights; ++l)
+        if (const char *e = light_error(lights[l])) return fail(c, LT_ERR_ARG, e);
     b.lights.assign(lights, lights + b.n_lights);
     LightDev *out = reinterpret_cast<LightDev *>(b.h_in + kHdrBytes);
     double bound = 0.0;

@@ -71,7 +71,7 @@ struct alignas(16) LightDev {
     float ci;           // cos(theta_in)
     float dn_dpitch[3];
     float inv_d;        // 1 / (ci - co)
-    float k_cos;        // emission cos = 1 - u1 k_cos: 2 (point), 1 - cos(theta_out) (spot)
+    float k_cos;        // emission cos = 1 - u1 k_cos: 2 (point), 1 - cos(theta_out) (spot), 1 (area)
     float sin_in;
     float sin_out;
     uint32_t design;    // design this light belongs to (Philox counter word 3, texel array)
@@ -79,8 +79,10 @@ struct alignas(16) LightDev {
     uint64_t end;
     uint64_t photon_base;   // first global photon of the light's design
     uint64_t texel_base;    // offset of the design's texel sums and weights (design slot x n_texels)
+    float half_u, half_v;   // area light: half width along e1, half height along -e2
+    float pad_area[2];
 };
-static_assert(sizeof(LightDev) == 144, "light layout");
+static_assert(sizeof(LightDev) == 160, "light layout");
 
 // Values a captured step reads from device memory, so one instantiated graph
 // serves every step (written with the lights from pinned host memory).

@@ -38,11 +38,13 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
     return c;
 }
 
-// Two uniforms in [0, 1): 24 high bits of counter lanes 0 and 1.
-__device__ __forceinline__ float2 uniforms(uint64_t seed, uint64_t photon, uint32_t segment, uint32_t design) {
+// Four uniforms in [0, 1): 24 high bits of the counter lanes. Lanes 0 and 1
+// give a direction, lanes 2 and 3 the position on an area light.
+__device__ __forceinline__ float4 uniforms(uint64_t seed, uint64_t photon, uint32_t segment, uint32_t design) {
     const uint4 r = philox(make_uint4((uint32_t)photon, (uint32_t)(photon >> 32), segment, design),
                            make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
-    return make_float2((float)(r.x >> 8) * 0x1p-24f, (float)(r.y >> 8) * 0x1p-24f);
+    return make_float4((float)(r.x >> 8) * 0x1p-24f, (float)(r.y >> 8) * 0x1p-24f, (float)(r.z >> 8) * 0x1p-24f,
+                       (float)(r.w >> 8) * 0x1p-24f);
 }
 
 // 3-input min / max (PTX ISA 8.8, sm_100 and later).
@@ -363,6 +365,7 @@ __device__ __forceinline__ int32_t tile_of(const TraceParams &P, int32_t tri) {
 
 // Quadratic spot soft edge in cos(theta) (Eq. S.11).
 __device__ __forceinline__ float falloff(const LightDev &L, float c) {
+    if (L.type == LT_AREA) return c;            // Lambertian emitter: Phi_r proportional to cos
     if (c >= L.ci) return 1.0f;
     if (c <= L.co) return 0.0f;
     const float s = (c - L.co) * L.inv_d;
@@ -415,6 +418,20 @@ __device__ __forceinline__ void bounce_frame(float3 n, float u1, float &c, float
     s = sqrtf(u1);
 }
 
+// Coordinates of an area light's ray origin along e1 and b = -e2.
+__device__ __forceinline__ float2 area_coords(const LightDev &L, float u3, float u4) {
+    return make_float2((2.0f * u3 - 1.0f) * L.half_u, (2.0f * u4 - 1.0f) * L.half_v);
+}
+
+// Ray origin of light L: its position, or a uniform point of the rectangle.
+__device__ __forceinline__ float3 emit_origin(const LightDev &L, float u3, float u4) {
+    if (L.type != LT_AREA) return make_float3(L.pos[0], L.pos[1], L.pos[2]);
+    const float2 q = area_coords(L, u3, u4);
+    return make_float3(__fmaf_rn(-q.y, L.e2[0], __fmaf_rn(q.x, L.e1[0], L.pos[0])),
+                       __fmaf_rn(-q.y, L.e2[1], __fmaf_rn(q.x, L.e1[1], L.pos[1])),
+                       __fmaf_rn(-q.y, L.e2[2], __fmaf_rn(q.x, L.e1[2], L.pos[2])));
+}
+
 // Exitant ray of light L and its flux Phi_r = flux_k a(theta).
 __device__ __forceinline__ float emit(const LightDev &L, float u1, float u2, float &wx, float &wy, float &wz,
                                       float &a) {
@@ -435,12 +452,59 @@ __device__ __forceinline__ void cosine_dir(float3 n, float u1, float u2, float &
     wx = w.x; wy = w.y; wz = w.z;
 }
 
+// Area light (supplement Eq. S.15-S.16): with the first hit x1 fixed and
+// the origin x0 at fixed coordinates (su, sv) on the rectangle,
+// dPhi_r/dq = I~ d(cos_1 / r^2)/dq + (2 P / N) d cos(theta)/dq, where x0
+// translates with the centroid and turns with the axis (t = e1, b = -e2:
+// dt/dyaw = -n_z e2, db/dyaw = t_z n - n_z t, dt/dpitch = -n).
+__device__ __forceinline__ void area_dflux(const LightDev &L, float phi_r, float a_emit, float2 q, float x1x,
+                                           float x1y, float x1z, float3 n1, float out[8]) {
+    const float3 x0 = make_float3(L.pos[0] + q.x * L.e1[0] - q.y * L.e2[0], L.pos[1] + q.x * L.e1[1] - q.y * L.e2[1],
+                                  L.pos[2] + q.x * L.e1[2] - q.y * L.e2[2]);
+    const float dx = x0.x - x1x, dy = x0.y - x1y, dz = x0.z - x1z;
+    const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+    const float ux = dx * il, uy = dy * il, uz = dz * il;           // from x1 towards the origin
+    const float c1 = n1.x * ux + n1.y * uy + n1.z * uz;
+    float gx = 0.0f, gy = 0.0f, gz = 0.0f;                           // dPhi_r / dx0
+    if (c1 > 0.0f) {
+        const float k = phi_r * il, ic1 = 1.0f / c1;
+        gx = k * (n1.x * ic1 - 3.0f * ux);
+        gy = k * (n1.y * ic1 - 3.0f * uy);
+        gz = k * (n1.z * ic1 - 3.0f * uz);
+    }
+    const float ct = -(L.ns[0] * ux + L.ns[1] * uy + L.ns[2] * uz);  // cos(theta) = n . w, w = -u
+    const float kk = L.flux_k * il;                                   // 2 P / N / r
+    gx -= kk * (L.ns[0] + ct * ux);
+    gy -= kk * (L.ns[1] + ct * uy);
+    gz -= kk * (L.ns[2] + ct * uz);
+    out[0] = gx;
+    out[1] = gy;
+    out[2] = gz;
+    const float nz = L.ns[2], tz = L.e1[2];
+    float dyaw[3], dpitch[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        dyaw[k] = -q.x * nz * L.e2[k] + q.y * (tz * L.ns[k] - nz * L.e1[k]);
+        dpitch[k] = -q.x * L.ns[k];
+    }
+    const float w_dny = -(ux * L.dn_dyaw[0] + uy * L.dn_dyaw[1] + uz * L.dn_dyaw[2]);
+    const float w_dnp = -(ux * L.dn_dpitch[0] + uy * L.dn_dpitch[1] + uz * L.dn_dpitch[2]);
+    out[3] = gx * dyaw[0] + gy * dyaw[1] + gz * dyaw[2] + L.flux_k * w_dny;
+    out[4] = gx * dpitch[0] + gy * dpitch[1] + gz * dpitch[2] + L.flux_k * w_dnp;
+    out[5] = L.dflux_dp_k * a_emit;         // P = p^2 / 2
+}
+
 // dPhi_r/dp at the first hit x1 (normal n1 facing the light), the hit held
 // fixed (Sec. 4.4.2). Order [x, y, z, yaw, pitch, p_int, theta_in, theta_out].
-__device__ __forceinline__ void dflux(const LightDev &L, float phi_r, float a_emit, float x1x, float x1y, float x1z,
-                                      float3 n1, float out[8]) {
+// q: the origin's coordinates on an area light.
+__device__ __forceinline__ void dflux(const LightDev &L, float phi_r, float a_emit, float2 q, float x1x, float x1y,
+                                      float x1z, float3 n1, float out[8]) {
 #pragma unroll
     for (int k = 0; k < 8; ++k) out[k] = 0.0f;
+    if (L.type == LT_AREA) {
+        area_dflux(L, phi_r, a_emit, q, x1x, x1y, x1z, n1, out);
+        return;
+    }
     const float dx = L.pos[0] - x1x, dy = L.pos[1] - x1y, dz = L.pos[2] - x1z;
     const float ell = sqrtf(dx * dx + dy * dy + dz * dz);
     const float il = 1.0f / ell;
@@ -537,10 +601,11 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
         l = light_of(P, photon);
         first_light = l;
         const LightDev &L = P.lights[l];
-        const float2 u = uniforms(seed, photon - L.photon_base, 0u, L.design);
+        const float4 u = uniforms(seed, photon - L.photon_base, 0u, L.design);
         float wx, wy, wz;
         phi = emit(L, u.x, u.y, wx, wy, wz, a_emit);
-        ray_init(r, L.pos[0], L.pos[1], L.pos[2], wx, wy, wz);
+        const float3 o = emit_origin(L, u.z, u.w);
+        ray_init(r, o.x, o.y, o.z, wx, wy, wz);
         seg = 1;
         trav_init(s, h);
     }
@@ -596,8 +661,13 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
                 if (kAdjoint && hit1) {
                     // Eq. 11: this photon's dO/dPhi_r * dPhi_r/dp into its light's slot
                     const LightDev &L = P.lights[l];
+                    float2 q = make_float2(0.0f, 0.0f);
+                    if (L.type == LT_AREA) {   // the origin's coordinates, from the emission's random numbers
+                        const float4 u0 = uniforms(seed, photon - L.photon_base, 0u, L.design);
+                        q = area_coords(L, u0.z, u0.w);
+                    }
                     float dp[8];
-                    dflux(L, L.flux_k * a_emit, a_emit, x1x, x1y, x1z, n1, dp);
+                    dflux(L, L.flux_k * a_emit, a_emit, q, x1x, x1y, x1z, n1, dp);
                     double *o = P.slots + (tid * (uint64_t)P.n_slots + (uint64_t)(l - first_light)) * 8;
 #pragma unroll
                     for (int k = 0; k < 8; ++k) o[k] += (double)(g * dp[k]);
@@ -610,7 +680,7 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
                 float3 t1, t2, axis, org;
                 if (!bounce) while (photon >= P.lights[l].end) ++l;
                 const LightDev &Ln = P.lights[l];
-                const float2 u = uniforms(seed, photon - Ln.photon_base, bounce ? (uint32_t)seg : 0u, Ln.design);
+                const float4 u = uniforms(seed, photon - Ln.photon_base, bounce ? (uint32_t)seg : 0u, Ln.design);
                 if (bounce) {
                     bounce_frame(nrm, u.x, c, sn, t1, t2);
                     axis = nrm;
@@ -618,7 +688,7 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
                     ++seg;
                 } else {
                     emit_frame(Ln, u.x, c, sn, t1, t2, axis);
-                    org = make_float3(Ln.pos[0], Ln.pos[1], Ln.pos[2]);
+                    org = emit_origin(Ln, u.z, u.w);
                     a_emit = falloff(Ln, c);
                     phi = Ln.flux_k * a_emit;
                     seg = 1;
@@ -658,8 +728,10 @@ __global__ void __launch_bounds__(128) paths_kernel(const TraceParams P, uint64_
     const LightDev &L = P.lights[l];
     float wx, wy, wz, a_emit;
     const uint64_t local = photon - L.photon_base;
-    const float2 u0 = uniforms(P.seed, local, 0u, L.design);
+    const float4 u0 = uniforms(P.seed, local, 0u, L.design);
     emit(L, u0.x, u0.y, wx, wy, wz, a_emit);
+    const float3 o = emit_origin(L, u0.z, u0.w);
+    const float2 q = L.type == LT_AREA ? area_coords(L, u0.z, u0.w) : make_float2(0.0f, 0.0f);
     int32_t skip = -1;
     int32_t *rt = P.rec_tri + k * P.max_hits;
     int64_t *rx = P.rec_texel + k * P.max_hits;
@@ -669,7 +741,7 @@ __global__ void __launch_bounds__(128) paths_kernel(const TraceParams P, uint64_
     float3 n1 = make_float3(0.0f, 0.0f, 0.0f);
     bool hit1 = false;
     Ray r;
-    ray_init(r, L.pos[0], L.pos[1], L.pos[2], wx, wy, wz);
+    ray_init(r, o.x, o.y, o.z, wx, wy, wz);
     for (int i = 1; i <= P.max_hits; ++i) {
         const Hit h = closest_hit(P, nullptr, r, skip);
         if (h.tri < 0) break;
@@ -683,7 +755,7 @@ __global__ void __launch_bounds__(128) paths_kernel(const TraceParams P, uint64_
             g += __ldg(P.w + L.texel_base + texel) * beta;
         }
         if (i == P.max_hits) break;
-        const float2 u = uniforms(P.seed, local, (uint32_t)i, L.design);
+        const float4 u = uniforms(P.seed, local, (uint32_t)i, L.design);
         cosine_dir(nrm, u.x, u.y, wx, wy, wz);
         beta *= albedo_of(P, h.tri);
         skip = tile_of(P, h.tri);
@@ -692,7 +764,7 @@ __global__ void __launch_bounds__(128) paths_kernel(const TraceParams P, uint64_
     if (P.rec_grad) {
         float dp[8];
         for (int j = 0; j < 8; ++j) dp[j] = 0.0f;
-        if (hit1) dflux(L, L.flux_k * a_emit, a_emit, x1x, x1y, x1z, n1, dp);
+        if (hit1) dflux(L, L.flux_k * a_emit, a_emit, q, x1x, x1y, x1z, n1, dp);
         for (int j = 0; j < 8; ++j) P.rec_grad[k * 8 + j] = (double)(g * dp[j]);
     }
 }

@@ -54,11 +54,12 @@ def _light_of_photons(n, n_lights, begin, count):
     return np.searchsorted(ends, np.arange(begin, begin + count), side="right")
 
 
-def _check_grad(tr, sc, L, seed, n, hits, w, g, g_ref, rtol=1e-3, max_diverged=1e-3):
+def _check_grad(tr, sc, L, seed, n, hits, w, g, g_ref, rtol=1e-3, max_diverged=1e-3, term_tol=1e-2):
     """Gradients agree to rtol (per component, against max(|g_ref|, rtol *
     max|g_ref|)) once the photons whose paths parted ways between the float
     GPU path and the double oracle are set aside; those must be rare and the
-    paths that agree must carry the same per-photon terms."""
+    paths that agree must carry the same per-photon terms (each within
+    term_tol, 99.9 % of them within 1e-3)."""
     tri, tex, c = tr.debug_paths(seed, n, hits, 0, n, grads=True)
     tri_o, tex_o, c_o = oracle.paths(sc, L, seed, n, hits, 0, n, w=w)
     same = np.all(tri == tri_o, axis=1) & np.all(tex == tex_o, axis=1)
@@ -68,7 +69,7 @@ def _check_grad(tr, sc, L, seed, n, hits, w, g, g_ref, rtol=1e-3, max_diverged=1
     # and the bulk (99.9 %) must sit within 1e-3.
     col = np.maximum(np.abs(c_o).max(axis=0), 1e-300)
     diff = np.abs(c[same] - c_o[same]) / np.maximum(np.abs(c_o[same]), 1e-4 * col)
-    assert np.all(diff <= 1e-2), f"per-photon terms differ: worst {diff.max():.3g}"
+    assert np.all(diff <= term_tol), f"per-photon terms differ: worst {diff.max():.3g}"
     assert np.quantile(diff.max(axis=1), 0.999) <= 1e-3
     lights = _light_of_photons(n, L.shape[0], 0, n)
     # the aggregate kernel sums the same per-photon terms
@@ -211,7 +212,7 @@ def test_loss_matches_oracle(tr):
     assert abs(O - O_ref) <= 1e-4 * O_ref, (O, O_ref)
 
 
-def _adjoint_case(tr, sc, L, target, n, hits, seed):
+def _adjoint_case(tr, sc, L, target, n, hits, seed, term_tol=1e-2):
     """GPU forward + loss + adjoint as a user runs them, then the same adjoint
     on both sides from identical weights (the oracle's, rounded to float)."""
     tr.upload_scene(sc)
@@ -227,7 +228,7 @@ def _adjoint_case(tr, sc, L, target, n, hits, seed):
     tr.set_adjoint_weights(w32)
     g = tr.trace_adjoint(seed, n, hits)
     g_ref, _ = oracle.adjoint(sc, L, seed, n, hits, w32.astype(np.float64))
-    _check_grad(tr, sc, L, seed, n, hits, w32.astype(np.float64), g, g_ref)
+    _check_grad(tr, sc, L, seed, n, hits, w32.astype(np.float64), g, g_ref, term_tol=term_tol)
     # with its own weights the GPU gradient still tracks the oracle's
     assert np.abs(g_own - g_ref).max() <= 1e-2 * np.abs(g_ref).max()
     return g
