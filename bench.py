@@ -673,6 +673,136 @@ def run_surrogate(args):
     tr.close()
 
 
+# ---------------------------------------------------------------------------
+# Large building: 64 area lights, 2^26 photons, 6 hits
+# ---------------------------------------------------------------------------
+BLD_PHOTONS, BLD_HITS = 1 << 26, 6
+
+
+def run_building(args):
+    """Forward + objective + adjoint on the procedural building (961,792
+    tris, 17.2 M texels at 4.5 cm, 64 ceiling-panel area lights), and
+    L-BFGS on the 64 powers with adjoint path replay (ms per evaluation)."""
+    import torch
+    from paper_2310_02043_gb300 import optim
+    from paper_2310_02043_gb300.lighttrace import Tracer
+
+    torch.cuda.set_device(0)
+    sc, L = scenes.building(), scenes.building_lights()
+    tr = Tracer(0)
+    t0 = time.perf_counter()
+    T = tr.upload_scene(sc)
+    upload_s = time.perf_counter() - t0
+    truth = L.copy()
+    truth[:, 6] *= np.sqrt(np.random.default_rng(5).uniform(0.6, 1.4, L.shape[0]))
+    truth[:, 1:3] += np.random.default_rng(6).normal(0.0, 0.3, (L.shape[0], 2))
+    tr.set_lights(truth)
+    tr.trace_forward(77, BLD_PHOTONS, BLD_HITS)
+    target = torch.empty(T, dtype=torch.float32, device="cuda")
+    tr.irradiance(out=target)
+    tr.set_target(target)
+    tr.set_lights(L)
+    work = tr.count_work(5, 1 << 24, BLD_HITS)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    grad = torch.zeros((L.shape[0], 8), dtype=torch.float64, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for k in range(args.warmup):
+        tr.trace_forward(100 + k, BLD_PHOTONS, BLD_HITS)
+        tr.loss(out=loss)
+        tr.trace_adjoint(200 + k, BLD_PHOTONS, BLD_HITS, out=grad)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clock = clock_sampler(0)
+    clock.start()
+    segs = 0
+    for k in range(args.steps):
+        flush.zero_()
+        e = ev[k]
+        e[0].record(stream)
+        tr.trace_forward(1000 + 2 * k, BLD_PHOTONS, BLD_HITS)
+        tr.loss(out=loss)
+        e[1].record(stream)
+        tr.trace_adjoint(1001 + 2 * k, BLD_PHOTONS, BLD_HITS, out=grad)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        st = tr.stats()
+        segs += st["segments_forward"] + st["segments_adjoint"]
+    clocks = clock.stop()
+    t_f = [e[0].elapsed_time(e[1]) for e in ev]
+    t_a = [e[1].elapsed_time(e[2]) for e in ev]
+    total_ms = sum(t_f) + sum(t_a)
+    value = segs / (total_ms / 1e3) / 1e6
+    # end to end: L-BFGS on the 64 powers, host parameters, 2^26 photons per evaluation
+    start = L.copy()
+    start[:, 6] *= np.sqrt(np.random.default_rng(7).uniform(0.5, 1.5, L.shape[0]))
+    prob = optim.LightingProblem(sc, target.cpu().numpy(), photons=BLD_PHOTONS, hits=BLD_HITS, tracer=tr)
+    rig = optim.LightRig(start, optimize=("p_int",))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    trace = optim.lbfgs(prob, rig, max_iter=max(2, args.steps), seed=9)
+    torch.cuda.synchronize()
+    lbfgs_s = time.perf_counter() - t0
+    evals = prob.evaluations
+    e2e_value = evals * BLD_PHOTONS * BLD_HITS * 2 / lbfgs_s / 1e6
+    seg = work["segments"]
+    ops = work["node_visits"] * OPS_PER_NODE + work["tri_tests"] * OPS_PER_TRI + seg * OPS_PER_SEGMENT
+    fwd_ms = statistics.mean(t_f)
+    achieved = ops / seg * (BLD_PHOTONS * BLD_HITS) / (fwd_ms / 1e3) / 1e12
+    peak_clock = clocks["sm_max_mhz"] if clocks and clocks.get("sm_max_mhz") else 2070.0
+    peak = alu_peak_tflops(peak_clock)
+    traffic = None
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "trace_kernel_building_traffic.json")))
+        if d.get("kernel_source_sha256_16") == kernel_hash():
+            traffic = d["trace_kernel_forward"]["dram_bytes_per_segment"] * BLD_PHOTONS * BLD_HITS
+    except (OSError, ValueError, KeyError):
+        pass
+    line = {"metric": METRIC, "value": value, "unit": "Msegments/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"procedural building: 8 storeys 48x24 m, {sc.n_tri} tris (tessellated floors, "
+                                   f"walls, columns, partitions, furniture), {T} texels at 4.5 cm, 64 rectangular "
+                                   "area lights, 2^26 photons, 6 hits",
+                       "triangles": sc.n_tri, "texels": T, "bvh_nodes": tr.stats()["n_nodes"], "lights": 64,
+                       "photons": BLD_PHOTONS, "hits": BLD_HITS, "scene_upload_s": upload_s,
+                       "l2": "flushed between steps (256 MiB write outside the timed events)",
+                       "parallelism": "single GPU"},
+            "e2e": {"value": e2e_value, "unit": "Msegments/s", "h2d_bytes_per_step": LIGHT_DEV_BYTES * 64,
+                    "d2h_bytes_per_step": 8 + 64 * 64, "what": "L-BFGS (strong Wolfe) on the 64 powers",
+                    "evaluations": evals, "ms_per_evaluation": 1e3 * lbfgs_s / max(1, evals),
+                    "objective": [trace[0], trace[-1]]},
+            "gpu_launches": KERNELS_PER_STEP * args.steps,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": traffic, "kernel": "trace_kernel (forward, BVH through L1/L2)",
+                         "peak_basis": f"FP32 issue peak 152 SMs x 128 lanes x {peak_clock:.0f} MHz (derived)",
+                         "work_per_segment": {"node_visits": work["node_visits"] / seg,
+                                              "tri_tests": work["tri_tests"] / seg, "fp32_ops": ops / seg}},
+            "kernel_ms": {"forward_and_loss": fwd_ms, "adjoint": statistics.mean(t_a)},
+            "cpu_baseline": None, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    tr.close()
+
+
+def run_profile_building(args):
+    """One forward + loss + adjoint of the building at --photons (for ncu)."""
+    import torch
+    from paper_2310_02043_gb300.lighttrace import Tracer
+    torch.cuda.set_device(0)
+    sc, L = scenes.building(), scenes.building_lights()
+    tr = Tracer(0)
+    T = tr.upload_scene(sc)
+    tr.set_target(np.zeros(T, np.float32))
+    tr.set_lights(L)
+    tr.trace_forward(2, args.photons, BLD_HITS)
+    tr.loss()
+    tr.trace_adjoint(3, args.photons, BLD_HITS)
+    st = tr.stats()
+    tr.close()
+    print(json.dumps({"profile_case": "building", "photons": args.photons, "segments_forward": st["segments_forward"],
+                      "segments_adjoint": st["segments_adjoint"]}))
+
+
 def run_profile_surrogate(args):
     """A small surrogate fit (64 solves at 2^18 photons), 5 training steps at
     batch 2^18 and 3 design evaluations of the 16 office spots (for ncu)."""
@@ -722,15 +852,19 @@ def main():
     ap.add_argument("--profile-only", action="store_true",
                     help="run one forward + loss + adjoint at --photons and exit (for profilers)")
     ap.add_argument("--photons", type=int, default=1 << 20)
-    ap.add_argument("--workload", choices=["office", "batch", "surrogate"], default="office",
+    ap.add_argument("--workload", choices=["office", "batch", "surrogate", "building"], default="office",
                     help="office: one design, 16 spots (default); batch: 64 designs in one launch per pass; "
-                         "surrogate: time to a target loss with the surrogate warm start")
+                         "surrogate: time to a target loss with the surrogate warm start; building: 961,792 tris, "
+                         "64 area lights, 2^26 photons, 6 hits")
     args = ap.parse_args()
     if args.workload == "batch" and args.impl == "ours" and not args.profile_only:
         run_batch(args)
         return
     if args.workload == "surrogate" and args.impl == "ours":
         run_profile_surrogate(args) if args.profile_only else run_surrogate(args)
+        return
+    if args.workload == "building" and args.impl == "ours":
+        run_profile_building(args) if args.profile_only else run_building(args)
         return
     if args.profile_only:
         run_profile_case(args)

@@ -38,13 +38,20 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
     return c;
 }
 
-// Four uniforms in [0, 1): 24 high bits of the counter lanes. Lanes 0 and 1
-// give a direction, lanes 2 and 3 the position on an area light.
+// The counter block of (photon, segment, design) under seed.
+__device__ __forceinline__ uint4 counter_block(uint64_t seed, uint64_t photon, uint32_t segment, uint32_t design) {
+    return philox(make_uint4((uint32_t)photon, (uint32_t)(photon >> 32), segment, design),
+                  make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+// A uniform in [0, 1) from the 24 high bits of one counter lane.
+__device__ __forceinline__ float unit24(uint32_t x) { return (float)(x >> 8) * 0x1p-24f; }
+
+// Four uniforms in [0, 1): lanes 0 and 1 give a direction, lanes 2 and 3
+// the position on an area light.
 __device__ __forceinline__ float4 uniforms(uint64_t seed, uint64_t photon, uint32_t segment, uint32_t design) {
-    const uint4 r = philox(make_uint4((uint32_t)photon, (uint32_t)(photon >> 32), segment, design),
-                           make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
-    return make_float4((float)(r.x >> 8) * 0x1p-24f, (float)(r.y >> 8) * 0x1p-24f, (float)(r.z >> 8) * 0x1p-24f,
-                       (float)(r.w >> 8) * 0x1p-24f);
+    const uint4 r = counter_block(seed, photon, segment, design);
+    return make_float4(unit24(r.x), unit24(r.y), unit24(r.z), unit24(r.w));
 }
 
 // 3-input min / max (PTX ISA 8.8, sm_100 and later).
@@ -680,7 +687,8 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
                 float3 t1, t2, axis, org;
                 if (!bounce) while (photon >= P.lights[l].end) ++l;
                 const LightDev &Ln = P.lights[l];
-                const float4 u = uniforms(seed, photon - Ln.photon_base, bounce ? (uint32_t)seg : 0u, Ln.design);
+                const uint4 rb = counter_block(seed, photon - Ln.photon_base, bounce ? (uint32_t)seg : 0u, Ln.design);
+                const float2 u = make_float2(unit24(rb.x), unit24(rb.y));
                 if (bounce) {
                     bounce_frame(nrm, u.x, c, sn, t1, t2);
                     axis = nrm;
@@ -688,7 +696,7 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
                     ++seg;
                 } else {
                     emit_frame(Ln, u.x, c, sn, t1, t2, axis);
-                    org = emit_origin(Ln, u.z, u.w);
+                    org = emit_origin(Ln, unit24(rb.z), unit24(rb.w));
                     a_emit = falloff(Ln, c);
                     phi = Ln.flux_k * a_emit;
                     seg = 1;

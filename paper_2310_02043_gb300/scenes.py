@@ -408,3 +408,153 @@ def perturb_lights_in_plane(lights: np.ndarray, seed: int, pos_sigma: float = 0.
     out[:, 7] = np.clip(out[:, 7] + np.radians(rng.uniform(-theta_in_deg, theta_in_deg, n)), 0.0, out[:, 8] - 1e-3)
     return out
 
+
+
+# --------------------------------------------------------------------------
+# Large procedural building (vectorised assembly)
+# --------------------------------------------------------------------------
+class _Chunks:
+    """Scene arrays assembled from vectorised chunks of quads."""
+
+    def __init__(self):
+        self.xyz, self.uv, self.tile_of_tri, self.albedo, self.res, self.area = [], [], [], [], [], []
+        self.n_tiles = 0
+
+    def quads(self, p00, p10, p11, p01, pitch, albedo):
+        """Quads with corners p00, p10, p11, p01 (arrays [K, 3], planar
+        parallelograms), one tile each, texel counts from the texel pitch.
+        Neighbouring quads must pass bitwise identical shared corners, so
+        that the mesh has no cracks."""
+        p00, p10, p11, p01 = (np.asarray(v, np.float64).reshape(-1, 3) for v in (p00, p10, p11, p01))
+        K = p00.shape[0]
+        tri = np.empty((2 * K, 3, 3))
+        tri[0::2] = np.stack([p00, p10, p11], 1)
+        tri[1::2] = np.stack([p00, p11, p01], 1)
+        uv = np.empty((2 * K, 3, 2))
+        uv[0::2] = [[0, 0], [1, 0], [1, 1]]
+        uv[1::2] = [[0, 0], [1, 1], [0, 1]]
+        ids = self.n_tiles + np.arange(K)
+        self.xyz.append(tri)
+        self.uv.append(uv)
+        self.tile_of_tri.append(np.repeat(ids, 2))
+        alb = np.broadcast_to(np.asarray(albedo, np.float64), (K,))
+        self.albedo.append(np.repeat(alb, 2))
+        a, b = p10 - p00, p01 - p00
+        la, lb = np.linalg.norm(a, axis=1), np.linalg.norm(b, axis=1)
+        self.res.append(np.stack([np.maximum(1, np.ceil(la / pitch - 1e-9)), np.maximum(1, np.ceil(lb / pitch - 1e-9))],
+                                 1).astype(np.int32))
+        self.area.append(np.linalg.norm(np.cross(a, b), axis=1))
+        self.n_tiles += K
+
+    def lattice(self, V, pitch, albedo, wrap=False):
+        """Quads between neighbouring points of a vertex lattice V [nu+1, nv+1, 3]
+        (with wrap, the last column closes onto the first)."""
+        if wrap:
+            V = np.concatenate([V, V[:1]], axis=0)
+        self.quads(V[:-1, :-1].reshape(-1, 3), V[1:, :-1].reshape(-1, 3), V[1:, 1:].reshape(-1, 3),
+                   V[:-1, 1:].reshape(-1, 3), pitch, albedo)
+
+    def grid(self, corner, a, b, nu, nv, pitch, albedo):
+        """A parallelogram split into nu x nv tiles on one shared lattice."""
+        corner, a, b = (np.asarray(v, np.float64) for v in (corner, a, b))
+        i, j = np.meshgrid(np.arange(nu + 1) / nu, np.arange(nv + 1) / nv, indexing="ij")
+        self.lattice(corner + i[..., None] * a + j[..., None] * b, pitch, albedo)
+
+    def box(self, lo, size, pitch, albedo):
+        """Five faces of a box (no bottom) on its 8 corners."""
+        lo = np.asarray(lo, np.float64)
+        sx, sy, sz = size
+        X = [lo[0], lo[0] + sx]
+        Y = [lo[1], lo[1] + sy]
+        Z = [lo[2], lo[2] + sz]
+        P = lambda i, j, k: np.array([X[i], Y[j], Z[k]])                           # noqa: E731
+        faces = [(P(0, 0, 0), P(0, 1, 0), P(0, 1, 1), P(0, 0, 1)), (P(1, 0, 0), P(1, 1, 0), P(1, 1, 1), P(1, 0, 1)),
+                 (P(0, 0, 0), P(1, 0, 0), P(1, 0, 1), P(0, 0, 1)), (P(0, 1, 0), P(1, 1, 0), P(1, 1, 1), P(0, 1, 1)),
+                 (P(0, 0, 1), P(1, 0, 1), P(1, 1, 1), P(0, 1, 1))]
+        F = np.array(faces)
+        self.quads(F[:, 0], F[:, 1], F[:, 2], F[:, 3], pitch, albedo)
+
+    def build(self, name, **meta) -> Scene:
+        return Scene(name=name,
+                     xyz=np.ascontiguousarray(np.concatenate(self.xyz).astype(np.float32)),
+                     uv=np.ascontiguousarray(np.concatenate(self.uv).astype(np.float32)),
+                     tile=np.ascontiguousarray(np.concatenate(self.tile_of_tri).astype(np.int32)),
+                     albedo=np.ascontiguousarray(np.concatenate(self.albedo).astype(np.float32)),
+                     tile_res=np.ascontiguousarray(np.concatenate(self.res)),
+                     tile_area=np.ascontiguousarray(np.concatenate(self.area)), meta=dict(meta))
+
+
+def building(seed: int = 0, floors: int = 8, width: float = 48.0, depth: float = 24.0, storey: float = 3.5,
+             slab: float = 0.3, tess: float = 0.25, pitch: float = 0.045) -> Scene:
+    """A closed office building: `floors` storeys of width x depth metres,
+    each a closed room between its floor (z = k storey) and the slab above
+    (ceiling at z = (k + 1) storey - slab). Floors, ceilings and the four
+    exterior walls are tessellated into tess x tess m tiles; per storey 21
+    columns (radius 0.3 m, 32 sides x 16 rings) on a 6 m grid, 8 partitions
+    (6 x 0.1 m, floor to ceiling) along the middle, and one desk or cabinet
+    (5 faces, lifted 1 cm) in each 3 x 3 m cell. Albedo U[0.3, 0.8] per
+    storey surface group and per box; texels at `pitch` metres."""
+    rng = np.random.default_rng(seed + 11000)
+    S = _Chunks()
+    h = storey - slab
+    nu, nv, nh = int(round(width / tess)), int(round(depth / tess)), int(np.ceil(h / tess))
+    for k in range(floors):
+        z0, z1 = k * storey, k * storey + h
+        alb = rng.uniform(0.3, 0.8, 6)
+        S.grid([0, 0, z0], [width, 0, 0], [0, depth, 0], nu, nv, pitch, alb[0])          # floor
+        S.grid([0, 0, z1], [width, 0, 0], [0, depth, 0], nu, nv, pitch, alb[1])          # ceiling
+        S.grid([0, 0, z0], [width, 0, 0], [0, 0, h], nu, nh, pitch, alb[2])              # walls
+        S.grid([0, depth, z0], [width, 0, 0], [0, 0, h], nu, nh, pitch, alb[2])
+        S.grid([0, 0, z0], [0, depth, 0], [0, 0, h], nv, nh, pitch, alb[3])
+        S.grid([width, 0, z0], [0, depth, 0], [0, 0, h], nv, nh, pitch, alb[3])
+        # columns: cylinders between floor and ceiling
+        sides, rings, rad = 32, 16, 0.3
+        phi = 2 * np.pi * np.arange(sides) / sides
+        zz = z0 + h * np.arange(rings + 1) / rings
+        zz[-1] = z1
+        cx, cy = np.meshgrid(6.0 * np.arange(1, int(width // 6)), 6.0 * np.arange(1, int(depth // 6)), indexing="ij")
+        for x, y in zip(cx.ravel(), cy.ravel()):
+            V = np.stack(np.broadcast_arrays((x + rad * np.cos(phi))[:, None], (y + rad * np.sin(phi))[:, None],
+                                             zz[None, :]), -1)
+            S.lattice(V, pitch, alb[4], wrap=True)
+        # partitions along y = depth / 2, between the columns (closed side
+        # walls on one lattice around the 0.1 m thick slab)
+        for i in range(int(width // 6)):
+            x0, x1 = 6.0 * i + 0.5, 6.0 * i + 5.5
+            y0, y1 = depth / 2 - 0.05, depth / 2 + 0.05
+            n_len = int(round((x1 - x0) / tess))
+            ring = np.concatenate([np.stack([x0 + (x1 - x0) * np.arange(n_len) / n_len, np.full(n_len, y0)], 1),
+                                   [[x1, y0]],
+                                   np.stack([x1 - (x1 - x0) * np.arange(n_len) / n_len, np.full(n_len, y1)], 1),
+                                   [[x0, y1]]])
+            zp = z0 + h * np.arange(nh + 1) / nh
+            zp[-1] = z1
+            V = np.stack(np.broadcast_arrays(ring[:, 0:1], ring[:, 1:2], zp[None, :]), -1)
+            S.lattice(V, pitch, alb[5], wrap=True)
+        # furniture: one box per 3 x 3 m cell
+        for i in range(int(width // 3)):
+            for j in range(int(depth // 3)):
+                if rng.uniform() < 0.6:
+                    sx, sy, sz = 1.6, 0.8, 0.75
+                else:
+                    sx, sy, sz = 0.8, 0.45, float(rng.uniform(1.0, 2.0))
+                if rng.uniform() < 0.5:
+                    sx, sy = sy, sx
+                cxm = 1.5 + 3 * i + rng.uniform(-0.3, 0.3)
+                cym = 1.5 + 3 * j + rng.uniform(-0.3, 0.3)
+                S.box([cxm - sx / 2, cym - sy / 2, z0 + 0.01], (sx, sy, sz), pitch, float(rng.uniform(0.3, 0.8)))
+    return S.build("building", seed=seed, floors=floors, pitch=pitch, tess=tess)
+
+
+def building_lights(floors: int = 8, width: float = 48.0, depth: float = 24.0, storey: float = 3.5,
+                    slab: float = 0.3, power: float = 200.0, size=(1.2, 0.6)) -> np.ndarray:
+    """8 ceiling panels per storey (64 for 8 storeys): rectangular area
+    lights 2 cm below each ceiling, facing down, at x = 9 + 12 i, y = 4.5 or
+    depth - 4.5 (clear of columns and partitions)."""
+    rows = []
+    for k in range(floors):
+        z = k * storey + storey - slab - 0.02
+        for y in (4.5, depth - 4.5):
+            for i in range(4):
+                rows.append(area_light((9.0 + 12.0 * i, y, z), 0.0, -np.pi / 2, power, size[0], size[1]))
+    return make_lights(rows)
