@@ -202,6 +202,14 @@ bool build_wide_bvh(const float *xyz, int32_t n_tri, BvhBuild *out, std::string 
     out->order.reserve(n_tri);
     out->depth = 0;
 
+    // Child boxes grow by pad on every side: the traversal computes a plane
+    // distance as fma(plane, 1/d, -o/d), whose rounding of o/d moves the
+    // plane by up to |o| 2^-24; 2^-19 (|coordinate| + 1) covers ray origins
+    // anywhere within eight times the scene's extent from the world origin.
+    float amax = 0.0f;
+    for (size_t i = 0; i < (size_t)n_tri * 9; ++i) amax = std::max(amax, std::fabs(xyz[i]));
+    const float pad = (amax + 1.0f) * 0x1p-19f;
+
     struct Item { int32_t bnode, wnode, depth; };
     std::deque<Item> queue;
     out->nodes.emplace_back();
@@ -246,9 +254,9 @@ bool build_wide_bvh(const float *xyz, int32_t n_tri, BvhBuild *out, std::string 
         for (int j = 0; j < (int)kids.size(); ++j) {
             const int k = slot_of[j];
             const BNode &c = b.nodes[kids[j]];
-            node.lox[k] = c.box.lo[0]; node.hix[k] = c.box.hi[0];
-            node.loy[k] = c.box.lo[1]; node.hiy[k] = c.box.hi[1];
-            node.loz[k] = c.box.lo[2]; node.hiz[k] = c.box.hi[2];
+            node.lox[k] = c.box.lo[0] - pad; node.hix[k] = c.box.hi[0] + pad;
+            node.loy[k] = c.box.lo[1] - pad; node.hiy[k] = c.box.hi[1] + pad;
+            node.loz[k] = c.box.lo[2] - pad; node.hiz[k] = c.box.hi[2] + pad;
             if (c.leaf()) {
                 int32_t first = (int32_t)out->order.size();
                 for (int32_t i = c.first; i < c.first + c.count; ++i) out->order.push_back(b.idx[i]);

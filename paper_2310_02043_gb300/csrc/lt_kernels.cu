@@ -22,6 +22,10 @@ constexpr int kTraceThreads = 256;
 #define LT_MIN_BLOCKS 3
 #endif
 constexpr int kTraceMinBlocks = LT_MIN_BLOCKS;   // resident blocks per SM the register budget targets
+#ifndef LT_MIN_BLOCKS_ADJ
+#define LT_MIN_BLOCKS_ADJ LT_MIN_BLOCKS
+#endif
+constexpr int kAdjointMinBlocks = LT_MIN_BLOCKS_ADJ;   // the same for the adjoint, which carries more state
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC 2011).
@@ -222,10 +226,14 @@ constexpr float kFarScale = 1.0f + 2.0f * (3.0f * 0x1p-24f) / (1.0f - 3.0f * 0x1
 // Slab test of 4 children (slots 4h .. 4h+3). The ray's near plane along an
 // axis is lo when it runs towards +a and hi otherwise, so the entry and exit
 // distances need no per-axis min/max: near and far planes are picked by
-// address (lo and hi of an axis are two 16-byte vectors apart).
+// address (lo and hi of an axis are two 16-byte vectors apart). A plane
+// distance is one fma, plane * (1/d) + q with q = -o/d rounded once per node
+// visit; the builder pads every child box by more than that rounding moves
+// a plane, and the exit distance is scaled as in Ize's test, so no box the
+// ray touches is rejected.
 template <bool kSmem>
 __device__ __forceinline__ uint32_t test4(const TraceParams &P, const float4 *smem, int32_t n, const Ray &r,
-                                          float tbest, int half) {
+                                          float qx, float qy, float qz, float tbest, int half) {
     const int xn = (r.octant & 1) << 1, yn = 4 + (r.octant & 2), zn = 8 + ((r.octant & 4) >> 1);
     const float4 nx = node_vec<kSmem>(P, smem, n, xn + half), fx = node_vec<kSmem>(P, smem, n, (xn ^ 2) + half);
     const float4 ny = node_vec<kSmem>(P, smem, n, yn + half), fy = node_vec<kSmem>(P, smem, n, (yn ^ 2) + half);
@@ -236,10 +244,14 @@ __device__ __forceinline__ uint32_t test4(const TraceParams &P, const float4 *sm
     uint32_t hit = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const float tn = max3f((a_nx[k] - r.ox) * r.ix, (a_ny[k] - r.oy) * r.iy,
-                               fmaxf((a_nz[k] - r.oz) * r.iz, 0.0f));
-        const float tf = min3f((a_fx[k] - r.ox) * r.ix, (a_fy[k] - r.oy) * r.iy, (a_fz[k] - r.oz) * r.iz) *
-                         kFarScale;
+        float tn, tf;
+        if (kSmem) {
+            tn = max3f(fmaf(a_nx[k], r.ix, qx), fmaf(a_ny[k], r.iy, qy), fmaxf(fmaf(a_nz[k], r.iz, qz), 0.0f));
+            tf = min3f(fmaf(a_fx[k], r.ix, qx), fmaf(a_fy[k], r.iy, qy), fmaf(a_fz[k], r.iz, qz)) * kFarScale;
+        } else {   // nodes through L1: the two-rounding form keeps fewer values live
+            tn = max3f((a_nx[k] - r.ox) * r.ix, (a_ny[k] - r.oy) * r.iy, fmaxf((a_nz[k] - r.oz) * r.iz, 0.0f));
+            tf = min3f((a_fx[k] - r.ox) * r.ix, (a_fy[k] - r.oy) * r.iy, (a_fz[k] - r.oz) * r.iz) * kFarScale;
+        }
         hit |= (tn <= tf && tn <= tbest ? 1u : 0u) << k;
     }
     return hit;
@@ -249,7 +261,8 @@ __device__ __forceinline__ uint32_t test4(const TraceParams &P, const float4 *sm
 template <bool kSmem>
 __device__ __forceinline__ uint32_t test_node(const TraceParams &P, const float4 *smem, int32_t n, const Ray &r,
                                               float tbest) {
-    return test4<kSmem>(P, smem, n, r, tbest, 0) | (test4<kSmem>(P, smem, n, r, tbest, 1) << 4);
+    const float qx = kSmem ? -r.ox * r.ix : 0.0f, qy = kSmem ? -r.oy * r.iy : 0.0f, qz = kSmem ? -r.oz * r.iz : 0.0f;
+    return test4<kSmem>(P, smem, n, r, qx, qy, qz, tbest, 0) | (test4<kSmem>(P, smem, n, r, qx, qy, qz, tbest, 1) << 4);
 }
 
 // Mask in the ray's visiting order: slot s becomes bit s ^ octant, so the
@@ -577,7 +590,8 @@ __device__ __forceinline__ void stage_nodes(const TraceParams &P, float4 *smem) 
 // waiting for, so lanes never idle until a neighbour's path ends.
 // ---------------------------------------------------------------------------
 template <bool kAdjoint, bool kCount, bool kSmem>
-__global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(const TraceParams P) {
+__global__ void __launch_bounds__(kTraceThreads, kAdjoint ? kAdjointMinBlocks : kTraceMinBlocks)
+    trace_kernel(const TraceParams P) {
     extern __shared__ float4 smem[];
     if (kSmem) stage_nodes(P, smem);
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -593,9 +607,8 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
 
     int32_t l = 0, seg = 0, skip = -1;
     float phi = 0.0f, a_emit = 0.0f, g = 0.0f, beta = 1.0f;
-    float x1x = 0.0f, x1y = 0.0f, x1z = 0.0f;      // adjoint: first hit and its normal
-    float3 n1 = make_float3(0.0f, 0.0f, 0.0f);
-    bool hit1 = false;
+    float x1x = 0.0f, x1y = 0.0f, x1z = 0.0f;      // adjoint: first hit point
+    int32_t n1code = -1;                          // adjoint: 2 x first-hit triangle + 1 if its normal was flipped
     Ray r;
     Trav s;
     Hit h;
@@ -653,7 +666,11 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
                 if (!kAdjoint) {
                     deposit_active(P.q + tb, texel, (unsigned long long)__float2ll_rn(phi * scale));   // Eq. 8
                 } else {
-                    if (seg == 1) { x1x = x.x; x1y = x.y; x1z = x.z; n1 = nrm; hit1 = true; }
+                    if (seg == 1) {
+                        x1x = x.x; x1y = x.y; x1z = x.z;
+                        n1code = 2 * h.tri + (nrm.x != __ldg(P.hits[h.tri].n) || nrm.y != __ldg(P.hits[h.tri].n + 1) ||
+                                              nrm.z != __ldg(P.hits[h.tri].n + 2) ? 1 : 0);
+                    }
                     g += __ldg(P.w + tb + texel) * beta;                                          // Eq. 12
                 }
                 if (seg < P.max_hits) {
@@ -665,7 +682,7 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
                 }
             }
             if (!bounce) {
-                if (kAdjoint && hit1) {
+                if (kAdjoint && n1code >= 0) {
                     // Eq. 11: this photon's dO/dPhi_r * dPhi_r/dp into its light's slot
                     const LightDev &L = P.lights[l];
                     float2 q = make_float2(0.0f, 0.0f);
@@ -673,6 +690,9 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
                         const float4 u0 = uniforms(seed, photon - L.photon_base, 0u, L.design);
                         q = area_coords(L, u0.z, u0.w);
                     }
+                    const float *nn = P.hits[n1code >> 1].n;
+                    const float sgn = (n1code & 1) ? -1.0f : 1.0f;
+                    const float3 n1 = make_float3(sgn * __ldg(nn), sgn * __ldg(nn + 1), sgn * __ldg(nn + 2));
                     float dp[8];
                     dflux(L, L.flux_k * a_emit, a_emit, q, x1x, x1y, x1z, n1, dp);
                     double *o = P.slots + (tid * (uint64_t)P.n_slots + (uint64_t)(l - first_light)) * 8;
@@ -703,7 +723,7 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) trace_kernel(c
                     skip = -1;
                     g = 0.0f;
                     beta = 1.0f;
-                    hit1 = false;
+                    n1code = -1;
                 }
                 const float3 w = frame_dir(c, sn, u.y, t1, t2, axis);
                 ray_init(r, org.x, org.y, org.z, w.x, w.y, w.z);
