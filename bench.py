@@ -608,6 +608,16 @@ def run_surrogate(args):
     b.record(stream)
     torch.cuda.synchronize()
     design_ms = a.elapsed_time(b) / n_rep
+    sg.set_kernels(False)            # the same call with the mma.sync forward, for comparison
+    sg.design(start, target)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(n_rep):
+        sg.design(start, target)
+    b.record(stream)
+    torch.cuda.synchronize()
+    design_ms_mma = a.elapsed_time(b) / n_rep
+    sg.set_kernels(True)
     rows = 16 * ((T + 15) // 16 * 16)
     design_flops = rows * SG_FWD_FLOPS * 3
     peaks = json.load(open(MEASURED_PEAKS)) if os.path.exists(MEASURED_PEAKS) else {}
@@ -658,7 +668,8 @@ def run_surrogate(args):
             "plain_tracer_s": plain_s, "speedup": (plain_s / warm_s) if (plain_s and warm_s) else None,
             "fit_s": {"solves": info["solve_s"], "train": info["train_s"], "total": fit_s},
             "warm_incl_fit_s": None if warm_s is None else warm_s + fit_s,
-            "heldout_rel_l2": errs, "design_ms": design_ms, "train_step_ms": train_ms,
+            "heldout_rel_l2": errs, "design_ms": design_ms, "design_ms_mma_sync_forward": design_ms_mma,
+            "train_step_ms": train_ms,
             "roofline": {"bound": "tensor", "achieved": design_flops / (design_ms / 1e3) / 1e12, "peak": peak,
                          "unit": "TFLOP/s", "frac": design_flops / (design_ms / 1e3) / 1e12 / peak, "traffic": None,
                          "kernel": "sg_design (network forward + backward over 16 spots x all texels)",

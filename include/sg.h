@@ -87,8 +87,8 @@ LT_API int sg_set_training_data(void *ctx, const lt_light *lights, int32_t n_sol
 
 /* One Adam step on a batch of `batch` samples (1..SG_MAX_BATCH). samples
  * [batch][2] = (solve, texel) pairs (host), or NULL to draw them on the
- * device from Philox4x32-10 keyed by `seed` with the step number in the
- * counter. Writes the batch loss (before the update) to *loss_out (host,
+ * device with splitmix64 (Steele, Lea and Flood 2014) of `seed`, the step
+ * number and the sample index. Writes the batch loss (before the update) to *loss_out (host,
  * may be NULL) and keeps the batch's gradients for sg_get_gradients. */
 LT_API int sg_train_step(void *ctx, uint64_t seed, int32_t batch, float lr, const int32_t *samples,
                          double *loss_out);
@@ -119,6 +119,14 @@ LT_API int sg_design(void *ctx, const lt_light *lights, int32_t n_lights, const 
  * SG_MAX_BATCH. */
 LT_API int sg_network(void *ctx, const float *X, int32_t rows, const float *dO, float *O_out, float *dX_out,
                       float *dW_out);
+
+/* Kernels of the design forward (sg_response, and the forward half of
+ * sg_design): tcgen05 = 1 (default) runs the network on the 5th-generation
+ * tensor cores (tcgen05.mma, fp32 accumulators in tensor memory, 128 rows per
+ * CTA); 0 runs it with warp-level mma.sync (16 rows per warp). Both take bf16
+ * inputs and accumulate in fp32; they agree up to the order of the fp32 sums.
+ * A tensor-core wait that gives up returns LT_ERR_TIMEOUT. */
+LT_API int sg_set_kernels(void *ctx, int tcgen05);
 
 /* Hash encoding of normalised positions xn [rows][3] (host) with the
  * current table: enc_out [rows][32] (host). */

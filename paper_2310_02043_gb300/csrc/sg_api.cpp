@@ -49,6 +49,8 @@ struct SgCtx {
     float *d_K = nullptr, *d_up = nullptr, *d_gpart = nullptr;
     size_t K_floats = 0, up_floats = 0, gpart_floats = 0;
     double *d_dout = nullptr;
+    int32_t *d_err = nullptr;                 // device error word of the tcgen05 kernels
+    int use_tc = 1;                           // design forward on tcgen05 (1) or mma.sync (0)
     double *h_pinned = nullptr;
     size_t h_pinned_bytes = 0;
 };
@@ -183,7 +185,7 @@ void free_all(SgCtx *c) {
     dfree(c->d_train); dfree(c->rb.act); dfree(c->rb.dz); dfree(c->d_wpart);
     dfree(c->d_lpart); dfree(c->d_loss); dfree(c->d_samples);
     dfree(c->d_X); dfree(c->d_dO); dfree(c->d_O); dfree(c->d_dX); dfree(c->d_xn); dfree(c->d_enc_out);
-    dfree(c->d_dl); dfree(c->d_K); dfree(c->d_up); dfree(c->d_gpart); dfree(c->d_dout);
+    dfree(c->d_dl); dfree(c->d_K); dfree(c->d_up); dfree(c->d_gpart); dfree(c->d_dout); dfree(c->d_err);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     c->h_pinned = nullptr;
 }
@@ -218,7 +220,9 @@ int sg_create(void **ctx_out, int device, void *cuda_stream) {
         cudaMalloc((void **)&c->d_vT, kTableFloats * sizeof(float)) != cudaSuccess ||
         cudaMalloc((void **)&c->d_gT, kTableFloats * sizeof(float)) != cudaSuccess ||
         cudaMalloc((void **)&c->d_lpart, 4096 * sizeof(double)) != cudaSuccess ||
-        cudaMalloc((void **)&c->d_loss, 16 * sizeof(double)) != cudaSuccess) {
+        cudaMalloc((void **)&c->d_loss, 16 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void **)&c->d_err, sizeof(int32_t)) != cudaSuccess ||
+        cudaMemset(c->d_err, 0, sizeof(int32_t)) != cudaSuccess) {
         free_all(c);
         delete c;
         return LT_ERR_OOM;
@@ -420,6 +424,24 @@ static int design_prepare(SgCtx *c, const lt_light *lights, int32_t n_lights) {
     return refresh_encoding(c);
 }
 
+static int forward_rows(SgCtx *c, const DesignArgs &a) {
+    if (c->use_tc) SG_CUDA(c, launch_design_forward_tc(a, c->d_err, c->stream));
+    else SG_CUDA(c, launch_design_forward(a, c->stream));
+    return LT_OK;
+}
+
+// Reads and clears the device error word (synchronises the stream).
+static int check_device(SgCtx *c) {
+    int32_t e = 0;
+    SG_CUDA(c, cudaMemcpyAsync(&e, c->d_err, sizeof(e), cudaMemcpyDeviceToHost, c->stream));
+    SG_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (e) {
+        SG_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), c->stream));
+        return fail(c, LT_ERR_TIMEOUT, "a tensor-core wait gave up (device error word " + std::to_string(e) + ")");
+    }
+    return LT_OK;
+}
+
 static DesignArgs design_args(SgCtx *c, int32_t n_lights) {
     DesignArgs a;
     a.tex = view(c);
@@ -440,7 +462,8 @@ int sg_response(void *ctx, const lt_light *light, float *K_out, int is_device) {
     if (rc) return rc;
     SG_CUDA(c, cudaSetDevice(c->device));
     if ((rc = design_prepare(c, light, 1))) return rc;
-    SG_CUDA(c, launch_design_forward(design_args(c, 1), c->stream));
+    if ((rc = forward_rows(c, design_args(c, 1)))) return rc;
+    if ((rc = check_device(c))) return rc;
     return copy_to(c, K_out, c->d_K, (size_t)c->n * sizeof(float), is_device);
 }
 
@@ -458,7 +481,7 @@ int sg_design(void *ctx, const lt_light *lights, int32_t n_lights, const float *
     SG_CUDA(c, ensure(c->d_gpart, c->gpart_floats, (size_t)n_lights * (size_t)tpl * 8));
     if (!c->d_dout) SG_CUDA(c, dalloc(c->d_dout, (size_t)LT_MAX_LIGHTS * 8 + 8));
     const DesignArgs a = design_args(c, n_lights);
-    SG_CUDA(c, launch_design_forward(a, c->stream));
+    if ((rc = forward_rows(c, a))) return rc;
     SG_CUDA(c, launch_design_reduce(a.tex, c->d_dl, n_lights, c->d_K, E_target, alpha, E_out, c->d_up, c->d_lpart,
                                     c->stream));
     SG_CUDA(c, launch_design_backward(a, c->stream));
@@ -466,7 +489,7 @@ int sg_design(void *ctx, const lt_light *lights, int32_t n_lights, const float *
     double *h = c->h_pinned + (n_lights * sizeof(LightC) + sizeof(double) - 1) / sizeof(double);
     SG_CUDA(c, cudaMemcpyAsync(h, c->d_dout, ((size_t)n_lights * 8 + 1) * sizeof(double), cudaMemcpyDeviceToHost,
                                c->stream));
-    SG_CUDA(c, cudaStreamSynchronize(c->stream));
+    if ((rc = check_device(c))) return rc;
     if (grad_out) std::memcpy(grad_out, h, (size_t)n_lights * 8 * sizeof(double));
     if (loss_out) *loss_out = h[(size_t)n_lights * 8];
     return LT_OK;
@@ -510,6 +533,13 @@ int sg_network(void *ctx, const float *X, int32_t rows, const float *dO, float *
     if (dO && dX_out)
         SG_CUDA(c, cudaMemcpyAsync(dX_out, c->d_dX, need * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
     SG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return LT_OK;
+}
+
+int sg_set_kernels(void *ctx, int tcgen05) {
+    SgCtx *c = static_cast<SgCtx *>(ctx);
+    if (!c || (tcgen05 != 0 && tcgen05 != 1)) return LT_ERR_ARG;
+    c->use_tc = tcgen05;
     return LT_OK;
 }
 

@@ -102,6 +102,8 @@ cudaError_t launch_adam(float *p, const float *g, float *m, float *v, int64_t n,
 cudaError_t launch_encode_points(const float *xn, int32_t n, const float *table, float *enc_out, cudaStream_t s);
 cudaError_t launch_encode_texels(const TexelView &t, const float *table, uint16_t *enc, cudaStream_t s);
 cudaError_t launch_design_forward(const DesignArgs &a, cudaStream_t s);
+// The same on tcgen05 (TMEM accumulators); err gets bit 1 if a wait gave up.
+cudaError_t launch_design_forward_tc(const DesignArgs &a, int32_t *err, cudaStream_t s);
 cudaError_t launch_design_reduce(const TexelView &t, const LightC *lights, int32_t n_lights, const float *K,
                                  const float *E_target, const float *alpha, float *E_out, float *up,
                                  double *loss_part, cudaStream_t s);

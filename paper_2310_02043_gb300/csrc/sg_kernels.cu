@@ -843,6 +843,204 @@ __global__ void design_final_kernel(const float *__restrict__ gpart, const Light
     }
 }
 
+// ---------------------------------------------------------------------------
+// The design forward on the 5th-generation tensor cores (tcgen05)
+//
+// A CTA of 128 threads takes 128 rows at a time, one row per thread. The
+// thread writes its input row into shared memory in the canonical
+// no-swizzle K-major layout (8 x 8 bf16 "core matrices" of 128 bytes; core
+// (r / 8, k / 8) at ((r / 8) * 8 + k / 8) * 128 bytes), one elected thread
+// issues the four K = 16 steps of each layer as tcgen05.mma (M = 128,
+// N = 64 or 16, bf16 x bf16 -> fp32 in tensor memory) and commits them to an
+// mbarrier; every thread then reads its accumulator row back with
+// tcgen05.ld, applies ReLU, rounds to bf16 and writes the next layer's
+// operand. The weights sit in the same layout, loaded once per CTA.
+// ---------------------------------------------------------------------------
+constexpr int kTcRows = 128;
+constexpr uint32_t kTcCols = 64;                 // TMEM columns of the 128 x 64 fp32 accumulator
+constexpr uint32_t kTcSpin = 1u << 20;           // mbarrier polls before giving up
+constexpr int kErrTc = 1;
+
+struct alignas(1024) TcSmem {
+    uint16_t a[kTcRows * 64];                    // A operand, 16 KB
+    uint16_t w[3 * 64 * 64 + 16 * 64];           // B operands, layer after layer
+    unsigned long long mbar;
+    uint32_t tmem;
+    int32_t abort;
+};
+
+__device__ __forceinline__ uint32_t core_offset(int r, int k) {      // bytes, 64-wide rows
+    return (uint32_t)((((r >> 3) << 3) + (k >> 3)) << 7) + (uint32_t)((r & 7) << 4) + (uint32_t)((k & 7) << 1);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: start address, leading byte offset
+// (between core matrices adjacent in K), stride byte offset (between core
+// matrices adjacent in M / N), descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: fp32 accumulator, bf16 A and B, both
+// K-major, N / 8 and M / 16.
+__host__ __device__ constexpr uint32_t mma_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+    for (uint32_t i = 0; i < kTcSpin; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// 16 fp32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(kTcRows, 1) design_forward_tc_kernel(const DesignArgs A, int32_t *err) {
+    extern __shared__ __align__(1024) unsigned char tc_raw[];
+    TcSmem &S = *reinterpret_cast<TcSmem *>(tc_raw);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    // weights into the canonical layout
+    for (int i = tid; i < kWeights; i += kTcRows) {
+        const int layer = i < kOffW3 ? i >> 12 : 3, r = i < kOffW3 ? i & 4095 : i - kOffW3;
+        const int n = r >> 6, k = r & 63;
+        *reinterpret_cast<uint16_t *>(reinterpret_cast<unsigned char *>(S.w) + layer * 8192 + core_offset(n, k)) =
+            A.Wb[i];
+    }
+    const uint32_t mbar = smem_u32(&S.mbar);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        S.abort = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&S.tmem)),
+                     "r"(kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem;
+    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t a_base = smem_u32(S.a), w_base = smem_u32(S.w);
+    const int64_t rows = A.tex.n_pad * (int64_t)A.n_lights;
+    const int64_t tiles = (rows + kTcRows - 1) / kTcRows;
+    uint32_t phase = 0;
+    unsigned char *arow = reinterpret_cast<unsigned char *>(S.a);
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int64_t row = tile * kTcRows + tid;
+        const bool valid = row < rows;
+        const int l = valid ? (int)(row / A.tex.n_pad) : 0;
+        const int64_t t = valid ? row % A.tex.n_pad : 0;
+        // the input row: encoding (cached per texel) and geometric features
+        uint16_t x[64];
+        const float D = geometry_row(A.lights[l], A.tex.pos[t], A.tex.nrm[t], A.tex, x);
+        const uint4 *enc = reinterpret_cast<const uint4 *>(A.enc + t * 32);
+#pragma unroll
+        for (int g8 = 0; g8 < 4; ++g8)
+            *reinterpret_cast<uint4 *>(arow + core_offset(tid, 8 * g8)) = valid ? enc[g8] : make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int g8 = 4; g8 < 8; ++g8) {
+            uint4 v;
+            v.x = valid ? (uint32_t)x[8 * g8] | ((uint32_t)x[8 * g8 + 1] << 16) : 0u;
+            v.y = valid ? (uint32_t)x[8 * g8 + 2] | ((uint32_t)x[8 * g8 + 3] << 16) : 0u;
+            v.z = valid ? (uint32_t)x[8 * g8 + 4] | ((uint32_t)x[8 * g8 + 5] << 16) : 0u;
+            v.w = valid ? (uint32_t)x[8 * g8 + 6] | ((uint32_t)x[8 * g8 + 7] << 16) : 0u;
+            *reinterpret_cast<uint4 *>(arow + core_offset(tid, 8 * g8)) = v;
+        }
+        proxy_fence();
+        __syncthreads();
+        float o0 = 0.0f, o1 = 0.0f;
+        for (int layer = 0; layer < 4; ++layer) {
+            const int N = layer < 3 ? 64 : 16;
+            if (tid == 0) {
+                tc_fence_after();
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    tc_mma(tmem, smem_desc(a_base + 256 * kk, 128, 1024),
+                           smem_desc(w_base + layer * 8192 + 256 * kk, 128, 1024), mma_idesc(128, N), kk > 0);
+                tc_commit(mbar);
+            }
+            const bool ok = mbar_wait(mbar, phase);
+            phase ^= 1u;
+            tc_fence_after();
+            if (!ok) atomicOr(&S.abort, 1);
+            __syncthreads();
+            if (S.abort) break;
+            if (layer < 3) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float v[16];
+                    tc_ld16(lane_addr + 16 * c, v);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        uint4 q;
+                        q.x = pack2(fmaxf(v[8 * h], 0.0f), fmaxf(v[8 * h + 1], 0.0f));
+                        q.y = pack2(fmaxf(v[8 * h + 2], 0.0f), fmaxf(v[8 * h + 3], 0.0f));
+                        q.z = pack2(fmaxf(v[8 * h + 4], 0.0f), fmaxf(v[8 * h + 5], 0.0f));
+                        q.w = pack2(fmaxf(v[8 * h + 6], 0.0f), fmaxf(v[8 * h + 7], 0.0f));
+                        *reinterpret_cast<uint4 *>(arow + core_offset(tid, 16 * c + 8 * h)) = q;
+                    }
+                }
+                tc_fence_before();
+                proxy_fence();
+                __syncthreads();
+            } else {
+                float v[16];
+                tc_ld16(lane_addr, v);
+                o0 = v[0];
+                o1 = v[1];
+                tc_fence_before();
+            }
+        }
+        if (S.abort) break;
+        if (valid) A.K[row] = sigmoidf_(o0) * D + kRScale * softplusf_(o1);
+        __syncthreads();
+    }
+    if (S.abort && tid == 0) atomicOr(err, kErrTc);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTcCols) : "memory");
+}
+
 int g_sms = 0;
 
 }  // namespace
@@ -922,6 +1120,19 @@ cudaError_t launch_design_reduce(const TexelView &t, const LightC *lights, int32
                                  const float *E_target, const float *alpha, float *E_out, float *up,
                                  double *loss_part, cudaStream_t s) {
     design_reduce_kernel<<<kReduceBlocks, 256, 0, s>>>(t, lights, n_lights, K, E_target, alpha, E_out, up, loss_part);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_design_forward_tc(const DesignArgs &a, int32_t *err, cudaStream_t s) {
+    const size_t smem = sizeof(TcSmem) + 1024;
+    cudaError_t e = set_smem((const void *)design_forward_tc_kernel, smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int64_t tiles = (a.tex.n_pad * (int64_t)a.n_lights + kTcRows - 1) / kTcRows;
+    // at most 4 CTAs per SM: 4 x 64 TMEM columns never wait for an allocation
+    const int grid = (int)std::min<int64_t>(tiles, (int64_t)train_grid(dev) * 2);
+    design_forward_tc_kernel<<<grid, kTcRows, smem, s>>>(a, err);
     return cudaGetLastError();
 }
 

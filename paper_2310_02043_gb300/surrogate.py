@@ -26,7 +26,7 @@ MAX_BATCH = 1 << 20
 
 EXPORTED = ("sg_create", "sg_destroy", "sg_last_error", "sg_set_texels", "sg_set_params", "sg_get_params",
             "sg_set_training_data", "sg_train_step", "sg_get_gradients", "sg_response", "sg_design", "sg_network",
-            "sg_encode")
+            "sg_encode", "sg_set_kernels")
 
 _declared = False
 
@@ -50,6 +50,7 @@ def _lib():
             "sg_design": [vp, vp, i32, vp, vp, vp, vp, vp],
             "sg_network": [vp, vp, i32, vp, vp, vp, vp],
             "sg_encode": [vp, vp, i32, vp],
+            "sg_set_kernels": [vp, ci],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -170,6 +171,10 @@ class Surrogate:
         dW = np.empty(WEIGHTS, np.float32)
         self._check(self.lib.sg_network(self.h, _ptr(X)[0], B, _ptr(dO)[0], _ptr(O)[0], _ptr(dX)[0], _ptr(dW)[0]))
         return O, dX, dW
+
+    def set_kernels(self, tcgen05: bool):
+        """Design forward on tcgen05 (True, default) or mma.sync (False)."""
+        self._check(self.lib.sg_set_kernels(self.h, 1 if tcgen05 else 0))
 
     def encode(self, xn):
         xn = np.ascontiguousarray(xn, np.float32)

@@ -196,3 +196,33 @@ def test_training_fits_a_smooth_response(sg):
     sg.set_training_data(lights, torch.tensor(E, device="cuda"))
     losses = [sg.train_step(1, 4096, 1e-2) for _ in range(300)]
     assert np.mean(losses[-20:]) < 0.1 * np.mean(losses[:5]), (losses[:5], losses[-5:])
+
+
+def test_tensor_core_paths_agree(sg):
+    # tcgen05 (TMEM accumulators, 128 rows per CTA) and mma.sync (16 rows per
+    # warp) run the same network on the same bf16 inputs; only the order of
+    # the fp32 sums differs
+    import torch
+    x, nt, area, lo, ext, inv_ext, lights, W, table = _problem(12, 5003, 5)
+    lights = lights.copy()
+    lights[:, 6] = [1.5, 1.0, 2.0, 0.7, 1.2]
+    sg.set_texels(x, nt, area, lo, ext)
+    sg.set_params(W, table)
+    target = torch.tensor(np.random.default_rng(13).uniform(0, 0.5, x.shape[0]).astype(np.float32), device="cuda")
+    out = {}
+    for tc in (True, False):
+        sg.set_kernels(tc)
+        E = torch.zeros(x.shape[0], device="cuda")
+        O, g = sg.design(lights, target, E_out=E)
+        out[tc] = (sg.response(lights[1]), O, g, E.cpu().numpy())
+    sg.set_kernels(True)
+    Kt, Ot, gt, Et = out[True]
+    Km, Om, gm, Em = out[False]
+    _close(Kt, Km.astype(np.float64), 0.99, 1e-2, "K")
+    _close(Et, Em.astype(np.float64), 0.99, 1e-2, "E")
+    assert Ot == pytest.approx(Om, rel=1e-3)
+    assert np.abs(gt - gm).max() <= 1e-2 * np.abs(gm).max()
+    Wm = [w.astype(np.float64) for w in split_weights(W)]
+    K_ref = S.response(table.astype(np.float64), Wm, lights[1], x, nt.astype(np.float64), lo, ext, inv_ext)
+    _close(Kt, K_ref, 0.97, 2e-2, "K vs oracle")
+
