@@ -2,18 +2,20 @@
 //
 // 1. A binary BVH by binned surface-area heuristic (16 bins along the largest
 //    centroid extent; leaves of at most kLeafMax triangles).
-// 2. Collapse to 8-wide nodes: a wide node starts from a binary inner node's
-//    two children and repeatedly opens the inner child with the largest
-//    surface area until it has 8 children or only leaves remain.
+// 2. Collapse to 8-wide nodes by the surface-area-optimal distribution of
+//    the 8 slots of every wide node over binary subtrees (dynamic program
+//    over the binary tree, see build_wide_bvh).
 // 3. Nodes are emitted breadth-first, so the top levels form a prefix of the
-//    node array (the part the kernels stage in shared memory), and leaf
-//    triangles are laid out contiguously in the order their leaves appear.
-// Child boxes are the exact float bounds of their triangles.
+//    node array, and leaf triangles are laid out contiguously in the order
+//    their leaves appear.
+// Child boxes are the float bounds of their triangles, padded (see step 3).
 #include <algorithm>
+#include <array>
 #include <cfloat>
 #include <cmath>
 #include <cstring>
 #include <deque>
+#include <functional>
 
 #include "lt_internal.h"
 
@@ -147,13 +149,13 @@ void build_binary(const float *xyz, int32_t n_tri, Binary *b) {
 // it lies relative to the parent's centre; the assignment minimising the sum
 // of -dot(child centre - parent centre, slot direction) is found exactly by
 // dynamic programming over subsets of slots (8 slots, at most 8 children).
-std::vector<int> assign_slots(const Binary &b, const std::vector<int32_t> &kids, const Box &parent) {
-    const int n = (int)kids.size();
+std::vector<int> assign_slots(const std::vector<Box> &boxes, const Box &parent) {
+    const int n = (int)boxes.size();
     double pc[3];
     for (int a = 0; a < 3; ++a) pc[a] = 0.5 * ((double)parent.lo[a] + parent.hi[a]);
     double cost[kWide][kWide];
     for (int j = 0; j < n; ++j) {
-        const Box &bx = b.nodes[kids[j]].box;
+        const Box &bx = boxes[j];
         for (int s = 0; s < kWide; ++s) {
             double c = 0.0;
             for (int a = 0; a < 3; ++a) {
@@ -202,6 +204,86 @@ bool build_wide_bvh(const float *xyz, int32_t n_tri, BvhBuild *out, std::string 
     out->order.reserve(n_tri);
     out->depth = 0;
 
+    // 1-2. Wide nodes by the surface-area-optimal distribution of slots
+    //    (Ylitie, Karras and Laine, "Efficient incoherent ray traversal on
+    //    GPUs through compressed wide BVHs", HPG 2017): C(n, i) is the least
+    //    cost of the subtree of binary node n occupying at most i slots of
+    //    the wide node above it, D(n, j) the least cost of giving j >= 2 slots
+    //    to n's two children. A subtree in one slot is a leaf (its triangles)
+    //    or a wide node of its own (one node visit plus D(n, 8)). The costs
+    //    are the kernel's: a node visit tests 8 boxes, about 4.3 triangle
+    //    tests' worth of arithmetic.
+    struct Entry { int32_t bnode; int32_t wide; };        // wide >= 0: an inner child
+    struct Wide { std::vector<Entry> kids; };
+    std::vector<Wide> wide;
+    {
+        constexpr double kNodeCost = 1.0, kTriCost = 0.23;
+        const int32_t NB = (int32_t)b.nodes.size();
+        std::vector<std::array<double, kWide + 1>> C(NB), D(NB);
+        std::vector<std::array<int8_t, kWide + 1>> split(NB), open(NB);
+        for (int32_t n = NB - 1; n >= 0; --n) {          // children come after their parent
+            const BNode &bn = b.nodes[n];
+            const double area = bn.box.area();
+            if (bn.leaf()) {
+                for (int i = 1; i <= kWide; ++i) { C[n][i] = area * kTriCost * bn.count; open[n][i] = 0; }
+                continue;
+            }
+            for (int j = 2; j <= kWide; ++j) {
+                double best = 1e300;
+                int arg = 1;
+                for (int k = 1; k < j; ++k) {
+                    const double c = C[bn.left][k] + C[bn.right][j - k];
+                    if (c < best) { best = c; arg = k; }
+                }
+                D[n][j] = best;
+                split[n][j] = (int8_t)arg;
+            }
+            C[n][1] = area * kNodeCost + D[n][kWide];
+            open[n][1] = 0;
+            for (int i = 2; i <= kWide; ++i) {
+                if (D[n][i] < C[n][i - 1]) { C[n][i] = D[n][i]; open[n][i] = 1; }
+                else { C[n][i] = C[n][i - 1]; open[n][i] = 0; }
+            }
+        }
+        // the entries of a wide node rooted at binary node r: its j slots
+        // distributed by the recorded choices
+        std::deque<std::pair<int32_t, int32_t>> queue;      // (binary node, wide node)
+        std::vector<Entry> entries;
+        std::function<void(int32_t, int)> take = [&](int32_t m, int i) {
+            while (i > 1 && !open[m][i]) --i;
+            if (i <= 1) {
+                if (b.nodes[m].leaf()) {
+                    entries.push_back({m, -1});
+                } else {
+                    const int32_t w = (int32_t)wide.size();
+                    wide.emplace_back();
+                    entries.push_back({m, w});
+                    queue.push_back({m, w});
+                }
+                return;
+            }
+            const int k = split[m][i];
+            take(b.nodes[m].left, k);
+            take(b.nodes[m].right, i - k);
+        };
+        wide.emplace_back();
+        queue.push_back({0, 0});
+        while (!queue.empty()) {
+            const auto [bn, wn] = queue.front();
+            queue.pop_front();
+            entries.clear();
+            if (b.nodes[bn].leaf()) {
+                entries.push_back({bn, -1});
+            } else {
+                const int k = split[bn][kWide];
+                take(b.nodes[bn].left, k);
+                take(b.nodes[bn].right, kWide - k);
+            }
+            wide[wn].kids = entries;
+        }
+    }
+
+    // 3. Emit breadth-first: slots by direction, padded boxes, leaf ranges.
     // Child boxes grow by pad on every side: the traversal computes a plane
     // distance as fma(plane, 1/d, -o/d), whose rounding of o/d moves the
     // plane by up to |o| 2^-24; 2^-19 (|coordinate| + 1) covers ray origins
@@ -210,38 +292,25 @@ bool build_wide_bvh(const float *xyz, int32_t n_tri, BvhBuild *out, std::string 
     for (size_t i = 0; i < (size_t)n_tri * 9; ++i) amax = std::max(amax, std::fabs(xyz[i]));
     const float pad = (amax + 1.0f) * 0x1p-19f;
 
-    struct Item { int32_t bnode, wnode, depth; };
+    struct Item { int32_t wide, node, depth; };
     std::deque<Item> queue;
     out->nodes.emplace_back();
     out->parent.push_back(-1);
     queue.push_back({0, 0, 0});
     while (!queue.empty()) {
-        Item it = queue.front();
+        const Item it = queue.front();
         queue.pop_front();
         out->depth = std::max(out->depth, it.depth + 1);
         if (it.depth >= kMaxDepth) {
             *err = "BVH deeper than the traversal trail supports";
             return false;
         }
-        std::vector<int32_t> kids;
-        const BNode &root = b.nodes[it.bnode];
-        if (root.leaf()) {
-            kids.push_back(it.bnode);
-        } else {
-            kids.push_back(root.left);
-            kids.push_back(root.right);
-            while ((int)kids.size() < kWide) {
-                int pick = -1;
-                double best = -1.0;
-                for (int k = 0; k < (int)kids.size(); ++k) {
-                    const BNode &c = b.nodes[kids[k]];
-                    if (!c.leaf() && c.box.area() > best) { best = c.box.area(); pick = k; }
-                }
-                if (pick < 0) break;
-                int32_t open = kids[pick];
-                kids[pick] = b.nodes[open].left;
-                kids.insert(kids.begin() + pick + 1, b.nodes[open].right);
-            }
+        const std::vector<Entry> &kids = wide[it.wide].kids;
+        std::vector<Box> boxes;
+        Box all;
+        for (const Entry &e : kids) {
+            boxes.push_back(b.nodes[e.bnode].box);
+            all.grow(boxes.back());
         }
         Node node;
         std::memset(&node, 0, sizeof(node));
@@ -250,27 +319,28 @@ bool build_wide_bvh(const float *xyz, int32_t n_tri, BvhBuild *out, std::string 
             node.hix[k] = node.hiy[k] = node.hiz[k] = -3.0e38f;
             node.child[k] = kEmptyChild;
         }
-        const std::vector<int> slot_of = assign_slots(b, kids, root.box);
+        const std::vector<int> slot_of = assign_slots(boxes, all);
         for (int j = 0; j < (int)kids.size(); ++j) {
             const int k = slot_of[j];
-            const BNode &c = b.nodes[kids[j]];
-            node.lox[k] = c.box.lo[0] - pad; node.hix[k] = c.box.hi[0] + pad;
-            node.loy[k] = c.box.lo[1] - pad; node.hiy[k] = c.box.hi[1] + pad;
-            node.loz[k] = c.box.lo[2] - pad; node.hiz[k] = c.box.hi[2] + pad;
-            if (c.leaf()) {
-                int32_t first = (int32_t)out->order.size();
+            const Box &bx = boxes[j];
+            node.lox[k] = bx.lo[0] - pad; node.hix[k] = bx.hi[0] + pad;
+            node.loy[k] = bx.lo[1] - pad; node.hiy[k] = bx.hi[1] + pad;
+            node.loz[k] = bx.lo[2] - pad; node.hiz[k] = bx.hi[2] + pad;
+            const BNode &c = b.nodes[kids[j].bnode];
+            if (kids[j].wide < 0) {
+                const int32_t first = (int32_t)out->order.size();
                 for (int32_t i = c.first; i < c.first + c.count; ++i) out->order.push_back(b.idx[i]);
                 node.child[k] = -1 - ((first << 2) | (c.count - 1));
             } else {
-                int32_t wn = (int32_t)out->nodes.size();
+                const int32_t wn = (int32_t)out->nodes.size();
                 out->nodes.emplace_back();
-                out->parent.push_back(it.wnode);
+                out->parent.push_back(it.node);
                 node.child[k] = wn;
                 node.inner_mask |= 1u << k;
-                queue.push_back({kids[j], wn, it.depth + 1});
+                queue.push_back({kids[j].wide, wn, it.depth + 1});
             }
         }
-        out->nodes[it.wnode] = node;
+        out->nodes[it.node] = node;
     }
     if ((int32_t)out->order.size() != n_tri) {
         *err = "BVH builder lost triangles";
