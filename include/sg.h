@@ -120,8 +120,8 @@ LT_API int sg_design(void *ctx, const lt_light *lights, int32_t n_lights, const 
 LT_API int sg_network(void *ctx, const float *X, int32_t rows, const float *dO, float *O_out, float *dX_out,
                       float *dW_out);
 
-/* Kernels of the design forward (sg_response, and the forward half of
- * sg_design): tcgen05 = 1 (default) runs the network on the 5th-generation
+/* Kernels of the design objective (sg_response and sg_design, forward and
+ * backward): tcgen05 = 1 (default) runs the network on the 5th-generation
  * tensor cores (tcgen05.mma, fp32 accumulators in tensor memory, 128 rows per
  * CTA); 0 runs it with warp-level mma.sync (16 rows per warp). Both take bf16
  * inputs and accumulate in fp32; they agree up to the order of the fp32 sums.

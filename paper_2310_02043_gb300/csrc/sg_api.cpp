@@ -484,7 +484,8 @@ int sg_design(void *ctx, const lt_light *lights, int32_t n_lights, const float *
     if ((rc = forward_rows(c, a))) return rc;
     SG_CUDA(c, launch_design_reduce(a.tex, c->d_dl, n_lights, c->d_K, E_target, alpha, E_out, c->d_up, c->d_lpart,
                                     c->stream));
-    SG_CUDA(c, launch_design_backward(a, c->stream));
+    if (c->use_tc) SG_CUDA(c, launch_design_backward_tc(a, c->d_err, c->stream));
+    else SG_CUDA(c, launch_design_backward(a, c->stream));
     SG_CUDA(c, launch_design_final(c->d_gpart, c->d_dl, n_lights, tpl, c->d_lpart, c->d_dout, c->stream));
     double *h = c->h_pinned + (n_lights * sizeof(LightC) + sizeof(double) - 1) / sizeof(double);
     SG_CUDA(c, cudaMemcpyAsync(h, c->d_dout, ((size_t)n_lights * 8 + 1) * sizeof(double), cudaMemcpyDeviceToHost,

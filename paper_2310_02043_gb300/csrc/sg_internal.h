@@ -108,6 +108,7 @@ cudaError_t launch_design_reduce(const TexelView &t, const LightC *lights, int32
                                  const float *E_target, const float *alpha, float *E_out, float *up,
                                  double *loss_part, cudaStream_t s);
 cudaError_t launch_design_backward(const DesignArgs &a, cudaStream_t s);
+cudaError_t launch_design_backward_tc(const DesignArgs &a, int32_t *err, cudaStream_t s);
 cudaError_t launch_design_final(const float *gpart, const LightC *lights, int32_t n_lights, int64_t tiles_per_light,
                                 const double *loss_part, double *out, cudaStream_t s);
 int train_grid(int device);

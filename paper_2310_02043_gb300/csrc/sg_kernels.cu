@@ -1041,6 +1041,227 @@ __global__ void __launch_bounds__(kTcRows, 1) design_forward_tc_kernel(const Des
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTcCols) : "memory");
 }
 
+// The design backward on tcgen05: per 128-row tile the forward again (ReLU
+// masks kept as bits), the loss head, then the gradient through W3^T, W2^T,
+// W1^T, W0^T as tcgen05.mma on transposed weights (the output layer's step
+// has K = 16), and each thread's row through the feature Jacobian.
+struct alignas(1024) TcBwdSmem {
+    uint16_t a[kTcRows * 64];                    // activations, then gradients (64 wide)
+    uint16_t d4[kTcRows * 16];                   // gradient at the outputs (16 wide)
+    uint16_t w[3 * 64 * 64 + 16 * 64];           // W0, W1, W2 [64][64], W3 [16][64]
+    uint16_t wt[3 * 64 * 64 + 64 * 16];          // W0^T, W1^T, W2^T [64][64], W3^T [64][16]
+    unsigned long long mbar;
+    uint32_t tmem;
+    int32_t abort;
+};
+
+__device__ __forceinline__ uint32_t core_offset16(int r, int k) {    // bytes, 16-wide rows
+    return (uint32_t)((((r >> 3) << 1) + (k >> 3)) << 7) + (uint32_t)((r & 7) << 4) + (uint32_t)((k & 7) << 1);
+}
+
+// Issues one layer (K / 16 steps) and waits for it; false if the wait gave up.
+__device__ __forceinline__ bool tc_layer(uint32_t tmem, uint32_t a, uint32_t a_sbo, uint32_t b, uint32_t b_sbo, int N,
+                                         int ksteps, uint32_t mbar, uint32_t &phase, int tid) {
+    if (tid == 0) {
+        tc_fence_after();
+        for (int kk = 0; kk < ksteps; ++kk)
+            tc_mma(tmem, smem_desc(a + 256 * kk, 128, a_sbo), smem_desc(b + 256 * kk, 128, b_sbo), mma_idesc(128, N),
+                   kk > 0);
+        tc_commit(mbar);
+    }
+    const bool ok = mbar_wait(mbar, phase);
+    phase ^= 1u;
+    tc_fence_after();
+    return ok;
+}
+
+__global__ void __launch_bounds__(kTcRows, 1) design_backward_tc_kernel(const DesignArgs A, int32_t *err) {
+    extern __shared__ __align__(1024) unsigned char tcb_raw[];
+    TcBwdSmem &S = *reinterpret_cast<TcBwdSmem *>(tcb_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char *wb = reinterpret_cast<unsigned char *>(S.w), *wtb = reinterpret_cast<unsigned char *>(S.wt);
+    for (int i = tid; i < kWeights; i += kTcRows) {
+        const uint16_t v = A.Wb[i];
+        if (i < kOffW3) {
+            const int layer = i >> 12, r = i & 4095, n = r >> 6, k = r & 63;
+            *reinterpret_cast<uint16_t *>(wb + layer * 8192 + core_offset(n, k)) = v;
+            *reinterpret_cast<uint16_t *>(wtb + layer * 8192 + core_offset(k, n)) = v;
+        } else {
+            const int r = i - kOffW3, n = r >> 6, k = r & 63;        // W3[n][k], n < 16
+            *reinterpret_cast<uint16_t *>(wb + 3 * 8192 + core_offset(n, k)) = v;
+            *reinterpret_cast<uint16_t *>(wtb + 3 * 8192 + core_offset16(k, n)) = v;
+        }
+    }
+    const uint32_t mbar = smem_u32(&S.mbar);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        S.abort = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&S.tmem)),
+                     "r"(kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem;
+    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t a_addr = smem_u32(S.a), d4_addr = smem_u32(S.d4), w_addr = smem_u32(S.w), wt_addr = smem_u32(S.wt);
+    const int64_t rows = A.tex.n_pad * (int64_t)A.n_lights;
+    const int64_t tiles = (rows + kTcRows - 1) / kTcRows;
+    uint32_t phase = 0;
+    unsigned char *arow = reinterpret_cast<unsigned char *>(S.a), *drow = reinterpret_cast<unsigned char *>(S.d4);
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int64_t row = tile * kTcRows + tid;
+        const bool valid = row < rows;
+        const int l = valid ? (int)(row / A.tex.n_pad) : 0;
+        const int64_t t = valid ? row % A.tex.n_pad : 0;
+        const LightC &L = A.lights[l];
+        const float4 P = A.tex.pos[t], Nt = A.tex.nrm[t];
+        uint16_t x[64];
+        const float D = geometry_row(L, P, Nt, A.tex, x);
+        const uint4 *enc = reinterpret_cast<const uint4 *>(A.enc + t * 32);
+#pragma unroll
+        for (int g8 = 0; g8 < 4; ++g8)
+            *reinterpret_cast<uint4 *>(arow + core_offset(tid, 8 * g8)) = valid ? enc[g8] : make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int g8 = 4; g8 < 8; ++g8) {
+            uint4 v;
+            v.x = valid ? (uint32_t)x[8 * g8] | ((uint32_t)x[8 * g8 + 1] << 16) : 0u;
+            v.y = valid ? (uint32_t)x[8 * g8 + 2] | ((uint32_t)x[8 * g8 + 3] << 16) : 0u;
+            v.z = valid ? (uint32_t)x[8 * g8 + 4] | ((uint32_t)x[8 * g8 + 5] << 16) : 0u;
+            v.w = valid ? (uint32_t)x[8 * g8 + 6] | ((uint32_t)x[8 * g8 + 7] << 16) : 0u;
+            *reinterpret_cast<uint4 *>(arow + core_offset(tid, 8 * g8)) = v;
+        }
+        proxy_fence();
+        __syncthreads();
+        uint32_t mask[3][2];
+        float o0 = 0.0f, o1 = 0.0f;
+        bool ok = true;
+        // forward
+        for (int layer = 0; layer < 4 && ok; ++layer) {
+            const int N = layer < 3 ? 64 : 16;
+            ok = tc_layer(tmem, a_addr, 1024, w_addr + layer * 8192, 1024, N, 4, mbar, phase, tid);
+            if (!ok) atomicOr(&S.abort, 1);
+            __syncthreads();
+            if (S.abort) { ok = false; break; }
+            if (layer < 3) {
+                mask[layer][0] = mask[layer][1] = 0u;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float v[16];
+                    tc_ld16(lane_addr + 16 * c, v);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        if (v[i] > 0.0f) mask[layer][c >> 1] |= 1u << ((c & 1) * 16 + i);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        uint4 q;
+                        q.x = pack2(fmaxf(v[8 * h], 0.0f), fmaxf(v[8 * h + 1], 0.0f));
+                        q.y = pack2(fmaxf(v[8 * h + 2], 0.0f), fmaxf(v[8 * h + 3], 0.0f));
+                        q.z = pack2(fmaxf(v[8 * h + 4], 0.0f), fmaxf(v[8 * h + 5], 0.0f));
+                        q.w = pack2(fmaxf(v[8 * h + 6], 0.0f), fmaxf(v[8 * h + 7], 0.0f));
+                        *reinterpret_cast<uint4 *>(arow + core_offset(tid, 16 * c + 8 * h)) = q;
+                    }
+                }
+            } else {
+                float v[16];
+                tc_ld16(lane_addr, v);
+                o0 = v[0];
+                o1 = v[1];
+            }
+            tc_fence_before();
+            proxy_fence();
+            __syncthreads();
+        }
+        if (!ok) break;
+        // loss head: dO/do of the row
+        const float sg0 = sigmoidf_(o0);
+        const float K = sg0 * D + kRScale * softplusf_(o1);
+        const float u = valid ? A.up[t] : 0.0f;
+        const float ui = u * L.intensity;
+        const float gD = ui * sg0, gI = u * K;
+        {
+            uint4 q0, q1 = make_uint4(0, 0, 0, 0);
+            q0.x = pack2(ui * sg0 * (1.0f - sg0) * D, ui * kRScale * sigmoidf_(o1));
+            q0.y = q0.z = q0.w = 0u;
+            *reinterpret_cast<uint4 *>(drow + core_offset16(tid, 0)) = q0;
+            *reinterpret_cast<uint4 *>(drow + core_offset16(tid, 8)) = q1;
+        }
+        proxy_fence();
+        __syncthreads();
+        // backward: W3^T (K = 16), then W2^T, W1^T (masked, rounded), W0^T
+        float gX[kGeom];
+        for (int layer = 3; layer >= 0 && ok; --layer) {
+            if (layer == 3) ok = tc_layer(tmem, d4_addr, 256, wt_addr + 3 * 8192, 256, 64, 1, mbar, phase, tid);
+            else ok = tc_layer(tmem, a_addr, 1024, wt_addr + layer * 8192, 1024, 64, 4, mbar, phase, tid);
+            if (!ok) atomicOr(&S.abort, 1);
+            __syncthreads();
+            if (S.abort) { ok = false; break; }
+            if (layer > 0) {
+                const int m = layer - 1;          // the mask of the product's input
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float v[16];
+                    tc_ld16(lane_addr + 16 * c, v);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        float z[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int col = 16 * c + 8 * h + i;
+                            z[i] = (mask[m][col >> 5] >> (col & 31)) & 1u ? v[8 * h + i] : 0.0f;
+                        }
+                        uint4 q;
+                        q.x = pack2(z[0], z[1]);
+                        q.y = pack2(z[2], z[3]);
+                        q.z = pack2(z[4], z[5]);
+                        q.w = pack2(z[6], z[7]);
+                        *reinterpret_cast<uint4 *>(arow + core_offset(tid, 16 * c + 8 * h)) = q;
+                    }
+                }
+            } else {
+                float v[16];
+                tc_ld16(lane_addr + 32, v);       // input entries 32..47
+#pragma unroll
+                for (int i = 0; i < 16; ++i) gX[i] = v[i];
+                tc_ld16(lane_addr + 48, v);       // 48..63
+                gX[16] = v[0];
+            }
+            tc_fence_before();
+            proxy_fence();
+            __syncthreads();
+        }
+        if (!ok) break;
+        float gs[7] = {0, 0, 0, 0, 0, 0, 0};
+        if (valid) {
+            float gr[6];
+            geometry_grad(L, P, Nt, A.tex, gX, gD, gr);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) gs[k] = gr[k];
+            gs[6] = gI;
+        }
+#pragma unroll
+        for (int k = 0; k < 7; ++k)
+#pragma unroll
+            for (int off = 8; off > 0; off >>= 1) gs[k] += __shfl_xor_sync(0xffffffffu, gs[k], off);
+        if ((lane & 15) == 0 && valid) {
+            float *out = A.gpart + (row / 16) * 8;
+#pragma unroll
+            for (int k = 0; k < 7; ++k) out[k] = gs[k];
+            out[7] = 0.0f;
+        }
+    }
+    if (S.abort && tid == 0) atomicOr(err, kErrTc);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTcCols) : "memory");
+}
+
 int g_sms = 0;
 
 }  // namespace
@@ -1133,6 +1354,19 @@ cudaError_t launch_design_forward_tc(const DesignArgs &a, int32_t *err, cudaStre
     // at most 4 CTAs per SM: 4 x 64 TMEM columns never wait for an allocation
     const int grid = (int)std::min<int64_t>(tiles, (int64_t)train_grid(dev) * 2);
     design_forward_tc_kernel<<<grid, kTcRows, smem, s>>>(a, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_design_backward_tc(const DesignArgs &a, int32_t *err, cudaStream_t s) {
+    const size_t smem = sizeof(TcBwdSmem) + 1024;
+    cudaError_t e = set_smem((const void *)design_backward_tc_kernel, smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int64_t tiles = (a.tex.n_pad * (int64_t)a.n_lights + kTcRows - 1) / kTcRows;
+    // at most 3 CTAs per SM fit (shared memory); 3 x 64 TMEM columns never wait
+    const int grid = (int)std::min<int64_t>(tiles, (int64_t)train_grid(dev) * 3 / 2);
+    design_backward_tc_kernel<<<grid, kTcRows, smem, s>>>(a, err);
     return cudaGetLastError();
 }
 
