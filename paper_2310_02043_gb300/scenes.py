@@ -558,3 +558,23 @@ def building_lights(floors: int = 8, width: float = 48.0, depth: float = 24.0, s
             for i in range(4):
                 rows.append(area_light((9.0 + 12.0 * i, y, z), 0.0, -np.pi / 2, power, size[0], size[1]))
     return make_lights(rows)
+
+
+def random_lights(n: int, seed: int, lo=(0.1, 0.1, 0.1), hi=(0.9, 0.9, 0.9)) -> np.ndarray:
+    """n luminaires cycling point, spot and area, positions uniform in the box
+    [lo, hi], random axes, intensity / power U[0.2, 2], spot cones
+    0 <= theta_in < theta_out <= 1.4, area sizes U[0.02, 0.2] m."""
+    rng = np.random.default_rng(seed + 13000)
+    rows = []
+    for i in range(n):
+        pos = tuple(rng.uniform(lo, hi))
+        yaw, pitch, I = float(rng.uniform(0, 2 * np.pi)), float(rng.uniform(-1.5, 1.5)), float(rng.uniform(0.2, 2.0))
+        kind = i % 3
+        if kind == 0:
+            rows.append(point_light(pos, I))
+        elif kind == 1:
+            to = float(rng.uniform(0.2, 1.4))
+            rows.append(spot_light(pos, yaw, pitch, I, float(rng.uniform(0.0, 0.95)) * to, to))
+        else:
+            rows.append(area_light(pos, yaw, pitch, I, float(rng.uniform(0.02, 0.2)), float(rng.uniform(0.02, 0.2))))
+    return make_lights(rows)
