@@ -604,19 +604,29 @@ int lt_set_lights(void *ctx, const lt_light *lights, int32_t n_lights) {
     return LT_OK;
 }
 
+// Fixed point: S = 2^k with S * (total power bound) * max_hits < 2^62, so
+// no texel (nor the sum of all texels) can overflow int64. Returns false
+// when k would fall below -120 (a power bound beyond 2^182 / max_hits): the
+// float deposit Phi * S would then lose its precision.
+static bool fixed_point_scale(double bound, int32_t max_hits, double *S) {
+    *S = std::ldexp(1.0, 40);
+    if (!(bound > 0.0)) return true;
+    if (!std::isfinite(bound)) return false;
+    const int k = (int)std::floor(std::log2(std::ldexp(1.0, 62) / (bound * (double)max_hits)));
+    if (k < -120) return false;
+    *S = std::ldexp(1.0, std::min(120, k));
+    return true;
+}
+
 static int forward_pass(Ctx *c, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
                  uint64_t photon_end, unsigned long long *d_work) {
     int rc = check_trace_args(c, n_photons, max_hits, photon_begin, photon_end);
     if (rc) return rc;
     LT_CUDA(c, cudaSetDevice(c->device));
     if ((rc = upload_lights(c, n_photons))) return rc;
-    // Fixed point: S = 2^k with S * (total power bound) * max_hits < 2^62, so
-    // no texel (nor the sum of all texels) can overflow int64.
-    double S = std::ldexp(1.0, 40);
-    if (c->power_bound > 0.0) {
-        const int k = (int)std::floor(std::log2(std::ldexp(1.0, 62) / (c->power_bound * (double)max_hits)));
-        S = std::ldexp(1.0, std::max(-120, std::min(120, k)));
-    }
+    double S;
+    if (!fixed_point_scale(c->power_bound, max_hits, &S))
+        return fail(c, LT_ERR_OVERFLOW, "total light power too large for the int64 texel accumulator");
     c->scale = S;
     TraceParams p = base_params(c, seed, max_hits, photon_begin, photon_end);
     p.q = c->d_q;
@@ -919,11 +929,9 @@ int lt_batch_set_lights(void *ctx, const lt_light *lights) {
         off += b.counts[d];
     }
     // one fixed-point scale for the batch, safe for its brightest design
-    double S = std::ldexp(1.0, 40);
-    if (bound > 0.0) {
-        const int k = (int)std::floor(std::log2(std::ldexp(1.0, 62) / (bound * (double)b.max_hits)));
-        S = std::ldexp(1.0, std::max(-120, std::min(120, k)));
-    }
+    double S;
+    if (!fixed_point_scale(bound, b.max_hits, &S))
+        return fail(c, LT_ERR_OVERFLOW, "total light power too large for the int64 texel accumulator");
     StepHeader *h = reinterpret_cast<StepHeader *>(b.h_in);
     h->scale = S;
     h->inv_scale = 1.0 / S;

@@ -73,3 +73,18 @@ def test_limits_are_rejected(tr):
     for bad in (0, 65):
         with pytest.raises(LtError):
             tr.trace_forward(1, 1000, bad)
+
+
+def test_power_beyond_the_fixed_point_range(tr):
+    from paper_2310_02043_gb300.lighttrace import LT_ERR_OVERFLOW
+    sc = scenes.cornell_box(res=4)
+    tr.upload_scene(sc)
+    L = scenes.make_lights([scenes.point_light((0.5, 0.5, 0.5), 1e60)])
+    tr.set_lights(L)
+    with pytest.raises(LtError) as e:
+        tr.trace_forward(1, 1000, 3)
+    assert e.value.status == LT_ERR_OVERFLOW
+    tr.set_lights(scenes.make_lights([scenes.point_light((0.5, 0.5, 0.5), 1e30)]))
+    tr.trace_forward(1, 1000, 3)                          # large but representable
+    assert np.isfinite(tr.irradiance()).all()
+
