@@ -558,10 +558,18 @@ __device__ __forceinline__ void dflux(const LightDev &L, float phi_r, float a_em
     out[7] = scale * (-2.0f) * (c - L.co) * (c - L.ci) * L.sin_out * id3;
 }
 
-// Deposit from the lanes of the warp that are depositing in this step: lanes
-// that hit the same texel add their values with shuffles and one of them does
-// the 64-bit atomic.
+// Deposit of the lanes of the warp that are depositing in this step (Eq. 8):
+// a 64-bit fixed-point atomic each. Built with LT_DEPOSIT_WARP_AGGREGATE,
+// lanes that hit the same texel first add their values with shuffles and one
+// of them does the atomic.
 __device__ __forceinline__ void deposit_active(unsigned long long *q, int64_t texel, unsigned long long val) {
+#ifndef LT_DEPOSIT_WARP_AGGREGATE
+    // lanes of a warp rarely hit the same texel (measured: aggregating with
+    // __match_any_sync costs more than it saves at 2-4.5 cm texels); integer
+    // addition keeps the sums independent of the order either way
+    atomicAdd(q + texel, val);
+    return;
+#endif
     const unsigned m = __activemask();
     const unsigned peers = __match_any_sync(m, (unsigned long long)texel);
     unsigned long long tot = 0;
