@@ -230,7 +230,7 @@ int launch_shape(Ctx *c, bool adjoint, int *grid, size_t *smem, int32_t *n_stage
     *smem = (size_t)(*n_staged) * sizeof(Node);
     int bps = c->blocks_per_sm;
     if (bps <= 0) {
-        cudaError_t e = trace_occupancy(adjoint, staged, c->threads, *smem, &bps);
+        cudaError_t e = trace_occupancy(adjoint, staged, c->depth, c->threads, *smem, &bps);
         if (e != cudaSuccess) return cuda_fail(c, e, "occupancy query");
         if (bps < 1) return fail(c, LT_ERR_ARG, "launch shape does not fit on an SM");
     }
@@ -257,6 +257,7 @@ TraceParams base_params(Ctx *c, uint64_t seed, int32_t max_hits, uint64_t begin,
     p.nodes = c->d_nodes;
     p.parent = c->d_parent;
     p.n_nodes = c->n_nodes;
+    p.depth = c->depth;
     p.tris = c->d_tris;
     p.hits = c->d_hits;
     p.lights = c->d_lights;

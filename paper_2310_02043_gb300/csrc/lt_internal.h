@@ -101,6 +101,7 @@ struct TraceParams {
     const int32_t *parent;
     int32_t n_nodes;
     int32_t n_staged;           // nodes copied to shared memory by every block
+    int32_t depth;              // levels of wide nodes (1..kMaxDepth)
     const Tri *tris;
     const TriHit *hits;
     const LightDev *lights;
@@ -159,7 +160,7 @@ cudaError_t launch_resolve(const unsigned long long *q, const float *area, doubl
                            float *E_out, cudaStream_t s);
 cudaError_t launch_grad_finalize(const TraceParams &p, double *out, cudaStream_t s);
 int trace_kernel_max_threads();
-cudaError_t trace_occupancy(bool adjoint, bool staged, int block, size_t smem, int *blocks_per_sm);
+cudaError_t trace_occupancy(bool adjoint, bool staged, int depth, int block, size_t smem, int *blocks_per_sm);
 
 // Wide-BVH builder (lt_bvh.cpp).
 struct BvhBuild {

@@ -147,10 +147,15 @@ __device__ __forceinline__ bool tri_intersect(const Ray &r, const float4 a, cons
 
 // ---------------------------------------------------------------------------
 // Wide-BVH traversal without a stack. The pending children of every level
-// are an 8-bit mask packed into two 64-bit registers (in the ray's visiting
+// are an 8-bit mask packed into 64-bit registers (in the ray's visiting
 // order, see order_mask); returning to a level follows the parent link and
 // re-tests that node's pending children against the current closest hit.
+// Trees of at most kShallowDepth levels keep the masks in one word, deeper
+// ones (up to kMaxDepth) in two.
 // ---------------------------------------------------------------------------
+constexpr int kShallowDepth = 8;
+
+template <bool kDeep>
 struct Trail {
     uint64_t w0 = 0, w1 = 0;
     __device__ __forceinline__ uint32_t get(int lvl) const {
@@ -162,6 +167,16 @@ struct Trail {
         const uint64_t clear = ~(0xffull << sh), put = (uint64_t)m << sh;
         if (lvl < 8) w0 = (w0 & clear) | put;
         else w1 = (w1 & clear) | put;
+    }
+};
+
+template <>
+struct Trail<false> {
+    uint64_t w0 = 0;
+    __device__ __forceinline__ uint32_t get(int lvl) const { return (uint32_t)(w0 >> (lvl * 8)) & 0xffu; }
+    __device__ __forceinline__ void set(int lvl, uint32_t m) {
+        const int sh = lvl * 8;
+        w0 = (w0 & ~(0xffull << sh)) | ((uint64_t)m << sh);
     }
 };
 
@@ -182,6 +197,7 @@ struct Work {
     uint32_t nodes = 0, tris = 0;   // node visits (including re-tests) and triangle tests
 };
 
+template <bool kDeep>
 struct Trav {
     int32_t node;       // node to test next, -1 when the traversal has no node left
     uint32_t mask;      // pending children (visiting order) of `node`; kFresh on a first visit
@@ -189,13 +205,14 @@ struct Trav {
     int32_t steps;
     int32_t leaf_node;  // node whose hit leaf children are pending
     uint32_t leaves;    // pending leaf children of leaf_node (slot order)
-    Trail trail;
+    Trail<kDeep> trail;
 };
 constexpr uint32_t kFresh = 0x1ffu;
 
-__device__ __forceinline__ void trav_init(Trav &s, Hit &h) {
+template <bool kDeep>
+__device__ __forceinline__ void trav_init(Trav<kDeep> &s, Hit &h) {
     s.node = 0; s.mask = kFresh; s.lvl = 0; s.steps = 0; s.leaf_node = 0; s.leaves = 0;
-    s.trail = Trail();
+    s.trail = Trail<kDeep>();
     h.tri = -1; h.prim = INT32_MAX; h.t = FLT_MAX; h.b0 = h.b1 = h.b2 = 0.0f;
 }
 
@@ -277,8 +294,8 @@ __device__ __forceinline__ uint32_t order_mask(uint32_t m, int oct) {
 // Test the children of s.node (all on a first visit, the pending ones on a
 // return); note hit leaves; descend to the first hit inner child in visiting
 // order, or climb to the nearest level with pending children.
-template <bool kCount, bool kSmem>
-__device__ __forceinline__ void node_step(const TraceParams &P, const float4 *smem, const Ray &r, Trav &s, Hit &h,
+template <bool kCount, bool kSmem, bool kDeep>
+__device__ __forceinline__ void node_step(const TraceParams &P, const float4 *smem, const Ray &r, Trav<kDeep> &s, Hit &h,
                                           Work &work) {
     if (kCount) work.nodes += 1;
     if (++s.steps > P.max_steps) {
@@ -298,7 +315,7 @@ __device__ __forceinline__ void node_step(const TraceParams &P, const float4 *sm
         s.trail.set(s.lvl, cand & ~(1u << j));
         s.node = child_word<kSmem>(P, smem, s.node, j ^ r.octant);
         s.mask = kFresh;
-        if (++s.lvl >= kMaxDepth) {
+        if (++s.lvl >= (kDeep ? kMaxDepth : kShallowDepth)) {
             atomicOr(P.err, kErrDepth);
             s.node = -1; s.leaves = 0; h.tri = -1;
         }
@@ -319,8 +336,8 @@ __device__ __forceinline__ void node_step(const TraceParams &P, const float4 *sm
 
 // Test the triangles of one pending leaf child. Ties in t go to the lower
 // uploaded triangle index.
-template <bool kCount, bool kSmem>
-__device__ __forceinline__ void leaf_step(const TraceParams &P, const float4 *smem, const Ray &r, Trav &s, Hit &h,
+template <bool kCount, bool kSmem, bool kDeep>
+__device__ __forceinline__ void leaf_step(const TraceParams &P, const float4 *smem, const Ray &r, Trav<kDeep> &s, Hit &h,
                                           int32_t skip_tile, Work &work) {
     const int k = __ffs(s.leaves) - 1;
     s.leaves &= s.leaves - 1;
@@ -341,13 +358,13 @@ __device__ __forceinline__ void leaf_step(const TraceParams &P, const float4 *sm
 // Closest hit excluding triangles of tile `skip_tile`, one ray at a time
 // (path record); the same steps as the tracing kernels, so the same hits.
 __device__ Hit closest_hit(const TraceParams &P, const float4 *smem, const Ray &r, int32_t skip_tile) {
-    Trav s;
+    Trav<true> s;
     Hit h;
     Work work;
     trav_init(s, h);
     while (true) {
-        if (s.leaves) leaf_step<false, false>(P, smem, r, s, h, skip_tile, work);
-        else if (s.node >= 0) node_step<false, false>(P, smem, r, s, h, work);
+        if (s.leaves) leaf_step<false, false, true>(P, smem, r, s, h, skip_tile, work);
+        else if (s.node >= 0) node_step<false, false, true>(P, smem, r, s, h, work);
         else return h;
     }
 }
@@ -582,6 +599,20 @@ __device__ __forceinline__ void deposit_active(unsigned long long *q, int64_t te
     if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(q + texel, tot);
 }
 
+// Seed and fixed-point scale of this launch: from the step header under
+// graph replay, else from the launch parameters. Read where they are used
+// rather than held across the loop, which keeps three registers free for
+// the traversal state.
+template <bool kAdjoint>
+__device__ __forceinline__ uint64_t launch_seed(const TraceParams &P) {
+    if (!P.hdr) return P.seed;
+    return __ldg(kAdjoint ? &P.hdr->seed_adj : &P.hdr->seed_fwd);
+}
+
+__device__ __forceinline__ float launch_scale(const TraceParams &P) {
+    return P.hdr ? (float)__ldg(&P.hdr->scale) : P.scale;
+}
+
 __device__ __forceinline__ void stage_nodes(const TraceParams &P, float4 *smem) {
     const int n = P.n_staged * kNodeVec;
     const float4 *src = reinterpret_cast<const float4 *>(P.nodes);
@@ -597,7 +628,7 @@ __device__ __forceinline__ void stage_nodes(const TraceParams &P, float4 *smem) 
 // iteration the warp votes and runs the kind of step most of its lanes are
 // waiting for, so lanes never idle until a neighbour's path ends.
 // ---------------------------------------------------------------------------
-template <bool kAdjoint, bool kCount, bool kSmem>
+template <bool kAdjoint, bool kCount, bool kSmem, bool kDeep>
 __global__ void __launch_bounds__(kTraceThreads, kAdjoint ? kAdjointMinBlocks : kTraceMinBlocks)
     trace_kernel(const TraceParams P) {
     extern __shared__ float4 smem[];
@@ -610,15 +641,13 @@ __global__ void __launch_bounds__(kTraceThreads, kAdjoint ? kAdjointMinBlocks : 
     int32_t first_light = 0;
     if (kAdjoint)
         for (int i = 0; i < P.n_slots * 8; ++i) P.slots[tid * (uint64_t)P.n_slots * 8 + i] = 0.0;
-    const uint64_t seed = P.hdr ? (kAdjoint ? P.hdr->seed_adj : P.hdr->seed_fwd) : P.seed;
-    const float scale = P.hdr ? (float)P.hdr->scale : P.scale;
 
     int32_t l = 0, seg = 0, skip = -1;
     float phi = 0.0f, a_emit = 0.0f, g = 0.0f, beta = 1.0f;
     float x1x = 0.0f, x1y = 0.0f, x1z = 0.0f;      // adjoint: first hit point
     int32_t n1code = -1;                          // adjoint: 2 x first-hit triangle + 1 if its normal was flipped
     Ray r;
-    Trav s;
+    Trav<kDeep> s;
     Hit h;
     Work work;
     unsigned long long segs = 0;
@@ -629,7 +658,7 @@ __global__ void __launch_bounds__(kTraceThreads, kAdjoint ? kAdjointMinBlocks : 
         l = light_of(P, photon);
         first_light = l;
         const LightDev &L = P.lights[l];
-        const float4 u = uniforms(seed, photon - L.photon_base, 0u, L.design);
+        const float4 u = uniforms(launch_seed<kAdjoint>(P), photon - L.photon_base, 0u, L.design);
         float wx, wy, wz;
         phi = emit(L, u.x, u.y, wx, wy, wz, a_emit);
         const float3 o = emit_origin(L, u.z, u.w);
@@ -657,9 +686,9 @@ __global__ void __launch_bounds__(kTraceThreads, kAdjoint ? kAdjointMinBlocks : 
         // The step kind with the most waiting lanes runs; it always has at
         // least one lane, so every iteration advances some lane.
         if (nn >= nl && nn >= nf) {
-            if (can_node) node_step<kCount, kSmem>(P, smem, r, s, h, work);
+            if (can_node) node_step<kCount, kSmem, kDeep>(P, smem, r, s, h, work);
         } else if (nl >= nf) {
-            if (can_leaf) leaf_step<kCount, kSmem>(P, smem, r, s, h, skip, work);
+            if (can_leaf) leaf_step<kCount, kSmem, kDeep>(P, smem, r, s, h, skip, work);
         } else if (fin) {
             // Finish the segment (one traced ray, hit or miss), then start the
             // next ray: a bounce from the hit or the next photon's emission.
@@ -672,7 +701,7 @@ __global__ void __launch_bounds__(kTraceThreads, kAdjoint ? kAdjointMinBlocks : 
                 nrm = facing_normal(P, h.tri, r.dx, r.dy, r.dz);
                 const uint64_t tb = P.lights[l].texel_base;
                 if (!kAdjoint) {
-                    deposit_active(P.q + tb, texel, (unsigned long long)__float2ll_rn(phi * scale));   // Eq. 8
+                    deposit_active(P.q + tb, texel, (unsigned long long)__float2ll_rn(phi * launch_scale(P)));   // Eq. 8
                 } else {
                     if (seg == 1) {
                         x1x = x.x; x1y = x.y; x1z = x.z;
@@ -695,7 +724,7 @@ __global__ void __launch_bounds__(kTraceThreads, kAdjoint ? kAdjointMinBlocks : 
                     const LightDev &L = P.lights[l];
                     float2 q = make_float2(0.0f, 0.0f);
                     if (L.type == LT_AREA) {   // the origin's coordinates, from the emission's random numbers
-                        const float4 u0 = uniforms(seed, photon - L.photon_base, 0u, L.design);
+                        const float4 u0 = uniforms(launch_seed<kAdjoint>(P), photon - L.photon_base, 0u, L.design);
                         q = area_coords(L, u0.z, u0.w);
                     }
                     const float *nn = P.hits[n1code >> 1].n;
@@ -715,7 +744,7 @@ __global__ void __launch_bounds__(kTraceThreads, kAdjoint ? kAdjointMinBlocks : 
                 float3 t1, t2, axis, org;
                 if (!bounce) while (photon >= P.lights[l].end) ++l;
                 const LightDev &Ln = P.lights[l];
-                const uint4 rb = counter_block(seed, photon - Ln.photon_base, bounce ? (uint32_t)seg : 0u, Ln.design);
+                const uint4 rb = counter_block(launch_seed<kAdjoint>(P), photon - Ln.photon_base, bounce ? (uint32_t)seg : 0u, Ln.design);
                 const float2 u = make_float2(unit24(rb.x), unit24(rb.y));
                 if (bounce) {
                     bounce_frame(nrm, u.x, c, sn, t1, t2);
@@ -889,25 +918,33 @@ cudaError_t allow_smem(K kernel, size_t smem) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
+using TraceFn = void (*)(TraceParams);
+
 }  // namespace
 
 int trace_kernel_max_threads() { return kTraceThreads; }
 
 // The kernel instantiation for a launch: all nodes in shared memory when the
-// launch stages the whole BVH, otherwise none.
+// launch stages the whole BVH, otherwise none; one word of pending masks
+// when the tree has at most kShallowDepth levels, otherwise two.
+template <bool kAdjoint, bool kCount>
+TraceFn trace_fn(bool staged, bool deep) {
+    if (deep) return staged ? trace_kernel<kAdjoint, kCount, true, true> : trace_kernel<kAdjoint, kCount, false, true>;
+    return staged ? trace_kernel<kAdjoint, kCount, true, false> : trace_kernel<kAdjoint, kCount, false, false>;
+}
+
 template <bool kAdjoint, bool kCount>
 cudaError_t launch_trace(const TraceParams &p, int grid, int block, size_t smem, cudaStream_t s) {
-    const bool staged = p.n_staged > 0;
-    auto fn = staged ? trace_kernel<kAdjoint, kCount, true> : trace_kernel<kAdjoint, kCount, false>;
+    const TraceFn fn = trace_fn<kAdjoint, kCount>(p.n_staged > 0, p.depth > kShallowDepth);
     cudaError_t e = allow_smem(fn, smem);
     if (e != cudaSuccess) return e;
     fn<<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
 }
 
-cudaError_t trace_occupancy(bool adjoint, bool staged, int block, size_t smem, int *blocks_per_sm) {
-    auto fn = adjoint ? (staged ? trace_kernel<true, false, true> : trace_kernel<true, false, false>)
-                      : (staged ? trace_kernel<false, false, true> : trace_kernel<false, false, false>);
+cudaError_t trace_occupancy(bool adjoint, bool staged, int depth, int block, size_t smem, int *blocks_per_sm) {
+    const bool deep = depth > kShallowDepth;
+    const TraceFn fn = adjoint ? trace_fn<true, false>(staged, deep) : trace_fn<false, false>(staged, deep);
     cudaError_t e = allow_smem(fn, smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem);
