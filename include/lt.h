@@ -291,11 +291,14 @@ LT_API int lt_loss_static(int device, void *cuda_stream, const int64_t *q, doubl
                           float *E_out, double *loss_out);
 
 /* Launch shape of the tracing kernels. threads_per_block: a multiple of 32
- * within the kernel's bound, 0 = the default 256. blocks_per_sm: resident
- * blocks per SM, 0 = as many as fit. smem_node_bytes: shared-memory budget
- * for staged BVH nodes in [0, 200 KiB] (the whole BVH is staged when it fits,
- * else none), 0 = stage nothing. A negative argument keeps the current
- * value. The defaults are 256 threads, as many blocks as fit, 72 KiB. */
+ * up to 1024, 0 = the bound of the kernel the BVH selects (1024 when the
+ * whole BVH is staged in shared memory, 768 when nodes are read through L1);
+ * a trace whose BVH selects a kernel with a smaller bound than the request
+ * fails with LT_ERR_ARG. blocks_per_sm: resident blocks per SM, 0 = as many
+ * as fit. smem_node_bytes: shared-memory budget for staged BVH nodes in
+ * [0, 200 KiB] (the whole BVH is staged when it fits, else none), 0 = stage
+ * nothing. A negative argument keeps the current value. The defaults are the
+ * kernel's bound, as many blocks as fit, 72 KiB. */
 LT_API int lt_set_launch(void *ctx, int32_t threads_per_block, int32_t blocks_per_sm, int32_t smem_node_bytes);
 
 #ifdef __cplusplus

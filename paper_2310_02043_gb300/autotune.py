@@ -12,13 +12,15 @@ import json
 import os
 import statistics
 
-# (threads per block, blocks per SM (0: as many as fit), shared-memory node
-# budget in bytes (0: nodes through L1)); every field is set explicitly.
+# (threads per block (0: the bound of the kernel the BVH selects, 1024 when it
+# is staged, 768 when nodes come through L1), blocks per SM (0: as many as
+# fit), shared-memory node budget in bytes (0: nodes through L1)); every field
+# is set explicitly.
 CANDIDATES = (
+    (0, 0, 200 * 1024), (0, 0, 0),
+    (512, 0, 200 * 1024), (512, 0, 0),
+    (384, 0, 200 * 1024), (384, 0, 0),
     (256, 0, 200 * 1024), (256, 0, 0),
-    (128, 0, 200 * 1024), (128, 0, 0),
-    (192, 0, 200 * 1024), (192, 0, 0),
-    (256, 2, 200 * 1024), (256, 2, 0),
 )
 
 

@@ -55,7 +55,7 @@ struct Ctx {
     int32_t *d_err = nullptr;
     double *h_pinned = nullptr;            // small pinned staging area
     // launch
-    int threads = 256, blocks_per_sm = 0, smem_node_bytes = 72 * 1024;
+    int threads = 0, blocks_per_sm = 0, smem_node_bytes = 72 * 1024;   // threads 0: the kernel's bound
     lt_stats stats{};
     // host copy of the uploaded charts (texel centres)
     std::vector<float> h_xyz, h_uv;
@@ -224,13 +224,19 @@ int upload_lights(Ctx *c, uint64_t n_photons) {
 
 // Launch shape of a tracing kernel. The whole BVH is staged in shared memory
 // when it fits the budget, otherwise no node is (nodes then come through L1).
-int launch_shape(Ctx *c, bool adjoint, int *grid, size_t *smem, int32_t *n_staged) {
+// The block is the requested size, else the bound of the kernel chosen.
+int launch_shape(Ctx *c, bool adjoint, int *grid, int *threads, size_t *smem, int32_t *n_staged) {
     const bool staged = (int64_t)c->n_nodes * (int64_t)sizeof(Node) <= (int64_t)c->smem_node_bytes;
     *n_staged = staged ? c->n_nodes : 0;
     *smem = (size_t)(*n_staged) * sizeof(Node);
+    const int bound = trace_kernel_max_threads(staged);
+    *threads = c->threads > 0 ? c->threads : bound;
+    if (*threads > bound)
+        return fail(c, LT_ERR_ARG, "threads_per_block " + std::to_string(*threads) + " exceeds the bound " +
+                                       std::to_string(bound) + " of the kernel for this BVH");
     int bps = c->blocks_per_sm;
     if (bps <= 0) {
-        cudaError_t e = trace_occupancy(adjoint, staged, c->depth, c->threads, *smem, &bps);
+        cudaError_t e = trace_occupancy(adjoint, staged, c->depth, *threads, *smem, &bps);
         if (e != cudaSuccess) return cuda_fail(c, e, "occupancy query");
         if (bps < 1) return fail(c, LT_ERR_ARG, "launch shape does not fit on an SM");
     }
@@ -309,7 +315,7 @@ void batch_free(Ctx *c) {
 struct BatchLaunch {
     TraceParams fwd, adj;
     LossParams loss;
-    int grid_f, grid_a;
+    int grid_f, grid_a, threads_f, threads_a;
     size_t smem_f, smem_a;
 };
 
@@ -327,22 +333,22 @@ int batch_prepare(Ctx *c, BatchLaunch *bl) {
     bl->fwd.hdr = hdr;
     bl->fwd.q = b.d_q;
     bl->fwd.segments = reinterpret_cast<unsigned long long *>(b.d_grad + (size_t)b.n_lights * 8);
-    if ((rc = launch_shape(c, false, &bl->grid_f, &bl->smem_f, &bl->fwd.n_staged))) return rc;
-    bl->fwd.chunk = photon_chunk(n_total, bl->grid_f, c->threads);
+    if ((rc = launch_shape(c, false, &bl->grid_f, &bl->threads_f, &bl->smem_f, &bl->fwd.n_staged))) return rc;
+    bl->fwd.chunk = photon_chunk(n_total, bl->grid_f, bl->threads_f);
     bl->fwd.max_iters = step_limit(bl->fwd);
     bl->adj = bl->fwd;
     bl->adj.q = nullptr;
     bl->adj.w = b.d_w;
     bl->adj.segments = bl->fwd.segments + 1;
-    if ((rc = launch_shape(c, true, &bl->grid_a, &bl->smem_a, &bl->adj.n_staged))) return rc;
-    bl->adj.chunk = photon_chunk(n_total, bl->grid_a, c->threads);
+    if ((rc = launch_shape(c, true, &bl->grid_a, &bl->threads_a, &bl->smem_a, &bl->adj.n_staged))) return rc;
+    bl->adj.chunk = photon_chunk(n_total, bl->grid_a, bl->threads_a);
     bl->adj.max_iters = step_limit(bl->adj);
     int32_t max_count = 1;
     for (int32_t n : b.counts) max_count = std::max(max_count, n);
     const uint64_t min_nl = b.photons / (uint64_t)max_count;
     bl->adj.n_slots = min_nl == 0 ? b.n_lights
                                   : (int32_t)std::min<uint64_t>((uint64_t)b.n_lights, bl->adj.chunk / min_nl + 2);
-    const size_t need = (size_t)bl->grid_a * (size_t)c->threads * (size_t)bl->adj.n_slots * 8 * sizeof(double);
+    const size_t need = (size_t)bl->grid_a * (size_t)bl->threads_a * (size_t)bl->adj.n_slots * 8 * sizeof(double);
     if (need > b.slots_bytes) {
         LT_CUDA(c, cudaStreamSynchronize(b.stream));
         dfree(b.d_slots);
@@ -376,9 +382,9 @@ int batch_issue(Ctx *c, const BatchLaunch &bl) {
     LT_CUDA(c, cudaMemcpyAsync(b.d_in, b.h_in, b.in_bytes, cudaMemcpyHostToDevice, s));
     LT_CUDA(c, cudaMemsetAsync(b.d_q, 0, D * T * sizeof(unsigned long long), s));
     LT_CUDA(c, cudaMemsetAsync(bl.fwd.segments, 0, 2 * sizeof(unsigned long long), s));
-    LT_CUDA(c, launch_forward(bl.fwd, bl.grid_f, c->threads, bl.smem_f, s));
+    LT_CUDA(c, launch_forward(bl.fwd, bl.grid_f, bl.threads_f, bl.smem_f, s));
     LT_CUDA(c, launch_loss(bl.loss, s));
-    LT_CUDA(c, launch_adjoint(bl.adj, bl.grid_a, c->threads, bl.smem_a, s));
+    LT_CUDA(c, launch_adjoint(bl.adj, bl.grid_a, bl.threads_a, bl.smem_a, s));
     LT_CUDA(c, launch_grad_finalize(bl.adj, b.d_grad, s));
     LT_CUDA(c, cudaMemcpyAsync(b.h_out, b.d_loss, D * sizeof(double), cudaMemcpyDeviceToHost, s));
     LT_CUDA(c, cudaMemcpyAsync(b.h_out + D, b.d_grad, (L * 8 + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -633,18 +639,18 @@ static int forward_pass(Ctx *c, uint64_t seed, uint64_t n_photons, int32_t max_h
     p.q = c->d_q;
     p.scale = (float)S;
     p.segments = c->d_seg;
-    int grid;
+    int grid, threads;
     size_t smem;
-    if ((rc = launch_shape(c, false, &grid, &smem, &p.n_staged))) return rc;
-    p.chunk = photon_chunk(photon_end - photon_begin, grid, c->threads);
+    if ((rc = launch_shape(c, false, &grid, &threads, &smem, &p.n_staged))) return rc;
+    p.chunk = photon_chunk(photon_end - photon_begin, grid, threads);
     p.max_iters = step_limit(p);
     LT_CUDA(c, cudaMemsetAsync(c->d_q, 0, (size_t)c->n_texels * sizeof(unsigned long long), c->stream));
     LT_CUDA(c, cudaMemsetAsync(c->d_seg, 0, sizeof(unsigned long long), c->stream));
     if (d_work) {
         p.work = d_work;
-        LT_CUDA(c, launch_forward_counted(p, grid, c->threads, smem, c->stream));
+        LT_CUDA(c, launch_forward_counted(p, grid, threads, smem, c->stream));
     } else {
-        LT_CUDA(c, launch_forward(p, grid, c->threads, smem, c->stream));
+        LT_CUDA(c, launch_forward(p, grid, threads, smem, c->stream));
     }
     c->fwd_done = true;
     c->has_w = false;
@@ -653,7 +659,7 @@ static int forward_pass(Ctx *c, uint64_t seed, uint64_t n_photons, int32_t max_h
     c->stats.staged_nodes = p.n_staged;
     c->stats.fixed_point_scale = S;
     c->stats.grid_blocks = grid;
-    c->stats.block_threads = c->threads;
+    c->stats.block_threads = threads;
     return LT_OK;
 }
 
@@ -781,16 +787,16 @@ int lt_trace_adjoint(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_h
     TraceParams p = base_params(c, seed, max_hits, photon_begin, photon_end);
     p.w = c->d_w;
     p.segments = c->d_seg + 1;
-    int grid;
+    int grid, threads;
     size_t smem;
-    if ((rc = launch_shape(c, true, &grid, &smem, &p.n_staged))) return rc;
+    if ((rc = launch_shape(c, true, &grid, &threads, &smem, &p.n_staged))) return rc;
     // Per-thread gradient slots: a thread's contiguous photon chunk touches at
     // most chunk / (fewest photons of a light) + 2 lights.
-    p.chunk = photon_chunk(photon_end - photon_begin, grid, c->threads);
+    p.chunk = photon_chunk(photon_end - photon_begin, grid, threads);
     p.max_iters = step_limit(p);
     const uint64_t min_nl = n_photons / (uint64_t)L;
     p.n_slots = min_nl == 0 ? L : (int32_t)std::min<uint64_t>((uint64_t)L, p.chunk / min_nl + 2);
-    const size_t need = (size_t)grid * (size_t)c->threads * (size_t)p.n_slots * 8 * sizeof(double);
+    const size_t need = (size_t)grid * (size_t)threads * (size_t)p.n_slots * 8 * sizeof(double);
     if (need > c->slots_bytes) {
         LT_CUDA(c, cudaStreamSynchronize(c->stream));
         dfree(c->d_slots);
@@ -799,7 +805,7 @@ int lt_trace_adjoint(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_h
     }
     p.slots = c->d_slots;
     LT_CUDA(c, cudaMemsetAsync(c->d_seg + 1, 0, sizeof(unsigned long long), c->stream));
-    LT_CUDA(c, launch_adjoint(p, grid, c->threads, smem, c->stream));
+    LT_CUDA(c, launch_adjoint(p, grid, threads, smem, c->stream));
     LT_CUDA(c, launch_grad_finalize(p, c->d_grad, c->stream));
     c->stats.photons_adjoint = photon_end - photon_begin;
     c->seg_single = true;
@@ -987,7 +993,7 @@ int lt_batch_step(void *ctx, uint64_t seed_fwd, uint64_t seed_adj, double *loss_
     c->stats.segments_adjoint = seg[1];
     c->stats.photons_forward = c->stats.photons_adjoint = b.photons * D;
     c->stats.grid_blocks = bl.grid_f;
-    c->stats.block_threads = c->threads;
+    c->stats.block_threads = bl.threads_f;
     c->stats.staged_nodes = bl.fwd.n_staged;
     c->seg_single = false;
     return LT_OK;
@@ -1084,10 +1090,11 @@ int lt_set_launch(void *ctx, int32_t threads_per_block, int32_t blocks_per_sm, i
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return LT_ERR_ARG;
     if (threads_per_block > 0 &&
-        (threads_per_block % 32 || threads_per_block > trace_kernel_max_threads()))
-        return fail(c, LT_ERR_ARG, "threads_per_block must be a multiple of 32 within the kernel's bound");
+        (threads_per_block % 32 || threads_per_block > std::max(trace_kernel_max_threads(true),
+                                                                 trace_kernel_max_threads(false))))
+        return fail(c, LT_ERR_ARG, "threads_per_block must be a multiple of 32 within the kernels' bounds");
     if (smem_node_bytes > 200 * 1024) return fail(c, LT_ERR_ARG, "smem_node_bytes must be in [0, 200 KiB]");
-    if (threads_per_block >= 0) c->threads = threads_per_block ? threads_per_block : 256;
+    if (threads_per_block >= 0) c->threads = threads_per_block;
     if (blocks_per_sm >= 0) c->blocks_per_sm = blocks_per_sm;
     if (smem_node_bytes >= 0) c->smem_node_bytes = smem_node_bytes;
     batch_drop_graph(c);     // a captured batch step holds the old launch shape

@@ -159,7 +159,7 @@ cudaError_t launch_loss(const LossParams &p, cudaStream_t s);
 cudaError_t launch_resolve(const unsigned long long *q, const float *area, double inv_scale, int64_t n,
                            float *E_out, cudaStream_t s);
 cudaError_t launch_grad_finalize(const TraceParams &p, double *out, cudaStream_t s);
-int trace_kernel_max_threads();
+int trace_kernel_max_threads(bool staged);   // block bound of the staged / L1-node kernels
 cudaError_t trace_occupancy(bool adjoint, bool staged, int depth, int block, size_t smem, int *blocks_per_sm);
 
 // Wide-BVH builder (lt_bvh.cpp).

@@ -17,15 +17,23 @@ namespace lt {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kTraceThreads = 256;
+// Block shapes of the tracing kernels. With the whole BVH staged in shared
+// memory, one block per SM holds it once and leaves the rest of the SM's
+// shared storage to L1; 32 warps at 64 registers then beat 24 at 80.
+// Kernels that read nodes through L1 (BVHs too large to stage) run 24 warps
+// at 80 registers. Both were chosen by measuring block shapes on GB300.
+#ifndef LT_THREADS_STAGED
+#define LT_THREADS_STAGED 1024
+#endif
+#ifndef LT_THREADS_L1
+#define LT_THREADS_L1 768
+#endif
 #ifndef LT_MIN_BLOCKS
-#define LT_MIN_BLOCKS 3
+#define LT_MIN_BLOCKS 1
 #endif
+constexpr int kThreadsStaged = LT_THREADS_STAGED;
+constexpr int kThreadsL1 = LT_THREADS_L1;
 constexpr int kTraceMinBlocks = LT_MIN_BLOCKS;   // resident blocks per SM the register budget targets
-#ifndef LT_MIN_BLOCKS_ADJ
-#define LT_MIN_BLOCKS_ADJ LT_MIN_BLOCKS
-#endif
-constexpr int kAdjointMinBlocks = LT_MIN_BLOCKS_ADJ;   // the same for the adjoint, which carries more state
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC 2011).
@@ -629,7 +637,7 @@ __device__ __forceinline__ void stage_nodes(const TraceParams &P, float4 *smem) 
 // waiting for, so lanes never idle until a neighbour's path ends.
 // ---------------------------------------------------------------------------
 template <bool kAdjoint, bool kCount, bool kSmem, bool kDeep>
-__global__ void __launch_bounds__(kTraceThreads, kAdjoint ? kAdjointMinBlocks : kTraceMinBlocks)
+__global__ void __launch_bounds__(kSmem ? kThreadsStaged : kThreadsL1, kTraceMinBlocks)
     trace_kernel(const TraceParams P) {
     extern __shared__ float4 smem[];
     if (kSmem) stage_nodes(P, smem);
@@ -922,7 +930,7 @@ using TraceFn = void (*)(TraceParams);
 
 }  // namespace
 
-int trace_kernel_max_threads() { return kTraceThreads; }
+int trace_kernel_max_threads(bool staged) { return staged ? kThreadsStaged : kThreadsL1; }
 
 // The kernel instantiation for a launch: all nodes in shared memory when the
 // launch stages the whole BVH, otherwise none; one word of pending masks

@@ -177,8 +177,9 @@ def test_fixed_point_sums_identical_across_launch_shapes(tr):
 
 
 def test_launch_shape_arguments(tr):
-    # 0 selects the default (256 threads / as many blocks as fit / no staged
-    # nodes), a negative argument keeps the current value
+    # 0 selects the default (the bound of the kernel the BVH selects: 1024
+    # threads when the BVH is staged, 768 through L1 / as many blocks as fit /
+    # no staged nodes), a negative argument keeps the current value
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     sc, L = scenes.office(seed=0, pitch=0.1), scenes.office_lights(0)
@@ -196,9 +197,17 @@ def test_launch_shape_arguments(tr):
     assert shape() == (2 * sms, 128, tr.stats()["n_nodes"])
     tr.set_launch(0, 0, -1)
     g, t, staged = shape()
-    assert t == 256 and g % sms == 0 and staged > 0
+    assert t == 1024 and g % sms == 0 and staged > 0
     tr.set_launch(0, 0, 0)
-    assert shape()[2] == 0
+    g, t, staged = shape()
+    assert t == 768 and g % sms == 0 and staged == 0
+    # a block above the bound of the kernel the BVH selects is refused on the
+    # host, before any launch
+    tr.set_launch(1024, 0, 0)
+    with pytest.raises(RuntimeError, match="exceeds the bound"):
+        tr.trace_forward(5, 1 << 14, 5)
+    tr.set_launch(1024, 0, 200 * 1024)
+    assert shape() == (sms, 1024, tr.stats()["n_nodes"])
     tr.set_launch(256, 0, 48 * 1024)
 
 
