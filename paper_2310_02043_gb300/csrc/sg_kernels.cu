@@ -846,28 +846,43 @@ __global__ void design_final_kernel(const float *__restrict__ gpart, const Light
 // ---------------------------------------------------------------------------
 // The design forward on the 5th-generation tensor cores (tcgen05)
 //
-// A CTA of 128 threads takes 128 rows at a time, one row per thread. The
-// thread writes its input row into shared memory in the canonical
+// A warpgroup of 128 threads takes 128 rows at a time, one row per thread.
+// The thread writes its input row into shared memory in the canonical
 // no-swizzle K-major layout (8 x 8 bf16 "core matrices" of 128 bytes; core
 // (r / 8, k / 8) at ((r / 8) * 8 + k / 8) * 128 bytes), one elected thread
 // issues the four K = 16 steps of each layer as tcgen05.mma (M = 128,
 // N = 64 or 16, bf16 x bf16 -> fp32 in tensor memory) and commits them to an
 // mbarrier; every thread then reads its accumulator row back with
 // tcgen05.ld, applies ReLU, rounds to bf16 and writes the next layer's
-// operand. The weights sit in the same layout, loaded once per CTA.
+// operand. A CTA holds kTcTiles such warpgroups, each with its own operand
+// tile, 64 TMEM columns, mbarrier and named barrier, so their tiles proceed
+// independently (one's MMA overlaps another's epilogue) while they share one
+// copy of the weights, stored in the same layout and loaded once per CTA.
 // ---------------------------------------------------------------------------
 constexpr int kTcRows = 128;
-constexpr uint32_t kTcCols = 64;                 // TMEM columns of the 128 x 64 fp32 accumulator
+constexpr int kTcTiles = 4;                      // warpgroups (128-row tiles) per CTA
+constexpr int kTcThreads = kTcRows * kTcTiles;
+constexpr uint32_t kTcCols = 64;                 // TMEM columns of one 128 x 64 fp32 accumulator
 constexpr uint32_t kTcSpin = 1u << 20;           // mbarrier polls before giving up
 constexpr int kErrTc = 1;
 
 struct alignas(1024) TcSmem {
-    uint16_t a[kTcRows * 64];                    // A operand, 16 KB
+    uint16_t a[kTcTiles][kTcRows * 64];          // A operand of each warpgroup, 16 KB each
     uint16_t w[3 * 64 * 64 + 16 * 64];           // B operands, layer after layer
-    unsigned long long mbar;
+    unsigned long long mbar[kTcTiles];
     uint32_t tmem;
-    int32_t abort;
+    int32_t abort[kTcTiles];                     // set and read by one warpgroup only
 };
+
+// Two CTAs fit an SM's 228 KB of shared memory and a third does not, so the
+// 2 x kTcTiles x 64 TMEM columns of the resident CTAs never exceed 512.
+static_assert(2 * (sizeof(TcSmem) + 2048) <= 228 * 1024 && 3 * (sizeof(TcSmem) + 1024) > 228 * 1024,
+              "design forward: exactly two CTAs per SM");
+static_assert(2 * kTcCols * kTcTiles <= 512, "TMEM columns of two CTAs");
+
+// Barrier of the 128 threads of warpgroup g (named barrier 1 + g; barrier 0
+// is __syncthreads).
+__device__ __forceinline__ void wg_sync(int g) { asm volatile("bar.sync %0, 128;\n" ::"r"(1 + g) : "memory"); }
 
 __device__ __forceinline__ uint32_t core_offset(int r, int k) {      // bytes, 64-wide rows
     return (uint32_t)((((r >> 3) << 3) + (k >> 3)) << 7) + (uint32_t)((r & 7) << 4) + (uint32_t)((k & 7) << 1);
@@ -931,41 +946,44 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__global__ void __launch_bounds__(kTcRows, 1) design_forward_tc_kernel(const DesignArgs A, int32_t *err) {
+__global__ void __launch_bounds__(kTcThreads, 2) design_forward_tc_kernel(const DesignArgs A, int32_t *err) {
     extern __shared__ __align__(1024) unsigned char tc_raw[];
     TcSmem &S = *reinterpret_cast<TcSmem *>(tc_raw);
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, g = tid / kTcRows, r = tid % kTcRows;
     // weights into the canonical layout
-    for (int i = tid; i < kWeights; i += kTcRows) {
-        const int layer = i < kOffW3 ? i >> 12 : 3, r = i < kOffW3 ? i & 4095 : i - kOffW3;
-        const int n = r >> 6, k = r & 63;
+    for (int i = tid; i < kWeights; i += kTcThreads) {
+        const int layer = i < kOffW3 ? i >> 12 : 3, q = i < kOffW3 ? i & 4095 : i - kOffW3;
+        const int n = q >> 6, k = q & 63;
         *reinterpret_cast<uint16_t *>(reinterpret_cast<unsigned char *>(S.w) + layer * 8192 + core_offset(n, k)) =
             A.Wb[i];
     }
-    const uint32_t mbar = smem_u32(&S.mbar);
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar) : "memory");
+        for (int k = 0; k < kTcTiles; ++k) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&S.mbar[k])) : "memory");
+            S.abort[k] = 0;
+        }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        S.abort = 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&S.tmem)),
-                     "r"(kTcCols)
+                     "r"(kTcCols * kTcTiles)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = S.tmem;
-    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-    const uint32_t a_base = smem_u32(S.a), w_base = smem_u32(S.w);
+    // this warpgroup's accumulator columns; a warp reads TMEM lanes 32 (warp % 4) ..
+    const uint32_t tmem = S.tmem + (uint32_t)g * kTcCols;
+    const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    const uint32_t mbar = smem_u32(&S.mbar[g]);
+    const uint32_t a_base = smem_u32(S.a[g]), w_base = smem_u32(S.w);
     const int64_t rows = A.tex.n_pad * (int64_t)A.n_lights;
     const int64_t tiles = (rows + kTcRows - 1) / kTcRows;
     uint32_t phase = 0;
-    unsigned char *arow = reinterpret_cast<unsigned char *>(S.a);
-    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const int64_t row = tile * kTcRows + tid;
+    unsigned char *arow = reinterpret_cast<unsigned char *>(S.a[g]);
+    for (int64_t tile = (int64_t)blockIdx.x * kTcTiles + g; tile < tiles; tile += (int64_t)gridDim.x * kTcTiles) {
+        const int64_t row = tile * kTcRows + r;
         const bool valid = row < rows;
         const int l = valid ? (int)(row / A.tex.n_pad) : 0;
         const int64_t t = valid ? row % A.tex.n_pad : 0;
@@ -975,7 +993,7 @@ __global__ void __launch_bounds__(kTcRows, 1) design_forward_tc_kernel(const Des
         const uint4 *enc = reinterpret_cast<const uint4 *>(A.enc + t * 32);
 #pragma unroll
         for (int g8 = 0; g8 < 4; ++g8)
-            *reinterpret_cast<uint4 *>(arow + core_offset(tid, 8 * g8)) = valid ? enc[g8] : make_uint4(0, 0, 0, 0);
+            *reinterpret_cast<uint4 *>(arow + core_offset(r, 8 * g8)) = valid ? enc[g8] : make_uint4(0, 0, 0, 0);
 #pragma unroll
         for (int g8 = 4; g8 < 8; ++g8) {
             uint4 v;
@@ -983,14 +1001,14 @@ __global__ void __launch_bounds__(kTcRows, 1) design_forward_tc_kernel(const Des
             v.y = valid ? (uint32_t)x[8 * g8 + 2] | ((uint32_t)x[8 * g8 + 3] << 16) : 0u;
             v.z = valid ? (uint32_t)x[8 * g8 + 4] | ((uint32_t)x[8 * g8 + 5] << 16) : 0u;
             v.w = valid ? (uint32_t)x[8 * g8 + 6] | ((uint32_t)x[8 * g8 + 7] << 16) : 0u;
-            *reinterpret_cast<uint4 *>(arow + core_offset(tid, 8 * g8)) = v;
+            *reinterpret_cast<uint4 *>(arow + core_offset(r, 8 * g8)) = v;
         }
         proxy_fence();
-        __syncthreads();
+        wg_sync(g);
         float o0 = 0.0f, o1 = 0.0f;
         for (int layer = 0; layer < 4; ++layer) {
             const int N = layer < 3 ? 64 : 16;
-            if (tid == 0) {
+            if (r == 0) {
                 tc_fence_after();
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk)
@@ -1001,9 +1019,9 @@ __global__ void __launch_bounds__(kTcRows, 1) design_forward_tc_kernel(const Des
             const bool ok = mbar_wait(mbar, phase);
             phase ^= 1u;
             tc_fence_after();
-            if (!ok) atomicOr(&S.abort, 1);
-            __syncthreads();
-            if (S.abort) break;
+            if (!ok) S.abort[g] = 1;
+            wg_sync(g);
+            if (S.abort[g]) break;
             if (layer < 3) {
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
@@ -1016,12 +1034,12 @@ __global__ void __launch_bounds__(kTcRows, 1) design_forward_tc_kernel(const Des
                         q.y = pack2(fmaxf(v[8 * h + 2], 0.0f), fmaxf(v[8 * h + 3], 0.0f));
                         q.z = pack2(fmaxf(v[8 * h + 4], 0.0f), fmaxf(v[8 * h + 5], 0.0f));
                         q.w = pack2(fmaxf(v[8 * h + 6], 0.0f), fmaxf(v[8 * h + 7], 0.0f));
-                        *reinterpret_cast<uint4 *>(arow + core_offset(tid, 16 * c + 8 * h)) = q;
+                        *reinterpret_cast<uint4 *>(arow + core_offset(r, 16 * c + 8 * h)) = q;
                     }
                 }
                 tc_fence_before();
                 proxy_fence();
-                __syncthreads();
+                wg_sync(g);
             } else {
                 float v[16];
                 tc_ld16(lane_addr, v);
@@ -1030,15 +1048,20 @@ __global__ void __launch_bounds__(kTcRows, 1) design_forward_tc_kernel(const Des
                 tc_fence_before();
             }
         }
-        if (S.abort) break;
+        if (S.abort[g]) break;
         if (valid) A.K[row] = sigmoidf_(o0) * D + kRScale * softplusf_(o1);
-        __syncthreads();
+        wg_sync(g);
     }
-    if (S.abort && tid == 0) atomicOr(err, kErrTc);
     tc_fence_before();
     __syncthreads();
+    if (tid == 0) {
+        int32_t any = 0;
+        for (int k = 0; k < kTcTiles; ++k) any |= S.abort[k];
+        if (any) atomicOr(err, kErrTc);
+    }
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTcCols) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(S.tmem), "r"(kTcCols * kTcTiles)
+                     : "memory");
 }
 
 // The design backward on tcgen05: per 128-row tile the forward again (ReLU
@@ -1046,23 +1069,28 @@ __global__ void __launch_bounds__(kTcRows, 1) design_forward_tc_kernel(const Des
 // W1^T, W0^T as tcgen05.mma on transposed weights (the output layer's step
 // has K = 16), and each thread's row through the feature Jacobian.
 struct alignas(1024) TcBwdSmem {
-    uint16_t a[kTcRows * 64];                    // activations, then gradients (64 wide)
-    uint16_t d4[kTcRows * 16];                   // gradient at the outputs (16 wide)
+    uint16_t a[kTcTiles][kTcRows * 64];          // per warpgroup: activations, then gradients (64 wide)
+    uint16_t d4[kTcTiles][kTcRows * 16];         // per warpgroup: gradient at the outputs (16 wide)
     uint16_t w[3 * 64 * 64 + 16 * 64];           // W0, W1, W2 [64][64], W3 [16][64]
     uint16_t wt[3 * 64 * 64 + 64 * 16];          // W0^T, W1^T, W2^T [64][64], W3^T [64][16]
-    unsigned long long mbar;
+    unsigned long long mbar[kTcTiles];
     uint32_t tmem;
-    int32_t abort;
+    int32_t abort[kTcTiles];                     // set and read by one warpgroup only
 };
+
+// One CTA per SM (shared memory admits no second): kTcTiles x 64 TMEM columns.
+static_assert(sizeof(TcBwdSmem) + 1024 <= 227 * 1024 && 2 * (sizeof(TcBwdSmem) + 1024) > 228 * 1024,
+              "design backward: exactly one CTA per SM");
 
 __device__ __forceinline__ uint32_t core_offset16(int r, int k) {    // bytes, 16-wide rows
     return (uint32_t)((((r >> 3) << 1) + (k >> 3)) << 7) + (uint32_t)((r & 7) << 4) + (uint32_t)((k & 7) << 1);
 }
 
-// Issues one layer (K / 16 steps) and waits for it; false if the wait gave up.
+// Issues one layer (K / 16 steps) from thread r == 0 of the warpgroup and
+// waits for it; false if the wait gave up.
 __device__ __forceinline__ bool tc_layer(uint32_t tmem, uint32_t a, uint32_t a_sbo, uint32_t b, uint32_t b_sbo, int N,
-                                         int ksteps, uint32_t mbar, uint32_t &phase, int tid) {
-    if (tid == 0) {
+                                         int ksteps, uint32_t mbar, uint32_t &phase, int r) {
+    if (r == 0) {
         tc_fence_after();
         for (int kk = 0; kk < ksteps; ++kk)
             tc_mma(tmem, smem_desc(a + 256 * kk, 128, a_sbo), smem_desc(b + 256 * kk, 128, b_sbo), mma_idesc(128, N),
@@ -1075,12 +1103,12 @@ __device__ __forceinline__ bool tc_layer(uint32_t tmem, uint32_t a, uint32_t a_s
     return ok;
 }
 
-__global__ void __launch_bounds__(kTcRows, 1) design_backward_tc_kernel(const DesignArgs A, int32_t *err) {
+__global__ void __launch_bounds__(kTcThreads, 1) design_backward_tc_kernel(const DesignArgs A, int32_t *err) {
     extern __shared__ __align__(1024) unsigned char tcb_raw[];
     TcBwdSmem &S = *reinterpret_cast<TcBwdSmem *>(tcb_raw);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = tid / kTcRows, r = tid % kTcRows;
     unsigned char *wb = reinterpret_cast<unsigned char *>(S.w), *wtb = reinterpret_cast<unsigned char *>(S.wt);
-    for (int i = tid; i < kWeights; i += kTcRows) {
+    for (int i = tid; i < kWeights; i += kTcThreads) {
         const uint16_t v = A.Wb[i];
         if (i < kOffW3) {
             const int layer = i >> 12, r = i & 4095, n = r >> 6, k = r & 63;
@@ -1092,30 +1120,33 @@ __global__ void __launch_bounds__(kTcRows, 1) design_backward_tc_kernel(const De
             *reinterpret_cast<uint16_t *>(wtb + 3 * 8192 + core_offset16(k, n)) = v;
         }
     }
-    const uint32_t mbar = smem_u32(&S.mbar);
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar) : "memory");
+        for (int k = 0; k < kTcTiles; ++k) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&S.mbar[k])) : "memory");
+            S.abort[k] = 0;
+        }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        S.abort = 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&S.tmem)),
-                     "r"(kTcCols)
+                     "r"(kTcCols * kTcTiles)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = S.tmem;
-    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-    const uint32_t a_addr = smem_u32(S.a), d4_addr = smem_u32(S.d4), w_addr = smem_u32(S.w), wt_addr = smem_u32(S.wt);
+    const uint32_t tmem = S.tmem + (uint32_t)g * kTcCols;
+    const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    const uint32_t mbar = smem_u32(&S.mbar[g]);
+    const uint32_t a_addr = smem_u32(S.a[g]), d4_addr = smem_u32(S.d4[g]), w_addr = smem_u32(S.w),
+                   wt_addr = smem_u32(S.wt);
     const int64_t rows = A.tex.n_pad * (int64_t)A.n_lights;
     const int64_t tiles = (rows + kTcRows - 1) / kTcRows;
     uint32_t phase = 0;
-    unsigned char *arow = reinterpret_cast<unsigned char *>(S.a), *drow = reinterpret_cast<unsigned char *>(S.d4);
-    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const int64_t row = tile * kTcRows + tid;
+    unsigned char *arow = reinterpret_cast<unsigned char *>(S.a[g]), *drow = reinterpret_cast<unsigned char *>(S.d4[g]);
+    for (int64_t tile = (int64_t)blockIdx.x * kTcTiles + g; tile < tiles; tile += (int64_t)gridDim.x * kTcTiles) {
+        const int64_t row = tile * kTcRows + r;
         const bool valid = row < rows;
         const int l = valid ? (int)(row / A.tex.n_pad) : 0;
         const int64_t t = valid ? row % A.tex.n_pad : 0;
@@ -1126,7 +1157,7 @@ __global__ void __launch_bounds__(kTcRows, 1) design_backward_tc_kernel(const De
         const uint4 *enc = reinterpret_cast<const uint4 *>(A.enc + t * 32);
 #pragma unroll
         for (int g8 = 0; g8 < 4; ++g8)
-            *reinterpret_cast<uint4 *>(arow + core_offset(tid, 8 * g8)) = valid ? enc[g8] : make_uint4(0, 0, 0, 0);
+            *reinterpret_cast<uint4 *>(arow + core_offset(r, 8 * g8)) = valid ? enc[g8] : make_uint4(0, 0, 0, 0);
 #pragma unroll
         for (int g8 = 4; g8 < 8; ++g8) {
             uint4 v;
@@ -1134,20 +1165,20 @@ __global__ void __launch_bounds__(kTcRows, 1) design_backward_tc_kernel(const De
             v.y = valid ? (uint32_t)x[8 * g8 + 2] | ((uint32_t)x[8 * g8 + 3] << 16) : 0u;
             v.z = valid ? (uint32_t)x[8 * g8 + 4] | ((uint32_t)x[8 * g8 + 5] << 16) : 0u;
             v.w = valid ? (uint32_t)x[8 * g8 + 6] | ((uint32_t)x[8 * g8 + 7] << 16) : 0u;
-            *reinterpret_cast<uint4 *>(arow + core_offset(tid, 8 * g8)) = v;
+            *reinterpret_cast<uint4 *>(arow + core_offset(r, 8 * g8)) = v;
         }
         proxy_fence();
-        __syncthreads();
+        wg_sync(g);
         uint32_t mask[3][2];
         float o0 = 0.0f, o1 = 0.0f;
         bool ok = true;
         // forward
         for (int layer = 0; layer < 4 && ok; ++layer) {
             const int N = layer < 3 ? 64 : 16;
-            ok = tc_layer(tmem, a_addr, 1024, w_addr + layer * 8192, 1024, N, 4, mbar, phase, tid);
-            if (!ok) atomicOr(&S.abort, 1);
-            __syncthreads();
-            if (S.abort) { ok = false; break; }
+            ok = tc_layer(tmem, a_addr, 1024, w_addr + layer * 8192, 1024, N, 4, mbar, phase, r);
+            if (!ok) S.abort[g] = 1;
+            wg_sync(g);
+            if (S.abort[g]) { ok = false; break; }
             if (layer < 3) {
                 mask[layer][0] = mask[layer][1] = 0u;
 #pragma unroll
@@ -1164,7 +1195,7 @@ __global__ void __launch_bounds__(kTcRows, 1) design_backward_tc_kernel(const De
                         q.y = pack2(fmaxf(v[8 * h + 2], 0.0f), fmaxf(v[8 * h + 3], 0.0f));
                         q.z = pack2(fmaxf(v[8 * h + 4], 0.0f), fmaxf(v[8 * h + 5], 0.0f));
                         q.w = pack2(fmaxf(v[8 * h + 6], 0.0f), fmaxf(v[8 * h + 7], 0.0f));
-                        *reinterpret_cast<uint4 *>(arow + core_offset(tid, 16 * c + 8 * h)) = q;
+                        *reinterpret_cast<uint4 *>(arow + core_offset(r, 16 * c + 8 * h)) = q;
                     }
                 }
             } else {
@@ -1175,7 +1206,7 @@ __global__ void __launch_bounds__(kTcRows, 1) design_backward_tc_kernel(const De
             }
             tc_fence_before();
             proxy_fence();
-            __syncthreads();
+            wg_sync(g);
         }
         if (!ok) break;
         // loss head: dO/do of the row
@@ -1188,19 +1219,19 @@ __global__ void __launch_bounds__(kTcRows, 1) design_backward_tc_kernel(const De
             uint4 q0, q1 = make_uint4(0, 0, 0, 0);
             q0.x = pack2(ui * sg0 * (1.0f - sg0) * D, ui * kRScale * sigmoidf_(o1));
             q0.y = q0.z = q0.w = 0u;
-            *reinterpret_cast<uint4 *>(drow + core_offset16(tid, 0)) = q0;
-            *reinterpret_cast<uint4 *>(drow + core_offset16(tid, 8)) = q1;
+            *reinterpret_cast<uint4 *>(drow + core_offset16(r, 0)) = q0;
+            *reinterpret_cast<uint4 *>(drow + core_offset16(r, 8)) = q1;
         }
         proxy_fence();
-        __syncthreads();
+        wg_sync(g);
         // backward: W3^T (K = 16), then W2^T, W1^T (masked, rounded), W0^T
         float gX[kGeom];
         for (int layer = 3; layer >= 0 && ok; --layer) {
-            if (layer == 3) ok = tc_layer(tmem, d4_addr, 256, wt_addr + 3 * 8192, 256, 64, 1, mbar, phase, tid);
-            else ok = tc_layer(tmem, a_addr, 1024, wt_addr + layer * 8192, 1024, 64, 4, mbar, phase, tid);
-            if (!ok) atomicOr(&S.abort, 1);
-            __syncthreads();
-            if (S.abort) { ok = false; break; }
+            if (layer == 3) ok = tc_layer(tmem, d4_addr, 256, wt_addr + 3 * 8192, 256, 64, 1, mbar, phase, r);
+            else ok = tc_layer(tmem, a_addr, 1024, wt_addr + layer * 8192, 1024, 64, 4, mbar, phase, r);
+            if (!ok) S.abort[g] = 1;
+            wg_sync(g);
+            if (S.abort[g]) { ok = false; break; }
             if (layer > 0) {
                 const int m = layer - 1;          // the mask of the product's input
 #pragma unroll
@@ -1220,7 +1251,7 @@ __global__ void __launch_bounds__(kTcRows, 1) design_backward_tc_kernel(const De
                         q.y = pack2(z[2], z[3]);
                         q.z = pack2(z[4], z[5]);
                         q.w = pack2(z[6], z[7]);
-                        *reinterpret_cast<uint4 *>(arow + core_offset(tid, 16 * c + 8 * h)) = q;
+                        *reinterpret_cast<uint4 *>(arow + core_offset(r, 16 * c + 8 * h)) = q;
                     }
                 }
             } else {
@@ -1233,7 +1264,7 @@ __global__ void __launch_bounds__(kTcRows, 1) design_backward_tc_kernel(const De
             }
             tc_fence_before();
             proxy_fence();
-            __syncthreads();
+            wg_sync(g);
         }
         if (!ok) break;
         float gs[7] = {0, 0, 0, 0, 0, 0, 0};
@@ -1255,11 +1286,16 @@ __global__ void __launch_bounds__(kTcRows, 1) design_backward_tc_kernel(const De
             out[7] = 0.0f;
         }
     }
-    if (S.abort && tid == 0) atomicOr(err, kErrTc);
     tc_fence_before();
     __syncthreads();
+    if (tid == 0) {
+        int32_t any = 0;
+        for (int k = 0; k < kTcTiles; ++k) any |= S.abort[k];
+        if (any) atomicOr(err, kErrTc);
+    }
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTcCols) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(S.tmem), "r"(kTcCols * kTcTiles)
+                     : "memory");
 }
 
 int g_sms = 0;
@@ -1351,9 +1387,10 @@ cudaError_t launch_design_forward_tc(const DesignArgs &a, int32_t *err, cudaStre
     int dev = 0;
     cudaGetDevice(&dev);
     const int64_t tiles = (a.tex.n_pad * (int64_t)a.n_lights + kTcRows - 1) / kTcRows;
-    // at most 4 CTAs per SM: 4 x 64 TMEM columns never wait for an allocation
-    const int grid = (int)std::min<int64_t>(tiles, (int64_t)train_grid(dev) * 2);
-    design_forward_tc_kernel<<<grid, kTcRows, smem, s>>>(a, err);
+    // two CTAs per SM (shared memory admits no third): 2 x 256 TMEM columns
+    // never wait for an allocation
+    const int grid = (int)std::min<int64_t>((tiles + kTcTiles - 1) / kTcTiles, (int64_t)train_grid(dev));
+    design_forward_tc_kernel<<<grid, kTcThreads, smem, s>>>(a, err);
     return cudaGetLastError();
 }
 
@@ -1364,9 +1401,10 @@ cudaError_t launch_design_backward_tc(const DesignArgs &a, int32_t *err, cudaStr
     int dev = 0;
     cudaGetDevice(&dev);
     const int64_t tiles = (a.tex.n_pad * (int64_t)a.n_lights + kTcRows - 1) / kTcRows;
-    // at most 3 CTAs per SM fit (shared memory); 3 x 64 TMEM columns never wait
-    const int grid = (int)std::min<int64_t>(tiles, (int64_t)train_grid(dev) * 3 / 2);
-    design_backward_tc_kernel<<<grid, kTcRows, smem, s>>>(a, err);
+    // one CTA per SM (shared memory admits no second): kTcTiles x 64 TMEM
+    // columns never wait for an allocation
+    const int grid = (int)std::min<int64_t>((tiles + kTcTiles - 1) / kTcTiles, (int64_t)train_grid(dev) / 2);
+    design_backward_tc_kernel<<<grid, kTcThreads, smem, s>>>(a, err);
     return cudaGetLastError();
 }
 

@@ -198,14 +198,16 @@ def test_training_fits_a_smooth_response(sg):
     assert np.mean(losses[-20:]) < 0.1 * np.mean(losses[:5]), (losses[:5], losses[-5:])
 
 
-def test_tensor_core_paths_agree(sg):
-    # tcgen05 (TMEM accumulators, 128 rows per CTA) and mma.sync (16 rows per
-    # warp) run the same network on the same bf16 inputs; only the order of
-    # the fp32 sums differs
+@pytest.mark.parametrize("n_texels,powers", [(5003, [1.5, 1.0, 2.0, 0.7, 1.2]), (301, [1.3, 0.8])])
+def test_tensor_core_paths_agree(sg, n_texels, powers):
+    # tcgen05 (TMEM accumulators, 128-row tiles, four per CTA) and mma.sync
+    # (16 rows per warp) run the same network on the same bf16 inputs; only
+    # the order of the fp32 sums differs. 301 texels x 2 lights make 5 tiles:
+    # the second CTA has one tile and three idle warpgroups.
     import torch
-    x, nt, area, lo, ext, inv_ext, lights, W, table = _problem(12, 5003, 5)
+    x, nt, area, lo, ext, inv_ext, lights, W, table = _problem(12, n_texels, len(powers))
     lights = lights.copy()
-    lights[:, 6] = [1.5, 1.0, 2.0, 0.7, 1.2]
+    lights[:, 6] = powers
     sg.set_texels(x, nt, area, lo, ext)
     sg.set_params(W, table)
     target = torch.tensor(np.random.default_rng(13).uniform(0, 0.5, x.shape[0]).astype(np.float32), device="cuda")
