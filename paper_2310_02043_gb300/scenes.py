@@ -334,6 +334,27 @@ def icosphere(radius: float = 1.0, subdiv: int = 3, albedo: float = 0.5) -> Scen
     return b.build("icosphere", radius=radius, subdiv=subdiv, albedo=albedo)
 
 
+NESTED_SHELF_APEX = (0.0, 0.5, 0.0)
+
+
+def nested_shelf(n_strips: int = 100, res: int = 8, strip_res: int = 2, albedo: float = 0.6) -> Scene:
+    """A closed box room [-1, 2] x [-0.5, 1.5] x [-0.3, 1] (res x res texels
+    per face) around a shelf of n_strips strips in the plane z = 0: strip i
+    covers x in [2^-(i+1), 2^-i], y in [0.2, 0.8]. The strips halve in width
+    towards NESTED_SHELF_APEX, so the surface-area heuristic peels them off
+    one at a time and the 8-wide BVH has more than 8 levels while holding a
+    few dozen nodes (small enough to stage in shared memory). A light at the
+    apex lies in the strips' plane: every ray it emits starts inside the
+    padded boxes of the whole chain, so it descends every level, and leaves
+    the plane at t = 0, so it hits no strip."""
+    b = _Builder()
+    b.box([-1.0, -0.5, -0.3], [2.0, 1.5, 1.0], res, albedo)
+    for i in range(n_strips):
+        w = 0.5 ** (i + 1)
+        b.quad([w, 0.2, 0.0], [w, 0.0, 0.0], [0.0, 0.6, 0.0], strip_res, strip_res, albedo)
+    return b.build("nested_shelf", n_strips=n_strips, res=res)
+
+
 def random_triangles(n: int, seed: int, extent: float = 1.0, albedo: float = 0.5) -> Scene:
     """n random triangles in [0, extent]^3 (a tiny scene for brute-force checks)."""
     rng = np.random.default_rng(seed)

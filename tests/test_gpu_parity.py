@@ -282,6 +282,37 @@ def test_adjoint_with_injected_weights(tr):
     _check_grad(tr, sc, L, seed, n, hits, w.astype(np.float64), g, g_ref)
 
 
+def test_deep_bvh_staged_and_through_l1(tr):
+    # A BVH of more than 8 levels that fits in shared memory: the staged
+    # kernel with two words of pending masks. Every ray from the apex light
+    # descends the whole chain of nested strips. Irradiance and gradients
+    # must match the oracle, and the kernel that reads nodes through L1 must
+    # give the same integer sums.
+    sc = scenes.nested_shelf()
+    L = scenes.make_lights([scenes.point_light(scenes.NESTED_SHELF_APEX, 1.0)])
+    n, hits, seed = 1 << 19, 3, 4
+    tr.set_launch(0, 0, 72 * 1024)
+    E, st = _forward(tr, sc, L, seed, n, hits)
+    assert st["bvh_depth"] > 8 and st["staged_nodes"] == st["n_nodes"] > 0, st
+    assert st["block_threads"] == 1024
+    q_staged = tr.texel_sums()
+    ref = oracle.forward(sc, L, seed, n, hits, counts=True)
+    assert _check_irradiance(sc, E, ref, min_count=1000) > 300
+    # the room is closed: every photon makes exactly `hits` segments
+    assert st["segments_forward"] == n * hits == ref["segments"]
+    tr.set_launch(0, 0, 0)
+    tr.trace_forward(seed, n, hits)
+    st = tr.stats()
+    assert st["staged_nodes"] == 0 and st["block_threads"] == 768
+    assert np.array_equal(tr.texel_sums(), q_staged)
+    tr.set_launch(0, 0, 72 * 1024)
+    Lt = L.copy()
+    Lt[0, 1:4] += (0.2, -0.1, 0.3)
+    target = oracle.forward(sc, Lt, 77, 1 << 16, hits)["E"].astype(np.float32)
+    g = _adjoint_case(tr, sc, L, target, 1 << 16, hits, 5)
+    assert np.all(np.abs(g[0, [0, 1, 2, 5]]) > 0)
+
+
 def test_call_order_and_argument_errors():
     t = Tracer(0)
     try:
