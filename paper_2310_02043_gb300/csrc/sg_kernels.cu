@@ -257,8 +257,8 @@ __device__ __forceinline__ void scatter_level(const float (&xn)[3], int level, f
         const int bx = cn & 1, by = (cn >> 1) & 1, bz = (cn >> 2) & 1;
         const float w = (bx ? f[0] : 1.0f - f[0]) * (by ? f[1] : 1.0f - f[1]) * (bz ? f[2] : 1.0f - f[2]);
         const uint32_t idx = vertex_index(level, i0[0] + bx, i0[1] + by, i0[2] + bz);
-        atomicAdd(tl + 2 * idx, w * g0);
-        atomicAdd(tl + 2 * idx + 1, w * g1);
+        // both features of the entry in one vector atomic (8-byte aligned)
+        atomicAdd(reinterpret_cast<float2 *>(tl) + idx, make_float2(w * g0, w * g1));
     }
 }
 
