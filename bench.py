@@ -640,7 +640,7 @@ def run_surrogate(args):
     b.record(stream)
     torch.cuda.synchronize()
     design_ms = a.elapsed_time(b) / n_rep
-    sg.set_kernels(False)            # the same call with the mma.sync forward, for comparison
+    sg.set_kernels(tcgen05=False)    # the same call with the mma.sync kernels, for comparison
     sg.design(start, target)
     torch.cuda.synchronize()
     a.record(stream)
@@ -649,7 +649,7 @@ def run_surrogate(args):
     b.record(stream)
     torch.cuda.synchronize()
     design_ms_mma = a.elapsed_time(b) / n_rep
-    sg.set_kernels(True)
+    sg.set_kernels()
     rows = 16 * ((T + 15) // 16 * 16)
     design_flops = rows * SG_FWD_FLOPS * 3
     peaks = json.load(open(MEASURED_PEAKS)) if os.path.exists(MEASURED_PEAKS) else {}
@@ -660,6 +660,16 @@ def run_surrogate(args):
     b.record(stream)
     torch.cuda.synchronize()
     train_ms = a.elapsed_time(b) / n_rep
+    sg.set_kernels(train_tcgen05=True)   # the training network on tcgen05, for comparison
+    sg.train_step(99, SG_BATCH, 0.0)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for k in range(n_rep):
+        sg.train_step(99, SG_BATCH, 0.0)
+    b.record(stream)
+    torch.cuda.synchronize()
+    train_ms_tc = a.elapsed_time(b) / n_rep
+    sg.set_kernels()
     held = scenes.surrogate_training_lights(777, 8)
     errs = []
     for L in held:
@@ -701,7 +711,7 @@ def run_surrogate(args):
             "fit_s": {"solves": info["solve_s"], "train": info["train_s"], "total": fit_s},
             "warm_incl_fit_s": None if warm_s is None else warm_s + fit_s,
             "heldout_rel_l2": errs, "design_ms": design_ms, "design_ms_mma_sync_forward": design_ms_mma,
-            "train_step_ms": train_ms,
+            "train_step_ms": train_ms, "train_step_ms_tcgen05": train_ms_tc,
             "roofline": {"bound": "tensor", "achieved": design_flops / (design_ms / 1e3) / 1e12, "peak": peak,
                          "unit": "TFLOP/s", "frac": design_flops / (design_ms / 1e3) / 1e12 / peak, "traffic": None,
                          "kernel": "sg_design (network forward + backward over 16 spots x all texels)",

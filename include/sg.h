@@ -120,13 +120,23 @@ LT_API int sg_design(void *ctx, const lt_light *lights, int32_t n_lights, const 
 LT_API int sg_network(void *ctx, const float *X, int32_t rows, const float *dO, float *O_out, float *dX_out,
                       float *dW_out);
 
-/* Kernels of the design objective (sg_response and sg_design, forward and
- * backward): tcgen05 = 1 (default) runs the network on the 5th-generation
- * tensor cores (tcgen05.mma, fp32 accumulators in tensor memory, 128 rows per
- * CTA); 0 runs it with warp-level mma.sync (16 rows per warp). Both take bf16
- * inputs and accumulate in fp32; they agree up to the order of the fp32 sums.
- * A tensor-core wait that gives up returns LT_ERR_TIMEOUT. */
-LT_API int sg_set_kernels(void *ctx, int tcgen05);
+/* Kernels of the network. flags: SG_KERNELS_DESIGN_TC runs the design
+ * objective (sg_response and sg_design, forward and backward) on the
+ * 5th-generation tensor cores (tcgen05.mma, fp32 accumulators in tensor
+ * memory, four 128-row tiles per CTA), SG_KERNELS_TRAIN_TC does the same for
+ * the training step's forward and backward (sg_train_step); a cleared flag
+ * selects warp-level mma.sync (16 rows per warp) for that part. The default
+ * is SG_KERNELS_DESIGN_TC alone: the measured fastest pair (the training
+ * step is bound by its hash-table gathers and atomics, where the mma.sync
+ * kernel hides latency better). Both kernels of each part take bf16 inputs
+ * and accumulate in fp32; they agree up to the order of the fp32 sums (and,
+ * in training, of the float atomics into the table gradient). Unknown flag
+ * bits return LT_ERR_ARG. A tensor-core wait that gives up returns
+ * LT_ERR_TIMEOUT (from sg_design, or from sg_train_step when it returns the
+ * loss). */
+#define SG_KERNELS_DESIGN_TC 1
+#define SG_KERNELS_TRAIN_TC 2
+LT_API int sg_set_kernels(void *ctx, int flags);
 
 /* Hash encoding of normalised positions xn [rows][3] (host) with the
  * current table: enc_out [rows][32] (host). */

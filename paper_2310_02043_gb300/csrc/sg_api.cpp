@@ -50,7 +50,8 @@ struct SgCtx {
     size_t K_floats = 0, up_floats = 0, gpart_floats = 0;
     double *d_dout = nullptr;
     int32_t *d_err = nullptr;                 // device error word of the tcgen05 kernels
-    int use_tc = 1;                           // design forward on tcgen05 (1) or mma.sync (0)
+    int use_tc = 1;                           // design objective on tcgen05 (1) or mma.sync (0)
+    int train_tc = 0;                         // training network on tcgen05 (1) or mma.sync (0)
     double *h_pinned = nullptr;
     size_t h_pinned_bytes = 0;
 };
@@ -339,6 +340,8 @@ int sg_set_training_data(void *ctx, const lt_light *lights, int32_t n_solves, co
     return LT_OK;
 }
 
+static int check_device(SgCtx *c);
+
 int sg_train_step(void *ctx, uint64_t seed, int32_t batch, float lr, const int32_t *samples, double *loss_out) {
     SgCtx *c = static_cast<SgCtx *>(ctx);
     if (!c) return LT_ERR_ARG;
@@ -377,9 +380,14 @@ int sg_train_step(void *ctx, uint64_t seed, int32_t batch, float lr, const int32
     a.Wb = c->d_Wb;
     a.rb = c->rb;
     a.loss_part = c->d_lpart;
-    const int64_t tiles = ((int64_t)batch + 15) / 16;
-    const int grid = (int)std::min<int64_t>((tiles + kMlpWarps - 1) / kMlpWarps, train_grid(c->device));
-    SG_CUDA(c, launch_train(a, grid, c->stream));
+    int grid = 0;
+    if (c->train_tc) {
+        SG_CUDA(c, launch_train_tc(a, c->d_err, c->stream, &grid));
+    } else {
+        const int64_t tiles = ((int64_t)batch + 15) / 16;
+        grid = (int)std::min<int64_t>((tiles + kMlpWarps - 1) / kMlpWarps, train_grid(c->device));
+        SG_CUDA(c, launch_train(a, grid, c->stream));
+    }
     SG_CUDA(c, launch_wgrad(c->rb, batch, c->d_wpart, c->d_gW, c->d_lpart, grid, c->d_loss, c->stream));
     ++c->step;
     const double b1 = 0.9, b2 = 0.99;
@@ -392,7 +400,7 @@ int sg_train_step(void *ctx, uint64_t seed, int32_t batch, float lr, const int32
     c->enc_dirty = true;
     if (loss_out) {
         SG_CUDA(c, cudaMemcpyAsync(loss_out, c->d_loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-        SG_CUDA(c, cudaStreamSynchronize(c->stream));
+        return check_device(c);   // synchronises; reports a tensor-core wait that gave up
     }
     return LT_OK;
 }
@@ -537,10 +545,11 @@ int sg_network(void *ctx, const float *X, int32_t rows, const float *dO, float *
     return LT_OK;
 }
 
-int sg_set_kernels(void *ctx, int tcgen05) {
+int sg_set_kernels(void *ctx, int flags) {
     SgCtx *c = static_cast<SgCtx *>(ctx);
-    if (!c || (tcgen05 != 0 && tcgen05 != 1)) return LT_ERR_ARG;
-    c->use_tc = tcgen05;
+    if (!c || (flags & ~(SG_KERNELS_DESIGN_TC | SG_KERNELS_TRAIN_TC))) return LT_ERR_ARG;
+    c->use_tc = (flags & SG_KERNELS_DESIGN_TC) ? 1 : 0;
+    c->train_tc = (flags & SG_KERNELS_TRAIN_TC) ? 1 : 0;
     return LT_OK;
 }
 

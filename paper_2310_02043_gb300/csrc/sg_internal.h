@@ -92,6 +92,8 @@ struct DesignArgs {
 };
 
 cudaError_t launch_train(const TrainArgs &a, int grid, cudaStream_t s);
+// tcgen05 training kernel; *grid_out = its grid (the number of loss partials)
+cudaError_t launch_train_tc(const TrainArgs &a, int32_t *err, cudaStream_t s, int *grid_out);
 cudaError_t launch_network(const NetworkArgs &a, cudaStream_t s);
 // Weight gradient of `rows` kept rows: partial sums per chunk, then their
 // ordered sum into dW [kWeights]; loss partials (if any) summed into *loss.

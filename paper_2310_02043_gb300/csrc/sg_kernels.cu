@@ -1068,22 +1068,60 @@ __global__ void __launch_bounds__(kTcThreads, 2) design_forward_tc_kernel(const 
 // masks kept as bits), the loss head, then the gradient through W3^T, W2^T,
 // W1^T, W0^T as tcgen05.mma on transposed weights (the output layer's step
 // has K = 16), and each thread's row through the feature Jacobian.
-struct alignas(1024) TcBwdSmem {
-    uint16_t a[kTcTiles][kTcRows * 64];          // per warpgroup: activations, then gradients (64 wide)
-    uint16_t d4[kTcTiles][kTcRows * 16];         // per warpgroup: gradient at the outputs (16 wide)
+template <int kTiles>
+struct alignas(1024) TcBwdSmemT {
+    uint16_t a[kTiles][kTcRows * 64];            // per warpgroup: activations, then gradients (64 wide)
+    uint16_t d4[kTiles][kTcRows * 16];           // per warpgroup: gradient at the outputs (16 wide)
     uint16_t w[3 * 64 * 64 + 16 * 64];           // W0, W1, W2 [64][64], W3 [16][64]
     uint16_t wt[3 * 64 * 64 + 64 * 16];          // W0^T, W1^T, W2^T [64][64], W3^T [64][16]
-    unsigned long long mbar[kTcTiles];
+    unsigned long long mbar[kTiles];
+    double red[kTiles * kTcRows / 32];           // per-warp loss sums (training)
     uint32_t tmem;
-    int32_t abort[kTcTiles];                     // set and read by one warpgroup only
+    int32_t abort[kTiles];                       // set and read by one warpgroup only
 };
+using TcBwdSmem = TcBwdSmemT<kTcTiles>;
 
 // One CTA per SM (shared memory admits no second): kTcTiles x 64 TMEM columns.
 static_assert(sizeof(TcBwdSmem) + 1024 <= 227 * 1024 && 2 * (sizeof(TcBwdSmem) + 1024) > 228 * 1024,
               "design backward: exactly one CTA per SM");
 
+// The training kernel's warpgroups per CTA (a build knob; its registers are
+// 65536 / (128 x tiles)), its TMEM allocation (a power of two), and the
+// guarantee that the CTAs resident on an SM never ask for more than 512
+// columns.
+#ifndef SG_TRAIN_TILES
+#define SG_TRAIN_TILES 4
+#endif
+constexpr int kTrainTiles = SG_TRAIN_TILES;
+constexpr int kTrainThreads = kTrainTiles * kTcRows;
+using TcTrainSmem = TcBwdSmemT<kTrainTiles>;
+constexpr uint32_t pow2_cols(uint32_t c) { return c <= 32 ? 32 : (c <= 64 ? 64 : (c <= 128 ? 128 : (c <= 256 ? 256 : 512))); }
+constexpr uint32_t kTrainCols = pow2_cols(kTcCols * kTrainTiles);
+static_assert(kTrainTiles >= 1 && kTcCols * kTrainTiles <= 512, "training tiles fit TMEM");
+static_assert(sizeof(TcTrainSmem) + 1024 <= 227 * 1024, "training CTA fits shared memory");
+static_assert(2 * (sizeof(TcTrainSmem) + 1024) > 228 * 1024 || 2 * kTrainCols <= 512,
+              "resident training CTAs never exceed 512 TMEM columns");
+
 __device__ __forceinline__ uint32_t core_offset16(int r, int k) {    // bytes, 16-wide rows
     return (uint32_t)((((r >> 3) << 1) + (k >> 3)) << 7) + (uint32_t)((r & 7) << 4) + (uint32_t)((k & 7) << 1);
+}
+
+// W and W^T into the canonical layouts (W3^T is 64 x 16: 16-wide rows).
+template <class Smem>
+__device__ __forceinline__ void stage_weights_bwd(Smem &S, const uint16_t *__restrict__ Wb, int tid, int nthreads) {
+    unsigned char *wb = reinterpret_cast<unsigned char *>(S.w), *wtb = reinterpret_cast<unsigned char *>(S.wt);
+    for (int i = tid; i < kWeights; i += nthreads) {
+        const uint16_t v = Wb[i];
+        if (i < kOffW3) {
+            const int layer = i >> 12, r = i & 4095, n = r >> 6, k = r & 63;
+            *reinterpret_cast<uint16_t *>(wb + layer * 8192 + core_offset(n, k)) = v;
+            *reinterpret_cast<uint16_t *>(wtb + layer * 8192 + core_offset(k, n)) = v;
+        } else {
+            const int r = i - kOffW3, n = r >> 6, k = r & 63;        // W3[n][k], n < 16
+            *reinterpret_cast<uint16_t *>(wb + 3 * 8192 + core_offset(n, k)) = v;
+            *reinterpret_cast<uint16_t *>(wtb + 3 * 8192 + core_offset16(k, n)) = v;
+        }
+    }
 }
 
 // Issues one layer (K / 16 steps) from thread r == 0 of the warpgroup and
@@ -1107,19 +1145,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) design_backward_tc_kernel(const
     extern __shared__ __align__(1024) unsigned char tcb_raw[];
     TcBwdSmem &S = *reinterpret_cast<TcBwdSmem *>(tcb_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = tid / kTcRows, r = tid % kTcRows;
-    unsigned char *wb = reinterpret_cast<unsigned char *>(S.w), *wtb = reinterpret_cast<unsigned char *>(S.wt);
-    for (int i = tid; i < kWeights; i += kTcThreads) {
-        const uint16_t v = A.Wb[i];
-        if (i < kOffW3) {
-            const int layer = i >> 12, r = i & 4095, n = r >> 6, k = r & 63;
-            *reinterpret_cast<uint16_t *>(wb + layer * 8192 + core_offset(n, k)) = v;
-            *reinterpret_cast<uint16_t *>(wtb + layer * 8192 + core_offset(k, n)) = v;
-        } else {
-            const int r = i - kOffW3, n = r >> 6, k = r & 63;        // W3[n][k], n < 16
-            *reinterpret_cast<uint16_t *>(wb + 3 * 8192 + core_offset(n, k)) = v;
-            *reinterpret_cast<uint16_t *>(wtb + 3 * 8192 + core_offset16(k, n)) = v;
-        }
-    }
+    stage_weights_bwd(S, A.Wb, tid, kTcThreads);
     if (tid == 0) {
         for (int k = 0; k < kTcTiles; ++k) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&S.mbar[k])) : "memory");
@@ -1298,6 +1324,222 @@ __global__ void __launch_bounds__(kTcThreads, 1) design_backward_tc_kernel(const
                      : "memory");
 }
 
+// The training step's network on tcgen05: per 128-row tile of samples the
+// input rows (hash encoding and geometric features), the forward with the
+// ReLU masks kept as bits, the loss head, the backward through W3^T .. W0^T
+// and the encoding gradient scattered into the table with float2 atomics,
+// four tiles per CTA as in the design kernels. The samples, the loss and the
+// bf16 rows kept for the weight gradient are those of train_kernel (the same
+// row buffers), so wgrad_kernel serves both.
+__global__ void __launch_bounds__(kTrainThreads, 1) train_tc_kernel(const TrainArgs A, int32_t *err) {
+    extern __shared__ __align__(1024) unsigned char tct_raw[];
+    TcTrainSmem &S = *reinterpret_cast<TcTrainSmem *>(tct_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = tid / kTcRows, r = tid % kTcRows;
+    stage_weights_bwd(S, A.Wb, tid, kTrainThreads);
+    if (tid == 0) {
+        for (int k = 0; k < kTrainTiles; ++k) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&S.mbar[k])) : "memory");
+            S.abort[k] = 0;
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&S.tmem)),
+                     "r"(kTrainCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem + (uint32_t)g * kTcCols;
+    const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    const uint32_t mbar = smem_u32(&S.mbar[g]);
+    const uint32_t a_addr = smem_u32(S.a[g]), d4_addr = smem_u32(S.d4[g]), w_addr = smem_u32(S.w),
+                   wt_addr = smem_u32(S.wt);
+    unsigned char *arow = reinterpret_cast<unsigned char *>(S.a[g]), *drow = reinterpret_cast<unsigned char *>(S.d4[g]);
+    const int64_t n = A.tex.n, cap = A.rb.rows;
+    const int64_t tiles = ((int64_t)A.batch + kTcRows - 1) / kTcRows;
+    const double inv_b = 1.0 / (double)A.batch;
+    uint32_t phase = 0;
+    double loss = 0.0;
+    for (int64_t tile = (int64_t)blockIdx.x * kTrainTiles + g; tile < tiles; tile += (int64_t)gridDim.x * kTrainTiles) {
+        const int64_t i = tile * kTcRows + r;
+        const bool valid = i < A.batch;
+        int32_t smp = 0, t = 0;
+        if (valid) {
+            if (A.samples) {
+                smp = A.samples[2 * i];
+                t = A.samples[2 * i + 1];
+            } else {
+                const uint64_t h = mix64(A.seed ^ mix64((A.step << 32) ^ (uint64_t)i));
+                smp = (int32_t)(((h >> 32) * (uint64_t)A.n_solves) >> 32);
+                t = (int32_t)(((h & 0xFFFFFFFFull) * (uint64_t)n) >> 32);
+            }
+        }
+        // the input row: hash encoding (entries 0..31) and geometric features
+        const float4 P = A.tex.pos[t], Nt = A.tex.nrm[t];
+        uint16_t x[64];
+        const float D = geometry_row(A.lights[smp], P, Nt, A.tex, x);
+        float xn[3];
+        normalised(A.tex, P, xn);
+        uint32_t enc[16];
+#pragma unroll
+        for (int level = 0; level < kLevels; ++level) {
+            const float2 e = encode_level(xn, level, A.table);
+            enc[level] = pack2(e.x, e.y);
+        }
+        uint16_t *kept = A.rb.act + i * 64;              // this row of the first product's input
+#pragma unroll
+        for (int g8 = 0; g8 < 8; ++g8) {
+            uint4 v;
+            if (g8 < 4) {
+                v = make_uint4(enc[4 * g8], enc[4 * g8 + 1], enc[4 * g8 + 2], enc[4 * g8 + 3]);
+            } else {
+                v.x = (uint32_t)x[8 * g8] | ((uint32_t)x[8 * g8 + 1] << 16);
+                v.y = (uint32_t)x[8 * g8 + 2] | ((uint32_t)x[8 * g8 + 3] << 16);
+                v.z = (uint32_t)x[8 * g8 + 4] | ((uint32_t)x[8 * g8 + 5] << 16);
+                v.w = (uint32_t)x[8 * g8 + 6] | ((uint32_t)x[8 * g8 + 7] << 16);
+            }
+            if (!valid) v = make_uint4(0, 0, 0, 0);
+            *reinterpret_cast<uint4 *>(arow + core_offset(r, 8 * g8)) = v;
+            if (valid) *reinterpret_cast<uint4 *>(kept + 8 * g8) = v;
+        }
+        proxy_fence();
+        wg_sync(g);
+        uint32_t mask[3][2];
+        float o0 = 0.0f, o1 = 0.0f;
+        bool ok = true;
+        // forward; the activations are also kept as the inputs of products 1..3
+        for (int layer = 0; layer < 4 && ok; ++layer) {
+            const int N = layer < 3 ? 64 : 16;
+            ok = tc_layer(tmem, a_addr, 1024, w_addr + layer * 8192, 1024, N, 4, mbar, phase, r);
+            if (!ok) S.abort[g] = 1;
+            wg_sync(g);
+            if (S.abort[g]) { ok = false; break; }
+            if (layer < 3) {
+                uint16_t *kl = A.rb.act + (int64_t)(layer + 1) * cap * 64 + i * 64;
+                mask[layer][0] = mask[layer][1] = 0u;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float v[16];
+                    tc_ld16(lane_addr + 16 * c, v);
+#pragma unroll
+                    for (int k = 0; k < 16; ++k)
+                        if (v[k] > 0.0f) mask[layer][c >> 1] |= 1u << ((c & 1) * 16 + k);
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        uint4 q;
+                        q.x = pack2(fmaxf(v[8 * hh], 0.0f), fmaxf(v[8 * hh + 1], 0.0f));
+                        q.y = pack2(fmaxf(v[8 * hh + 2], 0.0f), fmaxf(v[8 * hh + 3], 0.0f));
+                        q.z = pack2(fmaxf(v[8 * hh + 4], 0.0f), fmaxf(v[8 * hh + 5], 0.0f));
+                        q.w = pack2(fmaxf(v[8 * hh + 6], 0.0f), fmaxf(v[8 * hh + 7], 0.0f));
+                        *reinterpret_cast<uint4 *>(arow + core_offset(r, 16 * c + 8 * hh)) = q;
+                        if (valid) *reinterpret_cast<uint4 *>(kl + 16 * c + 8 * hh) = q;
+                    }
+                }
+            } else {
+                float v[16];
+                tc_ld16(lane_addr, v);
+                o0 = v[0];
+                o1 = v[1];
+            }
+            tc_fence_before();
+            proxy_fence();
+            wg_sync(g);
+        }
+        if (!ok) break;
+        // loss head: weighted squared error of K against the solve's irradiance
+        {
+            const float sv = sigmoidf_(o0), sp = softplusf_(o1);
+            const float K = sv * D + kRScale * sp;
+            const float Eo = valid ? __ldg(A.E_obs + (int64_t)smp * n + t) : 0.0f;
+            const float wgt = valid ? A.tex.area[t] * A.tex.inv_mean_area : 0.0f;
+            const float e = K - Eo;
+            loss += 0.5 * (double)wgt * (double)e * (double)e * inv_b;
+            const float dK = (float)((double)(wgt * e) * inv_b);
+            uint4 q0 = make_uint4(pack2(dK * sv * (1.0f - sv) * D, dK * kRScale * sigmoidf_(o1)), 0u, 0u, 0u);
+            const uint4 q1 = make_uint4(0, 0, 0, 0);
+            *reinterpret_cast<uint4 *>(drow + core_offset16(r, 0)) = q0;
+            *reinterpret_cast<uint4 *>(drow + core_offset16(r, 8)) = q1;
+            if (valid) {
+                uint16_t *kd = A.rb.dz + 3 * cap * 64 + i * 16;
+                *reinterpret_cast<uint4 *>(kd) = q0;
+                *reinterpret_cast<uint4 *>(kd + 8) = q1;
+            }
+        }
+        proxy_fence();
+        wg_sync(g);
+        // backward: W3^T (K = 16), then W2^T, W1^T (masked, rounded, kept), W0^T
+        float dX[32];
+        for (int layer = 3; layer >= 0 && ok; --layer) {
+            if (layer == 3) ok = tc_layer(tmem, d4_addr, 256, wt_addr + 3 * 8192, 256, 64, 1, mbar, phase, r);
+            else ok = tc_layer(tmem, a_addr, 1024, wt_addr + layer * 8192, 1024, 64, 4, mbar, phase, r);
+            if (!ok) S.abort[g] = 1;
+            wg_sync(g);
+            if (S.abort[g]) { ok = false; break; }
+            if (layer > 0) {
+                const int m = layer - 1;          // the mask of the product's input
+                uint16_t *kz = A.rb.dz + (int64_t)m * cap * 64 + i * 64;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float v[16];
+                    tc_ld16(lane_addr + 16 * c, v);
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        float z[8];
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            const int col = 16 * c + 8 * hh + k;
+                            z[k] = (mask[m][col >> 5] >> (col & 31)) & 1u ? v[8 * hh + k] : 0.0f;
+                        }
+                        uint4 q;
+                        q.x = pack2(z[0], z[1]);
+                        q.y = pack2(z[2], z[3]);
+                        q.z = pack2(z[4], z[5]);
+                        q.w = pack2(z[6], z[7]);
+                        *reinterpret_cast<uint4 *>(arow + core_offset(r, 16 * c + 8 * hh)) = q;
+                        if (valid) *reinterpret_cast<uint4 *>(kz + 16 * c + 8 * hh) = q;
+                    }
+                }
+            } else {
+                float v[16];
+                tc_ld16(lane_addr, v);            // input entries 0..15
+#pragma unroll
+                for (int k = 0; k < 16; ++k) dX[k] = v[k];
+                tc_ld16(lane_addr + 16, v);       // 16..31
+#pragma unroll
+                for (int k = 0; k < 16; ++k) dX[16 + k] = v[k];
+            }
+            tc_fence_before();
+            proxy_fence();
+            wg_sync(g);
+        }
+        if (!ok) break;
+        // encoding gradient: entries 2 level, 2 level + 1
+        if (valid) {
+#pragma unroll 1
+            for (int level = 0; level < kLevels; ++level)
+                scatter_level(xn, level, dX[2 * level], dX[2 * level + 1], A.dtable);
+        }
+    }
+    loss = warp_sum_d(loss);
+    if (lane == 0) S.red[warp] = loss;
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < kTrainThreads / 32; ++w) sum += S.red[w];
+        A.loss_part[blockIdx.x] = sum;
+        int32_t any = 0;
+        for (int k = 0; k < kTrainTiles; ++k) any |= S.abort[k];
+        if (any) atomicOr(err, kErrTc);
+    }
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(S.tmem), "r"(kTrainCols)
+                     : "memory");
+}
+
 int g_sms = 0;
 
 }  // namespace
@@ -1316,6 +1558,19 @@ cudaError_t launch_train(const TrainArgs &a, int grid, cudaStream_t s) {
     cudaError_t e = set_smem((const void *)train_kernel, smem);
     if (e != cudaSuccess) return e;
     train_kernel<<<grid, kMlpWarps * 32, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_train_tc(const TrainArgs &a, int32_t *err, cudaStream_t s, int *grid_out) {
+    const size_t smem = sizeof(TcTrainSmem) + 1024;
+    cudaError_t e = set_smem((const void *)train_tc_kernel, smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int64_t tiles = ((int64_t)a.batch + kTcRows - 1) / kTcRows;
+    const int grid = (int)std::min<int64_t>((tiles + kTrainTiles - 1) / kTrainTiles, (int64_t)train_grid(dev) / 2);
+    *grid_out = grid;
+    train_tc_kernel<<<grid, kTrainThreads, smem, s>>>(a, err);
     return cudaGetLastError();
 }
 

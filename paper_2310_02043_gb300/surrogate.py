@@ -172,9 +172,11 @@ class Surrogate:
         self._check(self.lib.sg_network(self.h, _ptr(X)[0], B, _ptr(dO)[0], _ptr(O)[0], _ptr(dX)[0], _ptr(dW)[0]))
         return O, dX, dW
 
-    def set_kernels(self, tcgen05: bool):
-        """Design forward on tcgen05 (True, default) or mma.sync (False)."""
-        self._check(self.lib.sg_set_kernels(self.h, 1 if tcgen05 else 0))
+    def set_kernels(self, tcgen05: bool = True, train_tcgen05: bool = False):
+        """Design objective on tcgen05 (default) or mma.sync; training
+        network on mma.sync (default, the faster here) or tcgen05."""
+        flags = (1 if tcgen05 else 0) | (2 if train_tcgen05 else 0)
+        self._check(self.lib.sg_set_kernels(self.h, flags))
 
     def encode(self, xn):
         xn = np.ascontiguousarray(xn, np.float32)

@@ -132,6 +132,31 @@ def test_training_gradients(sg):
     assert np.array_equal(dT != 0, dT_ref != 0) or np.mean((dT != 0) == (dT_ref != 0)) > 0.9999
 
 
+@pytest.mark.parametrize("batch,drawn", [(300, False), (2000, True)])
+def test_training_paths_agree(sg, batch, drawn):
+    # tcgen05 (four 128-row tiles per CTA) and mma.sync (16 rows per warp) run
+    # the same training step on the same samples, given or drawn on the
+    # device from the seed and step: the loss and the gradients agree up to
+    # the order of the fp32 sums and of the float atomics into the table.
+    # 300 samples leave one warpgroup of the tcgen05 CTA without a tile.
+    x, nt, area, lo, ext, inv_ext, lights, W, table, E_obs, E_dev, samples = _train_setup(sg, 21, B=batch)
+    out = {}
+    for tc in (True, False):
+        sg.set_kernels(train_tcgen05=tc)
+        sg.set_params(W, table)                  # restarts the step counter
+        loss = sg.train_step(7, batch, 0.0, None if drawn else samples)
+        out[tc] = (loss,) + sg.gradients()
+    sg.set_kernels()
+    (lt, dWt, dTt), (lm, dWm, dTm) = out[True], out[False]
+    assert lt == pytest.approx(lm, rel=1e-4)
+    assert np.abs(dWt - dWm).max() <= 1e-2 * np.abs(dWm).max()
+    for k, (a, b) in enumerate(zip(split_weights(dWt), split_weights(dWm))):
+        _close(a, b.astype(np.float64), 0.9, 1e-2, f"dW{k}")
+    assert np.mean((dTt != 0) == (dTm != 0)) > 0.9999
+    assert np.abs(dTt - dTm).max() <= 1e-2 * np.abs(dTm).max()
+    assert np.abs(dTt - dTm).sum() <= 2e-3 * np.abs(dTm).sum()
+
+
 def test_adam_step_moves_by_the_learning_rate(sg):
     x, nt, area, lo, ext, inv_ext, lights, W, table, E_obs, E_dev, samples = _train_setup(sg, 7)
     lr = 1e-3
