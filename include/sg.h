@@ -124,11 +124,13 @@ LT_API int sg_network(void *ctx, const float *X, int32_t rows, const float *dO, 
  * objective (sg_response and sg_design, forward and backward) on the
  * 5th-generation tensor cores (tcgen05.mma, fp32 accumulators in tensor
  * memory, four 128-row tiles per CTA), SG_KERNELS_TRAIN_TC does the same for
- * the training step's forward and backward (sg_train_step); a cleared flag
+ * the training step's forward and backward (sg_train_step; two threads per
+ * row, two 128-row tiles per CTA); a cleared flag
  * selects warp-level mma.sync (16 rows per warp) for that part. The default
- * is SG_KERNELS_DESIGN_TC alone: the measured fastest pair (the training
- * step is bound by its hash-table gathers and atomics, where the mma.sync
- * kernel hides latency better). Both kernels of each part take bf16 inputs
+ * is SG_KERNELS_DESIGN_TC alone, the measured faster pair: the training step
+ * is bound by its hash-table gathers and atomics, where the two kernels are
+ * within a few per cent and mma.sync leads. Both kernels of each part take
+ * bf16 inputs
  * and accumulate in fp32; they agree up to the order of the fp32 sums (and,
  * in training, of the float atomics into the table gradient). Unknown flag
  * bits return LT_ERR_ARG. A tensor-core wait that gives up returns

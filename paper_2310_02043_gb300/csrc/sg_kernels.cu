@@ -1075,7 +1075,7 @@ struct alignas(1024) TcBwdSmemT {
     uint16_t w[3 * 64 * 64 + 16 * 64];           // W0, W1, W2 [64][64], W3 [16][64]
     uint16_t wt[3 * 64 * 64 + 64 * 16];          // W0^T, W1^T, W2^T [64][64], W3^T [64][16]
     unsigned long long mbar[kTiles];
-    double red[kTiles * kTcRows / 32];           // per-warp loss sums (training)
+    double red[2 * kTiles * kTcRows / 32];       // per-warp loss sums (training: two threads per row)
     uint32_t tmem;
     int32_t abort[kTiles];                       // set and read by one warpgroup only
 };
@@ -1085,21 +1085,28 @@ using TcBwdSmem = TcBwdSmemT<kTcTiles>;
 static_assert(sizeof(TcBwdSmem) + 1024 <= 227 * 1024 && 2 * (sizeof(TcBwdSmem) + 1024) > 228 * 1024,
               "design backward: exactly one CTA per SM");
 
-// The training kernel's warpgroups per CTA (a build knob; its registers are
-// 65536 / (128 x tiles)), its TMEM allocation (a power of two), and the
-// guarantee that the CTAs resident on an SM never ask for more than 512
-// columns.
+// The training kernel's 128-row tiles per CTA (a build knob), each carried by
+// two threads per row (256 threads: warps w and w + 4 of a tile read the same
+// TMEM lanes, columns 0..31 and 32..63), its TMEM allocation (a power of
+// two), and the guarantee that the CTAs resident on an SM never ask for more
+// than 512 columns.
 #ifndef SG_TRAIN_TILES
-#define SG_TRAIN_TILES 4
+#define SG_TRAIN_TILES 2
 #endif
 constexpr int kTrainTiles = SG_TRAIN_TILES;
-constexpr int kTrainThreads = kTrainTiles * kTcRows;
+constexpr int kTrainTileThreads = 2 * kTcRows;
+constexpr int kTrainThreads = kTrainTiles * kTrainTileThreads;
 using TcTrainSmem = TcBwdSmemT<kTrainTiles>;
 constexpr uint32_t pow2_cols(uint32_t c) { return c <= 32 ? 32 : (c <= 64 ? 64 : (c <= 128 ? 128 : (c <= 256 ? 256 : 512))); }
 constexpr uint32_t kTrainCols = pow2_cols(kTcCols * kTrainTiles);
 static_assert(kTrainTiles >= 1 && kTcCols * kTrainTiles <= 512, "training tiles fit TMEM");
 static_assert(sizeof(TcTrainSmem) + 1024 <= 227 * 1024, "training CTA fits shared memory");
-static_assert(2 * (sizeof(TcTrainSmem) + 1024) > 228 * 1024 || 2 * kTrainCols <= 512,
+constexpr int kTrainCtasPerSm = (int)((228 * 1024) / (sizeof(TcTrainSmem) + 2048));
+#ifndef SG_TRAIN_MIN_CTAS
+#define SG_TRAIN_MIN_CTAS 2
+#endif
+constexpr int kTrainMinCtas = SG_TRAIN_MIN_CTAS;   // register budget: 65536 / (threads x this)
+static_assert(kTrainCtasPerSm >= 1 && kTrainCtasPerSm * kTrainCols <= 512,
               "resident training CTAs never exceed 512 TMEM columns");
 
 __device__ __forceinline__ uint32_t core_offset16(int r, int k) {    // bytes, 16-wide rows
@@ -1327,14 +1334,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) design_backward_tc_kernel(const
 // The training step's network on tcgen05: per 128-row tile of samples the
 // input rows (hash encoding and geometric features), the forward with the
 // ReLU masks kept as bits, the loss head, the backward through W3^T .. W0^T
-// and the encoding gradient scattered into the table with float2 atomics,
-// four tiles per CTA as in the design kernels. The samples, the loss and the
-// bf16 rows kept for the weight gradient are those of train_kernel (the same
-// row buffers), so wgrad_kernel serves both.
-__global__ void __launch_bounds__(kTrainThreads, 1) train_tc_kernel(const TrainArgs A, int32_t *err) {
+// and the encoding gradient scattered into the table with float2 atomics.
+// Two threads carry a row: the first builds the geometric features, encodes
+// levels 0..7 and runs the loss head, the second encodes levels 8..15; each
+// handles half of the row's 64 accumulator columns in every epilogue and
+// scatters the gradient of its own levels. The samples, the loss and the bf16
+// rows kept for the weight gradient are those of train_kernel (the same row
+// buffers), so wgrad_kernel serves both.
+__device__ __forceinline__ void tile_sync(int g) {
+    asm volatile("bar.sync %0, %1;\n" ::"r"(1 + g), "r"(kTrainTileThreads) : "memory");
+}
+
+__global__ void __launch_bounds__(kTrainThreads, kTrainMinCtas) train_tc_kernel(const TrainArgs A, int32_t *err) {
     extern __shared__ __align__(1024) unsigned char tct_raw[];
     TcTrainSmem &S = *reinterpret_cast<TcTrainSmem *>(tct_raw);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = tid / kTcRows, r = tid % kTcRows;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = tid / kTrainTileThreads, u = tid % kTrainTileThreads;
+    const int wt = u >> 5, hf = wt >> 2, r = (wt & 3) * 32 + lane;   // tile warp, column half, row
     stage_weights_bwd(S, A.Wb, tid, kTrainThreads);
     if (tid == 0) {
         for (int k = 0; k < kTrainTiles; ++k) {
@@ -1353,7 +1369,8 @@ __global__ void __launch_bounds__(kTrainThreads, 1) train_tc_kernel(const TrainA
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = S.tmem + (uint32_t)g * kTcCols;
-    const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    // TMEM lanes 32 (warp % 4) .. of this tile's columns, this thread's half
+    const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(32 * hf);
     const uint32_t mbar = smem_u32(&S.mbar[g]);
     const uint32_t a_addr = smem_u32(S.a[g]), d4_addr = smem_u32(S.d4[g]), w_addr = smem_u32(S.w),
                    wt_addr = smem_u32(S.wt);
@@ -1377,56 +1394,63 @@ __global__ void __launch_bounds__(kTrainThreads, 1) train_tc_kernel(const TrainA
                 t = (int32_t)(((h & 0xFFFFFFFFull) * (uint64_t)n) >> 32);
             }
         }
-        // the input row: hash encoding (entries 0..31) and geometric features
-        const float4 P = A.tex.pos[t], Nt = A.tex.nrm[t];
-        uint16_t x[64];
-        const float D = geometry_row(A.lights[smp], P, Nt, A.tex, x);
+        const float4 P = A.tex.pos[t];
         float xn[3];
         normalised(A.tex, P, xn);
-        uint32_t enc[16];
-#pragma unroll
-        for (int level = 0; level < kLevels; ++level) {
-            const float2 e = encode_level(xn, level, A.table);
-            enc[level] = pack2(e.x, e.y);
-        }
         uint16_t *kept = A.rb.act + i * 64;              // this row of the first product's input
+        // this thread's levels: entries 16 hf .. 16 hf + 15 of the row
+        {
+            uint32_t enc[8];
 #pragma unroll
-        for (int g8 = 0; g8 < 8; ++g8) {
-            uint4 v;
-            if (g8 < 4) {
-                v = make_uint4(enc[4 * g8], enc[4 * g8 + 1], enc[4 * g8 + 2], enc[4 * g8 + 3]);
-            } else {
-                v.x = (uint32_t)x[8 * g8] | ((uint32_t)x[8 * g8 + 1] << 16);
-                v.y = (uint32_t)x[8 * g8 + 2] | ((uint32_t)x[8 * g8 + 3] << 16);
-                v.z = (uint32_t)x[8 * g8 + 4] | ((uint32_t)x[8 * g8 + 5] << 16);
-                v.w = (uint32_t)x[8 * g8 + 6] | ((uint32_t)x[8 * g8 + 7] << 16);
+            for (int q = 0; q < 8; ++q) {
+                const float2 e = encode_level(xn, 8 * hf + q, A.table);
+                enc[q] = pack2(e.x, e.y);
             }
-            if (!valid) v = make_uint4(0, 0, 0, 0);
-            *reinterpret_cast<uint4 *>(arow + core_offset(r, 8 * g8)) = v;
-            if (valid) *reinterpret_cast<uint4 *>(kept + 8 * g8) = v;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const uint4 v = valid ? make_uint4(enc[4 * q], enc[4 * q + 1], enc[4 * q + 2], enc[4 * q + 3])
+                                      : make_uint4(0, 0, 0, 0);
+                *reinterpret_cast<uint4 *>(arow + core_offset(r, 16 * hf + 8 * q)) = v;
+                if (valid) *reinterpret_cast<uint4 *>(kept + 16 * hf + 8 * q) = v;
+            }
+        }
+        float D = 0.0f;
+        if (hf == 0) {   // geometric features, entries 32..63
+            uint16_t x[64];
+            D = geometry_row(A.lights[smp], P, A.tex.nrm[t], A.tex, x);
+#pragma unroll
+            for (int g8 = 4; g8 < 8; ++g8) {
+                uint4 v;
+                v.x = valid ? (uint32_t)x[8 * g8] | ((uint32_t)x[8 * g8 + 1] << 16) : 0u;
+                v.y = valid ? (uint32_t)x[8 * g8 + 2] | ((uint32_t)x[8 * g8 + 3] << 16) : 0u;
+                v.z = valid ? (uint32_t)x[8 * g8 + 4] | ((uint32_t)x[8 * g8 + 5] << 16) : 0u;
+                v.w = valid ? (uint32_t)x[8 * g8 + 6] | ((uint32_t)x[8 * g8 + 7] << 16) : 0u;
+                *reinterpret_cast<uint4 *>(arow + core_offset(r, 8 * g8)) = v;
+                if (valid) *reinterpret_cast<uint4 *>(kept + 8 * g8) = v;
+            }
         }
         proxy_fence();
-        wg_sync(g);
-        uint32_t mask[3][2];
+        tile_sync(g);
+        uint32_t mask[3];
         float o0 = 0.0f, o1 = 0.0f;
         bool ok = true;
         // forward; the activations are also kept as the inputs of products 1..3
         for (int layer = 0; layer < 4 && ok; ++layer) {
             const int N = layer < 3 ? 64 : 16;
-            ok = tc_layer(tmem, a_addr, 1024, w_addr + layer * 8192, 1024, N, 4, mbar, phase, r);
+            ok = tc_layer(tmem, a_addr, 1024, w_addr + layer * 8192, 1024, N, 4, mbar, phase, u);
             if (!ok) S.abort[g] = 1;
-            wg_sync(g);
+            tile_sync(g);
             if (S.abort[g]) { ok = false; break; }
             if (layer < 3) {
                 uint16_t *kl = A.rb.act + (int64_t)(layer + 1) * cap * 64 + i * 64;
-                mask[layer][0] = mask[layer][1] = 0u;
+                mask[layer] = 0u;
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
+                for (int c = 0; c < 2; ++c) {
                     float v[16];
                     tc_ld16(lane_addr + 16 * c, v);
 #pragma unroll
                     for (int k = 0; k < 16; ++k)
-                        if (v[k] > 0.0f) mask[layer][c >> 1] |= 1u << ((c & 1) * 16 + k);
+                        if (v[k] > 0.0f) mask[layer] |= 1u << (16 * c + k);
 #pragma unroll
                     for (int hh = 0; hh < 2; ++hh) {
                         uint4 q;
@@ -1434,11 +1458,12 @@ __global__ void __launch_bounds__(kTrainThreads, 1) train_tc_kernel(const TrainA
                         q.y = pack2(fmaxf(v[8 * hh + 2], 0.0f), fmaxf(v[8 * hh + 3], 0.0f));
                         q.z = pack2(fmaxf(v[8 * hh + 4], 0.0f), fmaxf(v[8 * hh + 5], 0.0f));
                         q.w = pack2(fmaxf(v[8 * hh + 6], 0.0f), fmaxf(v[8 * hh + 7], 0.0f));
-                        *reinterpret_cast<uint4 *>(arow + core_offset(r, 16 * c + 8 * hh)) = q;
-                        if (valid) *reinterpret_cast<uint4 *>(kl + 16 * c + 8 * hh) = q;
+                        const int col = 32 * hf + 16 * c + 8 * hh;
+                        *reinterpret_cast<uint4 *>(arow + core_offset(r, col)) = q;
+                        if (valid) *reinterpret_cast<uint4 *>(kl + col) = q;
                     }
                 }
-            } else {
+            } else if (hf == 0) {
                 float v[16];
                 tc_ld16(lane_addr, v);
                 o0 = v[0];
@@ -1446,11 +1471,11 @@ __global__ void __launch_bounds__(kTrainThreads, 1) train_tc_kernel(const TrainA
             }
             tc_fence_before();
             proxy_fence();
-            wg_sync(g);
+            tile_sync(g);
         }
         if (!ok) break;
         // loss head: weighted squared error of K against the solve's irradiance
-        {
+        if (hf == 0) {
             const float sv = sigmoidf_(o0), sp = softplusf_(o1);
             const float K = sv * D + kRScale * sp;
             const float Eo = valid ? __ldg(A.E_obs + (int64_t)smp * n + t) : 0.0f;
@@ -1458,7 +1483,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) train_tc_kernel(const TrainA
             const float e = K - Eo;
             loss += 0.5 * (double)wgt * (double)e * (double)e * inv_b;
             const float dK = (float)((double)(wgt * e) * inv_b);
-            uint4 q0 = make_uint4(pack2(dK * sv * (1.0f - sv) * D, dK * kRScale * sigmoidf_(o1)), 0u, 0u, 0u);
+            const uint4 q0 = make_uint4(pack2(dK * sv * (1.0f - sv) * D, dK * kRScale * sigmoidf_(o1)), 0u, 0u, 0u);
             const uint4 q1 = make_uint4(0, 0, 0, 0);
             *reinterpret_cast<uint4 *>(drow + core_offset16(r, 0)) = q0;
             *reinterpret_cast<uint4 *>(drow + core_offset16(r, 8)) = q1;
@@ -1469,58 +1494,52 @@ __global__ void __launch_bounds__(kTrainThreads, 1) train_tc_kernel(const TrainA
             }
         }
         proxy_fence();
-        wg_sync(g);
+        tile_sync(g);
         // backward: W3^T (K = 16), then W2^T, W1^T (masked, rounded, kept), W0^T
-        float dX[32];
+        float dX[16];
         for (int layer = 3; layer >= 0 && ok; --layer) {
-            if (layer == 3) ok = tc_layer(tmem, d4_addr, 256, wt_addr + 3 * 8192, 256, 64, 1, mbar, phase, r);
-            else ok = tc_layer(tmem, a_addr, 1024, wt_addr + layer * 8192, 1024, 64, 4, mbar, phase, r);
+            if (layer == 3) ok = tc_layer(tmem, d4_addr, 256, wt_addr + 3 * 8192, 256, 64, 1, mbar, phase, u);
+            else ok = tc_layer(tmem, a_addr, 1024, wt_addr + layer * 8192, 1024, 64, 4, mbar, phase, u);
             if (!ok) S.abort[g] = 1;
-            wg_sync(g);
+            tile_sync(g);
             if (S.abort[g]) { ok = false; break; }
             if (layer > 0) {
-                const int m = layer - 1;          // the mask of the product's input
-                uint16_t *kz = A.rb.dz + (int64_t)m * cap * 64 + i * 64;
+                const uint32_t mk = mask[layer - 1];     // the mask of the product's input
+                uint16_t *kz = A.rb.dz + (int64_t)(layer - 1) * cap * 64 + i * 64;
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
+                for (int c = 0; c < 2; ++c) {
                     float v[16];
                     tc_ld16(lane_addr + 16 * c, v);
 #pragma unroll
                     for (int hh = 0; hh < 2; ++hh) {
                         float z[8];
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            const int col = 16 * c + 8 * hh + k;
-                            z[k] = (mask[m][col >> 5] >> (col & 31)) & 1u ? v[8 * hh + k] : 0.0f;
-                        }
+                        for (int k = 0; k < 8; ++k) z[k] = (mk >> (16 * c + 8 * hh + k)) & 1u ? v[8 * hh + k] : 0.0f;
                         uint4 q;
                         q.x = pack2(z[0], z[1]);
                         q.y = pack2(z[2], z[3]);
                         q.z = pack2(z[4], z[5]);
                         q.w = pack2(z[6], z[7]);
-                        *reinterpret_cast<uint4 *>(arow + core_offset(r, 16 * c + 8 * hh)) = q;
-                        if (valid) *reinterpret_cast<uint4 *>(kz + 16 * c + 8 * hh) = q;
+                        const int col = 32 * hf + 16 * c + 8 * hh;
+                        *reinterpret_cast<uint4 *>(arow + core_offset(r, col)) = q;
+                        if (valid) *reinterpret_cast<uint4 *>(kz + col) = q;
                     }
                 }
             } else {
+                // input entries 16 hf .. 16 hf + 15: the gradient of this thread's levels
                 float v[16];
-                tc_ld16(lane_addr, v);            // input entries 0..15
+                tc_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(16 * hf), v);
 #pragma unroll
                 for (int k = 0; k < 16; ++k) dX[k] = v[k];
-                tc_ld16(lane_addr + 16, v);       // 16..31
-#pragma unroll
-                for (int k = 0; k < 16; ++k) dX[16 + k] = v[k];
             }
             tc_fence_before();
             proxy_fence();
-            wg_sync(g);
+            tile_sync(g);
         }
         if (!ok) break;
-        // encoding gradient: entries 2 level, 2 level + 1
         if (valid) {
 #pragma unroll 1
-            for (int level = 0; level < kLevels; ++level)
-                scatter_level(xn, level, dX[2 * level], dX[2 * level + 1], A.dtable);
+            for (int q = 0; q < 8; ++q) scatter_level(xn, 8 * hf + q, dX[2 * q], dX[2 * q + 1], A.dtable);
         }
     }
     loss = warp_sum_d(loss);
@@ -1568,7 +1587,9 @@ cudaError_t launch_train_tc(const TrainArgs &a, int32_t *err, cudaStream_t s, in
     int dev = 0;
     cudaGetDevice(&dev);
     const int64_t tiles = ((int64_t)a.batch + kTcRows - 1) / kTcRows;
-    const int grid = (int)std::min<int64_t>((tiles + kTrainTiles - 1) / kTrainTiles, (int64_t)train_grid(dev) / 2);
+    // as many CTAs as fit an SM's shared memory (two at two tiles per CTA)
+    const int grid = (int)std::min<int64_t>((tiles + kTrainTiles - 1) / kTrainTiles,
+                                            (int64_t)train_grid(dev) / 2 * kTrainCtasPerSm);
     *grid_out = grid;
     train_tc_kernel<<<grid, kTrainThreads, smem, s>>>(a, err);
     return cudaGetLastError();

@@ -173,8 +173,8 @@ class Surrogate:
         return O, dX, dW
 
     def set_kernels(self, tcgen05: bool = True, train_tcgen05: bool = False):
-        """Design objective on tcgen05 (default) or mma.sync; training
-        network on mma.sync (default, the faster here) or tcgen05."""
+        """Design objective on tcgen05 (default) or warp-level mma.sync;
+        training network on mma.sync (default, measured faster) or tcgen05."""
         flags = (1 if tcgen05 else 0) | (2 if train_tcgen05 else 0)
         self._check(self.lib.sg_set_kernels(self.h, flags))
 
