@@ -167,8 +167,12 @@ def l2_copy_gbs(sizes=(4 << 20, 8 << 20, 16 << 20, 32 << 20), reps=100):
 
 
 def kernel_hash():
-    src = os.path.join(ROOT, "paper_2310_02043_gb300", "csrc", "lt_kernels.cu")
-    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    """Hash of the sources the stored traffic depends on: the tracing kernels
+    and the BVH builder (node visits per segment)."""
+    h = hashlib.sha256()
+    for f in ("lt_kernels.cu", "lt_bvh.cpp"):
+        h.update(open(os.path.join(ROOT, "paper_2310_02043_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def stored_traffic(kernel):

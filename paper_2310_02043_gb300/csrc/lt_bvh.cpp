@@ -1,7 +1,9 @@
 // lt_bvh.cpp -- host builder of the 8-wide BVH the tracing kernels traverse.
 //
-// 1. A binary BVH by binned surface-area heuristic (16 bins along the largest
-//    centroid extent; leaves of at most kLeafMax triangles).
+// 1. A binary BVH by the surface-area heuristic: for nodes of at most
+//    kSahExactMax triangles every split between consecutive centroids along
+//    each axis (exact), above that 256 bins along the largest centroid
+//    extent; leaves of at most kLeafMax triangles.
 // 2. Collapse to 8-wide nodes by the surface-area-optimal distribution of
 //    the 8 slots of every wide node over binary subtrees (dynamic program
 //    over the binary tree, see build_wide_bvh).
@@ -18,6 +20,19 @@
 #include <functional>
 
 #include "lt_internal.h"
+
+// Build knobs: SAH bins of the binary build's large nodes, the largest node
+// split by the exact sweep, and the cost of a triangle test relative to a
+// wide-node visit in the 8-wide collapse.
+#ifndef LT_SAH_BINS
+#define LT_SAH_BINS 256
+#endif
+#ifndef LT_SAH_EXACT_MAX
+#define LT_SAH_EXACT_MAX 4096
+#endif
+#ifndef LT_SAH_TRI_COST
+#define LT_SAH_TRI_COST 0.23
+#endif
 
 namespace lt {
 namespace {
@@ -65,7 +80,10 @@ void build_binary(const float *xyz, int32_t n_tri, Binary *b) {
     struct Job { int32_t node, first, count; };
     std::vector<Job> stack;
     stack.push_back({0, 0, n_tri});
-    constexpr int kBins = 16;
+    constexpr int kBins = LT_SAH_BINS;
+    constexpr int32_t kSahExactMax = LT_SAH_EXACT_MAX;
+    std::vector<int32_t> sweep;          // the node's triangles sorted along one axis (exact sweep)
+    std::vector<double> right_area;      // area of the boxes right of each split (exact sweep)
     while (!stack.empty()) {
         Job j = stack.back();
         stack.pop_back();
@@ -88,7 +106,39 @@ void build_binary(const float *xyz, int32_t n_tri, Binary *b) {
         int32_t mid = j.first + j.count / 2;
         int32_t *beg = b->idx.data() + j.first, *end = beg + j.count;
         bool split_done = false;
-        if (ext[axis] > 0.0f) {
+        auto by_centroid = [&](int a) {
+            return [&cen, a](int32_t x, int32_t y) {
+                const float cx = cen[3 * (size_t)x + a], cy = cen[3 * (size_t)y + a];
+                return cx < cy || (cx == cy && x < y);
+            };
+        };
+        if (j.count <= kSahExactMax) {
+            // every split between consecutive centroids along each axis
+            double best = 1e300;
+            int best_axis = -1;
+            int32_t best_i = -1;
+            sweep.assign(beg, end);
+            right_area.resize((size_t)j.count);
+            for (int a = 0; a < 3; ++a) {
+                std::sort(sweep.begin(), sweep.end(), by_centroid(a));
+                Box acc;
+                for (int32_t i = j.count - 1; i > 0; --i) {
+                    acc.grow(tbox[sweep[i]]);
+                    right_area[i] = acc.area();
+                }
+                Box lacc;
+                for (int32_t i = 1; i < j.count; ++i) {
+                    lacc.grow(tbox[sweep[i - 1]]);
+                    const double cost = lacc.area() * i + right_area[i] * (j.count - i);
+                    if (cost < best) { best = cost; best_axis = a; best_i = i; }
+                }
+            }
+            if (best_axis >= 0) {
+                std::sort(beg, end, by_centroid(best_axis));
+                mid = j.first + best_i;
+                split_done = true;
+            }
+        } else if (ext[axis] > 0.0f) {
             Box bin_box[kBins];
             int32_t bin_cnt[kBins] = {0};
             const float inv = (float)kBins / ext[axis];
@@ -129,10 +179,7 @@ void build_binary(const float *xyz, int32_t n_tri, Binary *b) {
         }
         if (!split_done) {
             // all centroids in one bin: split at the median along the axis
-            std::nth_element(beg, b->idx.data() + mid, end, [&](int32_t x, int32_t y) {
-                float cx = cen[3 * (size_t)x + axis], cy = cen[3 * (size_t)y + axis];
-                return cx < cy || (cx == cy && x < y);
-            });
+            std::nth_element(beg, b->idx.data() + mid, end, by_centroid(axis));
         }
         int32_t l = (int32_t)b->nodes.size();
         b->nodes.emplace_back();
@@ -217,7 +264,7 @@ bool build_wide_bvh(const float *xyz, int32_t n_tri, BvhBuild *out, std::string 
     struct Wide { std::vector<Entry> kids; };
     std::vector<Wide> wide;
     {
-        constexpr double kNodeCost = 1.0, kTriCost = 0.23;
+        constexpr double kNodeCost = 1.0, kTriCost = LT_SAH_TRI_COST;
         const int32_t NB = (int32_t)b.nodes.size();
         std::vector<std::array<double, kWide + 1>> C(NB), D(NB);
         std::vector<std::array<int8_t, kWide + 1>> split(NB), open(NB);
