@@ -73,6 +73,40 @@ def test_batch_designs_equal_single_design_passes(setup):
     tr.set_design(0)
 
 
+def test_batch_with_point_spot_and_area_lights(setup):
+    # designs of mixed luminaire kinds (area lights draw their origin from
+    # Philox lanes 2-3): each design equals its single-design pass
+    tr, sc, target, designs = setup
+    mixed = [scenes.make_lights([scenes.point_light((4.0, 3.0, 2.7), 30.0),
+                                 scenes.area_light((10.0, 5.0, 2.95), 0.0, -np.pi / 2, 400.0, 1.2, 0.6)]),
+             scenes.make_lights([scenes.area_light((6.0, 7.0, 2.95), 0.5, -np.pi / 2 + 0.1, 300.0, 0.6, 0.6),
+                                 scenes.spot_light((15.0, 4.0, 2.8), 0.3, -1.4, 40.0, 0.6, 1.0),
+                                 scenes.area_light((3.0, 2.0, 2.95), 1.0, -np.pi / 2, 200.0, 1.0, 0.3)])]
+    counts = [len(L) for L in mixed]
+    tr.batch_setup(counts, N, HITS)
+    tr.batch_set_lights(np.concatenate(mixed))
+    loss, grad = tr.batch_step(31, 32)
+    off = 0
+    for d, L in enumerate(mixed):
+        Eb = tr.batch_irradiance(d).astype(np.float64)
+        E, O, g = _single(tr, L, d, 31, 32)
+        E = E.astype(np.float64)
+        diff = np.abs(Eb - E)
+        assert np.all(diff <= 1e-6 * np.abs(E) + 1e-9 * E.max()), d
+        assert loss[d] == pytest.approx(O, rel=1e-9), d
+        gb = grad[off:off + len(L)]
+        assert np.allclose(gb, g, rtol=1e-6, atol=1e-9 * np.abs(g).max()), d
+        # slots that exist for each kind: orientation for spots and area
+        # lights, cone angles for spots only
+        kinds = L[:, 0]
+        assert np.all(np.abs(gb[:, [0, 1, 2, 5]]) > 0), d
+        assert np.all(np.abs(gb[kinds != scenes.POINT][:, [3, 4]]) > 0), d
+        assert np.all(gb[kinds == scenes.POINT][:, [3, 4]] == 0), d
+        assert np.all(gb[kinds != scenes.SPOT][:, 6:] == 0), d
+        off += len(L)
+    tr.set_design(0)
+
+
 def test_graph_replay_equals_eager(setup):
     tr, sc, target, designs = setup
     tr.batch_setup(COUNTS, N, HITS)
