@@ -485,16 +485,33 @@ int sg_design(void *ctx, const lt_light *lights, int32_t n_lights, const float *
     SG_CUDA(c, cudaSetDevice(c->device));
     if ((rc = design_prepare(c, lights, n_lights))) return rc;
     SG_CUDA(c, ensure(c->d_up, c->up_floats, (size_t)c->n_pad));
-    const int64_t tpl = c->n_pad / 16;
-    SG_CUDA(c, ensure(c->d_gpart, c->gpart_floats, (size_t)n_lights * (size_t)tpl * 8));
     if (!c->d_dout) SG_CUDA(c, dalloc(c->d_dout, (size_t)LT_MAX_LIGHTS * 8 + 8));
-    const DesignArgs a = design_args(c, n_lights);
-    if ((rc = forward_rows(c, a))) return rc;
-    SG_CUDA(c, launch_design_reduce(a.tex, c->d_dl, n_lights, c->d_K, E_target, alpha, E_out, c->d_up, c->d_lpart,
-                                    c->stream));
-    if (c->use_tc) SG_CUDA(c, launch_design_backward_tc(a, c->d_err, c->stream));
-    else SG_CUDA(c, launch_design_backward(a, c->stream));
-    SG_CUDA(c, launch_design_final(c->d_gpart, c->d_dl, n_lights, tpl, c->d_lpart, c->d_dout, c->stream));
+    if (c->use_tc && n_lights <= kFusedMaxLights) {
+        // one kernel: forward, per-texel irradiance and weights, backward
+        FusedArgs f;
+        f.target = E_target;
+        f.alpha = alpha;
+        f.E_out = E_out;
+        f.loss_part = c->d_lpart;
+        f.texels_per_tile = 128 / n_lights;
+        f.n_tiles = (c->n_pad + f.texels_per_tile - 1) / f.texels_per_tile;
+        SG_CUDA(c, ensure(c->d_gpart, c->gpart_floats, (size_t)n_lights * (size_t)f.n_tiles * 8));
+        const DesignArgs a = design_args(c, n_lights);
+        int grid = 0;
+        SG_CUDA(c, launch_design_fused_tc(a, f, c->d_err, c->stream, &grid));
+        SG_CUDA(c, launch_design_final(c->d_gpart, c->d_dl, n_lights, f.n_tiles, c->d_lpart, grid, c->d_dout,
+                                       c->stream));
+    } else {
+        const int64_t tpl = c->n_pad / 16;
+        SG_CUDA(c, ensure(c->d_gpart, c->gpart_floats, (size_t)n_lights * (size_t)tpl * 8));
+        const DesignArgs a = design_args(c, n_lights);
+        if ((rc = forward_rows(c, a))) return rc;
+        SG_CUDA(c, launch_design_reduce(a.tex, c->d_dl, n_lights, c->d_K, E_target, alpha, E_out, c->d_up,
+                                        c->d_lpart, c->stream));
+        if (c->use_tc) SG_CUDA(c, launch_design_backward_tc(a, c->d_err, c->stream));
+        else SG_CUDA(c, launch_design_backward(a, c->stream));
+        SG_CUDA(c, launch_design_final(c->d_gpart, c->d_dl, n_lights, tpl, c->d_lpart, 0, c->d_dout, c->stream));
+    }
     double *h = c->h_pinned + (n_lights * sizeof(LightC) + sizeof(double) - 1) / sizeof(double);
     SG_CUDA(c, cudaMemcpyAsync(h, c->d_dout, ((size_t)n_lights * 8 + 1) * sizeof(double), cudaMemcpyDeviceToHost,
                                c->stream));

@@ -91,6 +91,20 @@ struct DesignArgs {
     float *gpart;             // [lights][T_pad / 16][8] (backward)
 };
 
+// The fused design objective (one kernel for forward, per-texel irradiance,
+// objective, weights and backward) serves designs of at most this many lights.
+constexpr int kFusedMaxLights = 32;
+struct FusedArgs {
+    const float *target;      // [n] E*
+    const float *alpha;       // [n] or null (ones)
+    float *E_out;             // [n] or null
+    double *loss_part;        // [grid] objective partials
+    int32_t texels_per_tile;  // 128 / n_lights
+    int64_t n_tiles;          // ceil(n_pad / texels_per_tile); gpart is [lights][n_tiles][8]
+};
+cudaError_t launch_design_fused_tc(const DesignArgs &a, const FusedArgs &f, int32_t *err, cudaStream_t s,
+                                   int *grid_out);
+
 cudaError_t launch_train(const TrainArgs &a, int grid, cudaStream_t s);
 // tcgen05 training kernel; *grid_out = its grid (the number of loss partials)
 cudaError_t launch_train_tc(const TrainArgs &a, int32_t *err, cudaStream_t s, int *grid_out);
@@ -111,8 +125,10 @@ cudaError_t launch_design_reduce(const TexelView &t, const LightC *lights, int32
                                  double *loss_part, cudaStream_t s);
 cudaError_t launch_design_backward(const DesignArgs &a, cudaStream_t s);
 cudaError_t launch_design_backward_tc(const DesignArgs &a, int32_t *err, cudaStream_t s);
+// Per-light sums of gpart [lights][tiles_per_light][8] and the objective (the
+// sum of n_loss_part partials; 0 = those of launch_design_reduce).
 cudaError_t launch_design_final(const float *gpart, const LightC *lights, int32_t n_lights, int64_t tiles_per_light,
-                                const double *loss_part, double *out, cudaStream_t s);
+                                const double *loss_part, int32_t n_loss_part, double *out, cudaStream_t s);
 int train_grid(int device);
 constexpr int kReduceBlocks = 256;   // blocks of the design reduce kernel (loss partials)
 

@@ -804,13 +804,13 @@ __global__ void __launch_bounds__(kMlpWarps * 32, 2) design_backward_kernel(cons
 
 __global__ void design_final_kernel(const float *__restrict__ gpart, const LightC *__restrict__ lights,
                                     int32_t n_lights, int64_t tpl, const double *__restrict__ loss_part,
-                                    double *__restrict__ out) {
+                                    int32_t n_loss_part, double *__restrict__ out) {
     __shared__ double red[7][256];
     const int l = blockIdx.x;
     if (l == n_lights) {   // the objective
         double s = 0.0;
         if (threadIdx.x == 0) {
-            for (int k = 0; k < kReduceBlocks; ++k) s += loss_part[k];
+            for (int k = 0; k < n_loss_part; ++k) s += loss_part[k];
             out[(int64_t)n_lights * 8] = s;
         }
         return;
@@ -1331,6 +1331,226 @@ __global__ void __launch_bounds__(kTcThreads, 1) design_backward_tc_kernel(const
                      : "memory");
 }
 
+// The design objective in one kernel for up to kFusedMaxLights lights: a
+// 128-row tile holds all lights of 128 / n texels (row = texel x n + light),
+// so after the forward the tile forms each texel's irradiance E_t (the sum
+// over its rows in light order), the objective's share and the weight
+// u_t = A_t alpha_t (E_t - E*_t) itself, and goes straight into the backward
+// without recomputing the forward; the per-light gradient sums over the
+// tile's texels go to gpart[light][tile].
+__global__ void __launch_bounds__(kTcThreads, 1) design_fused_tc_kernel(const DesignArgs A, const FusedArgs F,
+                                                                       int32_t *err) {
+    extern __shared__ __align__(1024) unsigned char tcb_raw[];
+    TcBwdSmem &S = *reinterpret_cast<TcBwdSmem *>(tcb_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = tid / kTcRows, r = tid % kTcRows;
+    stage_weights_bwd(S, A.Wb, tid, kTcThreads);
+    if (tid == 0) {
+        for (int k = 0; k < kTcTiles; ++k) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&S.mbar[k])) : "memory");
+            S.abort[k] = 0;
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&S.tmem)),
+                     "r"(kTcCols * kTcTiles)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem + (uint32_t)g * kTcCols;
+    const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    const uint32_t mbar = smem_u32(&S.mbar[g]);
+    const uint32_t a_addr = smem_u32(S.a[g]), d4_addr = smem_u32(S.d4[g]), w_addr = smem_u32(S.w),
+                   wt_addr = smem_u32(S.wt);
+    const int nl = A.n_lights, tpt = F.texels_per_tile;
+    const int tl = r / nl, l_row = r % nl;                  // this row: texel tl of the tile, light l_row
+    uint32_t phase = 0;
+    double loss = 0.0;
+    float *scr = reinterpret_cast<float *>(S.a[g]);         // free between the forward and the backward
+    float *gsum = reinterpret_cast<float *>(S.d4[g]);       // free after the backward's first product
+    unsigned char *arow = reinterpret_cast<unsigned char *>(S.a[g]), *drow = reinterpret_cast<unsigned char *>(S.d4[g]);
+    for (int64_t tile = (int64_t)blockIdx.x * kTcTiles + g; tile < F.n_tiles; tile += (int64_t)gridDim.x * kTcTiles) {
+        const int64_t tt = tile * tpt + tl;
+        const bool valid = tl < tpt && tt < A.tex.n_pad;
+        const int l = valid ? l_row : 0;
+        const int64_t t = valid ? tt : 0;
+        const LightC &L = A.lights[l];
+        const float4 P = A.tex.pos[t], Nt = A.tex.nrm[t];
+        uint16_t x[64];
+        const float D = geometry_row(L, P, Nt, A.tex, x);
+        const uint4 *enc = reinterpret_cast<const uint4 *>(A.enc + t * 32);
+#pragma unroll
+        for (int g8 = 0; g8 < 4; ++g8)
+            *reinterpret_cast<uint4 *>(arow + core_offset(r, 8 * g8)) = valid ? enc[g8] : make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int g8 = 4; g8 < 8; ++g8) {
+            uint4 v;
+            v.x = valid ? (uint32_t)x[8 * g8] | ((uint32_t)x[8 * g8 + 1] << 16) : 0u;
+            v.y = valid ? (uint32_t)x[8 * g8 + 2] | ((uint32_t)x[8 * g8 + 3] << 16) : 0u;
+            v.z = valid ? (uint32_t)x[8 * g8 + 4] | ((uint32_t)x[8 * g8 + 5] << 16) : 0u;
+            v.w = valid ? (uint32_t)x[8 * g8 + 6] | ((uint32_t)x[8 * g8 + 7] << 16) : 0u;
+            *reinterpret_cast<uint4 *>(arow + core_offset(r, 8 * g8)) = v;
+        }
+        proxy_fence();
+        wg_sync(g);
+        uint32_t mask[3][2];
+        float o0 = 0.0f, o1 = 0.0f;
+        bool ok = true;
+        // forward
+        for (int layer = 0; layer < 4 && ok; ++layer) {
+            const int N = layer < 3 ? 64 : 16;
+            ok = tc_layer(tmem, a_addr, 1024, w_addr + layer * 8192, 1024, N, 4, mbar, phase, r);
+            if (!ok) S.abort[g] = 1;
+            wg_sync(g);
+            if (S.abort[g]) { ok = false; break; }
+            if (layer < 3) {
+                mask[layer][0] = mask[layer][1] = 0u;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float v[16];
+                    tc_ld16(lane_addr + 16 * c, v);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        if (v[i] > 0.0f) mask[layer][c >> 1] |= 1u << ((c & 1) * 16 + i);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        uint4 q;
+                        q.x = pack2(fmaxf(v[8 * h], 0.0f), fmaxf(v[8 * h + 1], 0.0f));
+                        q.y = pack2(fmaxf(v[8 * h + 2], 0.0f), fmaxf(v[8 * h + 3], 0.0f));
+                        q.z = pack2(fmaxf(v[8 * h + 4], 0.0f), fmaxf(v[8 * h + 5], 0.0f));
+                        q.w = pack2(fmaxf(v[8 * h + 6], 0.0f), fmaxf(v[8 * h + 7], 0.0f));
+                        *reinterpret_cast<uint4 *>(arow + core_offset(r, 16 * c + 8 * h)) = q;
+                    }
+                }
+            } else {
+                float v[16];
+                tc_ld16(lane_addr, v);
+                o0 = v[0];
+                o1 = v[1];
+            }
+            tc_fence_before();
+            proxy_fence();
+            wg_sync(g);
+        }
+        if (!ok) break;
+        // loss head: dO/do of the row
+        const float sg0 = sigmoidf_(o0);
+        const float K = sg0 * D + kRScale * softplusf_(o1);
+        // the texel's irradiance E_t = sum_l I_l K(t, l), summed in light order
+        scr[r] = valid ? L.intensity * K : 0.0f;
+        wg_sync(g);
+        float u = 0.0f;
+        if (valid) {
+            float E = 0.0f;
+            for (int q = 0; q < nl; ++q) E += scr[tl * nl + q];
+            if (t < A.tex.n) {
+                const float d = E - F.target[t];
+                const float w = (F.alpha ? F.alpha[t] : 1.0f) * d;
+                u = A.tex.area[t] * w;
+                if (l == 0) {
+                    loss += 0.5 * (double)u * (double)d;
+                    if (F.E_out) F.E_out[t] = E;
+                }
+            }
+        }
+        const float ui = u * L.intensity;
+        const float gD = ui * sg0, gI = u * K;
+        {
+            uint4 q0, q1 = make_uint4(0, 0, 0, 0);
+            q0.x = pack2(ui * sg0 * (1.0f - sg0) * D, ui * kRScale * sigmoidf_(o1));
+            q0.y = q0.z = q0.w = 0u;
+            *reinterpret_cast<uint4 *>(drow + core_offset16(r, 0)) = q0;
+            *reinterpret_cast<uint4 *>(drow + core_offset16(r, 8)) = q1;
+        }
+        proxy_fence();
+        wg_sync(g);
+        // backward: W3^T (K = 16), then W2^T, W1^T (masked, rounded), W0^T
+        float gX[kGeom];
+        for (int layer = 3; layer >= 0 && ok; --layer) {
+            if (layer == 3) ok = tc_layer(tmem, d4_addr, 256, wt_addr + 3 * 8192, 256, 64, 1, mbar, phase, r);
+            else ok = tc_layer(tmem, a_addr, 1024, wt_addr + layer * 8192, 1024, 64, 4, mbar, phase, r);
+            if (!ok) S.abort[g] = 1;
+            wg_sync(g);
+            if (S.abort[g]) { ok = false; break; }
+            if (layer > 0) {
+                const int m = layer - 1;          // the mask of the product's input
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float v[16];
+                    tc_ld16(lane_addr + 16 * c, v);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        float z[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int col = 16 * c + 8 * h + i;
+                            z[i] = (mask[m][col >> 5] >> (col & 31)) & 1u ? v[8 * h + i] : 0.0f;
+                        }
+                        uint4 q;
+                        q.x = pack2(z[0], z[1]);
+                        q.y = pack2(z[2], z[3]);
+                        q.z = pack2(z[4], z[5]);
+                        q.w = pack2(z[6], z[7]);
+                        *reinterpret_cast<uint4 *>(arow + core_offset(r, 16 * c + 8 * h)) = q;
+                    }
+                }
+            } else {
+                float v[16];
+                tc_ld16(lane_addr + 32, v);       // input entries 32..47
+#pragma unroll
+                for (int i = 0; i < 16; ++i) gX[i] = v[i];
+                tc_ld16(lane_addr + 48, v);       // 48..63
+                gX[16] = v[0];
+            }
+            tc_fence_before();
+            proxy_fence();
+            wg_sync(g);
+        }
+        if (!ok) break;
+        float gs[7] = {0, 0, 0, 0, 0, 0, 0};
+        if (valid) {
+            float gr[6];
+            geometry_grad(L, P, Nt, A.tex, gX, gD, gr);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) gs[k] = gr[k];
+            gs[6] = gI;
+        }
+        // per-light sums over the tile's texels, in texel order
+#pragma unroll
+        for (int k = 0; k < 7; ++k) gsum[r * 8 + k] = gs[k];
+        wg_sync(g);
+        if (r < nl) {
+            float acc[7] = {0, 0, 0, 0, 0, 0, 0};
+            for (int q = 0; q < tpt; ++q)
+#pragma unroll
+                for (int k = 0; k < 7; ++k) acc[k] += gsum[(q * nl + r) * 8 + k];
+            float *out = A.gpart + ((int64_t)r * F.n_tiles + tile) * 8;
+#pragma unroll
+            for (int k = 0; k < 7; ++k) out[k] = acc[k];
+            out[7] = 0.0f;
+        }
+        wg_sync(g);
+    }
+    loss = warp_sum_d(loss);
+    if (lane == 0) S.red[warp] = loss;
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < kTcThreads / 32; ++w) sum += S.red[w];
+        F.loss_part[blockIdx.x] = sum;
+        int32_t any = 0;
+        for (int k = 0; k < kTcTiles; ++k) any |= S.abort[k];
+        if (any) atomicOr(err, kErrTc);
+    }
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(S.tmem), "r"(kTcCols * kTcTiles)
+                     : "memory");
+}
+
 // The training step's network on tcgen05: per 128-row tile of samples the
 // input rows (hash encoding and geometric features), the forward with the
 // ReLU masks kept as bits, the loss head, the backward through W3^T .. W0^T
@@ -1684,6 +1904,20 @@ cudaError_t launch_design_backward_tc(const DesignArgs &a, int32_t *err, cudaStr
     return cudaGetLastError();
 }
 
+cudaError_t launch_design_fused_tc(const DesignArgs &a, const FusedArgs &f, int32_t *err, cudaStream_t s,
+                                   int *grid_out) {
+    const size_t smem = sizeof(TcBwdSmem) + 1024;
+    cudaError_t e = set_smem((const void *)design_fused_tc_kernel, smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    // one CTA per SM (shared memory admits no second), as the design backward
+    const int grid = (int)std::min<int64_t>((f.n_tiles + kTcTiles - 1) / kTcTiles, (int64_t)train_grid(dev) / 2);
+    *grid_out = grid;
+    design_fused_tc_kernel<<<grid, kTcThreads, smem, s>>>(a, f, err);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_design_backward(const DesignArgs &a, cudaStream_t s) {
     const size_t smem = smem_bytes(true);
     cudaError_t e = set_smem((const void *)design_backward_kernel, smem);
@@ -1693,8 +1927,9 @@ cudaError_t launch_design_backward(const DesignArgs &a, cudaStream_t s) {
 }
 
 cudaError_t launch_design_final(const float *gpart, const LightC *lights, int32_t n_lights, int64_t tiles_per_light,
-                                const double *loss_part, double *out, cudaStream_t s) {
-    design_final_kernel<<<n_lights + 1, 256, 0, s>>>(gpart, lights, n_lights, tiles_per_light, loss_part, out);
+                                const double *loss_part, int32_t n_loss_part, double *out, cudaStream_t s) {
+    design_final_kernel<<<n_lights + 1, 256, 0, s>>>(gpart, lights, n_lights, tiles_per_light, loss_part,
+                                                     n_loss_part > 0 ? n_loss_part : kReduceBlocks, out);
     return cudaGetLastError();
 }
 

@@ -223,12 +223,15 @@ def test_training_fits_a_smooth_response(sg):
     assert np.mean(losses[-20:]) < 0.1 * np.mean(losses[:5]), (losses[:5], losses[-5:])
 
 
-@pytest.mark.parametrize("n_texels,powers", [(5003, [1.5, 1.0, 2.0, 0.7, 1.2]), (301, [1.3, 0.8])])
+@pytest.mark.parametrize("n_texels,powers", [(5003, [1.5, 1.0, 2.0, 0.7, 1.2]), (301, [1.3, 0.8]),
+                                             (301, list(np.linspace(0.6, 1.8, 40)))])
 def test_tensor_core_paths_agree(sg, n_texels, powers):
     # tcgen05 (TMEM accumulators, 128-row tiles, four per CTA) and mma.sync
     # (16 rows per warp) run the same network on the same bf16 inputs; only
-    # the order of the fp32 sums differs. 301 texels x 2 lights make 5 tiles:
-    # the second CTA has one tile and three idle warpgroups.
+    # the order of the fp32 sums differs. Up to 32 lights the tcgen05 design
+    # runs as one fused kernel (2 lights: 64 texels per tile, 5 tiles, the
+    # second CTA with three idle warpgroups); 40 lights take the four-kernel
+    # tcgen05 path.
     import torch
     x, nt, area, lo, ext, inv_ext, lights, W, table = _problem(12, n_texels, len(powers))
     lights = lights.copy()
