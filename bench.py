@@ -655,7 +655,7 @@ def run_surrogate(args):
     design_ms_mma = a.elapsed_time(b) / n_rep
     sg.set_kernels()
     rows = 16 * ((T + 15) // 16 * 16)
-    design_flops = rows * SG_FWD_FLOPS * 3
+    design_flops = rows * SG_FWD_FLOPS * 2   # forward + the input gradient (no weight gradient)
     peaks = json.load(open(MEASURED_PEAKS)) if os.path.exists(MEASURED_PEAKS) else {}
     peak = peaks.get("bf16_tflops", 1900.0)
     a.record(stream)
