@@ -213,13 +213,15 @@ struct Trav {
     int32_t steps;
     int32_t leaf_node;  // node whose hit leaf children are pending
     uint32_t leaves;    // pending leaf children of leaf_node (slot order)
+    int32_t leaf_node2; // a second node with pending leaves (speculative node steps only)
+    uint32_t leaves2;
     Trail<kDeep> trail;
 };
 constexpr uint32_t kFresh = 0x1ffu;
 
 template <bool kDeep>
 __device__ __forceinline__ void trav_init(Trav<kDeep> &s, Hit &h) {
-    s.node = 0; s.mask = kFresh; s.lvl = 0; s.steps = 0; s.leaf_node = 0; s.leaves = 0;
+    s.node = 0; s.mask = kFresh; s.lvl = 0; s.steps = 0; s.leaf_node = 0; s.leaves = 0; s.leaf_node2 = 0; s.leaves2 = 0;
     s.trail = Trail<kDeep>();
     h.tri = -1; h.prim = INT32_MAX; h.t = FLT_MAX; h.b0 = h.b1 = h.b2 = 0.0f;
 }
@@ -308,14 +310,17 @@ __device__ __forceinline__ void node_step(const TraceParams &P, const float4 *sm
     if (kCount) work.nodes += 1;
     if (++s.steps > P.max_steps) {
         atomicOr(P.err, kErrSteps);
-        s.node = -1; s.leaves = 0; h.tri = -1;
+        s.node = -1; s.leaves = 0; s.leaves2 = 0; h.tri = -1;
         return;
     }
     const uint32_t hit = test_node<kSmem>(P, smem, s.node, r, h.t);
     const uint32_t inner = (uint32_t)node_word<kSmem>(P, smem, s.node, 56);
     if (s.mask == kFresh) {
         const uint32_t leaves = hit & ~inner;
-        if (leaves) { s.leaf_node = s.node; s.leaves = leaves; }
+        if (leaves) {   // the second slot is taken only by a speculative step (first slot busy)
+            if (!kSmem || s.leaves == 0) { s.leaf_node = s.node; s.leaves = leaves; }
+            else { s.leaf_node2 = s.node; s.leaves2 = leaves; }
+        }
     }
     const uint32_t cand = order_mask(hit & inner, r.octant) & s.mask;
     if (cand) {
@@ -325,7 +330,7 @@ __device__ __forceinline__ void node_step(const TraceParams &P, const float4 *sm
         s.mask = kFresh;
         if (++s.lvl >= (kDeep ? kMaxDepth : kShallowDepth)) {
             atomicOr(P.err, kErrDepth);
-            s.node = -1; s.leaves = 0; h.tri = -1;
+            s.node = -1; s.leaves = 0; s.leaves2 = 0; h.tri = -1;
         }
         return;
     }
@@ -350,6 +355,7 @@ __device__ __forceinline__ void leaf_step(const TraceParams &P, const float4 *sm
     const int k = __ffs(s.leaves) - 1;
     s.leaves &= s.leaves - 1;
     const int32_t code = -1 - child_word<kSmem>(P, smem, s.leaf_node, k);
+    if (kSmem && s.leaves == 0 && s.leaves2 != 0) { s.leaf_node = s.leaf_node2; s.leaves = s.leaves2; s.leaves2 = 0; }
     const int32_t first = code >> 2, count = (code & 3) + 1;
     for (int32_t i = first; i < first + count; ++i) {
         const float4 *tp = reinterpret_cast<const float4 *>(P.tris + i);
@@ -683,8 +689,14 @@ __global__ void __launch_bounds__(kSmem ? kThreadsStaged : kThreadsL1, kTraceMin
             if ((threadIdx.x & 31) == 0) atomicOr(P.err, kErrSteps);
             break;
         }
+        // With the BVH staged, a lane whose first leaf slot is busy still
+        // takes node steps while its second slot is free (speculative
+        // traversal, Aila and Laine, HPG 2009): node steps run with more
+        // lanes, at the price of culling against an older closest hit.
+        // Nodes read through L1 make that price higher than the gain, so
+        // those kernels step a lane's leaves first.
         const bool can_leaf = active && s.leaves != 0;
-        const bool can_node = active && !can_leaf && s.node >= 0;
+        const bool can_node = active && (kSmem ? s.leaves2 == 0 : !can_leaf) && s.node >= 0;
         const bool fin = active && !can_leaf && s.node < 0;
         const unsigned bl = __ballot_sync(kFull, can_leaf);
         const unsigned bn = __ballot_sync(kFull, can_node);
