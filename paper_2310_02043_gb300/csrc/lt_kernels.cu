@@ -34,6 +34,9 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kThreadsStaged = LT_THREADS_STAGED;
 constexpr int kThreadsL1 = LT_THREADS_L1;
 constexpr int kTraceMinBlocks = LT_MIN_BLOCKS;   // resident blocks per SM the register budget targets
+// Lanes by which a node step may trail leaf steps in a vote and still run
+// (staged kernels; 4, 8 and 16 measured, 8 best).
+constexpr int kNodeBias = 8;
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC 2011).
@@ -703,11 +706,19 @@ __global__ void __launch_bounds__(kSmem ? kThreadsStaged : kThreadsL1, kTraceMin
         const unsigned bf = __ballot_sync(kFull, fin);
         if ((bl | bn | bf) == 0u) break;
         const int nl = __popc(bl), nn = __popc(bn), nf = __popc(bf);
-        // The step kind with the most waiting lanes runs; it always has at
-        // least one lane, so every iteration advances some lane.
-        if (nn >= nl && nn >= nf) {
+        // The step kind with the most waiting lanes runs; in the staged
+        // kernels node steps win ties with leaf steps up to kNodeBias lanes
+        // (lanes with pending leaves can take either there). The chosen kind
+        // always has a lane, so every iteration advances some lane.
+        const int bias = kSmem ? kNodeBias : 0;
+        int kind;
+        if (nn > 0 && nn + bias >= nl && nn >= nf) kind = 0;
+        else if (nl > 0 && nl >= nf) kind = 1;
+        else if (nf > 0) kind = 2;
+        else kind = nn > 0 ? 0 : 1;
+        if (kind == 0) {
             if (can_node) node_step<kCount, kSmem, kDeep>(P, smem, r, s, h, work);
-        } else if (nl >= nf) {
+        } else if (kind == 1) {
             if (can_leaf) leaf_step<kCount, kSmem, kDeep>(P, smem, r, s, h, skip, work);
         } else if (fin) {
             // Finish the segment (one traced ray, hit or miss), then start the
