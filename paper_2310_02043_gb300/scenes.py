@@ -296,6 +296,20 @@ def plane(half: float = 1.0, res: int = 16, albedo: float = 0.5, z: float = 0.0)
     return b.build("plane", half=half, res=res)
 
 
+def occluded_plane(half: float = 1.5, res: int = 8, occ_z: float = 0.4, occ_centre=(0.1, 0.0),
+                   occ_half: float = 0.25, albedo: float = 0.5) -> Scene:
+    """The plane z = 0 over [-half, half]^2 (res x res texels, the first
+    res^2 texels) under a horizontal square occluder of half size occ_half
+    centred at (occ_centre, occ_z) (2 x 2 texels): a light above casts a
+    shadow whose outline moves with it."""
+    b = _Builder()
+    b.quad([-half, -half, 0.0], [2 * half, 0, 0], [0, 2 * half, 0], res, res, albedo)
+    cx, cy = occ_centre
+    b.quad([cx - occ_half, cy - occ_half, occ_z], [2 * occ_half, 0, 0], [0, 2 * occ_half, 0], 2, 2, albedo)
+    return b.build("occluded_plane", half=half, res=res, occ_z=occ_z, occ_centre=tuple(occ_centre),
+                   occ_half=occ_half)
+
+
 def closed_cube(size: float = 1.0, res: int = 8, albedo: float = 0.5) -> Scene:
     """Closed cube [0, size]^3, 6 quads, uniform albedo (no ray escapes)."""
     b = _Builder()
