@@ -176,3 +176,42 @@ def test_sphere_direct_is_solid_angle_and_second_hit_is_uniform():
     sigma = rho * phi * np.sqrt(np.maximum(c2, 1)) / A
     chi2 = np.mean(((E2 - mean) / sigma) ** 2)
     assert 0.8 < chi2 < 1.3, chi2
+
+
+def test_sphere_interreflection_is_the_geometric_series():
+    """Inside a diffuse sphere every reflected photon lands uniformly per unit
+    area, whatever its origin, so with B hits each texel holds its direct
+    irradiance plus (4 pi I / A_sphere) (rho + ... + rho^(B-1)), which tends to
+    the direct term plus rho / (1 - rho) of the mean: the 1 / (1 - rho)
+    interreflection of Eq. 7 applied at every hit.
+
+    A bounce ray starts at the hit point without an offset, and a hit point
+    computed from a float distance can land a rounding error outside the
+    surface; near an edge, a grazing bounce towards the neighbouring face can
+    then leave the closed mesh (about one segment in a million here). The
+    energy identity is checked exactly against the hits each photon made."""
+    R, rho, I, B = 1.0, 0.5, 1.0, 12
+    sc = scenes.icosphere(radius=R, subdiv=3, albedo=rho)
+    pos = np.array([-0.25, 0.4, 0.1])
+    L = scenes.make_lights([scenes.point_light(pos, I)])
+    n = 1 << 18
+    r1 = oracle.forward(sc, L, seed=9, n_photons=n, max_hits=1)
+    rB = oracle.forward(sc, L, seed=9, n_photons=n, max_hits=B)
+    tri, _ = oracle.paths(sc, L, 9, n, B, 0, n)
+    hits = np.sum(tri >= 0, axis=1)
+    assert np.all(tri[np.arange(B)[None, :] >= hits[:, None]] < 0)      # a path ends at its first miss
+    assert np.all(hits >= 1) and np.sum(B - hits) <= 1e-5 * n * B       # escapes are rare
+    A = sc.tile_area
+    phi = I * 4 * np.pi / n
+    Eind = rB["E"] - r1["E"]
+    geo = np.concatenate([[0.0], np.cumsum(rho ** np.arange(1, B))])      # rho + ... + rho^(h-1)
+    assert np.sum(A * Eind) == pytest.approx(phi * np.sum(geo[hits - 1]), rel=1e-10)
+    series = geo[B - 1]
+    mean = I * 4 * np.pi / np.sum(A) * series
+    assert mean * (1 - rho) / rho == pytest.approx(I * 4 * np.pi / np.sum(A), rel=1e-3)   # the 1/(1-rho) limit
+    # per texel: a photon's hits after the first are nearly independent
+    # uniform draws, one deposit of rho^i phi each
+    p = A / np.sum(A)
+    sigma = phi * np.sqrt(n * p * np.sum(rho ** (2.0 * np.arange(1, B)))) / A
+    chi2 = np.mean(((Eind - mean) / sigma) ** 2)
+    assert 0.75 < chi2 < 1.35, chi2
