@@ -8,7 +8,8 @@
   (point light) or the quadrature of I a cos / r^2 (spot);
 * interior sphere: cosine-weighted reflection from any point of a sphere lands
   uniformly on it, so the second-hit irradiance is uniform even for an
-  off-centre light."""
+  off-centre light, and B hits add the geometric series of rho;
+* several lights: the budget split and each light's normalisation."""
 import numpy as np
 import pytest
 from scipy import stats
@@ -215,3 +216,38 @@ def test_sphere_interreflection_is_the_geometric_series():
     sigma = phi * np.sqrt(n * p * np.sum(rho ** (2.0 * np.arange(1, B)))) / A
     chi2 = np.mean(((Eind - mean) / sigma) ** 2)
     assert 0.75 < chi2 < 1.35, chi2
+
+
+def test_two_lights_split_the_budget_and_superpose():
+    """With L lights a budget of N photons is split evenly, the first N mod L
+    lights taking one extra, and each photon carries I Omega / N_l of its own
+    light: irradiance is the sum of the lights' closed forms, and light 0's
+    photon range reproduces light 0 traced alone with N_0 photons exactly."""
+    half, res = 1.5, 10
+    point = scenes.point_light((0.15, -0.1, 0.6), 1.3)
+    spot = scenes.spot_light((0.1, 0.2, 1.0), 0.4, -np.pi / 2 + 0.25, 2.0, 0.25, 0.7)
+    sc = scenes.plane(half=half, res=res)
+    L = scenes.make_lights([point, spot])
+    n = (1 << 20) + 1
+    n0, n1 = (n + 1) // 2, n // 2
+    r = oracle.forward(sc, L, seed=23, n_photons=n, max_hits=1)
+    A = (2 * half / res) ** 2
+    omega = cf.plane_texel_solid_angles(half, res, np.array(point[1:4]))
+    e_point = 1.3 * omega / A
+    e_spot = cf.plane_texel_spot_flux(half, res, np.array(spot), sub=8, order=6) / A
+    phi_p = 1.3 * 4 * np.pi / n0
+    phi_s = 2.0 * 2 * np.pi * (1 - np.cos(0.7)) / n1
+    p = omega / (4 * np.pi)
+    var = (phi_p / A) ** 2 * n0 * p * (1 - p) + phi_s * np.maximum(e_spot, 1e-30) / A
+    z = (r["E"] - e_point - e_spot) / np.sqrt(var)
+    assert np.max(np.abs(z)) < 5.0
+    # light 0 owns photons [0, n0) and normalises by its own count
+    alone = oracle.forward(sc, scenes.make_lights([point]), seed=23, n_photons=n0, max_hits=1)
+    part = oracle.forward(sc, L, seed=23, n_photons=n, max_hits=1, begin=0, end=n0)
+    assert np.array_equal(part["E"], alone["E"])
+    rest = oracle.forward(sc, L, seed=23, n_photons=n, max_hits=1, begin=n0, end=n)
+    np.testing.assert_allclose(part["E"] + rest["E"], r["E"], rtol=1e-12)
+    w = np.random.default_rng(3).normal(size=sc.n_texels)
+    g_part, _ = oracle.adjoint(sc, L, 23, n, 1, w, begin=0, end=n0)
+    g_alone, _ = oracle.adjoint(sc, scenes.make_lights([point]), 23, n0, 1, w)
+    assert np.array_equal(g_part[0], g_alone[0]) and not np.any(g_part[1])
