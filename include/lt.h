@@ -123,6 +123,39 @@ LT_API int lt_upload_scene(void *ctx, const float *tri_xyz, const float *tri_uv,
                     const float *tri_albedo, int32_t n_tri, const int32_t *tile_res, const double *tile_area,
                     int32_t n_tiles, int64_t *n_texels_out);
 
+/* One node of the 8-wide BVH (240 bytes), the layout the traversal kernels
+ * read from device memory. Slot k (0..7) holds a child with the box
+ * [lo_x[k], hi_x[k]] x [lo_y[k], hi_y[k]] x [lo_z[k], hi_z[k]]: the float
+ * bounds of its triangles grown by a margin on every side, so that a plane
+ * distance rounded by the traversal never cuts a triangle off. child[k] >= 0
+ * is an inner node (bit k of inner_mask set); INT32_MIN is an empty slot,
+ * whose box is inverted (lo > hi) so that no ray enters it; any other
+ * negative value is a leaf of ((-1 - child[k]) & 3) + 1 triangles starting
+ * at leaf-order position (-1 - child[k]) >> 2. Slot k faces the direction
+ * whose component a is + when bit a of k is set: children are assigned to
+ * slots so that the sum over children of -dot(child centre - node centre,
+ * slot direction) is least, which lets the traversal visit near children
+ * first by a per-ray XOR of the slot index. */
+typedef struct {
+    float lo_x[8], hi_x[8], lo_y[8], hi_y[8], lo_z[8], hi_z[8];
+    int32_t child[8];
+    uint32_t inner_mask;
+    uint32_t pad[3];
+} lt_bvh_node;
+
+/* Build the wide BVH of n_tri triangles (tri_xyz as for lt_upload_scene) on
+ * the host, without a context or a device: the same builder lt_upload_scene
+ * runs, exposed for inspection. Nodes are breadth-first (node 0 is the root,
+ * parents come before their children). Outputs, each optional (NULL):
+ *   nodes_out    [nodes_cap] lt_bvh_node
+ *   order_out    [n_tri] int32: leaf-order position -> input triangle index
+ *   n_nodes_out  node count; depth_out levels of wide nodes (<= 16)
+ * Returns LT_ERR_ARG for an empty or non-finite input, for a tree deeper
+ * than 16 levels, or when nodes_cap is below the node count (the counts are
+ * still written); LT_ERR_OOM when host memory runs out. */
+LT_API int lt_build_bvh(const float *tri_xyz, int32_t n_tri, lt_bvh_node *nodes_out, int32_t nodes_cap,
+                        int32_t *order_out, int32_t *n_nodes_out, int32_t *depth_out);
+
 /* Target irradiance E*_t and weights alpha_t of the objective (Eq. 6),
  * [n_texels] floats each; alpha may be NULL (all ones). */
 LT_API int lt_set_target(void *ctx, const float *E_target, const float *alpha, int is_device);

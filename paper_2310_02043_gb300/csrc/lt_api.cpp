@@ -2,6 +2,7 @@
 // scene/BVH upload, light constants, launches and error reporting.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -409,6 +410,34 @@ int batch_check_device(Ctx *c) {
 extern "C" {
 
 int lt_version(void) { return 1; }
+
+static_assert(sizeof(lt_bvh_node) == sizeof(Node), "lt_bvh_node mirrors lt::Node");
+static_assert(offsetof(lt_bvh_node, hi_z) == offsetof(Node, hiz) && offsetof(lt_bvh_node, child) == offsetof(Node, child) &&
+                  offsetof(lt_bvh_node, inner_mask) == offsetof(Node, inner_mask),
+              "lt_bvh_node field offsets");
+
+int lt_build_bvh(const float *tri_xyz, int32_t n_tri, lt_bvh_node *nodes_out, int32_t nodes_cap, int32_t *order_out,
+                 int32_t *n_nodes_out, int32_t *depth_out) {
+    if (!tri_xyz || n_tri <= 0) return LT_ERR_ARG;
+    for (size_t k = 0; k < (size_t)n_tri * 9; ++k)
+        if (!std::isfinite(tri_xyz[k])) return LT_ERR_ARG;
+    try {
+        BvhBuild bvh;
+        std::string err;
+        if (!build_wide_bvh(tri_xyz, n_tri, &bvh, &err)) return LT_ERR_ARG;
+        const int32_t n_nodes = (int32_t)bvh.nodes.size();
+        if (n_nodes_out) *n_nodes_out = n_nodes;
+        if (depth_out) *depth_out = bvh.depth;
+        if (nodes_out) {
+            if (nodes_cap < n_nodes) return LT_ERR_ARG;
+            std::memcpy(nodes_out, bvh.nodes.data(), sizeof(Node) * (size_t)n_nodes);
+        }
+        if (order_out) std::memcpy(order_out, bvh.order.data(), sizeof(int32_t) * (size_t)n_tri);
+    } catch (const std::bad_alloc &) {
+        return LT_ERR_OOM;
+    }
+    return LT_OK;
+}
 
 int lt_create(void **ctx_out, int device, void *cuda_stream) {
     if (!ctx_out) return LT_ERR_ARG;

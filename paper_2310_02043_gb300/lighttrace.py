@@ -29,7 +29,7 @@ EXPORTED = ("lt_version", "lt_create", "lt_destroy", "lt_set_stream", "lt_last_e
             "lt_get_irradiance", "lt_texel_areas", "lt_set_adjoint_weights", "lt_trace_adjoint", "lt_debug_paths",
             "lt_get_stats", "lt_set_launch", "lt_count_work", "lt_loss_static", "lt_set_design", "lt_batch_setup",
             "lt_batch_set_lights", "lt_batch_step", "lt_batch_texel_sums", "lt_batch_irradiance",
-            "lt_batch_stream", "lt_texel_centres")
+            "lt_batch_stream", "lt_texel_centres", "lt_build_bvh")
 
 
 class LtError(RuntimeError):
@@ -51,6 +51,17 @@ class lt_stats(ctypes.Structure):
                 ("bvh_depth", ctypes.c_int32), ("staged_nodes", ctypes.c_int32),
                 ("fixed_point_scale", ctypes.c_double), ("grid_blocks", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32)]
+
+
+class lt_bvh_node(ctypes.Structure):
+    _fields_ = [("lo_x", ctypes.c_float * 8), ("hi_x", ctypes.c_float * 8), ("lo_y", ctypes.c_float * 8),
+                ("hi_y", ctypes.c_float * 8), ("lo_z", ctypes.c_float * 8), ("hi_z", ctypes.c_float * 8),
+                ("child", ctypes.c_int32 * 8), ("inner_mask", ctypes.c_uint32), ("pad", ctypes.c_uint32 * 3)]
+
+
+BVH_NODE_DTYPE = np.dtype([("lo_x", "<f4", 8), ("hi_x", "<f4", 8), ("lo_y", "<f4", 8), ("hi_y", "<f4", 8),
+                           ("lo_z", "<f4", 8), ("hi_z", "<f4", 8), ("child", "<i4", 8), ("inner_mask", "<u4"),
+                           ("pad", "<u4", 3)])
 
 
 _lib = None
@@ -102,6 +113,7 @@ def _declare(lib):
         "lt_batch_irradiance": [vp, i32, vp, ci],
         "lt_batch_stream": [vp, ctypes.POINTER(ctypes.c_void_p)],
         "lt_texel_centres": [vp, vp, vp],
+        "lt_build_bvh": [vp, i32, vp, i32, vp, ctypes.POINTER(i32), ctypes.POINTER(i32)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -150,6 +162,26 @@ def loss_static(device: int, stream: int, q_ptr: int, scale: float, area, E_targ
                             _ptr(E_out)[0] if E_out is not None else None, _ptr(loss_out)[0])
     if rc != LT_OK:
         raise LtError(rc, "lt_loss_static failed")
+
+
+def build_bvh(tri_xyz):
+    """lt_build_bvh: the wide BVH of [n_tri, 3, 3] float triangles, built on
+    the host (no device). Returns (nodes as a BVH_NODE_DTYPE array, order
+    int32 [n_tri] leaf position -> triangle, depth)."""
+    lib = load_library()
+    xyz = np.ascontiguousarray(tri_xyz, np.float32).reshape(-1, 9)
+    n_tri = xyz.shape[0]
+    n_nodes, depth = ctypes.c_int32(0), ctypes.c_int32(0)
+    rc = lib.lt_build_bvh(_ptr(xyz)[0], n_tri, None, 0, None, ctypes.byref(n_nodes), ctypes.byref(depth))
+    if rc != LT_OK:
+        raise LtError(rc, "lt_build_bvh failed")
+    nodes = np.zeros(n_nodes.value, BVH_NODE_DTYPE)
+    order = np.empty(n_tri, np.int32)
+    rc = lib.lt_build_bvh(_ptr(xyz)[0], n_tri, nodes.ctypes.data_as(ctypes.c_void_p), n_nodes.value, _ptr(order)[0],
+                          ctypes.byref(n_nodes), ctypes.byref(depth))
+    if rc != LT_OK:
+        raise LtError(rc, "lt_build_bvh failed")
+    return nodes, order, depth.value
 
 
 class Tracer:
