@@ -11,7 +11,12 @@
  *
  * Conventions for every call:
  *   - Returns LT_OK (0) or a negative lt_status. A failed call leaves a
- *     message for lt_last_error(). No C++ exception crosses this interface.
+ *     message for lt_last_error(). No C++ exception crosses this interface:
+ *     host memory running out is LT_ERR_OOM.
+ *   - Fault injection for testing callers: with the environment variable
+ *     LT_FAULT_HOST_ALLOC set and non-empty, the BVH build of lt_upload_scene
+ *     and lt_build_bvh fails as if host memory ran out (LT_ERR_OOM); a context
+ *     stays usable after it.
  *   - Work is queued on the context's CUDA stream (lt_create / lt_set_stream).
  *     Calls that return a value in host memory synchronise that stream.
  *   - Host input arrays are copied; the caller keeps ownership. Output
@@ -118,7 +123,8 @@ LT_API const char *lt_last_error(const void *ctx);
  * Texels are numbered tile by tile, u fastest. A texel's area is
  * tile_area / (res_u res_v) (the box basis standing in for the per-vertex
  * hat basis of Eq. 4; mass-lumped projection, Eq. S.6). Writes the texel
- * count to *n_texels_out. Invalidates targets, weights and pass results. */
+ * count to *n_texels_out. Invalidates targets, weights and pass results.
+ * An argument error or a failed BVH build leaves the previous scene in place. */
 LT_API int lt_upload_scene(void *ctx, const float *tri_xyz, const float *tri_uv, const int32_t *tri_tile,
                     const float *tri_albedo, int32_t n_tri, const int32_t *tile_res, const double *tile_area,
                     int32_t n_tiles, int64_t *n_texels_out);

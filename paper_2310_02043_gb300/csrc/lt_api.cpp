@@ -3,9 +3,11 @@
 #include <algorithm>
 #include <cmath>
 #include <cstddef>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -88,6 +90,46 @@ int fail(Ctx *c, int code, const std::string &msg) {
     if (c) c->err = msg;
     return code;
 }
+
+// No C++ exception crosses the C ABI: every entry point runs its body between
+// LT_TRY and LT_CATCH, which turn an exception into a status and, when there
+// is a context, its message. Called only from inside a catch handler.
+int exception_status(Ctx *c) noexcept {
+    int code = LT_ERR_STATE;
+    const char *msg = "unexpected C++ exception";
+    try {
+        throw;
+    } catch (const std::bad_alloc &) {
+        code = LT_ERR_OOM;
+        msg = "host memory exhausted";
+    } catch (const std::length_error &) {
+        code = LT_ERR_ARG;
+        msg = "a size exceeds what a host container can hold";
+    } catch (...) {
+    }
+    if (c) {
+        try {
+            c->err = msg;
+        } catch (...) {
+        }
+    }
+    return code;
+}
+
+// Host-side fault injection for testing callers' error paths: with the
+// environment variable LT_FAULT_HOST_ALLOC set and non-empty, the host
+// allocations of a BVH build fail as if memory ran out.
+void maybe_inject_host_oom() {
+    const char *v = std::getenv("LT_FAULT_HOST_ALLOC");
+    if (v && v[0]) throw std::bad_alloc();
+}
+
+#define LT_TRY try {
+#define LT_CATCH(ctx)                                      \
+    }                                                      \
+    catch (...) {                                          \
+        return exception_status(static_cast<Ctx *>(ctx));  \
+    }
 
 int cuda_fail(Ctx *c, cudaError_t e, const char *what) {
     return fail(c, e == cudaErrorMemoryAllocation ? LT_ERR_OOM : LT_ERR_CUDA,
@@ -418,28 +460,28 @@ static_assert(offsetof(lt_bvh_node, hi_z) == offsetof(Node, hiz) && offsetof(lt_
 
 int lt_build_bvh(const float *tri_xyz, int32_t n_tri, lt_bvh_node *nodes_out, int32_t nodes_cap, int32_t *order_out,
                  int32_t *n_nodes_out, int32_t *depth_out) {
+    LT_TRY
     if (!tri_xyz || n_tri <= 0) return LT_ERR_ARG;
     for (size_t k = 0; k < (size_t)n_tri * 9; ++k)
         if (!std::isfinite(tri_xyz[k])) return LT_ERR_ARG;
-    try {
-        BvhBuild bvh;
-        std::string err;
-        if (!build_wide_bvh(tri_xyz, n_tri, &bvh, &err)) return LT_ERR_ARG;
-        const int32_t n_nodes = (int32_t)bvh.nodes.size();
-        if (n_nodes_out) *n_nodes_out = n_nodes;
-        if (depth_out) *depth_out = bvh.depth;
-        if (nodes_out) {
-            if (nodes_cap < n_nodes) return LT_ERR_ARG;
-            std::memcpy(nodes_out, bvh.nodes.data(), sizeof(Node) * (size_t)n_nodes);
-        }
-        if (order_out) std::memcpy(order_out, bvh.order.data(), sizeof(int32_t) * (size_t)n_tri);
-    } catch (const std::bad_alloc &) {
-        return LT_ERR_OOM;
+    BvhBuild bvh;
+    std::string err;
+    maybe_inject_host_oom();
+    if (!build_wide_bvh(tri_xyz, n_tri, &bvh, &err)) return LT_ERR_ARG;
+    const int32_t n_nodes = (int32_t)bvh.nodes.size();
+    if (n_nodes_out) *n_nodes_out = n_nodes;
+    if (depth_out) *depth_out = bvh.depth;
+    if (nodes_out) {
+        if (nodes_cap < n_nodes) return LT_ERR_ARG;
+        std::memcpy(nodes_out, bvh.nodes.data(), sizeof(Node) * (size_t)n_nodes);
     }
+    if (order_out) std::memcpy(order_out, bvh.order.data(), sizeof(int32_t) * (size_t)n_tri);
     return LT_OK;
+    LT_CATCH(nullptr)
 }
 
 int lt_create(void **ctx_out, int device, void *cuda_stream) {
+    LT_TRY
     if (!ctx_out) return LT_ERR_ARG;
     *ctx_out = nullptr;
     Ctx *c = new (std::nothrow) Ctx();
@@ -471,9 +513,11 @@ int lt_create(void **ctx_out, int device, void *cuda_stream) {
     }
     *ctx_out = c;
     return LT_OK;
+    LT_CATCH(nullptr)
 }
 
 int lt_destroy(void *ctx) {
+    LT_TRY
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return LT_OK;
     cudaSetDevice(c->device);
@@ -488,13 +532,16 @@ int lt_destroy(void *ctx) {
     if (c->lights_copied) cudaEventDestroy(c->lights_copied);
     delete c;
     return LT_OK;
+    LT_CATCH(ctx)
 }
 
 int lt_set_stream(void *ctx, void *cuda_stream) {
+    LT_TRY
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return LT_ERR_ARG;
     c->stream = (cudaStream_t)cuda_stream;
     return LT_OK;
+    LT_CATCH(ctx)
 }
 
 const char *lt_last_error(const void *ctx) {
@@ -505,6 +552,7 @@ const char *lt_last_error(const void *ctx) {
 int lt_upload_scene(void *ctx, const float *tri_xyz, const float *tri_uv, const int32_t *tri_tile,
                     const float *tri_albedo, int32_t n_tri, const int32_t *tile_res, const double *tile_area,
                     int32_t n_tiles, int64_t *n_texels_out) {
+    LT_TRY
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return LT_ERR_ARG;
     if (!tri_xyz || !tri_uv || !tri_tile || !tri_albedo || !tile_res || !tile_area || n_tri <= 0 || n_tiles <= 0)
@@ -525,6 +573,7 @@ int lt_upload_scene(void *ctx, const float *tri_xyz, const float *tri_uv, const 
     }
     BvhBuild bvh;
     std::string berr;
+    maybe_inject_host_oom();
     if (!build_wide_bvh(tri_xyz, n_tri, &bvh, &berr)) return fail(c, LT_ERR_ARG, berr);
     std::vector<Tri> tris((size_t)n_tri);
     std::vector<TriHit> hits((size_t)n_tri);
@@ -593,9 +642,11 @@ int lt_upload_scene(void *ctx, const float *tri_xyz, const float *tri_uv, const 
     c->stats.bvh_depth = c->depth;
     if (n_texels_out) *n_texels_out = T;
     return LT_OK;
+    LT_CATCH(ctx)
 }
 
 int lt_set_target(void *ctx, const float *E_target, const float *alpha, int is_device) {
+    LT_TRY
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return LT_ERR_ARG;
     if (!c->d_nodes) return fail(c, LT_ERR_STATE, "no scene uploaded");
@@ -613,6 +664,7 @@ int lt_set_target(void *ctx, const float *E_target, const float *alpha, int is_d
     if (!is_device) LT_CUDA(c, cudaStreamSynchronize(c->stream));
     c->has_target = true;
     return LT_OK;
+    LT_CATCH(ctx)
 }
 
 // Argument checks of one luminaire; empty on success.
@@ -630,6 +682,7 @@ static const char *light_error(const lt_light &s) {
 }
 
 int lt_set_lights(void *ctx, const lt_light *lights, int32_t n_lights) {
+    LT_TRY
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return LT_ERR_ARG;
     if (!lights || n_lights < 1 || n_lights > LT_MAX_LIGHTS) return fail(c, LT_ERR_ARG, "n_lights out of range");
@@ -638,6 +691,7 @@ int lt_set_lights(void *ctx, const lt_light *lights, int32_t n_lights) {
     c->lights.assign(lights, lights + n_lights);
     c->lights_dirty = true;
     return LT_OK;
+    LT_CATCH(ctx)
 }
 
 // Fixed point: S = 2^k with S * (total power bound) * max_hits < 2^62, so
@@ -694,13 +748,16 @@ static int forward_pass(Ctx *c, uint64_t seed, uint64_t n_photons, int32_t max_h
 
 int lt_trace_forward(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
                      uint64_t photon_end) {
+    LT_TRY
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return LT_ERR_ARG;
     return forward_pass(c, seed, n_photons, max_hits, photon_begin, photon_end, nullptr);
+    LT_CATCH(ctx)
 }
 
 int lt_count_work(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
                   uint64_t photon_end, uint64_t *counts_out) {
+    LT_TRY
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return LT_ERR_ARG;
     if (!counts_out) return fail(c, LT_ERR_ARG, "null counts output");
@@ -725,26 +782,32 @@ int lt_count_work(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits
     counts_out[2] = h[1];
     counts_out[3] = photon_end - photon_begin;
     return check_device(c);
+    LT_CATCH(ctx)
 }
 
 int lt_texel_accumulator(void *ctx, int64_t **q_device, double *scale_out) {
+    LT_TRY
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c || !q_device) return LT_ERR_ARG;
     if (!c->d_q) return fail(c, LT_ERR_STATE, "no scene uploaded");
     *q_device = reinterpret_cast<int64_t *>(c->d_q);
     if (scale_out) *scale_out = c->scale;
     return LT_OK;
+    LT_CATCH(ctx)
 }
 
 int lt_get_texel_sums(void *ctx, int64_t *q_out, int is_device) {
+    LT_TRY
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c || !q_out) return LT_ERR_ARG;
     if (!c->fwd_done) return fail(c, LT_ERR_STATE, "no forward pass");
     LT_CUDA(c, cudaSetDevice(c->device));
     return copy_out(c, q_out, c->d_q, (size_t)c->n_texels * sizeof(int64_t), is_device);
+    LT_CATCH(ctx)
 }
 
 int lt_loss(void *ctx, double *loss_out, int is_device) {
+    LT_TRY
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return LT_ERR_ARG;
     if (!c->fwd_done) return fail(c, LT_ERR_STATE, "lt_loss needs a forward pass");
@@ -771,26 +834,32 @@ int lt_loss(void *ctx, double *loss_out, int is_device) {
         if (!is_device) return check_device(c);
     }
     return LT_OK;
+    LT_CATCH(ctx)
 }
 
 int lt_get_irradiance(void *ctx, float *E_out, int is_device) {
+    LT_TRY
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c || !E_out) return LT_ERR_ARG;
     if (!c->fwd_done) return fail(c, LT_ERR_STATE, "no forward pass");
     LT_CUDA(c, cudaSetDevice(c->device));
     LT_CUDA(c, launch_resolve(c->d_q, c->d_area, 1.0 / c->scale, c->n_texels, c->d_E, c->stream));
     return copy_out(c, E_out, c->d_E, (size_t)c->n_texels * sizeof(float), is_device);
+    LT_CATCH(ctx)
 }
 
 int lt_texel_areas(void *ctx, float *A_out, int is_device) {
+    LT_TRY
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c || !A_out) return LT_ERR_ARG;
     if (!c->d_area) return fail(c, LT_ERR_STATE, "no scene uploaded");
     LT_CUDA(c, cudaSetDevice(c->device));
     return copy_out(c, A_out, c->d_area, (size_t)c->n_texels * sizeof(float), is_device);
+    LT_CATCH(ctx)
 }
 
 int lt_set_adjoint_weights(void *ctx, const float *w, int is_device) {
+    LT_TRY
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c || !w) return LT_ERR_ARG;
     if (!c->d_w) return fail(c, LT_ERR_STATE, "no scene uploaded");
@@ -800,10 +869,12 @@ int lt_set_adjoint_weights(void *ctx, const float *w, int is_device) {
     if (!is_device) LT_CUDA(c, cudaStreamSynchronize(c->stream));
     c->has_w = true;
     return LT_OK;
+    LT_CATCH(ctx)
 }
 
 int lt_trace_adjoint(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
                      uint64_t photon_end, double *grad_out, int is_device) {
+    LT_TRY
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return LT_ERR_ARG;
     if (!grad_out) return fail(c, LT_ERR_ARG, "null gradient output");
@@ -842,10 +913,12 @@ int lt_trace_adjoint(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_h
     if (rc) return rc;
     if (!is_device) return check_device(c);
     return LT_OK;
+    LT_CATCH(ctx)
 }
 
 int lt_debug_paths(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
                    uint64_t count, int32_t *tri_out, int64_t *texel_out, double *grad_out) {
+    LT_TRY
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return LT_ERR_ARG;
     if (!tri_out || !texel_out) return fail(c, LT_ERR_ARG, "null output");
@@ -880,9 +953,11 @@ int lt_debug_paths(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hit
     cudaFree(d_grad);
     if (e != cudaSuccess) return cuda_fail(c, e, "lt_debug_paths");
     return check_device(c);
+    LT_CATCH(ctx)
 }
 
 int lt_get_stats(void *ctx, lt_stats *out) {
+    LT_TRY
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c || !out) return LT_ERR_ARG;
     LT_CUDA(c, cudaSetDevice(c->device));
@@ -895,18 +970,22 @@ int lt_get_stats(void *ctx, lt_stats *out) {
     }
     *out = c->stats;
     return check_device(c);
+    LT_CATCH(ctx)
 }
 
 int lt_set_design(void *ctx, uint32_t design) {
+    LT_TRY
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return LT_ERR_ARG;
     c->design_word = design;
     c->lights_dirty = true;
     return LT_OK;
+    LT_CATCH(ctx)
 }
 
 int lt_batch_setup(void *ctx, int32_t n_designs, const int32_t *lights_per_design, uint64_t photons_per_design,
                    int32_t max_hits) {
+    LT_TRY
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return LT_ERR_ARG;
     if (!c->d_nodes) return fail(c, LT_ERR_STATE, "no scene uploaded");
@@ -945,9 +1024,11 @@ int lt_batch_setup(void *ctx, int32_t n_designs, const int32_t *lights_per_desig
     }
     std::memset(b.h_in, 0, b.in_bytes);
     return LT_OK;
+    LT_CATCH(ctx)
 }
 
 int lt_batch_set_lights(void *ctx, const lt_light *lights) {
+    LT_TRY
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return LT_ERR_ARG;
     Ctx::Batch &b = c->batch;
@@ -973,10 +1054,12 @@ int lt_batch_set_lights(void *ctx, const lt_light *lights) {
     h->inv_scale = 1.0 / S;
     b.has_lights = true;
     return LT_OK;
+    LT_CATCH(ctx)
 }
 
 int lt_batch_step(void *ctx, uint64_t seed_fwd, uint64_t seed_adj, double *loss_out, double *grad_out,
                   int use_graph) {
+    LT_TRY
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return LT_ERR_ARG;
     Ctx::Batch &b = c->batch;
@@ -1026,9 +1109,11 @@ int lt_batch_step(void *ctx, uint64_t seed_fwd, uint64_t seed_adj, double *loss_
     c->stats.staged_nodes = bl.fwd.n_staged;
     c->seg_single = false;
     return LT_OK;
+    LT_CATCH(ctx)
 }
 
 int lt_texel_centres(void *ctx, float *pos_out, float *normal_out) {
+    LT_TRY
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c || !pos_out || !normal_out) return LT_ERR_ARG;
     if (c->h_off.empty()) return fail(c, LT_ERR_STATE, "no scene uploaded");
@@ -1080,16 +1165,20 @@ int lt_texel_centres(void *ctx, float *pos_out, float *normal_out) {
             }
     }
     return LT_OK;
+    LT_CATCH(ctx)
 }
 
 int lt_batch_stream(void *ctx, void **stream_out) {
+    LT_TRY
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c || !stream_out) return LT_ERR_ARG;
     *stream_out = (void *)c->batch.stream;
     return LT_OK;
+    LT_CATCH(ctx)
 }
 
 int lt_batch_texel_sums(void *ctx, int32_t design, int64_t *q_out, int is_device) {
+    LT_TRY
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c || !q_out) return LT_ERR_ARG;
     Ctx::Batch &b = c->batch;
@@ -1100,9 +1189,11 @@ int lt_batch_texel_sums(void *ctx, int32_t design, int64_t *q_out, int is_device
                                is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b.stream));
     LT_CUDA(c, cudaStreamSynchronize(b.stream));
     return LT_OK;
+    LT_CATCH(ctx)
 }
 
 int lt_batch_irradiance(void *ctx, int32_t design, float *E_out, int is_device) {
+    LT_TRY
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c || !E_out) return LT_ERR_ARG;
     Ctx::Batch &b = c->batch;
@@ -1113,9 +1204,11 @@ int lt_batch_irradiance(void *ctx, int32_t design, float *E_out, int is_device) 
                                is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b.stream));
     LT_CUDA(c, cudaStreamSynchronize(b.stream));
     return LT_OK;
+    LT_CATCH(ctx)
 }
 
 int lt_set_launch(void *ctx, int32_t threads_per_block, int32_t blocks_per_sm, int32_t smem_node_bytes) {
+    LT_TRY
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return LT_ERR_ARG;
     if (threads_per_block > 0 &&
@@ -1128,6 +1221,7 @@ int lt_set_launch(void *ctx, int32_t threads_per_block, int32_t blocks_per_sm, i
     if (smem_node_bytes >= 0) c->smem_node_bytes = smem_node_bytes;
     batch_drop_graph(c);     // a captured batch step holds the old launch shape
     return LT_OK;
+    LT_CATCH(ctx)
 }
 
 }  // extern "C"

@@ -75,16 +75,22 @@ __global__ void __launch_bounds__(kThreads) loss_sum_kernel(const double *partia
 }
 
 // Device address of the partials array on `device` (which must be current).
-cudaError_t partials_on(int device, double **out) {
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_partials_addr[device]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_loss_partials);
-        if (e != cudaSuccess) return e;
-        g_partials_addr[device] = static_cast<double *>(p);
+// Locking a mutex may throw std::system_error; that stays on this side of
+// the C ABI as a CUDA-style error.
+cudaError_t partials_on(int device, double **out) noexcept {
+    try {
+        std::lock_guard<std::mutex> lock(g_mutex);
+        if (!g_partials_addr[device]) {
+            void *p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_loss_partials);
+            if (e != cudaSuccess) return e;
+            g_partials_addr[device] = static_cast<double *>(p);
+        }
+        *out = g_partials_addr[device];
+        return cudaSuccess;
+    } catch (...) {
+        return cudaErrorUnknown;
     }
-    *out = g_partials_addr[device];
-    return cudaSuccess;
 }
 
 }  // namespace

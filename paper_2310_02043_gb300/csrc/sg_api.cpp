@@ -3,6 +3,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <new>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -65,6 +67,38 @@ int cuda_fail(SgCtx *c, cudaError_t e, const char *what) {
     c->err = std::string(what) + ": " + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? LT_ERR_OOM : LT_ERR_CUDA;
 }
+
+// No C++ exception crosses the C ABI: every entry point runs its body between
+// LT_TRY and LT_CATCH, which turn an exception into a status and, when there
+// is a context, its message. Called only from inside a catch handler.
+int exception_status(SgCtx *c) noexcept {
+    int code = LT_ERR_STATE;
+    const char *msg = "unexpected C++ exception";
+    try {
+        throw;
+    } catch (const std::bad_alloc &) {
+        code = LT_ERR_OOM;
+        msg = "host memory exhausted";
+    } catch (const std::length_error &) {
+        code = LT_ERR_ARG;
+        msg = "a size exceeds what a host container can hold";
+    } catch (...) {
+    }
+    if (c) {
+        try {
+            c->err = msg;
+        } catch (...) {
+        }
+    }
+    return code;
+}
+
+#define LT_TRY try {
+#define LT_CATCH(ctx)                                        \
+    }                                                        \
+    catch (...) {                                            \
+        return exception_status(static_cast<SgCtx *>(ctx));  \
+    }
 
 #define SG_CUDA(c, expr)                                   \
     do {                                                   \
@@ -203,6 +237,7 @@ int copy_to(SgCtx *c, void *dst, const void *src, size_t bytes, int dst_is_devic
 extern "C" {
 
 int sg_create(void **ctx_out, int device, void *cuda_stream) {
+    LT_TRY
     if (!ctx_out) return LT_ERR_ARG;
     *ctx_out = nullptr;
     int n_dev = 0;
@@ -230,9 +265,11 @@ int sg_create(void **ctx_out, int device, void *cuda_stream) {
     }
     *ctx_out = c;
     return LT_OK;
+    LT_CATCH(nullptr)
 }
 
 int sg_destroy(void *ctx) {
+    LT_TRY
     SgCtx *c = static_cast<SgCtx *>(ctx);
     if (!c) return LT_ERR_ARG;
     cudaSetDevice(c->device);
@@ -240,6 +277,7 @@ int sg_destroy(void *ctx) {
     free_all(c);
     delete c;
     return LT_OK;
+    LT_CATCH(ctx)
 }
 
 const char *sg_last_error(const void *ctx) {
@@ -249,6 +287,7 @@ const char *sg_last_error(const void *ctx) {
 
 int sg_set_texels(void *ctx, const float *pos, const float *normal, const float *area, int64_t n_texels,
                   const float *lo, float ext) {
+    LT_TRY
     SgCtx *c = static_cast<SgCtx *>(ctx);
     if (!c) return LT_ERR_ARG;
     if (!pos || !normal || !area || !lo || n_texels <= 0) return fail(c, LT_ERR_ARG, "null texel array or no texels");
@@ -289,9 +328,11 @@ int sg_set_texels(void *ctx, const float *pos, const float *normal, const float 
     c->n_solves = 0;
     c->E_obs = nullptr;
     return LT_OK;
+    LT_CATCH(ctx)
 }
 
 int sg_set_params(void *ctx, const float *weights, const float *table, int is_device) {
+    LT_TRY
     SgCtx *c = static_cast<SgCtx *>(ctx);
     if (!c || !weights || !table) return LT_ERR_ARG;
     SG_CUDA(c, cudaSetDevice(c->device));
@@ -312,9 +353,11 @@ int sg_set_params(void *ctx, const float *weights, const float *table, int is_de
     c->step = 0;
     c->enc_dirty = true;
     return LT_OK;
+    LT_CATCH(ctx)
 }
 
 int sg_get_params(void *ctx, float *weights, float *table, int is_device) {
+    LT_TRY
     SgCtx *c = static_cast<SgCtx *>(ctx);
     if (!c || !weights || !table) return LT_ERR_ARG;
     if (!c->has_params) return fail(c, LT_ERR_STATE, "no parameters (sg_set_params)");
@@ -322,9 +365,11 @@ int sg_get_params(void *ctx, float *weights, float *table, int is_device) {
     int rc = copy_to(c, weights, c->d_W, kWeights * sizeof(float), is_device);
     if (rc) return rc;
     return copy_to(c, table, c->d_table, kTableFloats * sizeof(float), is_device);
+    LT_CATCH(ctx)
 }
 
 int sg_set_training_data(void *ctx, const lt_light *lights, int32_t n_solves, const float *E_obs) {
+    LT_TRY
     SgCtx *c = static_cast<SgCtx *>(ctx);
     if (!c || !lights || !E_obs || n_solves <= 0) return LT_ERR_ARG;
     if (!c->n) return fail(c, LT_ERR_STATE, "no texels (sg_set_texels)");
@@ -338,11 +383,13 @@ int sg_set_training_data(void *ctx, const lt_light *lights, int32_t n_solves, co
     c->n_solves = n_solves;
     c->E_obs = E_obs;
     return LT_OK;
+    LT_CATCH(ctx)
 }
 
 static int check_device(SgCtx *c);
 
 int sg_train_step(void *ctx, uint64_t seed, int32_t batch, float lr, const int32_t *samples, double *loss_out) {
+    LT_TRY
     SgCtx *c = static_cast<SgCtx *>(ctx);
     if (!c) return LT_ERR_ARG;
     int rc = need_params(c);
@@ -403,15 +450,18 @@ int sg_train_step(void *ctx, uint64_t seed, int32_t batch, float lr, const int32
         return check_device(c);   // synchronises; reports a tensor-core wait that gave up
     }
     return LT_OK;
+    LT_CATCH(ctx)
 }
 
 int sg_get_gradients(void *ctx, float *dweights, float *dtable, int is_device) {
+    LT_TRY
     SgCtx *c = static_cast<SgCtx *>(ctx);
     if (!c || !dweights || !dtable) return LT_ERR_ARG;
     SG_CUDA(c, cudaSetDevice(c->device));
     int rc = copy_to(c, dweights, c->d_gW, kWeights * sizeof(float), is_device);
     if (rc) return rc;
     return copy_to(c, dtable, c->d_gT, kTableFloats * sizeof(float), is_device);
+    LT_CATCH(ctx)
 }
 
 static int design_prepare(SgCtx *c, const lt_light *lights, int32_t n_lights) {
@@ -464,6 +514,7 @@ static DesignArgs design_args(SgCtx *c, int32_t n_lights) {
 }
 
 int sg_response(void *ctx, const lt_light *light, float *K_out, int is_device) {
+    LT_TRY
     SgCtx *c = static_cast<SgCtx *>(ctx);
     if (!c || !light || !K_out) return LT_ERR_ARG;
     int rc = need_params(c);
@@ -473,10 +524,12 @@ int sg_response(void *ctx, const lt_light *light, float *K_out, int is_device) {
     if ((rc = forward_rows(c, design_args(c, 1)))) return rc;
     if ((rc = check_device(c))) return rc;
     return copy_to(c, K_out, c->d_K, (size_t)c->n * sizeof(float), is_device);
+    LT_CATCH(ctx)
 }
 
 int sg_design(void *ctx, const lt_light *lights, int32_t n_lights, const float *E_target, const float *alpha,
               double *loss_out, double *grad_out, float *E_out) {
+    LT_TRY
     SgCtx *c = static_cast<SgCtx *>(ctx);
     if (!c || !lights || !E_target || n_lights <= 0) return LT_ERR_ARG;
     if (n_lights > LT_MAX_LIGHTS) return fail(c, LT_ERR_ARG, "more lights than LT_MAX_LIGHTS");
@@ -519,9 +572,11 @@ int sg_design(void *ctx, const lt_light *lights, int32_t n_lights, const float *
     if (grad_out) std::memcpy(grad_out, h, (size_t)n_lights * 8 * sizeof(double));
     if (loss_out) *loss_out = h[(size_t)n_lights * 8];
     return LT_OK;
+    LT_CATCH(ctx)
 }
 
 int sg_network(void *ctx, const float *X, int32_t rows, const float *dO, float *O_out, float *dX_out, float *dW_out) {
+    LT_TRY
     SgCtx *c = static_cast<SgCtx *>(ctx);
     if (!c || !X || !O_out || rows <= 0 || rows > SG_MAX_BATCH) return LT_ERR_ARG;
     if (!c->has_params) return fail(c, LT_ERR_STATE, "no parameters (sg_set_params)");
@@ -560,17 +615,21 @@ int sg_network(void *ctx, const float *X, int32_t rows, const float *dO, float *
         SG_CUDA(c, cudaMemcpyAsync(dX_out, c->d_dX, need * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
     SG_CUDA(c, cudaStreamSynchronize(c->stream));
     return LT_OK;
+    LT_CATCH(ctx)
 }
 
 int sg_set_kernels(void *ctx, int flags) {
+    LT_TRY
     SgCtx *c = static_cast<SgCtx *>(ctx);
     if (!c || (flags & ~(SG_KERNELS_DESIGN_TC | SG_KERNELS_TRAIN_TC))) return LT_ERR_ARG;
     c->use_tc = (flags & SG_KERNELS_DESIGN_TC) ? 1 : 0;
     c->train_tc = (flags & SG_KERNELS_TRAIN_TC) ? 1 : 0;
     return LT_OK;
+    LT_CATCH(ctx)
 }
 
 int sg_encode(void *ctx, const float *xn, int32_t rows, float *enc_out) {
+    LT_TRY
     SgCtx *c = static_cast<SgCtx *>(ctx);
     if (!c || !xn || !enc_out || rows <= 0 || rows > SG_MAX_BATCH) return LT_ERR_ARG;
     if (!c->has_params) return fail(c, LT_ERR_STATE, "no parameters (sg_set_params)");
@@ -592,6 +651,7 @@ int sg_encode(void *ctx, const float *xn, int32_t rows, float *enc_out) {
                                c->stream));
     SG_CUDA(c, cudaStreamSynchronize(c->stream));
     return LT_OK;
+    LT_CATCH(ctx)
 }
 
 }  // extern "C"

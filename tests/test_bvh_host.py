@@ -142,3 +142,18 @@ def test_refusals(lib):
                           None, ctypes.byref(n_nodes), ctypes.byref(d))
     assert rc == lighttrace.LT_ERR_ARG and n_nodes.value > 1 and d.value >= 2     # counts still written
     assert lighttrace.BVH_NODE_DTYPE.itemsize == ctypes.sizeof(lighttrace.lt_bvh_node) == 240
+
+
+def test_host_allocation_failure_is_a_status(lib, monkeypatch):
+    """An exception inside the library (here an injected std::bad_alloc in
+    the BVH build) comes back as LT_ERR_OOM, not as a crash, and the next
+    call works."""
+    xyz = np.ascontiguousarray(scenes.cornell_box(res=8).xyz, np.float32)
+    n_nodes, d = ctypes.c_int32(-1), ctypes.c_int32(-1)
+    monkeypatch.setenv("LT_FAULT_HOST_ALLOC", "1")
+    rc = lib.lt_build_bvh(xyz.ctypes.data_as(ctypes.c_void_p), xyz.shape[0], None, 0, None, ctypes.byref(n_nodes),
+                          ctypes.byref(d))
+    assert rc == lighttrace.LT_ERR_OOM and n_nodes.value == -1
+    monkeypatch.delenv("LT_FAULT_HOST_ALLOC")
+    nodes, order, depth = lighttrace.build_bvh(xyz)
+    _check_tree(xyz, nodes, order, depth)

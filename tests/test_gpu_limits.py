@@ -1,7 +1,8 @@
 """Edge sizes on the GPU against the oracle: the maximum light count
 (LT_MAX_LIGHTS luminaires of all three kinds, a photon budget that does not
 divide evenly), the maximum path length (64 hits in a closed box, against
-the closed-form energy), and the arguments beyond the limits."""
+the closed-form energy), the arguments beyond the limits, and a failed scene
+upload (host allocation failure, injected on the host)."""
 import numpy as np
 import pytest
 
@@ -88,3 +89,25 @@ def test_power_beyond_the_fixed_point_range(tr):
     tr.trace_forward(1, 1000, 3)                          # large but representable
     assert np.isfinite(tr.irradiance()).all()
 
+
+
+def test_failed_scene_upload_keeps_the_previous_scene(tr, monkeypatch):
+    """A host allocation failure inside lt_upload_scene (injected) is
+    LT_ERR_OOM with a message; the context keeps the scene it had, traces it
+    bit for bit as before, and takes the next upload."""
+    from paper_2310_02043_gb300.lighttrace import LT_ERR_OOM
+    sc = scenes.cornell_box(res=8)
+    L = scenes.make_lights([scenes.point_light((0.5, 0.5, 0.9), 1.0)])
+    tr.upload_scene(sc)
+    tr.set_lights(L)
+    tr.trace_forward(5, 1 << 16, 3)
+    q = tr.texel_sums().copy()
+    monkeypatch.setenv("LT_FAULT_HOST_ALLOC", "1")
+    with pytest.raises(LtError) as e:
+        tr.upload_scene(scenes.cornell_box(res=16))
+    assert e.value.status == LT_ERR_OOM and "host memory" in str(e.value)
+    monkeypatch.delenv("LT_FAULT_HOST_ALLOC")
+    tr.trace_forward(5, 1 << 16, 3)
+    assert np.array_equal(tr.texel_sums(), q)
+    big = scenes.cornell_box(res=16)
+    assert tr.upload_scene(big) == big.n_texels
