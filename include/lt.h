@@ -21,6 +21,9 @@
  *     Calls that return a value in host memory synchronise that stream.
  *   - Host input arrays are copied; the caller keeps ownership. Output
  *     pointers are caller-owned and must hold the stated number of elements.
+ *   - A context is not thread-safe: calls on one context must not overlap
+ *     (the caller serialises them). Separate contexts share no state, except
+ *     the fixed scratch array of lt_loss_static (see there).
  *   - "is_device" arguments say whether a pointer is device memory (1) or
  *     host memory (0) of the context's device.
  *   - Light parameter / gradient slot order is LT_GRAD_*:

@@ -39,7 +39,10 @@
  * error, message in sg_last_error); host inputs are copied; device pointers
  * are caller-owned and must stay valid for the calls that use them; all work
  * runs on the context's stream, and calls that return host values
- * synchronise it. The light record is lt_light (lt.h); only spot lights are
+ * synchronise it. No C++ exception crosses the interface (host memory
+ * running out is LT_ERR_OOM). A context is not thread-safe: calls on one
+ * context must not overlap; separate contexts share no state. The light
+ * record is lt_light (lt.h); only spot lights are
  * modelled, and the surrogate gives no gradient for theta_out (it is trained
  * at one outer cone).
  */
