@@ -227,7 +227,11 @@ LT_API int lt_set_adjoint_weights(void *ctx, const float *w, int is_device);
  * held fixed (Sec. 4.4.2: Eq. 14 for position, Eq. S.11-S.12 for the spot
  * edge, Eq. 15 for orientation, I_e = p^2/2 for intensity). Writes dO/dp as
  * double [n_lights][LT_GRAD_N] to grad_out. Needs weights from lt_loss or
- * lt_set_adjoint_weights. Deterministic for a given launch configuration. */
+ * lt_set_adjoint_weights. Each thread sums its photons' terms in FP32 in
+ * photon order and the sums over threads are formed in FP64 in a fixed
+ * order: deterministic for a given launch configuration; another launch
+ * shape or photon partition regroups the FP32 sums (relative changes of
+ * order 1e-7). */
 LT_API int lt_trace_adjoint(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
                      uint64_t photon_end, double *grad_out, int is_device);
 

@@ -52,7 +52,7 @@ struct Ctx {
     double scale = 1.0;
     bool fwd_done = false, has_w = false;
     double *d_loss = nullptr, *d_partial = nullptr, *d_grad = nullptr;
-    double *d_slots = nullptr;             // per-thread adjoint gradient sums
+    float *d_slots = nullptr;              // per-thread adjoint gradient sums (FP32)
     size_t slots_bytes = 0;
     unsigned long long *d_seg = nullptr;   // [2]: forward, adjoint
     int32_t *d_err = nullptr;
@@ -78,7 +78,8 @@ struct Ctx {
         double *h_out = nullptr;              // pinned: loss[n_designs], grad[n_lights][8]
         unsigned long long *d_q = nullptr;
         float *d_E = nullptr, *d_w = nullptr;
-        double *d_partial = nullptr, *d_loss = nullptr, *d_grad = nullptr, *d_slots = nullptr;
+        double *d_partial = nullptr, *d_loss = nullptr, *d_grad = nullptr;
+        float *d_slots = nullptr;
         size_t in_bytes = 0, slots_bytes = 0;
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
@@ -391,7 +392,7 @@ int batch_prepare(Ctx *c, BatchLaunch *bl) {
     const uint64_t min_nl = b.photons / (uint64_t)max_count;
     bl->adj.n_slots = min_nl == 0 ? b.n_lights
                                   : (int32_t)std::min<uint64_t>((uint64_t)b.n_lights, bl->adj.chunk / min_nl + 2);
-    const size_t need = (size_t)bl->grid_a * (size_t)bl->threads_a * (size_t)bl->adj.n_slots * 8 * sizeof(double);
+    const size_t need = (size_t)bl->grid_a * (size_t)bl->threads_a * (size_t)bl->adj.n_slots * 8 * sizeof(float);
     if (need > b.slots_bytes) {
         LT_CUDA(c, cudaStreamSynchronize(b.stream));
         dfree(b.d_slots);
@@ -896,7 +897,7 @@ int lt_trace_adjoint(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_h
     p.max_iters = step_limit(p);
     const uint64_t min_nl = n_photons / (uint64_t)L;
     p.n_slots = min_nl == 0 ? L : (int32_t)std::min<uint64_t>((uint64_t)L, p.chunk / min_nl + 2);
-    const size_t need = (size_t)grid * (size_t)threads * (size_t)p.n_slots * 8 * sizeof(double);
+    const size_t need = (size_t)grid * (size_t)threads * (size_t)p.n_slots * 8 * sizeof(float);
     if (need > c->slots_bytes) {
         LT_CUDA(c, cudaStreamSynchronize(c->stream));
         dfree(c->d_slots);

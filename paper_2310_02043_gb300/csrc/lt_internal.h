@@ -119,7 +119,7 @@ struct TraceParams {
     uint64_t chunk;             // photons per thread (contiguous)
     // adjoint
     const float *w;             // [n_texels] dO/dPhi per deposit
-    double *slots;              // [threads][n_slots][8] per-thread gradient sums
+    float *slots;               // [threads][n_slots][8] per-thread gradient sums (FP32, fixed order)
     int32_t n_slots;            // lights a thread's chunk can touch
     // debug record
     int32_t *rec_tri;

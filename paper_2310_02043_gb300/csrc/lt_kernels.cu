@@ -657,7 +657,7 @@ __global__ void __launch_bounds__(kSmem ? kThreadsStaged : kThreadsL1, kTraceMin
     const uint64_t p_end = P.photon_begin + min((tid + 1) * chunk, n);
     int32_t first_light = 0;
     if (kAdjoint)
-        for (int i = 0; i < P.n_slots * 8; ++i) P.slots[tid * (uint64_t)P.n_slots * 8 + i] = 0.0;
+        for (int i = 0; i < P.n_slots * 8; ++i) P.slots[tid * (uint64_t)P.n_slots * 8 + i] = 0.0f;
 
     int32_t l = 0, seg = 0, skip = -1;
     float phi = 0.0f, a_emit = 0.0f, g = 0.0f, beta = 1.0f;
@@ -763,9 +763,12 @@ __global__ void __launch_bounds__(kSmem ? kThreadsStaged : kThreadsL1, kTraceMin
                     const float3 n1 = make_float3(sgn * __ldg(nn), sgn * __ldg(nn + 1), sgn * __ldg(nn + 2));
                     float dp[8];
                     dflux(L, L.flux_k * a_emit, a_emit, q, x1x, x1y, x1z, n1, dp);
-                    double *o = P.slots + (tid * (uint64_t)P.n_slots + (uint64_t)(l - first_light)) * 8;
+                    // FP32 per-thread sums in photon order (FP64 arithmetic runs at a
+                    // small fraction of the FP32 rate on this GPU); the totals over
+                    // threads are formed in FP64 by grad_finalize_kernel.
+                    float *o = P.slots + (tid * (uint64_t)P.n_slots + (uint64_t)(l - first_light)) * 8;
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) o[k] += (double)(g * dp[k]);
+                    for (int k = 0; k < 8; ++k) o[k] = fmaf(g, dp[k], o[k]);
                 }
                 ++photon;
                 if (photon >= p_end) active = false;
@@ -932,9 +935,9 @@ __global__ void __launch_bounds__(256) grad_finalize_kernel(const TraceParams P,
         const uint64_t t0 = (lo - P.photon_begin) / P.chunk, t1 = (hi - 1 - P.photon_begin) / P.chunk;
         for (uint64_t t = t0 + threadIdx.x; t <= t1; t += blockDim.x) {
             const int32_t s = l - light_of(P, P.photon_begin + t * P.chunk);
-            const double *src = P.slots + (t * (uint64_t)P.n_slots + (uint64_t)s) * 8;
+            const float *src = P.slots + (t * (uint64_t)P.n_slots + (uint64_t)s) * 8;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) v[k] += src[k];
+            for (int k = 0; k < 8; ++k) v[k] += (double)src[k];
         }
     }
     for (int k = 0; k < 8; ++k) {

@@ -68,7 +68,7 @@ def test_batch_designs_equal_single_design_passes(setup):
         assert np.mean(diff == 0) > 0.999, info
         assert loss[d] == pytest.approx(O, rel=1e-9), d
         gb = grad[off:off + len(L)]
-        assert np.allclose(gb, g, rtol=1e-6, atol=1e-9 * np.abs(g).max()), d
+        assert np.allclose(gb, g, rtol=1e-5, atol=1e-6 * np.abs(g).max()), d
         off += len(L)
     tr.set_design(0)
 
@@ -95,7 +95,7 @@ def test_batch_with_point_spot_and_area_lights(setup):
         assert np.all(diff <= 1e-6 * np.abs(E) + 1e-9 * E.max()), d
         assert loss[d] == pytest.approx(O, rel=1e-9), d
         gb = grad[off:off + len(L)]
-        assert np.allclose(gb, g, rtol=1e-6, atol=1e-9 * np.abs(g).max()), d
+        assert np.allclose(gb, g, rtol=1e-5, atol=1e-6 * np.abs(g).max()), d
         # slots that exist for each kind: orientation for spots and area
         # lights, cone angles for spots only
         kinds = L[:, 0]
@@ -156,5 +156,6 @@ def test_autotuned_shape_keeps_the_results(setup, tmp_path):
     loss, grad = tr.batch_step(3, 4, use_graph=True)
     assert np.array_equal(tr.batch_texel_sums(2), q0)
     assert np.allclose(loss, ref_loss, rtol=1e-12)
-    assert np.allclose(grad, ref_grad, rtol=1e-9, atol=1e-12 * np.abs(ref_grad).max())
+    # another launch shape regroups the photons of the per-thread FP32 sums
+    assert np.allclose(grad, ref_grad, rtol=1e-5, atol=1e-6 * np.abs(ref_grad).max())
     tr.set_launch(256, 0, 200 * 1024)

@@ -69,7 +69,9 @@ def test_gradient_partition_and_sampled_range(office):
     g_full = tr.trace_adjoint(SEED, N, HITS)
     cuts = [0, 3_000_001, 9_999_999, N]
     g_sum = sum(tr.trace_adjoint(SEED, N, HITS, a, b) for a, b in zip(cuts[:-1], cuts[1:]))
-    assert np.allclose(g_sum, g_full, rtol=1e-9, atol=1e-9 * np.abs(g_full).max())
+    # a partition changes which photons share a thread's FP32 sum (the totals
+    # over threads are FP64), so the parts agree with the whole to FP32 rounding
+    assert np.allclose(g_sum, g_full, rtol=1e-5, atol=1e-6 * np.abs(g_full).max())
     begin, count = (1 << 22) + 99, 8192
     g = tr.trace_adjoint(SEED, N, HITS, begin, begin + count)
     g_ref, _ = oracle.adjoint(sc, L, SEED, N, HITS, w.astype(np.float64), begin=begin, end=begin + count)
