@@ -110,10 +110,23 @@ typedef struct {
 LT_API int lt_version(void);
 
 /* Create a context on CUDA device `device`; work goes to `cuda_stream`
- * (a cudaStream_t; NULL = the legacy default stream). */
+ * (a cudaStream_t; NULL = the legacy default stream). The context owns every
+ * device buffer it allocates. LT_ERR_ARG for a NULL ctx_out or a device
+ * index out of range, LT_ERR_CUDA if the device cannot be set up; *ctx_out
+ * is NULL on failure. */
 LT_API int lt_create(void **ctx_out, int device, void *cuda_stream);
+
+/* Free a context and all its device and pinned host memory (waits for its
+ * stream). NULL is allowed and does nothing. */
 LT_API int lt_destroy(void *ctx);
+
+/* Queue later work of the context on `cuda_stream` (a cudaStream_t of the
+ * context's device; the caller keeps it alive). Work already queued is not
+ * moved: order the two streams if they overlap. */
 LT_API int lt_set_stream(void *ctx, void *cuda_stream);
+
+/* Message of the context's last failed call ("" if none), valid until the
+ * next call on the context; "null context" for NULL. */
 LT_API const char *lt_last_error(const void *ctx);
 
 /* Upload a triangle scene (host arrays, copied) and build its wide BVH.
@@ -243,6 +256,9 @@ LT_API int lt_trace_adjoint(void *ctx, uint64_t seed, uint64_t n_photons, int32_
 LT_API int lt_debug_paths(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
                    uint64_t count, int32_t *tri_out, int64_t *texel_out, double *grad_out);
 
+/* Counters of the last forward and adjoint passes and facts about the
+ * uploaded scene (lt_stats above), copied into caller memory. Synchronises
+ * the context's stream (the segment counters are read from the device). */
 LT_API int lt_get_stats(void *ctx, lt_stats *out);
 
 /* Forward pass exactly as lt_trace_forward (same texel sums) through a
