@@ -315,8 +315,12 @@ LT_API int lt_batch_step(void *ctx, uint64_t seed_fwd, uint64_t seed_adj, double
  * one, on this stream. */
 LT_API int lt_batch_stream(void *ctx, void **stream_out);
 
-/* Texel sums (int64) and irradiance (float) of one design after a step. */
+/* Texel sums (int64 [n_texels], fixed point with the batch's scale) of one
+ * design after a step, into host or device memory (is_device). */
 LT_API int lt_batch_texel_sums(void *ctx, int32_t design, int64_t *q_out, int is_device);
+
+/* Irradiance (float [n_texels]) of one design after a step, into host or
+ * device memory (is_device). */
 LT_API int lt_batch_irradiance(void *ctx, int32_t design, float *E_out, int is_device);
 
 /* Objective and adjoint weights for callers that cannot allocate device

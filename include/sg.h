@@ -65,10 +65,18 @@ extern "C" {
 #define SG_OUT 16
 #define SG_MAX_BATCH (1 << 20)
 
-/* Create / destroy a surrogate context on CUDA device `device`, work on
- * `cuda_stream` (a cudaStream_t; NULL = legacy default stream). */
+/* Create a surrogate context on CUDA device `device`, work on `cuda_stream`
+ * (a cudaStream_t; NULL = legacy default stream). The context owns its
+ * device buffers. LT_ERR_ARG for a NULL ctx_out; LT_ERR_CUDA when the device
+ * does not exist or its buffers cannot be set up. */
 LT_API int sg_create(void **ctx_out, int device, void *cuda_stream);
+
+/* Free a context and its device memory after its stream drains; LT_ERR_ARG
+ * for NULL. */
 LT_API int sg_destroy(void *ctx);
+
+/* Message of the context's last failed call, valid until the next call on
+ * it; "null context" for NULL. */
 LT_API const char *sg_last_error(const void *ctx);
 
 /* Texel centres pos [n][3] and unit normals normal [n][3] (as lt_texel_centres
@@ -81,6 +89,10 @@ LT_API int sg_set_texels(void *ctx, const float *pos, const float *normal, const
  * [out][in]) and table [SG_TABLE_FLOATS] fp32 ([level][entry][feature]),
  * host or device (is_device). Setting resets the Adam moments and step. */
 LT_API int sg_set_params(void *ctx, const float *weights, const float *table, int is_device);
+
+/* Copy of the current parameters, laid out as for sg_set_params: the fp32
+ * master weights and the table, into host or device memory (is_device).
+ * LT_ERR_STATE before sg_set_params. */
 LT_API int sg_get_params(void *ctx, float *weights, float *table, int is_device);
 
 /* Training data: n_solves unit-intensity spots (host, copied) and their

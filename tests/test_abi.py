@@ -55,3 +55,16 @@ def test_version_and_argument_checks(lib):
 def test_struct_layouts_match_the_header():
     assert ctypes.sizeof(lighttrace.lt_light) == 36
     assert ctypes.sizeof(lighttrace.lt_stats) == 8 * 5 + 4 * 4 + 8 + 4 * 2
+
+
+def test_every_declaration_is_documented():
+    """Each exported function of the headers sits directly under a comment
+    that states what it does."""
+    for header in ("lt.h", "sg.h"):
+        lines = open(os.path.join(ROOT, "include", header)).read().split("\n")
+        for i, line in enumerate(lines):
+            m = re.match(r"^(LT_API|SG_API)\b.*?\b((lt|sg)_[a-z_0-9]+)\(", line)
+            if not m:
+                continue
+            prev = lines[i - 1]
+            assert prev.rstrip().endswith("*/") or prev.startswith("#define"), (header, m.group(2))
