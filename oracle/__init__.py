@@ -1,7 +1,8 @@
 """CPU oracle for view-independent adjoint light tracing (test infrastructure).
 
 Only the test suite, ``__graft_entry__.smoke()`` and the benchmark's
-CPU-baseline leg may import this package. The product path never does.
+CPU-baseline and reference legs may import this package. The product path
+never does.
 
 The light transport lives in ``oracle.c`` (plain C, double precision; see its
 header for what it follows in the paper). This module compiles it, loads it

@@ -2,7 +2,7 @@
  * oracle.c -- plain, slow CPU oracle for view-independent adjoint light tracing.
  *
  * TEST INFRASTRUCTURE. Only the test suite, the package smoke check and the
- * benchmark's CPU-baseline leg load this library. The product path (the CUDA
+ * benchmark's CPU-baseline and reference legs load this library. The product path (the CUDA
  * library and its Python binding) never calls it, shares no code with it and
  * fails when its own extension is missing.
  *
