@@ -209,9 +209,20 @@ def cpu_baseline(sc, lights, truth, budget_s=15.0):
     _, seg_adj = oracle.adjoint(sc, lights, 3, PHOTONS, HITS, w, begin=0, end=n)
     t3 = time.perf_counter()
     segs = f["segments"] + seg_adj
+    # the same passes on one thread, over a smaller photon range
+    n1 = 1 << 12
+    t4 = time.perf_counter()
+    f1 = oracle.forward(sc, lights, 2, PHOTONS, HITS, begin=0, end=n1, threads=1)
+    _, w1 = oracle.loss(sc, f1["E"], target, np.ones(sc.n_texels))
+    _, seg1 = oracle.adjoint(sc, lights, 3, PHOTONS, HITS, w1, begin=0, end=n1, threads=1)
+    t5 = time.perf_counter()
+    segs1 = f1["segments"] + seg1
     return {"value": segs / (t3 - t0) / 1e6, "unit": "Msegments/s", "cores": cores, "kind": "oracle",
             "sample": f"photons [0, {n}) of the 2^24 budget, forward + loss + adjoint, brute-force FP64 oracle "
-                      f"({segs} segments in {t3 - t0:.1f} s: forward {t1 - t0:.1f} s, adjoint {t3 - t2:.1f} s)"}
+                      f"({segs} segments in {t3 - t0:.1f} s: forward {t1 - t0:.1f} s, adjoint {t3 - t2:.1f} s)",
+            "single_thread": {"value": segs1 / (t5 - t4) / 1e6, "unit": "Msegments/s",
+                              "sample": f"photons [0, {n1}), same passes, one thread ({segs1} segments in "
+                                        f"{t5 - t4:.1f} s)"}}
 
 
 def run_reference(args):
