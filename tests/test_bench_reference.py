@@ -40,3 +40,16 @@ def test_reference_arm_other_ranks_do_nothing():
     r = _run({"RANK": "1", "WORLD_SIZE": "2"})
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [l for l in r.stdout.splitlines() if l.strip().startswith("{")]
+
+
+def test_cpu_baseline_record():
+    """The GPU arm's cpu_baseline record: the oracle timed on the host cores
+    over a bounded sample, with a single-thread figure beside it."""
+    sys.path.insert(0, ROOT)
+    import bench
+    sc, lights, truth = bench.workload()
+    r = bench.cpu_baseline(sc, lights, truth, budget_s=1.0)
+    assert r["kind"] == "oracle" and r["unit"] == "Msegments/s" and r["cores"] == (os.cpu_count() or 1)
+    assert r["value"] > 0 and r["sample"].startswith("photons [0, ")
+    st = r["single_thread"]
+    assert st["unit"] == "Msegments/s" and 0 < st["value"] and "one thread" in st["sample"]
