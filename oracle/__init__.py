@@ -59,7 +59,7 @@ def _declare(lib):
     scene = [vp, vp, vp, vp, i32, vp, vp, i32]
     lib.or_forward.argtypes = scene + [vp, i32, u64, u32, u64, u64, u64, i32, vp, vp, vp, ci]
     lib.or_adjoint.argtypes = scene + [vp, i32, u64, u32, u64, u64, u64, i32, vp, vp, vp, ci]
-    lib.or_paths.argtypes = scene + [vp, i32, u64, u32, u64, u64, u64, i32, vp, vp, vp, vp, ci]
+    lib.or_paths.argtypes = scene + [vp, i32, u64, u32, u64, u64, u64, i32, vp, vp, vp, vp, vp, ci]
     lib.or_closest_hits.argtypes = [vp, i32, vp, vp, vp, i64, i32, vp, vp, vp]
     lib.or_philox4x32_10.argtypes = [vp, vp, vp]
     lib.or_philox4x32_10.restype = None
@@ -128,21 +128,26 @@ def adjoint(scene, lights, seed: int, n_photons: int, max_hits: int, w, begin: i
 
 
 def paths(scene, lights, seed: int, n_photons: int, max_hits: int, begin: int, count: int, design: int = 0,
-          threads: int = 0, w=None):
+          threads: int = 0, w=None, flux: bool = False):
     """Triangle and texel of every hit of photons [begin, begin + count); with
-    adjoint weights w, also each photon's gradient term [count, 8]."""
+    adjoint weights w, also each photon's gradient term [count, 8]; with
+    flux=True, also the flux Phi_i deposited at every hit [count, max_hits]
+    (last in the returned tuple)."""
     lib = _load()
     sargs, keep = _scene_args(scene)
     lp = np.ascontiguousarray(lights, np.float64)
     tri = np.empty((count, max_hits), np.int32)
     tex = np.empty((count, max_hits), np.int64)
+    phi = np.empty((count, max_hits), np.float64) if flux else None
     wv = np.ascontiguousarray(w, np.float64) if w is not None else None
     g = np.empty((count, 8), np.float64) if w is not None else None
     rc = lib.or_paths(*sargs, _p(lp), lp.shape[0], seed, design, n_photons, begin, count, max_hits, _p(tri),
-                      _p(tex), _p(wv) if w is not None else None, _p(g) if w is not None else None, threads)
+                      _p(tex), _p(phi) if flux else None, _p(wv) if w is not None else None,
+                      _p(g) if w is not None else None, threads)
     if rc != 0:
         raise ValueError(f"or_paths failed ({rc})")
-    return (tri, tex, g) if w is not None else (tri, tex)
+    out = (tri, tex) + ((g,) if w is not None else ()) + ((phi,) if flux else ())
+    return out
 
 
 def loss(scene, E, target, alpha):

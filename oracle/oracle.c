@@ -502,6 +502,7 @@ typedef struct {
     double grad[8]; int has_grad;
     /* path record */
     int32_t *rec_tri; int64_t *rec_texel;
+    double *rec_phi;        /* flux Phi_i deposited at each hit (may be NULL) */
     uint64_t segments;
 } or_path_io;
 
@@ -530,6 +531,7 @@ static void trace_photon(const or_scene *s, const or_light *L, int32_t n_lights,
         tri_normal(s, h.tri, n);
         if (dot3(n, w) > 0.0) { n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2]; }
         if (io->rec_tri) { io->rec_tri[i - 1] = h.tri; io->rec_texel[i - 1] = t; }
+        if (io->rec_phi) io->rec_phi[i - 1] = phi;
         if (io->dep) {                                  /* Eq. 8, n = 0 box basis */
             io->dep[io->n_dep].texel = t;
             io->dep[io->n_dep].phi = phi;
@@ -679,13 +681,16 @@ int or_adjoint(const float *xyz, const float *uv, const int32_t *tile, const flo
 }
 
 /* Path record for photons [begin, begin + count): triangle and texel of every
- * hit (-1 after the path ends). With adjoint weights w (may be NULL),
- * grad_out [count][8] receives each photon's own gradient term. */
+ * hit (-1 after the path ends). phi_out (may be NULL) [count][max_hits]
+ * receives the flux Phi_i each hit deposits (0 after the path ends). With
+ * adjoint weights w (may be NULL), grad_out [count][8] receives each
+ * photon's own gradient term. */
 int or_paths(const float *xyz, const float *uv, const int32_t *tile, const float *albedo, int32_t n_tri,
              const int32_t *res, const double *tile_area, int32_t n_tiles,
              const double *light_params, int32_t n_lights,
              uint64_t seed, uint32_t design, uint64_t n_photons, uint64_t begin, uint64_t count, int32_t max_hits,
-             int32_t *tri_out, int64_t *texel_out, const double *w, double *grad_out, int n_threads)
+             int32_t *tri_out, int64_t *texel_out, double *phi_out, const double *w, double *grad_out,
+             int n_threads)
 {
     if (n_lights <= 0 || max_hits <= 0 || begin + count > n_photons) return -1;
     or_scene s;
@@ -700,6 +705,10 @@ int or_paths(const float *xyz, const float *uv, const int32_t *tile, const float
         io.rec_tri = tri_out + (size_t)k * max_hits;
         io.rec_texel = texel_out + (size_t)k * max_hits;
         for (int32_t i = 0; i < max_hits; ++i) { io.rec_tri[i] = -1; io.rec_texel[i] = -1; }
+        if (phi_out) {
+            io.rec_phi = phi_out + (size_t)k * max_hits;
+            for (int32_t i = 0; i < max_hits; ++i) io.rec_phi[i] = 0.0;
+        }
         io.w = w;
         trace_photon(&s, L, n_lights, seed, design, begin + (uint64_t)k, max_hits, &io);
         if (grad_out)

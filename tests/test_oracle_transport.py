@@ -80,6 +80,31 @@ def test_energy_closed_cube_point_light_is_exact():
     assert r["segments"] == 20000 * B and r["deposits"] == 20000 * B
 
 
+def test_path_record_flux_per_hit():
+    # The path record's per-hit flux (Eq. 7): in a closed cube with a point
+    # light every ray carries I 4 pi / N, and hit i of every photon carries
+    # rho^(i-1) of it, so the flux of hit i summed over photons is
+    # 4 pi I rho^(i-1) exactly; with per-face albedo, hit i + 1 carries hit
+    # i's flux times the albedo of the face hit i landed on.
+    rho, B, I, n = 0.6, 4, 1.7, 5000
+    sc = scenes.closed_cube(size=1.0, res=6, albedo=rho)
+    L = scenes.make_lights([scenes.point_light((0.31, 0.62, 0.44), I)])
+    tri, tex, phi = oracle.paths(sc, L, 3, n, B, 0, n, flux=True)
+    assert np.all(tri >= 0)
+    rho32 = float(np.float32(rho))
+    for i in range(B):
+        assert phi[:, i].sum() == pytest.approx(4 * np.pi * I * rho32 ** i, rel=1e-12)
+    rho_face = np.array([0.9, 0.1, 0.3, 0.6, 0.45, 0.75], np.float32)
+    sc.albedo = np.ascontiguousarray(rho_face[sc.tile])
+    tri, tex, phi = oracle.paths(sc, L, 3, n, B, 0, n, flux=True)
+    ratio = phi[:, 1:] / phi[:, :-1]
+    np.testing.assert_allclose(ratio, rho_face[sc.tile[tri[:, :-1]]].astype(np.float64), rtol=1e-13)
+    # the record's deposits are the forward pass's (Eq. 8)
+    A = oracle.texel_areas(sc)
+    E = np.bincount(tex.ravel(), weights=phi.ravel(), minlength=sc.n_texels) / A
+    np.testing.assert_allclose(E, oracle.forward(sc, L, 3, n, B)["E"], rtol=1e-12, atol=0)
+
+
 def test_bounce_flux_uses_the_albedo_of_the_surface_left():
     # Eq. 7 with a Lambertian f and cosine sampling: Phi_{i+1} = rho(x_i) Phi_i.
     # With per-face albedo, the second-hit energy equals sum_f rho_f times the
