@@ -101,7 +101,7 @@ typedef struct {
     int32_t n_nodes;             /* wide-BVH nodes */
     int32_t bvh_depth;           /* levels of wide nodes */
     int32_t staged_nodes;        /* nodes held in shared memory per block */
-    double fixed_point_scale;    /* S: a texel accumulates round(Phi * S) */
+    double fixed_point_scale;    /* S of the last forward pass (single or batch): a texel accumulates round(Phi * S) */
     int32_t grid_blocks;         /* launch shape of the last forward pass (single or batch) */
     int32_t block_threads;
 } lt_stats;
@@ -240,13 +240,31 @@ LT_API int lt_set_adjoint_weights(void *ctx, const float *w, int is_device);
  * held fixed (Sec. 4.4.2: Eq. 14 for position, Eq. S.11-S.12 for the spot
  * edge, Eq. 15 for orientation, I_e = p^2/2 for intensity). Writes dO/dp as
  * double [n_lights][LT_GRAD_N] to grad_out. Needs weights from lt_loss or
- * lt_set_adjoint_weights. Each thread sums its photons' terms in FP32 in
- * photon order and the sums over threads are formed in FP64 in a fixed
- * order: deterministic for a given launch configuration; another launch
- * shape or photon partition regroups the FP32 sums (relative changes of
- * order 1e-7). */
+ * lt_set_adjoint_weights. Exact summation: every photon's term (a float) is
+ * multiplied by the gradient scale G = 2^-e, e the binary exponent of
+ * max_t |w_t| times the largest flux constant I_e Omega / N_l of the lights
+ * (the size of a typical term), rounded to a multiple of 2^-64 and added as
+ * a 128-bit two's-complement integer; the integer sums are converted once,
+ * correctly rounded, to double and scaled by 2^-64 / G. The result is
+ * therefore bitwise the same for every launch shape, and the integer sums
+ * of a partition of the photon range add up exactly to those of the whole
+ * (lt_gradient_fixed). A term that is not finite or reaches 2^62 / G
+ * returns LT_ERR_OVERFLOW. The pass keeps a 16-byte record per photon of
+ * the range (its adjoint state and first hit) between its trace kernel and
+ * its gradient kernel; the context holds that buffer and reuses it. */
 LT_API int lt_trace_adjoint(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
                      uint64_t photon_end, double *grad_out, int is_device);
+
+/* The exact gradient sums of the last lt_trace_adjoint: per light and slot
+ * ([n_lights][LT_GRAD_N]) a 128-bit two's-complement integer as two int64,
+ * low word first (sums_out: [n_lights][LT_GRAD_N][2] host), and the scale G
+ * (scale_out, host): dO/dp = integer x 2^-64 / G. Callers that split the
+ * photons of one budget over several passes or ranks (same weights, same
+ * lights, so the same G) add these integers (exactly, e.g. in 128-bit or
+ * arbitrary-precision arithmetic) and convert the sum once; the result
+ * equals the gradient of one pass over the whole range bit for bit.
+ * Synchronises the context's stream. LT_ERR_STATE before any adjoint pass. */
+LT_API int lt_gradient_fixed(void *ctx, int64_t *sums_out, double *scale_out);
 
 /* Debug record of photons [photon_begin, photon_begin + count): original
  * triangle index and texel of every hit, -1 after the path ends (host
@@ -346,6 +364,11 @@ LT_API int lt_batch_irradiance(void *ctx, int32_t design, float *E_out, int is_d
  * synchronised; the calling thread's current device is restored. The first
  * call on a device looks up the array's device address
  * (cudaGetSymbolAddress): make that first call before any stream capture.
+ * The address is kept for the life of the process: after cudaDeviceReset
+ * (or anything else that replaces the device's primary context) this call
+ * must not be used on that device again. If a CUDA error from earlier work
+ * is pending on the calling thread, the call returns LT_ERR_STATE without
+ * launching and leaves that error pending.
  * All calls on a device share the array -- nothing in it needs clearing, each
  * call writes every slot it reads -- so calls that overlap on the GPU (two
  * streams, two threads) race: order them on one stream. Returns only a
@@ -366,6 +389,25 @@ LT_API int lt_loss_static(int device, void *cuda_stream, const int64_t *q, doubl
  * nothing. A negative argument keeps the current value. The defaults are the
  * kernel's bound, as many blocks as fit, 72 KiB. */
 LT_API int lt_set_launch(void *ctx, int32_t threads_per_block, int32_t blocks_per_sm, int32_t smem_node_bytes);
+
+/* Give-up limit of the tracing kernels: BVH node visits one ray may make
+ * before the kernel ends that ray as a miss, records the give-up in the
+ * device error word and carries on (no kernel waits or traps). The next call
+ * that synchronises (lt_get_stats, lt_loss or lt_trace_adjoint into host
+ * memory, ...) then returns LT_ERR_TIMEOUT once and clears the word; the
+ * context stays usable. max_steps >= 1 sets the limit, 0 restores the
+ * default (16 x BVH nodes + 64, more than any ray of a valid tree needs);
+ * negative is LT_ERR_ARG. A test hook for that error path. */
+LT_API int lt_set_step_limit(void *ctx, int32_t max_steps);
+
+/* L2 read bandwidth of `device` (no context; a measurement aid, not part of
+ * the paper's method): a buffer of `bytes` (1 MiB .. 96 MiB, so it stays
+ * in the 129 MB L2) is swept `reps` times with 16-byte loads cached in L2
+ * only, after one warm-up sweep; writes the best of five timed runs (CUDA
+ * events) in GB/s to *gbs_out. Allocates and frees its own buffer and
+ * stream, synchronises, restores the calling thread's current device.
+ * LT_ERR_ARG for sizes out of range, LT_ERR_OOM / LT_ERR_CUDA on failure. */
+LT_API int lt_probe_l2_read(int device, uint64_t bytes, int32_t reps, double *gbs_out);
 
 #ifdef __cplusplus
 }

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libltrace.so")
-SOURCES = ["lt_kernels.cu", "lt_api.cpp", "lt_bvh.cpp", "lt_noalloc.cu", "sg_kernels.cu", "sg_api.cpp"]
+SOURCES = ["lt_kernels.cu", "lt_api.cpp", "lt_bvh.cpp", "lt_noalloc.cu", "lt_probe.cu", "sg_kernels.cu", "sg_api.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/lt.h"
 #include "lt_internal.h"
 
@@ -52,13 +54,23 @@ struct Ctx {
     double scale = 1.0;
     bool fwd_done = false, has_w = false;
     double *d_loss = nullptr, *d_partial = nullptr, *d_grad = nullptr;
-    float *d_slots = nullptr;              // per-thread adjoint gradient sums (FP32)
+    ulonglong2 *d_slots = nullptr;         // gradient kernel's per-thread sums (128-bit fixed point)
     size_t slots_bytes = 0;
+    PhotonAdj *d_rec = nullptr;            // per-photon adjoint records of the last adjoint pass
+    size_t rec_bytes = 0;
+    ulonglong2 *d_gpart = nullptr;         // [lights][parts][8] partial gradient sums
+    size_t gpart_bytes = 0;
+    ulonglong2 *d_gfix = nullptr;          // [LT_MAX_LIGHTS][8] exact gradient sums of the last adjoint pass
+    double *d_gscale = nullptr;            // their scale G
+    uint32_t *d_wmax = nullptr;            // max |w_t| (float bits) of the last adjoint pass
+    float flux_max = 0.0f;                 // largest flux constant of the uploaded lights
+    int32_t adj_lights = 0;                // lights of the last adjoint pass (0: none yet)
     unsigned long long *d_seg = nullptr;   // [2]: forward, adjoint
     int32_t *d_err = nullptr;
     double *h_pinned = nullptr;            // small pinned staging area
     // launch
     int threads = 0, blocks_per_sm = 0, smem_node_bytes = 72 * 1024;   // threads 0: the kernel's bound
+    int32_t max_steps = 0;                 // node visits per ray before giving up; 0: 16 x nodes + 64
     lt_stats stats{};
     // host copy of the uploaded charts (texel centres)
     std::vector<float> h_xyz, h_uv;
@@ -79,12 +91,28 @@ struct Ctx {
         unsigned long long *d_q = nullptr;
         float *d_E = nullptr, *d_w = nullptr;
         double *d_partial = nullptr, *d_loss = nullptr, *d_grad = nullptr;
-        float *d_slots = nullptr;
+        ulonglong2 *d_slots = nullptr;
+        PhotonAdj *d_rec = nullptr;
+        size_t rec_bytes = 0;
+        ulonglong2 *d_gfix = nullptr;         // [n_lights][8] exact gradient sums
+        ulonglong2 *d_gpart = nullptr;        // [n_lights][parts][8] partial gradient sums
+        size_t gpart_bytes = 0;
+        double *d_gscale = nullptr;
+        uint32_t *d_wmax = nullptr;
         size_t in_bytes = 0, slots_bytes = 0;
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
         uint64_t segments = 0;
     } batch;
+};
+
+// An NVTX range around an entry point, so profiler timelines show the ABI
+// calls with the kernels they launch (no cost without an attached tool).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
 int fail(Ctx *c, int code, const std::string &msg) {
@@ -156,6 +184,14 @@ cudaError_t dalloc(T *&p, size_t n) {
     return cudaMalloc(reinterpret_cast<void **>(&p), n * sizeof(T));
 }
 
+// Status of a non-zero device error word.
+int device_error(Ctx *c, int32_t e) {
+    if (e & kErrSteps) return fail(c, LT_ERR_TIMEOUT, "a ray exceeded its traversal step limit");
+    if (e & kErrRange)
+        return fail(c, LT_ERR_OVERFLOW, "a photon's gradient term is not finite or beyond the fixed-point range");
+    return fail(c, LT_ERR_DEVICE, "kernel error word " + std::to_string(e));
+}
+
 // Reads the device error word (synchronises the stream) and clears it.
 int check_device(Ctx *c) {
     int32_t e = 0;
@@ -163,8 +199,7 @@ int check_device(Ctx *c) {
     LT_CUDA(c, cudaStreamSynchronize(c->stream));
     if (e) {
         LT_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), c->stream));
-        if (e & kErrSteps) return fail(c, LT_ERR_TIMEOUT, "a ray exceeded its traversal step limit");
-        return fail(c, LT_ERR_DEVICE, "kernel error word " + std::to_string(e));
+        return device_error(c, e);
     }
     return LT_OK;
 }
@@ -251,6 +286,46 @@ double derive_lights(const lt_light *in, int32_t L, uint64_t n_photons, uint64_t
     return bound;
 }
 
+// Grows a device buffer to at least `bytes` (waits for `s` before freeing the
+// old one, whose contents are not kept). Sets *grown when it reallocated.
+template <class T>
+int grow(Ctx *c, T *&buf, size_t &cap, size_t bytes, cudaStream_t s, bool *grown = nullptr) {
+    if (bytes <= cap) return LT_OK;
+    LT_CUDA(c, cudaStreamSynchronize(s));
+    dfree(buf);
+    LT_CUDA(c, cudaMalloc(reinterpret_cast<void **>(&buf), bytes));
+    cap = bytes;
+    if (grown) *grown = true;
+    return LT_OK;
+}
+
+// Launch parameters of the gradient kernel (Eq. 11) after an adjoint trace
+// over the photons of `p`: kGradPhotonsPerThread photons per thread, a slot
+// per light that a thread's chunk can touch (chunk / fewest photons of a
+// light + 2, at most all lights).
+TraceParams grad_params(const TraceParams &p, uint64_t min_photons_per_light, ulonglong2 *slots) {
+    TraceParams g = p;
+    g.chunk = kGradPhotonsPerThread;
+    g.n_slots = min_photons_per_light == 0
+                    ? p.n_lights
+                    : (int32_t)std::min<uint64_t>((uint64_t)p.n_lights, g.chunk / min_photons_per_light + 2);
+    g.slots = slots;
+    return g;
+}
+
+size_t grad_slot_bytes(const TraceParams &g) {
+    const uint64_t n = g.photon_end - g.photon_begin;
+    return (size_t)((n + g.chunk - 1) / g.chunk) * (size_t)g.n_slots * 8 * sizeof(ulonglong2);
+}
+
+// Largest flux constant of n derived lights: with the largest adjoint weight
+// it sets the size of a typical gradient term and so the gradient scale.
+float max_flux(const LightDev *lights, int32_t n) {
+    float m = 0.0f;
+    for (int32_t l = 0; l < n; ++l) m = std::max(m, std::fabs(lights[l].flux_k));
+    return m;
+}
+
 int upload_lights(Ctx *c, uint64_t n_photons) {
     if (!c->lights_dirty && c->lights_for_n == n_photons) return LT_OK;
     const int32_t L = (int32_t)c->lights.size();
@@ -258,6 +333,7 @@ int upload_lights(Ctx *c, uint64_t n_photons) {
     LT_CUDA(c, cudaEventSynchronize(c->lights_copied));
     LightDev *h = c->h_lights;
     const double bound = derive_lights(c->lights.data(), L, n_photons, 0, 0, c->design_word, h);
+    c->flux_max = max_flux(h, L);
     LT_CUDA(c, cudaMemcpyAsync(c->d_lights, h, sizeof(LightDev) * (size_t)L, cudaMemcpyHostToDevice, c->stream));
     LT_CUDA(c, cudaEventRecord(c->lights_copied, c->stream));
     c->lights_for_n = n_photons;
@@ -290,10 +366,11 @@ int launch_shape(Ctx *c, bool adjoint, int *grid, int *threads, size_t *smem, in
 
 // Upper bound on the step-loop iterations of a warp: every iteration
 // advances at least one of its 32 lanes by one step, and a lane needs at most
-// max_hits segments per photon, each at most max_steps node tests, 8 leaf
-// tests and one finish.
+// max_hits segments per photon, each at most max_steps + 1 node steps (the
+// last one gives up), 8 leaf steps per node visited and one finish.
 uint64_t step_limit(const TraceParams &p) {
-    return 32ull * ((uint64_t)p.chunk * (uint64_t)p.max_hits * ((uint64_t)p.max_steps + kWide + 2) + 1);
+    const uint64_t per_segment = (uint64_t)(kWide + 1) * (uint64_t)p.max_steps + 2;
+    return 32ull * ((uint64_t)p.chunk * (uint64_t)p.max_hits * per_segment + 1);
 }
 
 uint64_t photon_chunk(uint64_t n, int grid, int threads) {
@@ -313,7 +390,7 @@ TraceParams base_params(Ctx *c, uint64_t seed, int32_t max_hits, uint64_t begin,
     p.lights = c->d_lights;
     p.n_lights = (int32_t)c->lights.size();
     p.max_hits = max_hits;
-    p.max_steps = 16 * c->n_nodes + 64;
+    p.max_steps = c->max_steps > 0 ? c->max_steps : 16 * c->n_nodes + 64;
     p.hdr = nullptr;
     p.seed = seed;
     p.photon_begin = begin;
@@ -349,7 +426,7 @@ void batch_free(Ctx *c) {
     if (b.stream) cudaStreamSynchronize(b.stream);
     batch_drop_graph(c);
     dfree(b.d_in); dfree(b.d_q); dfree(b.d_E); dfree(b.d_w); dfree(b.d_partial); dfree(b.d_loss); dfree(b.d_grad);
-    dfree(b.d_slots);
+    dfree(b.d_slots); dfree(b.d_gfix); dfree(b.d_gscale); dfree(b.d_wmax); dfree(b.d_gpart); dfree(b.d_rec);
     if (b.h_in) cudaFreeHost(b.h_in);
     if (b.h_out) cudaFreeHost(b.h_out);
     if (b.stream) cudaStreamDestroy(b.stream);
@@ -357,10 +434,11 @@ void batch_free(Ctx *c) {
 }
 
 struct BatchLaunch {
-    TraceParams fwd, adj;
+    TraceParams fwd, adj, grad;
     LossParams loss;
     int grid_f, grid_a, threads_f, threads_a;
     size_t smem_f, smem_a;
+    int32_t grad_parts;
 };
 
 // Launch parameters of a batch step; grows the gradient slots if needed.
@@ -383,24 +461,26 @@ int batch_prepare(Ctx *c, BatchLaunch *bl) {
     bl->adj = bl->fwd;
     bl->adj.q = nullptr;
     bl->adj.w = b.d_w;
+    bl->adj.wmax = b.d_wmax;
     bl->adj.segments = bl->fwd.segments + 1;
     if ((rc = launch_shape(c, true, &bl->grid_a, &bl->threads_a, &bl->smem_a, &bl->adj.n_staged))) return rc;
     bl->adj.chunk = photon_chunk(n_total, bl->grid_a, bl->threads_a);
     bl->adj.max_iters = step_limit(bl->adj);
-    int32_t max_count = 1;
-    for (int32_t n : b.counts) max_count = std::max(max_count, n);
-    const uint64_t min_nl = b.photons / (uint64_t)max_count;
-    bl->adj.n_slots = min_nl == 0 ? b.n_lights
-                                  : (int32_t)std::min<uint64_t>((uint64_t)b.n_lights, bl->adj.chunk / min_nl + 2);
-    const size_t need = (size_t)bl->grid_a * (size_t)bl->threads_a * (size_t)bl->adj.n_slots * 8 * sizeof(float);
-    if (need > b.slots_bytes) {
-        LT_CUDA(c, cudaStreamSynchronize(b.stream));
-        dfree(b.d_slots);
-        LT_CUDA(c, cudaMalloc(&b.d_slots, need));
-        b.slots_bytes = need;
-        batch_drop_graph(c);
+    int32_t max_count = 1, min_count = INT32_MAX;
+    for (int32_t n : b.counts) {
+        max_count = std::max(max_count, n);
+        min_count = std::min(min_count, n);
     }
-    bl->adj.slots = b.d_slots;
+    bool grown = false;
+    if ((rc = grow(c, b.d_rec, b.rec_bytes, (size_t)n_total * sizeof(PhotonAdj), b.stream, &grown))) return rc;
+    bl->adj.rec_adj = b.d_rec;
+    bl->grad = grad_params(bl->adj, b.photons / (uint64_t)max_count, nullptr);
+    if ((rc = grow(c, b.d_slots, b.slots_bytes, grad_slot_bytes(bl->grad), b.stream, &grown))) return rc;
+    bl->grad.slots = b.d_slots;
+    bl->grad_parts = grad_parts((b.photons + (uint64_t)min_count - 1) / (uint64_t)min_count, bl->grad.chunk);
+    const size_t need_parts = (size_t)b.n_lights * (size_t)bl->grad_parts * 8 * sizeof(ulonglong2);
+    if ((rc = grow(c, b.d_gpart, b.gpart_bytes, need_parts, b.stream, &grown))) return rc;
+    if (grown) batch_drop_graph(c);     // a captured step holds the old buffers
     LossParams &lp = bl->loss;
     lp.q = b.d_q;
     lp.E_target = c->d_target;
@@ -428,8 +508,10 @@ int batch_issue(Ctx *c, const BatchLaunch &bl) {
     LT_CUDA(c, cudaMemsetAsync(bl.fwd.segments, 0, 2 * sizeof(unsigned long long), s));
     LT_CUDA(c, launch_forward(bl.fwd, bl.grid_f, bl.threads_f, bl.smem_f, s));
     LT_CUDA(c, launch_loss(bl.loss, s));
+    LT_CUDA(c, launch_weight_range(b.d_w, (int64_t)(D * T), b.d_wmax, s));
     LT_CUDA(c, launch_adjoint(bl.adj, bl.grid_a, bl.threads_a, bl.smem_a, s));
-    LT_CUDA(c, launch_grad_finalize(bl.adj, b.d_grad, s));
+    LT_CUDA(c, launch_grad_photons(bl.grad, s));
+    LT_CUDA(c, launch_grad_finalize(bl.grad, b.d_gpart, bl.grad_parts, b.d_grad, b.d_gfix, b.d_gscale, s));
     LT_CUDA(c, cudaMemcpyAsync(b.h_out, b.d_loss, D * sizeof(double), cudaMemcpyDeviceToHost, s));
     LT_CUDA(c, cudaMemcpyAsync(b.h_out + D, b.d_grad, (L * 8 + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
     return LT_OK;
@@ -442,8 +524,7 @@ int batch_check_device(Ctx *c) {
     if (e) {
         LT_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), c->batch.stream));
         LT_CUDA(c, cudaStreamSynchronize(c->batch.stream));
-        if (e & kErrSteps) return fail(c, LT_ERR_TIMEOUT, "a ray exceeded its traversal step limit");
-        return fail(c, LT_ERR_DEVICE, "kernel error word " + std::to_string(e));
+        return device_error(c, e);
     }
     return LT_OK;
 }
@@ -505,6 +586,9 @@ int lt_create(void **ctx_out, int device, void *cuda_stream) {
         cudaMalloc(&c->d_lights, LT_MAX_LIGHTS * sizeof(LightDev)) != cudaSuccess ||
         cudaMallocHost(&c->h_lights, LT_MAX_LIGHTS * sizeof(LightDev)) != cudaSuccess ||
         cudaMalloc(&c->d_grad, LT_MAX_LIGHTS * 8 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->d_gfix, LT_MAX_LIGHTS * 8 * sizeof(ulonglong2)) != cudaSuccess ||
+        cudaMalloc(&c->d_gscale, sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->d_wmax, sizeof(uint32_t)) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->lights_copied, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventRecord(c->lights_copied, c->stream) != cudaSuccess ||
         cudaMemset(c->d_err, 0, sizeof(int32_t)) != cudaSuccess ||
@@ -526,7 +610,7 @@ int lt_destroy(void *ctx) {
     dfree(c->d_nodes); dfree(c->d_parent); dfree(c->d_tris); dfree(c->d_hits); dfree(c->d_area);
     dfree(c->d_target); dfree(c->d_alpha); dfree(c->d_lights); dfree(c->d_q); dfree(c->d_E); dfree(c->d_w);
     dfree(c->d_loss); dfree(c->d_partial); dfree(c->d_grad); dfree(c->d_slots); dfree(c->d_seg);
-    dfree(c->d_err);
+    dfree(c->d_err); dfree(c->d_gfix); dfree(c->d_gscale); dfree(c->d_wmax); dfree(c->d_gpart); dfree(c->d_rec);
     batch_free(c);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     if (c->h_lights) cudaFreeHost(c->h_lights);
@@ -554,6 +638,7 @@ int lt_upload_scene(void *ctx, const float *tri_xyz, const float *tri_uv, const 
                     const float *tri_albedo, int32_t n_tri, const int32_t *tile_res, const double *tile_area,
                     int32_t n_tiles, int64_t *n_texels_out) {
     LT_TRY
+    NvtxRange nvtx_range("lt_upload_scene");
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return LT_ERR_ARG;
     if (!tri_xyz || !tri_uv || !tri_tile || !tri_albedo || !tile_res || !tile_area || n_tri <= 0 || n_tiles <= 0)
@@ -684,6 +769,7 @@ static const char *light_error(const lt_light &s) {
 
 int lt_set_lights(void *ctx, const lt_light *lights, int32_t n_lights) {
     LT_TRY
+    NvtxRange nvtx_range("lt_set_lights");
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return LT_ERR_ARG;
     if (!lights || n_lights < 1 || n_lights > LT_MAX_LIGHTS) return fail(c, LT_ERR_ARG, "n_lights out of range");
@@ -750,6 +836,7 @@ static int forward_pass(Ctx *c, uint64_t seed, uint64_t n_photons, int32_t max_h
 int lt_trace_forward(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
                      uint64_t photon_end) {
     LT_TRY
+    NvtxRange nvtx_range("lt_trace_forward");
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return LT_ERR_ARG;
     return forward_pass(c, seed, n_photons, max_hits, photon_begin, photon_end, nullptr);
@@ -759,6 +846,7 @@ int lt_trace_forward(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_h
 int lt_count_work(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
                   uint64_t photon_end, uint64_t *counts_out) {
     LT_TRY
+    NvtxRange nvtx_range("lt_count_work");
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return LT_ERR_ARG;
     if (!counts_out) return fail(c, LT_ERR_ARG, "null counts output");
@@ -809,6 +897,7 @@ int lt_get_texel_sums(void *ctx, int64_t *q_out, int is_device) {
 
 int lt_loss(void *ctx, double *loss_out, int is_device) {
     LT_TRY
+    NvtxRange nvtx_range("lt_loss");
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return LT_ERR_ARG;
     if (!c->fwd_done) return fail(c, LT_ERR_STATE, "lt_loss needs a forward pass");
@@ -876,6 +965,7 @@ int lt_set_adjoint_weights(void *ctx, const float *w, int is_device) {
 int lt_trace_adjoint(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
                      uint64_t photon_end, double *grad_out, int is_device) {
     LT_TRY
+    NvtxRange nvtx_range("lt_trace_adjoint");
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return LT_ERR_ARG;
     if (!grad_out) return fail(c, LT_ERR_ARG, "null gradient output");
@@ -887,27 +977,29 @@ int lt_trace_adjoint(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_h
     const int32_t L = (int32_t)c->lights.size();
     TraceParams p = base_params(c, seed, max_hits, photon_begin, photon_end);
     p.w = c->d_w;
+    p.wmax = c->d_wmax;
+    p.flux_max = c->flux_max;
     p.segments = c->d_seg + 1;
     int grid, threads;
     size_t smem;
     if ((rc = launch_shape(c, true, &grid, &threads, &smem, &p.n_staged))) return rc;
-    // Per-thread gradient slots: a thread's contiguous photon chunk touches at
-    // most chunk / (fewest photons of a light) + 2 lights.
     p.chunk = photon_chunk(photon_end - photon_begin, grid, threads);
     p.max_iters = step_limit(p);
-    const uint64_t min_nl = n_photons / (uint64_t)L;
-    p.n_slots = min_nl == 0 ? L : (int32_t)std::min<uint64_t>((uint64_t)L, p.chunk / min_nl + 2);
-    const size_t need = (size_t)grid * (size_t)threads * (size_t)p.n_slots * 8 * sizeof(float);
-    if (need > c->slots_bytes) {
-        LT_CUDA(c, cudaStreamSynchronize(c->stream));
-        dfree(c->d_slots);
-        LT_CUDA(c, cudaMalloc(&c->d_slots, need));
-        c->slots_bytes = need;
-    }
-    p.slots = c->d_slots;
+    if ((rc = grow(c, c->d_rec, c->rec_bytes, (size_t)(photon_end - photon_begin) * sizeof(PhotonAdj), c->stream)))
+        return rc;
+    p.rec_adj = c->d_rec;
+    TraceParams pg = grad_params(p, n_photons / (uint64_t)L, nullptr);
+    if ((rc = grow(c, c->d_slots, c->slots_bytes, grad_slot_bytes(pg), c->stream))) return rc;
+    pg.slots = c->d_slots;
+    const int32_t parts = grad_parts((n_photons + (uint64_t)L - 1) / (uint64_t)L, pg.chunk);
+    const size_t need_parts = (size_t)L * (size_t)parts * 8 * sizeof(ulonglong2);
+    if ((rc = grow(c, c->d_gpart, c->gpart_bytes, need_parts, c->stream))) return rc;
     LT_CUDA(c, cudaMemsetAsync(c->d_seg + 1, 0, sizeof(unsigned long long), c->stream));
+    LT_CUDA(c, launch_weight_range(c->d_w, c->n_texels, c->d_wmax, c->stream));
     LT_CUDA(c, launch_adjoint(p, grid, threads, smem, c->stream));
-    LT_CUDA(c, launch_grad_finalize(p, c->d_grad, c->stream));
+    LT_CUDA(c, launch_grad_photons(pg, c->stream));
+    LT_CUDA(c, launch_grad_finalize(pg, c->d_gpart, parts, c->d_grad, c->d_gfix, c->d_gscale, c->stream));
+    c->adj_lights = L;
     c->stats.photons_adjoint = photon_end - photon_begin;
     c->seg_single = true;
     rc = copy_out(c, grad_out, c->d_grad, (size_t)L * 8 * sizeof(double), is_device);
@@ -917,9 +1009,25 @@ int lt_trace_adjoint(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_h
     LT_CATCH(ctx)
 }
 
+int lt_gradient_fixed(void *ctx, int64_t *sums_out, double *scale_out) {
+    LT_TRY
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return LT_ERR_ARG;
+    if (!sums_out || !scale_out) return fail(c, LT_ERR_ARG, "null output");
+    if (!c->adj_lights) return fail(c, LT_ERR_STATE, "no adjoint pass");
+    LT_CUDA(c, cudaSetDevice(c->device));
+    LT_CUDA(c, cudaMemcpyAsync(sums_out, c->d_gfix, (size_t)c->adj_lights * 8 * sizeof(ulonglong2),
+                               cudaMemcpyDeviceToHost, c->stream));
+    LT_CUDA(c, cudaMemcpyAsync(scale_out, c->d_gscale, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LT_CUDA(c, cudaStreamSynchronize(c->stream));
+    return check_device(c);
+    LT_CATCH(ctx)
+}
+
 int lt_debug_paths(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
                    uint64_t count, int32_t *tri_out, int64_t *texel_out, double *grad_out) {
     LT_TRY
+    NvtxRange nvtx_range("lt_debug_paths");
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return LT_ERR_ARG;
     if (!tri_out || !texel_out) return fail(c, LT_ERR_ARG, "null output");
@@ -1019,6 +1127,9 @@ int lt_batch_setup(void *ctx, int32_t n_designs, const int32_t *lights_per_desig
     if (e == cudaSuccess) e = cudaMalloc(&b.d_partial, (size_t)n_designs * kLossBlocksBatch * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&b.d_loss, (size_t)n_designs * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&b.d_grad, ((size_t)total * 8 + 2) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&b.d_gfix, (size_t)total * 8 * sizeof(ulonglong2));
+    if (e == cudaSuccess) e = cudaMalloc(&b.d_gscale, sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&b.d_wmax, sizeof(uint32_t));
     if (e != cudaSuccess) {
         batch_free(c);
         return cuda_fail(c, e, "lt_batch_setup");
@@ -1030,6 +1141,7 @@ int lt_batch_setup(void *ctx, int32_t n_designs, const int32_t *lights_per_desig
 
 int lt_batch_set_lights(void *ctx, const lt_light *lights) {
     LT_TRY
+    NvtxRange nvtx_range("lt_batch_set_lights");
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return LT_ERR_ARG;
     Ctx::Batch &b = c->batch;
@@ -1053,6 +1165,7 @@ int lt_batch_set_lights(void *ctx, const lt_light *lights) {
     StepHeader *h = reinterpret_cast<StepHeader *>(b.h_in);
     h->scale = S;
     h->inv_scale = 1.0 / S;
+    h->flux_max = max_flux(out, b.n_lights);
     b.has_lights = true;
     return LT_OK;
     LT_CATCH(ctx)
@@ -1061,6 +1174,7 @@ int lt_batch_set_lights(void *ctx, const lt_light *lights) {
 int lt_batch_step(void *ctx, uint64_t seed_fwd, uint64_t seed_adj, double *loss_out, double *grad_out,
                   int use_graph) {
     LT_TRY
+    NvtxRange nvtx_range("lt_batch_step");
     Ctx *c = static_cast<Ctx *>(ctx);
     if (!c) return LT_ERR_ARG;
     Ctx::Batch &b = c->batch;
@@ -1105,6 +1219,7 @@ int lt_batch_step(void *ctx, uint64_t seed_fwd, uint64_t seed_adj, double *loss_
     c->stats.segments_forward = seg[0];
     c->stats.segments_adjoint = seg[1];
     c->stats.photons_forward = c->stats.photons_adjoint = b.photons * D;
+    c->stats.fixed_point_scale = h->scale;
     c->stats.grid_blocks = bl.grid_f;
     c->stats.block_threads = bl.threads_f;
     c->stats.staged_nodes = bl.fwd.n_staged;
@@ -1221,6 +1336,17 @@ int lt_set_launch(void *ctx, int32_t threads_per_block, int32_t blocks_per_sm, i
     if (blocks_per_sm >= 0) c->blocks_per_sm = blocks_per_sm;
     if (smem_node_bytes >= 0) c->smem_node_bytes = smem_node_bytes;
     batch_drop_graph(c);     // a captured batch step holds the old launch shape
+    return LT_OK;
+    LT_CATCH(ctx)
+}
+
+int lt_set_step_limit(void *ctx, int32_t max_steps) {
+    LT_TRY
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return LT_ERR_ARG;
+    if (max_steps < 0) return fail(c, LT_ERR_ARG, "max_steps must be >= 0");
+    c->max_steps = max_steps;
+    batch_drop_graph(c);     // a captured batch step holds the old limit
     return LT_OK;
     LT_CATCH(ctx)
 }

@@ -91,10 +91,24 @@ struct alignas(16) StepHeader {
     uint64_t seed_adj;
     double scale;       // fixed-point scale S of the texel sums
     double inv_scale;
+    float flux_max;     // largest flux constant of the batch's lights (gradient scale anchor)
+    float pad[3];
 };
 
+// What the adjoint trace keeps of one photon for the gradient kernel: its
+// adjoint state dO/dPhi_r = sum_i w_{t_i} beta_i (Eq. 12), the distance to
+// its first hit along the emitted ray, and 2 x first-hit triangle + 1 if the
+// normal was flipped towards the light (-1: no hit).
+struct alignas(16) PhotonAdj {
+    float g;
+    float t_first;
+    int32_t n1code;
+    uint32_t pad;
+};
+static_assert(sizeof(PhotonAdj) == 16, "photon record layout");
+
 // Device error word bits.
-enum : int32_t { kErrSteps = 1, kErrTexel = 2, kErrDepth = 4 };
+enum : int32_t { kErrSteps = 1, kErrRange = 2, kErrDepth = 4 };
 
 struct TraceParams {
     const Node *nodes;
@@ -119,8 +133,11 @@ struct TraceParams {
     uint64_t chunk;             // photons per thread (contiguous)
     // adjoint
     const float *w;             // [n_texels] dO/dPhi per deposit
-    float *slots;               // [threads][n_slots][8] per-thread gradient sums (FP32, fixed order)
-    int32_t n_slots;            // lights a thread's chunk can touch
+    const uint32_t *wmax;       // bits of max_t |w_t| (gradient scale anchor, written by the weight-range kernel)
+    float flux_max;             // largest flux constant of the lights (single-design passes; else hdr->flux_max)
+    PhotonAdj *rec_adj;         // [photon_end - photon_begin] adjoint records (adjoint trace writes, gradient reads)
+    ulonglong2 *slots;          // [threads][n_slots][8] gradient kernel's per-thread sums: 128-bit fixed point
+    int32_t n_slots;            // lights a gradient thread's chunk can touch
     // debug record
     int32_t *rec_tri;
     int64_t *rec_texel;
@@ -158,7 +175,22 @@ cudaError_t launch_paths(const TraceParams &p, uint64_t count, cudaStream_t s);
 cudaError_t launch_loss(const LossParams &p, cudaStream_t s);
 cudaError_t launch_resolve(const unsigned long long *q, const float *area, double inv_scale, int64_t n,
                            float *E_out, cudaStream_t s);
-cudaError_t launch_grad_finalize(const TraceParams &p, double *out, cudaStream_t s);
+// Gradient sums in two steps: n_lights x parts partial sums into `partial`
+// ([n_lights][parts][8]), then one conversion per light.
+cudaError_t launch_grad_finalize(const TraceParams &p, ulonglong2 *partial, int32_t parts, double *out,
+                                 ulonglong2 *fixed_out, double *scale_out, cudaStream_t s);
+// Partial sums per light: one per 4096 threads covering the light's photons
+// (a light of max_nl photons in chunks of `chunk` spans up to
+// ceil(max_nl / chunk) + 1 threads), at least 1, at most 64.
+inline int32_t grad_parts(uint64_t max_nl, uint64_t chunk) {
+    const uint64_t threads = (max_nl + chunk - 1) / chunk + 1;
+    const uint64_t parts = (threads + 4095) / 4096;
+    return (int32_t)(parts < 1 ? 1 : (parts > 64 ? 64 : parts));
+}
+cudaError_t launch_weight_range(const float *w, int64_t n, uint32_t *wmax, cudaStream_t s);
+// The gradient kernel: p.chunk photons per thread, p.n_slots slots each.
+cudaError_t launch_grad_photons(const TraceParams &p, cudaStream_t s);
+constexpr uint64_t kGradPhotonsPerThread = 64;
 int trace_kernel_max_threads(bool staged);   // block bound of the staged / L1-node kernels
 cudaError_t trace_occupancy(bool adjoint, bool staged, int depth, int block, size_t smem, int *blocks_per_sm);
 

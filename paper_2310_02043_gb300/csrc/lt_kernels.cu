@@ -592,28 +592,12 @@ __device__ __forceinline__ void dflux(const LightDev &L, float phi_r, float a_em
     out[7] = scale * (-2.0f) * (c - L.co) * (c - L.ci) * L.sin_out * id3;
 }
 
-// Deposit of the lanes of the warp that are depositing in this step (Eq. 8):
-// a 64-bit fixed-point atomic each. Built with LT_DEPOSIT_WARP_AGGREGATE,
-// lanes that hit the same texel first add their values with shuffles and one
-// of them does the atomic.
-__device__ __forceinline__ void deposit_active(unsigned long long *q, int64_t texel, unsigned long long val) {
-#ifndef LT_DEPOSIT_WARP_AGGREGATE
-    // lanes of a warp rarely hit the same texel (measured: aggregating with
-    // __match_any_sync costs more than it saves at 2-4.5 cm texels); integer
-    // addition keeps the sums independent of the order either way
+// Deposit (Eq. 8): one 64-bit fixed-point atomic. Lanes of a warp rarely hit
+// the same 2-4.5 cm texel, so aggregating them first (__match_any_sync and
+// shuffles) was measured slower (forward -1.5 % office, -3.9 % building);
+// integer addition keeps the sums independent of the order either way.
+__device__ __forceinline__ void deposit(unsigned long long *q, int64_t texel, unsigned long long val) {
     atomicAdd(q + texel, val);
-    return;
-#endif
-    const unsigned m = __activemask();
-    const unsigned peers = __match_any_sync(m, (unsigned long long)texel);
-    unsigned long long tot = 0;
-    unsigned rest = peers;
-    while (rest) {
-        const int src = __ffs(rest) - 1;
-        tot += __shfl_sync(peers, val, src);
-        rest &= rest - 1;
-    }
-    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(q + texel, tot);
 }
 
 // Seed and fixed-point scale of this launch: from the step header under
@@ -628,6 +612,90 @@ __device__ __forceinline__ uint64_t launch_seed(const TraceParams &P) {
 
 __device__ __forceinline__ float launch_scale(const TraceParams &P) {
     return P.hdr ? (float)__ldg(&P.hdr->scale) : P.scale;
+}
+
+// ---------------------------------------------------------------------------
+// Gradient sums in fixed point. Every photon's term g dPhi_r/dp (Eq. 11), a
+// float, is scaled by a power of two G and rounded to a multiple of 2^-64
+// (ties away from zero); the rounded terms are added as 128-bit
+// two's-complement integers, so the sums do not depend on how photons are
+// grouped into threads, launches or ranks. G = 2^-e with e the binary
+// exponent of max_t |w_t| x (largest flux constant of the lights), the size
+// of a typical term: a term 2^64 times smaller rounds away, and a term of
+// 2^62 G^-1 or more, or one that is not finite, is an error.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float grad_scale(const TraceParams &P) {
+    const float fm = P.hdr ? __ldg(&P.hdr->flux_max) : P.flux_max;
+    const float t0 = __uint_as_float(__ldg(P.wmax)) * fm;
+    int e = (int)((__float_as_uint(t0) >> 23) & 0xffu) - 127;   // floor(log2 t0) for a normal t0
+    if (!(t0 > 0.0f)) e = 0;
+    e = min(max(e, -120), 120);
+    return __uint_as_float((uint32_t)(127 - e) << 23);           // 2^-e
+}
+
+// acc += round(v 2^64) as 128-bit two's complement (acc.x low, acc.y high
+// word). False (nothing added) when |v| >= 2^62 or v is not finite.
+__device__ __forceinline__ bool fix128_add(ulonglong2 &acc, float v) {
+    const uint32_t b = __float_as_uint(v);
+    const int e = (int)((b >> 23) & 0xffu);
+    if (e == 0) return true;                 // zero or below 2^-126: rounds to 0
+    if (e >= 127 + 62) return false;         // |v| >= 2^62, inf or NaN
+    const uint64_t m = (uint64_t)((b & 0x7fffffu) | 0x800000u);
+    const int s = e - 86;                    // |v| 2^64 = m 2^(e - 86)
+    uint64_t lo, hi;
+    if (s < 0) {
+        hi = 0;
+        lo = s <= -25 ? 0 : (m + (1ull << (-s - 1))) >> (-s);
+    } else if (s < 64) {
+        lo = m << s;
+        hi = s == 0 ? 0 : m >> (64 - s);
+    } else {
+        lo = 0;
+        hi = m << (s - 64);
+    }
+    if (b >> 31) {
+        lo = ~lo + 1;
+        hi = ~hi + (lo == 0 ? 1 : 0);
+    }
+    const uint64_t nlo = acc.x + lo;
+    acc.y += hi + (nlo < lo ? 1 : 0);
+    acc.x = nlo;
+    return true;
+}
+
+// 128-bit two's-complement integers as (low, high) words.
+__device__ __forceinline__ void add128(ulonglong2 &a, ulonglong2 b) {
+    const uint64_t lo = a.x + b.x;
+    a.y += b.y + (lo < b.x ? 1 : 0);
+    a.x = lo;
+}
+
+// The 128-bit integer as a double, rounded once (to nearest even).
+__device__ __forceinline__ double int128_to_double(ulonglong2 v) {
+    const bool neg = (int64_t)v.y < 0;
+    uint64_t lo = v.x, hi = v.y;
+    if (neg) {
+        lo = ~lo + 1;
+        hi = ~hi + (lo == 0 ? 1 : 0);
+    }
+    double d;
+    if (hi == 0) {
+        d = __ull2double_rn(lo);
+    } else {
+        const int n = __clzll((long long)hi);
+        const uint64_t top = n == 0 ? hi : (hi << n) | (lo >> (64 - n));
+        const uint64_t rest = lo << n;       // the bits below top; only whether any is set matters
+        // top x 2^(64 - n), with the lost bits folded into top's last bit
+        d = __ull2double_rn(top | (rest != 0 ? 1ull : 0ull)) * __longlong_as_double((long long)(1023 + 64 - n) << 52);
+    }
+    return neg ? -d : d;
+}
+
+__device__ __forceinline__ uint64_t thread_index() { return (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; }
+
+// One past the last photon of this thread's chunk.
+__device__ __forceinline__ uint64_t thread_end(const TraceParams &P) {
+    return P.photon_begin + min((thread_index() + 1) * P.chunk, P.photon_end - P.photon_begin);
 }
 
 __device__ __forceinline__ void stage_nodes(const TraceParams &P, float4 *smem) {
@@ -650,33 +718,30 @@ __global__ void __launch_bounds__(kSmem ? kThreadsStaged : kThreadsL1, kTraceMin
     trace_kernel(const TraceParams P) {
     extern __shared__ float4 smem[];
     if (kSmem) stage_nodes(P, smem);
-    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint64_t n = P.photon_end - P.photon_begin;
-    const uint64_t chunk = P.chunk;
-    uint64_t photon = P.photon_begin + min(tid * chunk, n);
-    const uint64_t p_end = P.photon_begin + min((tid + 1) * chunk, n);
-    int32_t first_light = 0;
-    if (kAdjoint)
-        for (int i = 0; i < P.n_slots * 8; ++i) P.slots[tid * (uint64_t)P.n_slots * 8 + i] = 0.0f;
+    // The thread's photons are [begin + tid chunk, begin + (tid + 1) chunk)
+    // clipped to the range; the end and the first photon's light are
+    // recomputed where needed rather than held in registers.
+    uint64_t photon = P.photon_begin + min(thread_index() * P.chunk, P.photon_end - P.photon_begin);
 
     int32_t l = 0, seg = 0, skip = -1;
-    float phi = 0.0f, a_emit = 0.0f, g = 0.0f, beta = 1.0f;
-    float x1x = 0.0f, x1y = 0.0f, x1z = 0.0f;      // adjoint: first hit point
-    int32_t n1code = -1;                          // adjoint: 2 x first-hit triangle + 1 if its normal was flipped
+    float phi = 0.0f, g = 0.0f, beta = 1.0f;
+    // adjoint: distance to the first hit along the emitted ray and 2 x
+    // first-hit triangle + 1 if its normal was flipped (the photon's record)
+    float t_first = 0.0f;
+    int32_t n1code = -1;
     Ray r;
     Trav<kDeep> s;
     Hit h;
     Work work;
     unsigned long long segs = 0;
-    bool active = photon < p_end;
+    bool active = photon < thread_end(P);
 
     // Emission of the first photon (Alg. 1: exitant ray carrying Phi_r).
     if (active) {
         l = light_of(P, photon);
-        first_light = l;
         const LightDev &L = P.lights[l];
         const float4 u = uniforms(launch_seed<kAdjoint>(P), photon - L.photon_base, 0u, L.design);
-        float wx, wy, wz;
+        float wx, wy, wz, a_emit;
         phi = emit(L, u.x, u.y, wx, wy, wz, a_emit);
         const float3 o = emit_origin(L, u.z, u.w);
         ray_init(r, o.x, o.y, o.z, wx, wy, wz);
@@ -732,10 +797,10 @@ __global__ void __launch_bounds__(kSmem ? kThreadsStaged : kThreadsL1, kTraceMin
                 nrm = facing_normal(P, h.tri, r.dx, r.dy, r.dz);
                 const uint64_t tb = P.lights[l].texel_base;
                 if (!kAdjoint) {
-                    deposit_active(P.q + tb, texel, (unsigned long long)__float2ll_rn(phi * launch_scale(P)));   // Eq. 8
+                    deposit(P.q + tb, texel, (unsigned long long)__float2ll_rn(phi * launch_scale(P)));   // Eq. 8
                 } else {
                     if (seg == 1) {
-                        x1x = x.x; x1y = x.y; x1z = x.z;
+                        t_first = h.t;
                         n1code = 2 * h.tri + (nrm.x != __ldg(P.hits[h.tri].n) || nrm.y != __ldg(P.hits[h.tri].n + 1) ||
                                               nrm.z != __ldg(P.hits[h.tri].n + 2) ? 1 : 0);
                     }
@@ -750,28 +815,18 @@ __global__ void __launch_bounds__(kSmem ? kThreadsStaged : kThreadsL1, kTraceMin
                 }
             }
             if (!bounce) {
-                if (kAdjoint && n1code >= 0) {
-                    // Eq. 11: this photon's dO/dPhi_r * dPhi_r/dp into its light's slot
-                    const LightDev &L = P.lights[l];
-                    float2 q = make_float2(0.0f, 0.0f);
-                    if (L.type == LT_AREA) {   // the origin's coordinates, from the emission's random numbers
-                        const float4 u0 = uniforms(launch_seed<kAdjoint>(P), photon - L.photon_base, 0u, L.design);
-                        q = area_coords(L, u0.z, u0.w);
-                    }
-                    const float *nn = P.hits[n1code >> 1].n;
-                    const float sgn = (n1code & 1) ? -1.0f : 1.0f;
-                    const float3 n1 = make_float3(sgn * __ldg(nn), sgn * __ldg(nn + 1), sgn * __ldg(nn + 2));
-                    float dp[8];
-                    dflux(L, L.flux_k * a_emit, a_emit, q, x1x, x1y, x1z, n1, dp);
-                    // FP32 per-thread sums in photon order (FP64 arithmetic runs at a
-                    // small fraction of the FP32 rate on this GPU); the totals over
-                    // threads are formed in FP64 by grad_finalize_kernel.
-                    float *o = P.slots + (tid * (uint64_t)P.n_slots + (uint64_t)(l - first_light)) * 8;
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) o[k] = fmaf(g, dp[k], o[k]);
+                if (kAdjoint) {
+                    // the photon's adjoint state dO/dPhi_r (Eq. 12) and first hit,
+                    // for the gradient kernel (Eq. 11)
+                    PhotonAdj rec;
+                    rec.g = g;
+                    rec.t_first = t_first;
+                    rec.n1code = n1code;
+                    rec.pad = 0;
+                    P.rec_adj[photon - P.photon_begin] = rec;
                 }
                 ++photon;
-                if (photon >= p_end) active = false;
+                if (photon >= thread_end(P)) active = false;
             }
             if (active) {
                 float c, sn;
@@ -788,8 +843,7 @@ __global__ void __launch_bounds__(kSmem ? kThreadsStaged : kThreadsL1, kTraceMin
                 } else {
                     emit_frame(Ln, u.x, c, sn, t1, t2, axis);
                     org = emit_origin(Ln, unit24(rb.z), unit24(rb.w));
-                    a_emit = falloff(Ln, c);
-                    phi = Ln.flux_k * a_emit;
+                    phi = Ln.flux_k * falloff(Ln, c);
                     seg = 1;
                     skip = -1;
                     g = 0.0f;
@@ -815,6 +869,60 @@ __global__ void __launch_bounds__(kSmem ? kThreadsStaged : kThreadsL1, kTraceMin
         }
         if ((threadIdx.x & 31) == 0) { atomicAdd(P.work, nodes); atomicAdd(P.work + 1, tris); }
     }
+}
+
+// Eq. 11 per photon: thread t takes photons [begin + t K, begin + (t + 1) K)
+// (K = P.chunk), recomputes each one's emitted ray from its Philox block (the
+// same operations as at emission), its first hit x1 = o + t_first d and
+// dPhi_r/dp there, and adds g dPhi_r/dp into 128-bit register sums for the
+// photon's light; a light's run of photons ends in one store to the thread's
+// slot for that light (slot = light - light of the thread's first photon).
+// Slots of lights with no photon in the chunk are zero.
+__global__ void __launch_bounds__(128) grad_photon_kernel(const TraceParams P) {
+    const uint64_t n = P.photon_end - P.photon_begin;
+    const uint64_t t = thread_index();
+    uint64_t photon = P.photon_begin + min(t * P.chunk, n);
+    const uint64_t p_end = P.photon_begin + min((t + 1) * P.chunk, n);
+    ulonglong2 *slots = P.slots + t * (uint64_t)P.n_slots * 8;
+    if (photon >= p_end) return;             // no photons: the slots are never read
+    const float G = grad_scale(P);
+    const uint64_t seed = launch_seed<true>(P);
+    int32_t l = light_of(P, photon);
+    ulonglong2 acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = make_ulonglong2(0, 0);
+    bool in_range = true;
+    for (int32_t s = 0; s < P.n_slots; ++s) {
+        const LightDev &L = P.lights[l];
+        const uint64_t stop = min(p_end, L.end);
+        for (; photon < stop; ++photon) {
+            const PhotonAdj rec = P.rec_adj[photon - P.photon_begin];
+            if (rec.n1code < 0) continue;
+            const uint4 r0 = counter_block(seed, photon - L.photon_base, 0u, L.design);
+            float c0, s0;
+            float3 e1, e2, ax;
+            emit_frame(L, unit24(r0.x), c0, s0, e1, e2, ax);
+            const float3 o0 = emit_origin(L, unit24(r0.z), unit24(r0.w));
+            const float3 d0 = frame_dir(c0, s0, unit24(r0.y), e1, e2, ax);
+            const float a_emit = falloff(L, c0);
+            const float2 q = L.type == LT_AREA ? area_coords(L, unit24(r0.z), unit24(r0.w)) : make_float2(0.0f, 0.0f);
+            const float *nn = P.hits[rec.n1code >> 1].n;
+            const float sgn = (rec.n1code & 1) ? -1.0f : 1.0f;
+            const float3 n1 = make_float3(sgn * __ldg(nn), sgn * __ldg(nn + 1), sgn * __ldg(nn + 2));
+            float dp[8];
+            dflux(L, L.flux_k * a_emit, a_emit, q, fmaf(rec.t_first, d0.x, o0.x), fmaf(rec.t_first, d0.y, o0.y),
+                  fmaf(rec.t_first, d0.z, o0.z), n1, dp);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) in_range &= fix128_add(acc[k], (rec.g * dp[k]) * G);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            slots[s * 8 + k] = acc[k];
+            acc[k] = make_ulonglong2(0, 0);
+        }
+        if (photon < p_end) ++l;
+    }
+    if (!in_range) atomicOr(P.err, kErrRange);
 }
 
 // Path record for debugging: one thread per photon, the same per-segment
@@ -920,30 +1028,85 @@ __global__ void resolve_kernel(const unsigned long long *q, const float *area, d
         E[t] = (float)((double)(long long)q[t] * inv_scale / (double)area[t]);
 }
 
-// Sum of the per-thread gradient slots of every light in thread order: one
-// block per light; thread t's chunk of photons starts at begin + t * chunk and
-// its slot s holds light (light of its first photon) + s.
-__global__ void __launch_bounds__(256) grad_finalize_kernel(const TraceParams P, double *out) {
-    __shared__ double sh[256 / 32];
+// Sums of the per-thread 128-bit gradient slots, in two steps. Thread t's
+// chunk of photons starts at begin + t * chunk and its slot s holds light
+// (light of its first photon) + s. Step 1: block (l, p) of a grid of
+// n_lights x P blocks sums every P-th group of 256 of the threads that cover
+// light l into partial[l][p]. Step 2: one warp per light sums the P partials
+// and writes the 128-bit sums (fixed_out), their value dO/dp = sum 2^-64 / G as
+// doubles (out) and G (scale_out). Integer sums are exact, so neither the
+// split nor the order of the additions changes a bit.
+__global__ void __launch_bounds__(256) grad_partial_kernel(const TraceParams P, ulonglong2 *partial) {
+    __shared__ ulonglong2 sh[256 / 32];
     const int32_t l = blockIdx.x;
+    const uint32_t parts = gridDim.y, p = blockIdx.y;
     const uint64_t n = P.photon_end - P.photon_begin;
     const uint64_t lo = max(P.lights[l].first, P.photon_begin), hi = min(P.lights[l].end, P.photon_end);
-    double v[8];
+    ulonglong2 v[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = 0.0;
+    for (int k = 0; k < 8; ++k) v[k] = make_ulonglong2(0, 0);
     if (lo < hi && n > 0) {
         const uint64_t t0 = (lo - P.photon_begin) / P.chunk, t1 = (hi - 1 - P.photon_begin) / P.chunk;
-        for (uint64_t t = t0 + threadIdx.x; t <= t1; t += blockDim.x) {
+        for (uint64_t t = t0 + (uint64_t)p * blockDim.x + threadIdx.x; t <= t1; t += (uint64_t)parts * blockDim.x) {
             const int32_t s = l - light_of(P, P.photon_begin + t * P.chunk);
-            const float *src = P.slots + (t * (uint64_t)P.n_slots + (uint64_t)s) * 8;
+            const ulonglong2 *src = P.slots + (t * (uint64_t)P.n_slots + (uint64_t)s) * 8;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) v[k] += (double)src[k];
+            for (int k = 0; k < 8; ++k) add128(v[k], src[k]);
         }
     }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
     for (int k = 0; k < 8; ++k) {
-        const double tot = block_sum(v[k], sh);
-        if (threadIdx.x == 0) out[l * 8 + k] = tot;
+        ulonglong2 x = v[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            ulonglong2 y;
+            y.x = __shfl_xor_sync(kFull, x.x, off);
+            y.y = __shfl_xor_sync(kFull, x.y, off);
+            add128(x, y);
+        }
+        if (lane == 0) sh[w] = x;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            ulonglong2 tot = make_ulonglong2(0, 0);
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) add128(tot, sh[i]);
+            partial[((uint64_t)l * parts + p) * 8 + k] = tot;
+        }
+        __syncthreads();
     }
+}
+
+__global__ void __launch_bounds__(32) grad_finalize_kernel(const TraceParams P, const ulonglong2 *partial,
+                                                           int32_t parts, double *out, ulonglong2 *fixed_out,
+                                                           double *scale_out) {
+    const int32_t l = blockIdx.x;
+    const double unit = 0x1p-64 / (double)grad_scale(P);          // a power of two: exact
+    for (int k = 0; k < 8; ++k) {
+        ulonglong2 x = make_ulonglong2(0, 0);
+        for (int32_t p = threadIdx.x; p < parts; p += 32) add128(x, partial[((uint64_t)l * parts + p) * 8 + k]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            ulonglong2 y;
+            y.x = __shfl_xor_sync(kFull, x.x, off);
+            y.y = __shfl_xor_sync(kFull, x.y, off);
+            add128(x, y);
+        }
+        if (threadIdx.x == 0) {
+            fixed_out[l * 8 + k] = x;
+            out[l * 8 + k] = int128_to_double(x) * unit;
+        }
+    }
+    if (l == 0 && threadIdx.x == 0) scale_out[0] = (double)grad_scale(P);
+}
+
+// max_t |w_t| as float bits (non-negative floats order as unsigned integers)
+// into *wmax, which the caller cleared.
+__global__ void __launch_bounds__(256) weight_range_kernel(const float *w, int64_t n, uint32_t *wmax) {
+    uint32_t m = 0;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, __float_as_uint(fabsf(w[t])));
+    m = __reduce_max_sync(kFull, m);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(wmax, m);
 }
 
 template <class K>
@@ -1017,8 +1180,25 @@ cudaError_t launch_resolve(const unsigned long long *q, const float *area, doubl
     return cudaGetLastError();
 }
 
-cudaError_t launch_grad_finalize(const TraceParams &p, double *out, cudaStream_t s) {
-    grad_finalize_kernel<<<p.n_lights, 256, 0, s>>>(p, out);
+cudaError_t launch_grad_finalize(const TraceParams &p, ulonglong2 *partial, int32_t parts, double *out,
+                                 ulonglong2 *fixed_out, double *scale_out, cudaStream_t s) {
+    grad_partial_kernel<<<dim3(p.n_lights, parts), 256, 0, s>>>(p, partial);
+    grad_finalize_kernel<<<p.n_lights, 32, 0, s>>>(p, partial, parts, out, fixed_out, scale_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_photons(const TraceParams &p, cudaStream_t s) {
+    const uint64_t n = p.photon_end - p.photon_begin;
+    const uint64_t threads = (n + p.chunk - 1) / p.chunk;
+    if (threads == 0) return cudaSuccess;
+    grad_photon_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_weight_range(const float *w, int64_t n, uint32_t *wmax, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(wmax, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    weight_range_kernel<<<1024, 256, 0, s>>>(w, n, wmax);
     return cudaGetLastError();
 }
 

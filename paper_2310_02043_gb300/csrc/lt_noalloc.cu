@@ -101,6 +101,9 @@ extern "C" int lt_loss_static(int device, void *cuda_stream, const int64_t *q, d
     if (device < 0 || device >= kMaxDevices || !q || !area || !E_target || !w_out || !loss_out || !(scale > 0.0))
         return LT_ERR_ARG;
     if (n_texels < 1 || n_texels > LT_LOSS_STATIC_MAX_TEXELS) return LT_ERR_ARG;
+    // An error left pending by earlier, unrelated CUDA work would be reported
+    // as this call's launch failure; refuse instead, and leave it pending.
+    if (cudaPeekAtLastError() != cudaSuccess) return LT_ERR_STATE;
     int prev = -1;
     if (cudaGetDevice(&prev) != cudaSuccess) return LT_ERR_CUDA;
     if (prev != device && cudaSetDevice(device) != cudaSuccess) return LT_ERR_CUDA;

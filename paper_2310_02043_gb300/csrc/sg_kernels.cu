@@ -929,6 +929,16 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
     return false;
 }
 
+// After a warpgroup gave up waiting (its flag set): wait once more, with a
+// limit eight times as long, for the commit it gave up on, so that no MMA of
+// its own is still writing tensor memory when the CTA frees it. If that wait
+// gives up too, the memory is freed all the same (the kernel has already
+// reported the error).
+__device__ __forceinline__ void tc_drain(uint32_t mbar, uint32_t pending_phase) {
+    for (int i = 0; i < 8; ++i)
+        if (mbar_wait(mbar, pending_phase)) return;
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
@@ -1052,6 +1062,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) design_forward_tc_kernel(const 
         if (valid) A.K[row] = sigmoidf_(o0) * D + kRScale * softplusf_(o1);
         wg_sync(g);
     }
+    if (S.abort[g]) tc_drain(mbar, phase ^ 1u);      // the commit given up on is the pending phase
     tc_fence_before();
     __syncthreads();
     if (tid == 0) {
@@ -1319,6 +1330,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) design_backward_tc_kernel(const
             out[7] = 0.0f;
         }
     }
+    if (S.abort[g]) tc_drain(mbar, phase ^ 1u);      // the commit given up on is the pending phase
     tc_fence_before();
     __syncthreads();
     if (tid == 0) {
@@ -1536,6 +1548,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) design_fused_tc_kernel(const De
     }
     loss = warp_sum_d(loss);
     if (lane == 0) S.red[warp] = loss;
+    if (S.abort[g]) tc_drain(mbar, phase ^ 1u);      // the commit given up on is the pending phase
     tc_fence_before();
     __syncthreads();
     if (tid == 0) {
@@ -1764,6 +1777,7 @@ __global__ void __launch_bounds__(kTrainThreads, kTrainMinCtas) train_tc_kernel(
     }
     loss = warp_sum_d(loss);
     if (lane == 0) S.red[warp] = loss;
+    if (S.abort[g]) tc_drain(mbar, phase ^ 1u);      // the commit given up on is the pending phase
     tc_fence_before();
     __syncthreads();
     if (tid == 0) {

@@ -22,6 +22,7 @@ STATUS_NAMES = {0: "LT_OK", -1: "LT_ERR_ARG", -2: "LT_ERR_CUDA", -3: "LT_ERR_OOM
                 -5: "LT_ERR_TIMEOUT", -6: "LT_ERR_OVERFLOW", -7: "LT_ERR_DEVICE"}
 MAX_LIGHTS = 1024
 GRAD_N = 8
+GRAD_FRACTION_BITS = 64   # fixed-point gradient sums count units of 2^-64 / G
 
 # Every symbol the header declares (checked by the test suite).
 EXPORTED = ("lt_version", "lt_create", "lt_destroy", "lt_set_stream", "lt_last_error", "lt_upload_scene",
@@ -29,7 +30,8 @@ EXPORTED = ("lt_version", "lt_create", "lt_destroy", "lt_set_stream", "lt_last_e
             "lt_get_irradiance", "lt_texel_areas", "lt_set_adjoint_weights", "lt_trace_adjoint", "lt_debug_paths",
             "lt_get_stats", "lt_set_launch", "lt_count_work", "lt_loss_static", "lt_set_design", "lt_batch_setup",
             "lt_batch_set_lights", "lt_batch_step", "lt_batch_texel_sums", "lt_batch_irradiance",
-            "lt_batch_stream", "lt_texel_centres", "lt_build_bvh")
+            "lt_batch_stream", "lt_texel_centres", "lt_build_bvh", "lt_set_step_limit",
+            "lt_probe_l2_read", "lt_gradient_fixed")
 
 
 class LtError(RuntimeError):
@@ -114,6 +116,9 @@ def _declare(lib):
         "lt_batch_stream": [vp, ctypes.POINTER(ctypes.c_void_p)],
         "lt_texel_centres": [vp, vp, vp],
         "lt_build_bvh": [vp, i32, vp, i32, vp, ctypes.POINTER(i32), ctypes.POINTER(i32)],
+        "lt_set_step_limit": [vp, i32],
+        "lt_probe_l2_read": [ci, u64, i32, ctypes.POINTER(ctypes.c_double)],
+        "lt_gradient_fixed": [vp, vp, ctypes.POINTER(ctypes.c_double)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -155,13 +160,57 @@ def loss_static(device: int, stream: int, q_ptr: int, scale: float, area, E_targ
     """lt_loss_static: the objective and adjoint weights without any device
     allocation (for callers that cannot allocate). All buffers are device
     tensors; q_ptr is the device address of the int64 texel sums."""
+    import torch
     lib = load_library()
     n = int(area.numel())
+
+    def need(name, t, dtype, count):
+        if t is None:
+            return
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()
+                and t.numel() >= count):
+            raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor of at least {count} elements")
+
+    for name, t in (("area", area), ("E_target", E_target), ("w_out", w_out), ("alpha", alpha), ("E_out", E_out)):
+        need(name, t, torch.float32, n)
+    need("loss_out", loss_out, torch.float64, 1)
     rc = lib.lt_loss_static(device, ctypes.c_void_p(stream), ctypes.c_void_p(q_ptr), float(scale), _ptr(area)[0],
                             _ptr(E_target)[0], _ptr(alpha)[0] if alpha is not None else None, n, _ptr(w_out)[0],
                             _ptr(E_out)[0] if E_out is not None else None, _ptr(loss_out)[0])
     if rc != LT_OK:
         raise LtError(rc, "lt_loss_static failed")
+
+
+def probe_l2_read(device: int = 0, nbytes: int = 32 << 20, reps: int = 64) -> float:
+    """lt_probe_l2_read: L2 read bandwidth of the device in GB/s."""
+    lib = load_library()
+    out = ctypes.c_double()
+    rc = lib.lt_probe_l2_read(device, nbytes, reps, ctypes.byref(out))
+    if rc != LT_OK:
+        raise LtError(rc, "lt_probe_l2_read failed")
+    return out.value
+
+
+def gradient_from_fixed(sums, scale: float) -> np.ndarray:
+    """dO/dp from exact gradient sums ([L, 8, 2] int64: low, high word of a
+    128-bit two's-complement integer, as lt_gradient_fixed returns them, or
+    the exact sum of several such arrays given as Python integers [L, 8]):
+    integer x 2^-64 / scale, rounded once, as the library converts them."""
+    ints = fixed_to_ints(sums) if np.asarray(sums, dtype=object).ndim == 3 else np.asarray(sums, dtype=object)
+    out = np.empty(ints.shape, np.float64)
+    for idx in np.ndindex(ints.shape):
+        out[idx] = np.ldexp(float(int(ints[idx])), -GRAD_FRACTION_BITS) / scale
+    return out
+
+
+def fixed_to_ints(sums) -> np.ndarray:
+    """[L, 8, 2] int64 (low, high words) -> [L, 8] array of Python integers."""
+    a = np.asarray(sums, np.int64)
+    out = np.empty(a.shape[:-1], dtype=object)
+    for idx in np.ndindex(out.shape):
+        lo, hi = int(a[idx][0]) & ((1 << 64) - 1), int(a[idx][1])
+        out[idx] = (hi << 64) + lo
+    return out
 
 
 def build_bvh(tri_xyz):
@@ -304,6 +353,14 @@ class Tracer:
         self._check(self.lib.lt_trace_adjoint(self.h, seed, n_photons, max_hits, begin, end, p, dev))
         return out
 
+    def gradient_fixed(self):
+        """(sums [n_lights, 8, 2] int64, scale G) of the last adjoint pass:
+        dO/dp = (high 2^64 + low) 2^-64 / G, summed exactly."""
+        sums = np.empty((self.n_lights, GRAD_N, 2), np.int64)
+        scale = ctypes.c_double()
+        self._check(self.lib.lt_gradient_fixed(self.h, _ptr(sums)[0], ctypes.byref(scale)))
+        return sums, scale.value
+
     def debug_paths(self, seed: int, n_photons: int, max_hits: int, begin: int, count: int, grads: bool = False):
         """Per-photon record: (triangle [count, hits], texel [count, hits]) and,
         with grads=True, each photon's gradient term [count, 8]."""
@@ -379,3 +436,8 @@ class Tracer:
         bound, 1024 staged / 768 through L1 / as many blocks as fit / no
         staged nodes; negative: keep)."""
         self._check(self.lib.lt_set_launch(self.h, threads_per_block, blocks_per_sm, smem_node_bytes))
+
+    def set_step_limit(self, max_steps: int = 0):
+        """Node visits per ray before the tracing kernels give up on it (0:
+        the default); the next synchronising call reports LT_ERR_TIMEOUT."""
+        self._check(self.lib.lt_set_step_limit(self.h, max_steps))
