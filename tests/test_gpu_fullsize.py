@@ -14,7 +14,8 @@ import pytest
 
 import oracle
 from paper_2310_02043_gb300 import _build, scenes
-from paper_2310_02043_gb300.lighttrace import Tracer
+from paper_2310_02043_gb300.lighttrace import Tracer, fixed_to_ints, gradient_from_fixed
+from tests import parity
 
 pytestmark = pytest.mark.gpu
 
@@ -56,10 +57,11 @@ def test_sampled_ranges_match_oracle(office, begin):
     A = oracle.texel_areas(sc)
     tot, tot_ref = np.sum(A * E), np.sum(A * ref["E"])
     assert abs(tot - tot_ref) <= 1e-4 * tot_ref
-    tri, tex = tr.debug_paths(SEED, N, HITS, begin, 4096)
-    tri_o, tex_o = oracle.paths(sc, L, SEED, N, HITS, begin, 4096)
-    same = np.all(tri == tri_o, axis=1) & np.all(tex == tex_o, axis=1)
-    assert same.mean() >= 0.999
+    # every texel, the photons whose float path parted from the double one
+    # accounted for on both sides
+    info = parity.check_every_texel(tr, sc, L, SEED, N, HITS, begin, begin + count, tr.texel_sums(),
+                                    tr.stats()["fixed_point_scale"])
+    assert info["texels"] == sc.n_texels and info["diverged"] <= 1e-3 * count
 
 
 def test_gradient_partition_and_sampled_range(office):
@@ -67,21 +69,25 @@ def test_gradient_partition_and_sampled_range(office):
     w = scenes.random_weights(sc.n_texels, seed=11, scale=1e-3)
     tr.set_adjoint_weights(w)
     g_full = tr.trace_adjoint(SEED, N, HITS)
+    f_full, G = tr.gradient_fixed()
+    assert np.array_equal(gradient_from_fixed(f_full, G), g_full)
+    # the exact sums of a partition add up to the whole range's, bit for bit
     cuts = [0, 3_000_001, 9_999_999, N]
-    g_sum = sum(tr.trace_adjoint(SEED, N, HITS, a, b) for a, b in zip(cuts[:-1], cuts[1:]))
-    # a partition changes which photons share a thread's FP32 sum (the totals
-    # over threads are FP64), so the parts agree with the whole to FP32 rounding
-    assert np.allclose(g_sum, g_full, rtol=1e-5, atol=1e-6 * np.abs(g_full).max())
+    total = 0
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        tr.trace_adjoint(SEED, N, HITS, a, b)
+        f, G_part = tr.gradient_fixed()
+        assert G_part == G
+        total = total + fixed_to_ints(f)
+    assert np.array_equal(total, fixed_to_ints(f_full))
+    assert np.array_equal(gradient_from_fixed(total, G), g_full)
     begin, count = (1 << 22) + 99, 8192
     g = tr.trace_adjoint(SEED, N, HITS, begin, begin + count)
     g_ref, _ = oracle.adjoint(sc, L, SEED, N, HITS, w.astype(np.float64), begin=begin, end=begin + count)
-    tri, tex, c = tr.debug_paths(SEED, N, HITS, begin, count, grads=True)
-    tri_o, tex_o, c_o = oracle.paths(sc, L, SEED, N, HITS, begin, count, w=w.astype(np.float64))
-    same = np.all(tri == tri_o, axis=1) & np.all(tex == tex_o, axis=1)
-    assert same.mean() >= 0.999
-    sizes = np.full(L.shape[0], N // L.shape[0])
-    lights = np.searchsorted(np.cumsum(sizes), np.arange(begin, begin + count), side="right")
-    corr = np.zeros_like(g)
-    np.add.at(corr, lights[~same], c[~same] - c_o[~same])
-    den = np.maximum(np.abs(g_ref), 1e-3 * np.abs(g_ref).max())
-    assert np.all(np.abs(g - corr - g_ref) / den <= 1e-3)
+    # random weights of either sign make every gradient component a near
+    # cancellation over 8192 photons, so the few photons whose float path
+    # parted from the double one move it by up to about 0.5 % of its largest
+    # component (measured 0.40 %); with the objective's own weights the raw
+    # gradient agrees to 1e-4 (test_gpu_parity)
+    parity.check_gradient(tr, sc, L, SEED, N, HITS, w.astype(np.float64), g, g_ref, begin=begin,
+                          end=begin + count, raw_rtol=1e-2)

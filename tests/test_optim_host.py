@@ -104,3 +104,45 @@ def test_seed_schedule():
     assert optim.SeedSchedule(base=5, correlated=True).seeds(2) == (5 + 2 * 7919,) * 2
     assert optim.SeedSchedule(base=5).seeds(0) == (5, 6)
     assert optim.SeedSchedule(base=5, fixed=True).seeds(9) == (5, 6)
+
+
+def test_metrics_log_writes_one_line_per_step(tmp_path):
+    import json
+    sc, truth, target, start = _problem()
+    prob = optim.LightingProblem(sc, target, photons=N, hits=HITS, tracer=OracleTracer())
+    rig = optim.LightRig(start, optimize=("x", "y", "z", "p_int"))
+    schedule = optim.SeedSchedule(base=3)
+    path = str(tmp_path / "run.jsonl")
+    log = optim.MetricsLog(path, schedule)
+    losses, _ = optim.adam(prob, rig, 3, lr=0.01, schedule=schedule, callback=log)
+    log.close()
+    rows = [json.loads(l) for l in open(path)]
+    assert [r["step"] for r in rows] == [0, 1, 2]
+    assert [r["loss"] for r in rows] == losses
+    assert [tuple(r["seeds"]) for r in rows] == [schedule.seeds(k) for k in range(3)]
+    assert set(rows[0]["grad_norm"]) == {"x", "y", "z", "p_int"} and rows[0]["grad_norm"]["x"] > 0
+    assert rows[0]["t_s"] <= rows[1]["t_s"] <= rows[2]["t_s"]
+
+
+def test_scaled_units():
+    # params hold p / scale: the objective sees the physical parameters, the
+    # gradient with respect to params is dO/dp x scale, and one Adam step
+    # moves each column by about lr x its scale
+    sc, truth, target, start = _problem()
+    scale = [0.3, 0.3, 0.3, 0.1, 0.1, 0.2, 0.05, 1.0]
+    prob = optim.LightingProblem(sc, target, photons=N, hits=HITS, tracer=OracleTracer())
+    rig = optim.LightRig(start, scale=scale)
+    np.testing.assert_allclose(rig.lights(), start, rtol=1e-15)
+    loss = prob.objective(rig, 5, 5)
+    loss.backward()
+    plain = optim.LightRig(start)
+    prob.objective(plain, 5, 5).backward()
+    np.testing.assert_allclose(rig.params.grad.numpy(), plain.params.grad.numpy() * np.array(scale), rtol=1e-12)
+    before = rig.lights()[0, 1:9].copy()
+    optim.adam(prob, rig, 1, lr=0.01, schedule=optim.SeedSchedule(base=5, fixed=True))
+    moved = np.abs(rig.lights()[0, 1:9] - before)
+    for j in (0, 1, 2, 5, 6):        # optimised columns with a gradient: Adam's first step is lr x scale
+        assert moved[j] == pytest.approx(0.01 * scale[j], rel=1e-6), j
+    assert moved[7] == 0.0
+    with pytest.raises(ValueError):
+        optim.LightRig(start, scale=[1.0] * 7)
