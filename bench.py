@@ -38,13 +38,20 @@ from paper_2310_02043_gb300 import scenes  # noqa: E402
 METRIC = "Msegments/s fwd+adjoint"
 PHOTONS, HITS = 1 << 24, 5
 TARGET_PHOTONS = 1 << 26
-KERNELS_PER_STEP = 5          # forward, loss, loss reduction, adjoint, gradient reduction
+KERNELS_PER_STEP = 8          # forward, loss, loss reduction, weight range, adjoint, gradient, 2 gradient reductions
 LIGHT_DEV_BYTES = 160         # device light record the library uploads per light
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "trace_kernel_traffic.json")
 
 
-def workload():
+def workload(name: str = "office"):
+    """(scene, lights, ground-truth lights) of a single-design workload: the
+    office (16 spots, 2 cm texels) or the Cornell box (1 point light)."""
+    if name == "cornell":
+        sc = scenes.cornell_box(res=32)
+        lights = scenes.cornell_lights()
+        truth = scenes.perturb_lights(lights, seed=1, pos_sigma=0.05, intensity_range=(0.8, 1.2))
+        return sc, lights, truth
     sc = scenes.office(seed=0, pitch=0.02)
     lights = scenes.office_lights(0)
     truth = scenes.perturb_lights(lights, seed=1, pos_sigma=0.3, angle_sigma=0.1, intensity_range=(0.7, 1.3),
@@ -52,11 +59,21 @@ def workload():
     return sc, lights, truth
 
 
-def config_of(sc, lights, n_gpus):
-    return {"workload": f"procedural office 20x10x3 m, 200 desks/cabinets ({sc.n_tri} tris), {sc.n_texels} texels "
-                        f"at 2 cm, {lights.shape[0]} spots, 2^24 photons/GPU, 5 hits, target traced at 2^26",
-            "triangles": sc.n_tri, "texels": sc.n_texels, "lights": int(lights.shape[0]), "photons_per_gpu": PHOTONS,
-            "hits": HITS, "l2": "flushed between steps (256 MiB write outside the timed events)",
+# photons per GPU, hits per photon and target photons of each single-design workload
+PASS = {"office": (PHOTONS, HITS, TARGET_PHOTONS), "cornell": (1 << 18, 3, 1 << 22)}
+
+
+def config_of(sc, lights, n_gpus, name: str = "office"):
+    photons, hits, target = PASS[name]
+    if name == "cornell":
+        what = (f"Cornell box 1 m room, front open, 2 boxes ({sc.n_tri} tris), {sc.n_texels} texels (32x32 per "
+                f"face), 1 point light, 2^18 photons/GPU, 3 hits, target traced at 2^22")
+    else:
+        what = (f"procedural office 20x10x3 m, 200 desks/cabinets ({sc.n_tri} tris), {sc.n_texels} texels "
+                f"at 2 cm, {lights.shape[0]} spots, 2^24 photons/GPU, 5 hits, target traced at 2^26")
+    return {"workload": what, "triangles": sc.n_tri, "texels": sc.n_texels, "lights": int(lights.shape[0]),
+            "photons_per_gpu": photons, "hits": hits,
+            "l2": "flushed between steps (256 MiB write outside the timed events)",
             "parallelism": f"photon shards x{n_gpus}" if n_gpus > 1 else "single GPU"}
 
 
@@ -125,17 +142,25 @@ def clock_sampler(local):
 # ---------------------------------------------------------------------------
 # Roofline helpers
 # ---------------------------------------------------------------------------
-# Algorithmic FP32 operations of the traversal (counted from the method, not
-# from the compiled code): a node visit tests 8 child boxes, each 6 plane
-# subtractions, 6 multiplications by the inverse direction, 10 min/max to
-# form and combine the slab intervals, 1 scale and 2 comparisons (25 ops);
-# a watertight ray/triangle test is 9 subtractions, 12 shear operations,
-# 9 edge-function operations, 2 additions for the determinant, 8 for the
-# distance and 6 sign tests (46 ops); every segment also samples a direction
-# and a flux (about 40 ops) and computes the hit's texel and normal (about 40).
-OPS_PER_NODE = 8 * 25
+# FP32 operations the traversal issues (counted from the kernel's arithmetic,
+# one fma per slab plane): a node visit forms -o/d once (3 ops) and tests 8
+# child boxes, each 6 plane fmas, one 3-input max, one max with 0, one
+# 3-input min, the exit scaling and 2 comparisons (12 ops); a watertight
+# ray/triangle test is 9 subtractions, 12 shear operations, 9 edge-function
+# operations, 2 additions for the determinant, 8 for the distance and 6 sign
+# tests (46 ops); every segment also samples a direction and a flux (about
+# 40 ops) and computes the hit's texel and normal (about 40).
+OPS_PER_NODE = 8 * 12 + 3
 OPS_PER_TRI = 46
 OPS_PER_SEGMENT = 80
+# Algorithmic bytes per segment of the traversal, as the scope defines them:
+# an 8-wide node with quantised child boxes (80 B, five 16-byte loads), a
+# triangle (48 B, three 16-byte loads), and the texel access (8 B deposit in
+# the forward pass, 4 B weight gather in the adjoint); random numbers are
+# computed in registers. This build stores float nodes of 240 B, of which a
+# visit loads the ray's near and far planes (192 B) and the inner-slot mask.
+NODE_BYTES, NODE_BYTES_LOADED, TRI_BYTES = 80, 196, 48
+HBM_FALLBACK_GBS = 6800.0
 
 
 def alu_peak_tflops(sm_mhz):
@@ -144,26 +169,51 @@ def alu_peak_tflops(sm_mhz):
     return 152 * 128 * sm_mhz * 1e6 / 1e12
 
 
-def l2_copy_gbs(sizes=(4 << 20, 8 << 20, 16 << 20, 32 << 20), reps=100):
-    """L2 bandwidth estimate: device-to-device copies of buffers that stay
-    resident in the 129 MB L2 (4-32 MiB), read + write bytes per second, the
-    best over sizes and 5 batches each, timed with CUDA events."""
-    import torch
-    best = 0.0
-    for nbytes in sizes:
-        a = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
-        b = torch.empty_like(a)
-        b.copy_(a)
-        for _ in range(5):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            e0.record()
-            for _ in range(reps):
-                b.copy_(a)
-            e1.record()
-            torch.cuda.synchronize()
-            best = max(best, 2.0 * nbytes * reps / (e0.elapsed_time(e1) / 1e3) / 1e9)
-    return best
+def hbm_peak():
+    """(GB/s, basis): the measured copy bandwidth, else the fallback figure."""
+    try:
+        v = json.load(open(MEASURED_PEAKS)).get("hbm_gbs")
+        if v:
+            return float(v), "of measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, ValueError):
+        pass
+    return HBM_FALLBACK_GBS, "of fallback (6.8 TB/s, one earlier GB300 measurement)"
+
+
+def traversal_roofline(work, seg_launch, kernel_ms, adjoint, l2_gbs, peak_clock, traffic_per_seg, name):
+    """Roofline record of one trace launch: algorithmic bytes (per segment from
+    the counting kernel, times the launch's segments) over its CUDA-event time
+    against the L2 read rate; beside it the same bytes against HBM, the bytes
+    the float nodes actually load, and the FP32 operations against the issue
+    peak."""
+    segs = work["segments"]
+    nv, tt = work["node_visits"] / segs, work["tri_tests"] / segs
+    per_seg = nv * NODE_BYTES + tt * TRI_BYTES + (4 if adjoint else 8)
+    per_seg_loaded = nv * NODE_BYTES_LOADED + tt * TRI_BYTES + (4 if adjoint else 8)
+    secs = kernel_ms / 1e3
+    achieved = per_seg * seg_launch / secs / 1e9
+    ops_seg = nv * OPS_PER_NODE + tt * OPS_PER_TRI + OPS_PER_SEGMENT
+    ops = ops_seg * seg_launch / secs / 1e12
+    alu = alu_peak_tflops(peak_clock)
+    hbm, hbm_basis = hbm_peak()
+    return {"bound": "l2", "achieved": achieved, "peak": l2_gbs, "unit": "GB/s", "frac": achieved / l2_gbs,
+            "traffic": traffic_per_seg * seg_launch if traffic_per_seg is not None else None,
+            "kernel": f"trace_kernel ({'adjoint' if adjoint else 'forward'}, {name})",
+            "peak_basis": "L2 read rate of the library's own probe (lt_probe_l2_read: 32 MiB swept with 16-byte "
+                          "L2-only loads), measured in this run",
+            "bytes_per_segment": {"algorithmic": per_seg, "node_visits": nv, "tri_tests": tt,
+                                  "node_bytes": NODE_BYTES, "tri_bytes": TRI_BYTES,
+                                  "as_loaded_from_float_nodes": per_seg_loaded},
+            "hbm": {"achieved": achieved, "peak": hbm, "frac": achieved / hbm, "unit": "GB/s",
+                    "peak_basis": hbm_basis},
+            "alu": {"achieved": ops, "peak": alu, "frac": ops / alu, "unit": "TFLOP/s",
+                    "fp32_ops_per_segment": ops_seg,
+                    "peak_basis": f"FP32 issue peak 152 SMs x 128 lanes x {peak_clock:.0f} MHz (derived)"}}
+
+
+def l2_read_gbs():
+    from paper_2310_02043_gb300.lighttrace import probe_l2_read
+    return probe_l2_read(0, 32 << 20, 64)
 
 
 def kernel_hash():
@@ -190,35 +240,40 @@ def stored_traffic(kernel):
 # ---------------------------------------------------------------------------
 # CPU baseline: the oracle on the host cores, a bounded sample of the workload
 # ---------------------------------------------------------------------------
-def cpu_baseline(sc, lights, truth, budget_s=15.0):
+def cpu_baseline(sc, lights, truth, budget_s=15.0, name="office"):
+    """The oracle on the host cores over a bounded sample of the workload
+    (photons [0, n) of its budget, n sized to about budget_s, capped at the
+    whole budget), with a single-thread figure over a smaller sample."""
     import oracle
     oracle.build()
+    photons, hits, _ = PASS[name]
     cores = os.cpu_count() or 1
-    small = 1 << 14
-    target = oracle.forward(sc, truth, 77, small, HITS)["E"]
+    small = min(1 << 14, photons)
+    target = oracle.forward(sc, truth, 77, small, hits)["E"]
     t0 = time.perf_counter()
-    oracle.forward(sc, lights, 2, PHOTONS, HITS, begin=0, end=small)
+    oracle.forward(sc, lights, 2, photons, hits, begin=0, end=small)
     probe = time.perf_counter() - t0
-    n = int(min(1 << 20, max(small, small * budget_s / 2.0 / max(probe, 1e-3))))
+    n = int(min(1 << 20, photons, max(small, small * budget_s / 2.0 / max(probe, 1e-3))))
     n = max(small, (n // 4096) * 4096)
     t0 = time.perf_counter()
-    f = oracle.forward(sc, lights, 2, PHOTONS, HITS, begin=0, end=n)
+    f = oracle.forward(sc, lights, 2, photons, hits, begin=0, end=n)
     t1 = time.perf_counter()
     _, w = oracle.loss(sc, f["E"], target, np.ones(sc.n_texels))
     t2 = time.perf_counter()
-    _, seg_adj = oracle.adjoint(sc, lights, 3, PHOTONS, HITS, w, begin=0, end=n)
+    _, seg_adj = oracle.adjoint(sc, lights, 3, photons, hits, w, begin=0, end=n)
     t3 = time.perf_counter()
     segs = f["segments"] + seg_adj
     # the same passes on one thread, over a smaller photon range
-    n1 = 1 << 12
+    n1 = min(1 << 12, photons)
     t4 = time.perf_counter()
-    f1 = oracle.forward(sc, lights, 2, PHOTONS, HITS, begin=0, end=n1, threads=1)
+    f1 = oracle.forward(sc, lights, 2, photons, hits, begin=0, end=n1, threads=1)
     _, w1 = oracle.loss(sc, f1["E"], target, np.ones(sc.n_texels))
-    _, seg1 = oracle.adjoint(sc, lights, 3, PHOTONS, HITS, w1, begin=0, end=n1, threads=1)
+    _, seg1 = oracle.adjoint(sc, lights, 3, photons, hits, w1, begin=0, end=n1, threads=1)
     t5 = time.perf_counter()
     segs1 = f1["segments"] + seg1
+    budget = "the whole budget" if n == photons else f"the 2^{photons.bit_length() - 1} budget"
     return {"value": segs / (t3 - t0) / 1e6, "unit": "Msegments/s", "cores": cores, "kind": "oracle",
-            "sample": f"photons [0, {n}) of the 2^24 budget, forward + loss + adjoint, brute-force FP64 oracle "
+            "sample": f"photons [0, {n}) of {budget}, forward + loss + adjoint, brute-force FP64 oracle "
                       f"({segs} segments in {t3 - t0:.1f} s: forward {t1 - t0:.1f} s, adjoint {t3 - t2:.1f} s)",
             "single_thread": {"value": segs1 / (t5 - t4) / 1e6, "unit": "Msegments/s",
                               "sample": f"photons [0, {n1}), same passes, one thread ({segs1} segments in "
@@ -230,30 +285,33 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    sc, lights, truth = workload()
+    name = args.workload if args.workload in PASS else "office"
+    photons, hits, _ = PASS[name]
+    sc, lights, truth = workload(name)
     import oracle
     oracle.build()
-    small = 1 << 12
-    target = oracle.forward(sc, truth, 77, small * 4, HITS)["E"]
-    n = 1 << 13
+    small = min(1 << 12, photons)
+    target = oracle.forward(sc, truth, 77, small * 4, hits)["E"]
+    n = min(1 << 13, photons) if name == "office" else photons
     for _ in range(args.warmup):
-        oracle.forward(sc, lights, 2, PHOTONS, HITS, begin=0, end=small)
+        oracle.forward(sc, lights, 2, photons, hits, begin=0, end=small)
     times, segs = [], 0
     for k in range(args.steps):
         t0 = time.perf_counter()
-        f = oracle.forward(sc, lights, 2 + k, PHOTONS, HITS, begin=0, end=n)
+        f = oracle.forward(sc, lights, 2 + k, photons, hits, begin=0, end=n)
         _, w = oracle.loss(sc, f["E"], target, np.ones(sc.n_texels))
-        _, sa = oracle.adjoint(sc, lights, 3 + k, PHOTONS, HITS, w, begin=0, end=n)
+        _, sa = oracle.adjoint(sc, lights, 3 + k, photons, hits, w, begin=0, end=n)
         times.append(time.perf_counter() - t0)
         segs += f["segments"] + sa
     value = segs / sum(times) / 1e6
     cores = os.cpu_count() or 1
+    budget = "the whole budget" if n == photons else f"the 2^{photons.bit_length() - 1} budget"
     line = {"metric": METRIC, "value": value, "unit": "Msegments/s", "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_of(sc, lights, args.gpus),
+            "data": "synthetic", "config": config_of(sc, lights, args.gpus, name),
             "cpu_baseline": {"value": value, "unit": "Msegments/s", "cores": cores, "kind": "oracle",
-                             "sample": f"each step: photons [0, {n}) of the 2^24 budget, forward + loss + adjoint"},
+                             "sample": f"each step: photons [0, {n}) of {budget}, forward + loss + adjoint"},
             "e2e": {"value": value, "unit": "Msegments/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -294,8 +352,11 @@ def apply_update(lights, grad, opt):
 def run_ours(args):
     import torch
     import torch.distributed as dist
+    from paper_2310_02043_gb300 import shard
     from paper_2310_02043_gb300.lighttrace import Tracer
 
+    name = args.workload
+    photons, hits, target_photons = PASS[name]
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -303,52 +364,32 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
-    sc, lights, truth = workload()
+    sc, lights, truth = workload(name)
     tr = Tracer(local, stream.cuda_stream)
     T = tr.upload_scene(sc)
 
-    # Target: traced from the perturbed ("ground-truth") lights at 2^26 photons.
+    # Target: traced from the perturbed ("ground-truth") lights.
     tr.set_lights(truth)
-    tr.trace_forward(77, TARGET_PHOTONS, HITS)
+    tr.trace_forward(77, target_photons, hits)
     target = torch.empty(T, dtype=torch.float32, device="cuda")
     tr.irradiance(out=target)
     tr.set_target(target)
     tr.set_lights(lights)
 
     # Work accounting (untimed): node visits and triangle tests per segment.
-    work = tr.count_work(5, PHOTONS, HITS)
-    from paper_2310_02043_gb300 import shard
+    work = tr.count_work(5, photons, hits)
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     grad_dev = torch.zeros((lights.shape[0], 8), dtype=torch.float64, device="cuda")
     loss_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
     # Every rank traces its own range of one common photon budget (weak
-    # scaling: 2^24 photons per GPU); the integer texel sums and the gradients
+    # scaling: `photons` per GPU); the integer texel sums and the gradients
     # are summed across ranks.
-    n_total, p_begin, p_end = shard.photon_range(rank, world, PHOTONS)
-    q_view = None
-    if world > 1:
-        ptr, _ = tr.texel_accumulator()
-        q_view = shard.device_view(ptr, T)
-
-    def forward(seed):
-        tr.trace_forward(seed, n_total, HITS, p_begin, p_end)
-        if q_view is not None:
-            shard.allreduce_sum(q_view)
-
-    def adjoint(seed, out):
-        tr.trace_adjoint(seed, n_total, HITS, p_begin, p_end, out=out)
-        if world > 1 and not isinstance(out, np.ndarray):
-            shard.allreduce_sum(out)
-
-    def step(k, grad_out, loss_out):
-        seed = 1000 + 7919 * k
-        forward(seed)
-        tr.loss(out=loss_out)
-        adjoint(seed + 1, grad_out)
+    q_view = shard.device_view(tr.texel_accumulator()[0], T) if world > 1 else None
+    sp = shard.ShardedPass(tr, rank, world, photons, hits, accumulator=q_view)
 
     for k in range(args.warmup):
-        step(k, grad_dev, loss_dev)
+        sp.step(1000 + 7919 * k, 1001 + 7919 * k, grad_dev, loss_dev)
     torch.cuda.synchronize()
 
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
@@ -357,16 +398,15 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
-    seg_f = seg_a = 0
     for k in range(args.steps):
         flush.zero_()
         e = ev[k]
         e[0].record(stream)
-        forward(1000 + 7919 * (k + 50))
+        sp.forward(1000 + 7919 * (k + 50))
         e[1].record(stream)
-        tr.loss(out=loss_dev)
+        sp.loss(loss_dev)
         e[2].record(stream)
-        adjoint(1001 + 7919 * (k + 50), grad_dev)
+        sp.adjoint(1001 + 7919 * (k + 50), grad_dev)
         e[3].record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -398,13 +438,7 @@ def run_ours(args):
     for k in range(args.steps):
         tr.set_lights(pinned.numpy())
         seed = 5000 + 7919 * k
-        forward(seed)
-        tr.loss()
-        adjoint(seed + 1, grad_host)
-        if world > 1:
-            gd = torch.from_numpy(grad_host).cuda()
-            shard.allreduce_sum(gd)
-            grad_host[:] = gd.cpu().numpy()
+        sp.step(seed, seed + 1, grad_host)
         cur = apply_update(cur, grad_host, opt)
         pinned.copy_(torch.from_numpy(cur))
     torch.cuda.synchronize()
@@ -423,42 +457,29 @@ def run_ours(args):
             dist.destroy_process_group()
         return
 
-    # Roofline of the dominant kernel (forward and adjoint trace kernels take
-    # about equal time; the forward one is reported, its work counted exactly).
+    # Roofline of the dominant kernel (the slower of the two trace launches),
+    # with its per-segment work counted by the counting kernel.
     fwd_ms = statistics.mean(t_fwd)
     adj_ms = statistics.mean(t_adj)
-    dom_ms, dom = (fwd_ms, "forward") if fwd_ms >= adj_ms else (adj_ms, "adjoint")
-    segs = work["segments"]
-    ops = work["node_visits"] * OPS_PER_NODE + work["tri_tests"] * OPS_PER_TRI + segs * OPS_PER_SEGMENT
-    achieved = ops / (dom_ms / 1e3) / 1e12
-    sm_mhz = clocks["sm_mhz"] if clocks else 1477.0
+    adjoint_dominant = adj_ms >= fwd_ms
+    dom_ms = adj_ms if adjoint_dominant else fwd_ms
+    dom = "adjoint" if adjoint_dominant else "forward"
     peak_clock = clocks["sm_max_mhz"] if clocks and clocks.get("sm_max_mhz") else 2070.0
-    peak = alu_peak_tflops(peak_clock)
-    traffic = stored_traffic(f"trace_kernel_{dom}")
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic * segs if traffic is not None else None,
-                "kernel": f"trace_kernel ({dom})",
-                "peak_basis": f"FP32 issue peak 152 SMs x 128 lanes x {peak_clock:.0f} MHz (derived, not measured)",
-                "work_per_segment": {"node_visits": work["node_visits"] / segs, "tri_tests": work["tri_tests"] / segs,
-                                     "fp32_ops": ops / segs},
-                "frac_at_sampled_clock": achieved / alu_peak_tflops(sm_mhz)}
-    # the traversal's algorithmic bytes (node boxes, triangles, deposits)
-    # against the L2 copy rate: the nodes come from shared memory here, so
-    # this is the rate L2 would have to sustain without staging
-    l2 = l2_copy_gbs()
-    bytes_seg = (work["node_visits"] * 240 + work["tri_tests"] * 48 + segs * 8) / segs
-    l2_achieved = bytes_seg * segs / (dom_ms / 1e3) / 1e9
-    roofline["l2"] = {"achieved": l2_achieved, "peak": l2, "unit": "GB/s", "frac": l2_achieved / l2,
-                      "bytes_per_segment": bytes_seg,
-                      "peak_basis": "best device copy of 4-32 MiB buffers resident in L2, read + write "
-                                    "(measured here; a lower bound on the L2 rate)"}
+    traffic = stored_traffic(f"trace_kernel_{dom}") if name == "office" else None
+    l2 = l2_read_gbs()
+    roofline = traversal_roofline(work, seg_a if adjoint_dominant else seg_f, dom_ms, adjoint_dominant, l2,
+                                  peak_clock, traffic, name)
+    other = traversal_roofline(work, seg_f if adjoint_dominant else seg_a, fwd_ms if adjoint_dominant else adj_ms,
+                               not adjoint_dominant, l2, peak_clock, None, name)
+    roofline["other_trace_kernel"] = {"kernel": other["kernel"], "achieved": other["achieved"], "frac": other["frac"],
+                                      "alu_frac": other["alu"]["frac"]}
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline(sc, lights, truth)
+        cpu = cpu_baseline(sc, lights, truth, name=name)
     line = {"metric": METRIC, "value": value, "unit": "Msegments/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": config_of(sc, lights, world),
+            "config": config_of(sc, lights, world, name),
             "e2e": {"value": e2e_value, "unit": "Msegments/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_opt_iter": 1e3 * e2e_s / args.steps},
             "gpu_launches": KERNELS_PER_STEP * args.steps,
@@ -473,10 +494,100 @@ def run_ours(args):
 
 
 # ---------------------------------------------------------------------------
+# The office's optimisation run: 200 Adam iterations through the autograd layer
+# ---------------------------------------------------------------------------
+ADAM_STEPS, ADAM_LR = 200, 0.05
+# Units of the optimised columns (Adam's steps are lr x these): the size of
+# the ground truth's perturbation of each (position 0.3 m, yaw/pitch 0.1 rad,
+# intensity parameter 15 % of its mean, inner cone 5 degrees).
+ADAM_SCALE = (0.3, 0.3, 0.3, 0.1, 0.1, None, float(np.radians(5.0)), 1.0)
+
+
+def run_adam(args):
+    """200 Adam iterations (beta 0.9/0.999, lr 0.05) on the 16 office spots
+    from the 4 x 4 grid towards the perturbed ground-truth lights, 2^24
+    photons x 5 hits per iteration, decorrelated adjoint seeds (Sec. 4.3),
+    through optim.adam (TraceObjective: forward + objective, then adjoint
+    path replay): the objective and the parameter errors along the way, and
+    the wall-clock ms per optimisation iteration."""
+    import torch
+    from paper_2310_02043_gb300 import optim
+    from paper_2310_02043_gb300.lighttrace import Tracer
+
+    torch.cuda.set_device(0)
+    sc, lights, truth = workload("office")
+    tr = Tracer(0)
+    T = tr.upload_scene(sc)
+    tr.set_lights(truth)
+    tr.trace_forward(77, TARGET_PHOTONS, HITS)
+    target = tr.irradiance()
+    area = tr.texel_areas().astype(np.float64)
+    norm = 0.5 * float(np.sum(area * target.astype(np.float64) ** 2))
+    prob = optim.LightingProblem(sc, target, photons=PHOTONS, hits=HITS, tracer=tr)
+    scale = list(ADAM_SCALE)
+    scale[5] = 0.15 * float(np.mean(lights[:, 6]))
+    rig = optim.LightRig(lights, scale=scale)
+    schedule = optim.SeedSchedule(base=11)
+    truth_p = truth[:, 1:9]
+    # the objective's Monte Carlo floor: the ground-truth lights themselves
+    floor = prob.forward_loss(truth, 3)[0] / norm
+
+    def axis(p):
+        return np.stack([np.cos(p[:, 4]) * np.cos(p[:, 3]), np.cos(p[:, 4]) * np.sin(p[:, 3]), np.sin(p[:, 4])], 1)
+
+    def errors(r):
+        p = r.lights()[:, 1:9]
+        cosang = np.clip(np.sum(axis(p) * axis(truth_p), axis=1), -1.0, 1.0)
+        return {"position_m": float(np.sqrt(np.mean(np.sum((p[:, 0:3] - truth_p[:, 0:3]) ** 2, axis=1)))),
+                "axis_rad": float(np.sqrt(np.mean(np.arccos(cosang) ** 2))),
+                "p_int_rel": float(np.sqrt(np.mean(((p[:, 5] - truth_p[:, 5]) / truth_p[:, 5]) ** 2))),
+                "theta_in_rad": float(np.sqrt(np.mean((p[:, 6] - truth_p[:, 6]) ** 2)))}
+
+    start_err = errors(rig)
+    warm = optim.LightRig(lights, scale=scale)
+    optim.adam(prob, warm, max(args.warmup, 1), lr=ADAM_LR, schedule=optim.SeedSchedule(base=5))
+    history = []
+
+    def log(k, loss, r):
+        if k % 10 == 9 or k == 0:
+            history.append({"iteration": k + 1, "relative_objective": loss / norm, **errors(r)})
+
+    clock = clock_sampler(0)
+    clock.start()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses, _ = optim.adam(prob, rig, ADAM_STEPS, lr=ADAM_LR, schedule=schedule, callback=log)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clocks = clock.stop()
+    ms = 1e3 * wall / ADAM_STEPS
+    line = {"metric": "ms per opt-iter (forward + objective + adjoint + Adam step)", "value": ms, "unit": "ms",
+            "n_gpus": 1, "steps": ADAM_STEPS, "warmup": max(args.warmup, 1), "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(config_of(sc, lights, 1, "office"),
+                           workload=f"procedural office ({sc.n_tri} tris, {T} texels at 2 cm), 16 spots from the "
+                                    "4x4 grid towards perturbed ground-truth spots (target traced at 2^26), "
+                                    f"{ADAM_STEPS} Adam iterations, lr {ADAM_LR} in scaled units, 2^24 photons x 5 "
+                                    "hits each, decorrelated adjoint seeds",
+                           l2="not flushed (end-to-end optimisation timing)"),
+            "objective": {"first": losses[0] / norm, "last": losses[-1] / norm, "at_ground_truth": floor,
+                          "unit": "relative (O / (1/2 sum A E*^2)); the ground truth's value is the Monte Carlo "
+                                  "floor of a 2^24-photon trace against the 2^26-photon target"},
+            "units": {"lr": ADAM_LR, "scale": dict(zip(("x", "y", "z", "yaw", "pitch", "p_int", "theta_in",
+                                                        "theta_out"), scale))},
+            "errors": {"start": start_err, "end": errors(rig)}, "history": history,
+            "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": LIGHT_DEV_BYTES * lights.shape[0],
+                    "d2h_bytes_per_step": 8 + 8 * 8 * lights.shape[0]},
+            "gpu_launches": KERNELS_PER_STEP * ADAM_STEPS, "cpu_baseline": None, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    tr.close()
+
+
+# ---------------------------------------------------------------------------
 # Batched designs: 64 candidate designs in one launch per pass
 # ---------------------------------------------------------------------------
 BATCH_DESIGNS, BATCH_PHOTONS = 64, 1 << 22
-BATCH_KERNELS_PER_STEP = 5    # forward, loss, loss reduction, adjoint, gradient reduction
+BATCH_KERNELS_PER_STEP = 8    # forward, loss, loss reduction, weight range, adjoint, gradient, 2 gradient reductions
 
 
 def batch_config(sc, counts, shape):
@@ -577,32 +688,28 @@ def run_batch(args):
     h2d = 256 + LIGHT_DEV_BYTES * int(counts.sum())
     d2h = 8 * (len(counts) + 8 * int(counts.sum()) + 2)
 
-    # Roofline: FP32 work of the whole step from the counting kernel on a few
-    # designs (single-design passes with the same design words).
-    ops_seg = []
+    # Roofline of the whole step (forward + adjoint launches of all designs):
+    # work per segment from the counting kernel on every 16th design
+    # (single-design passes with the same design words).
+    acc = {"segments": 0, "node_visits": 0, "tri_tests": 0}
     for d in range(0, len(counts), 16):
         tr.set_design(d)
         tr.set_lights(designs[offs[d]:offs[d + 1]])
         w = tr.count_work(100, BATCH_PHOTONS, HITS)
-        ops_seg.append((w["node_visits"] * OPS_PER_NODE + w["tri_tests"] * OPS_PER_TRI
-                        + w["segments"] * OPS_PER_SEGMENT) / w["segments"])
+        for key in acc:
+            acc[key] += w[key]
     tr.set_design(0)
-    ops = statistics.mean(ops_seg) * seg_step
     step_ms = total_ms / args.steps
-    achieved = ops / (step_ms / 1e3) / 1e12
     peak_clock = clocks["sm_max_mhz"] if clocks and clocks.get("sm_max_mhz") else 2070.0
-    peak = alu_peak_tflops(peak_clock)
+    roofline = traversal_roofline(acc, seg_step, step_ms, False, l2_read_gbs(), peak_clock, None,
+                                  "whole batch step: forward + adjoint of 64 designs")
     line = {"metric": METRIC, "value": value, "unit": "Msegments/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": batch_config(sc, counts, shape),
             "e2e": {"value": e2e_value, "unit": "Msegments/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_opt_iter": 1e3 * e2e_s / args.steps},
             "gpu_launches": BATCH_KERNELS_PER_STEP * args.steps,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "kernel": "trace_kernel forward + adjoint (whole batch step)",
-                         "peak_basis": f"FP32 issue peak 152 SMs x 128 lanes x {peak_clock:.0f} MHz (derived)",
-                         "fp32_ops_per_segment": statistics.mean(ops_seg)},
+            "roofline": roofline,
             "sequential": {"value": seq_value, "unit": "Msegments/s", "ms_per_step": statistics.mean(seq_ms),
                            "what": "the same designs as single-design passes, one after another"},
             "autotune_ms": {json.dumps(list(k)): v for k, v in tuned.items()},
@@ -796,6 +903,7 @@ def run_building(args):
         torch.cuda.synchronize()
         st = tr.stats()
         segs += st["segments_forward"] + st["segments_adjoint"]
+        seg_adj = st["segments_adjoint"]
     clocks = clock.stop()
     t_f = [e[0].elapsed_time(e[1]) for e in ev]
     t_a = [e[1].elapsed_time(e[2]) for e in ev]
@@ -813,19 +921,20 @@ def run_building(args):
     lbfgs_s = time.perf_counter() - t0
     evals = prob.evaluations
     e2e_value = evals * BLD_PHOTONS * BLD_HITS * 2 / lbfgs_s / 1e6
-    seg = work["segments"]
-    ops = work["node_visits"] * OPS_PER_NODE + work["tri_tests"] * OPS_PER_TRI + seg * OPS_PER_SEGMENT
     fwd_ms = statistics.mean(t_f)
-    achieved = ops / seg * (BLD_PHOTONS * BLD_HITS) / (fwd_ms / 1e3) / 1e12
+    adj_ms = statistics.mean(t_a)
     peak_clock = clocks["sm_max_mhz"] if clocks and clocks.get("sm_max_mhz") else 2070.0
-    peak = alu_peak_tflops(peak_clock)
     traffic = None
     try:
         d = json.load(open(os.path.join(ROOT, "profiles", "trace_kernel_building_traffic.json")))
         if d.get("kernel_source_sha256_16") == kernel_hash():
-            traffic = d["trace_kernel_forward"]["dram_bytes_per_segment"] * BLD_PHOTONS * BLD_HITS
+            traffic = d["trace_kernel_adjoint"]["dram_bytes_per_segment"]
     except (OSError, ValueError, KeyError):
         pass
+    # the adjoint launch (its time excludes the objective, which the forward
+    # interval includes)
+    roofline = traversal_roofline(work, seg_adj, adj_ms, True,
+                                  l2_read_gbs(), peak_clock, traffic, "building, BVH through L1/L2")
     line = {"metric": METRIC, "value": value, "unit": "Msegments/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -841,12 +950,8 @@ def run_building(args):
                     "evaluations": evals, "ms_per_evaluation": 1e3 * lbfgs_s / max(1, evals),
                     "objective": [trace[0], trace[-1]]},
             "gpu_launches": KERNELS_PER_STEP * args.steps,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                         "traffic": traffic, "kernel": "trace_kernel (forward, BVH through L1/L2)",
-                         "peak_basis": f"FP32 issue peak 152 SMs x 128 lanes x {peak_clock:.0f} MHz (derived)",
-                         "work_per_segment": {"node_visits": work["node_visits"] / seg,
-                                              "tri_tests": work["tri_tests"] / seg, "fp32_ops": ops / seg}},
-            "kernel_ms": {"forward_and_loss": fwd_ms, "adjoint": statistics.mean(t_a)},
+            "roofline": roofline,
+            "kernel_ms": {"forward_and_loss": fwd_ms, "adjoint": adj_ms},
             "cpu_baseline": None, "clocks": clocks}
     print(json.dumps(line), flush=True)
     tr.close()
@@ -896,14 +1001,16 @@ def run_profile_case(args):
     import torch
     from paper_2310_02043_gb300.lighttrace import Tracer
     torch.cuda.set_device(0)
-    sc, lights, _ = workload()
+    name = args.workload if args.workload in PASS else "office"
+    hits = PASS[name][1]
+    sc, lights, _ = workload(name)
     tr = Tracer(0)
     T = tr.upload_scene(sc)
     tr.set_target(np.zeros(T, np.float32))
     tr.set_lights(lights)
-    tr.trace_forward(2, args.photons, HITS)
+    tr.trace_forward(2, args.photons, hits)
     tr.loss()
-    tr.trace_adjoint(3, args.photons, HITS)
+    tr.trace_adjoint(3, args.photons, hits)
     st = tr.stats()
     tr.close()
     print(json.dumps({"profile_case": True, "photons": args.photons, "segments_forward": st["segments_forward"],
@@ -920,16 +1027,21 @@ def main():
     ap.add_argument("--profile-only", action="store_true",
                     help="run one forward + loss + adjoint at --photons and exit (for profilers)")
     ap.add_argument("--photons", type=int, default=1 << 20)
-    ap.add_argument("--workload", choices=["office", "batch", "surrogate", "building"], default="office",
-                    help="office: one design, 16 spots (default); batch: 64 designs in one launch per pass; "
-                         "surrogate: time to a target loss with the surrogate warm start; building: 961,792 tris, "
-                         "64 area lights, 2^26 photons, 6 hits")
+    ap.add_argument("--workload", choices=["office", "cornell", "adam", "batch", "surrogate", "building"],
+                    default="office",
+                    help="office: one design, 16 spots (default); cornell: the Cornell box, 1 point light, 2^18 "
+                         "photons, 3 hits; adam: 200 Adam iterations on the office; batch: 64 designs in one launch per pass; surrogate: time to a target "
+                         "loss with the surrogate warm start; building: 961,792 tris, 64 area lights, 2^26 photons, "
+                         "6 hits")
     args = ap.parse_args()
     if args.workload == "batch" and args.impl == "ours" and not args.profile_only:
         run_batch(args)
         return
     if args.workload == "surrogate" and args.impl == "ours":
         run_profile_surrogate(args) if args.profile_only else run_surrogate(args)
+        return
+    if args.workload == "adam" and args.impl == "ours":
+        run_adam(args)
         return
     if args.workload == "building" and args.impl == "ours":
         run_profile_building(args) if args.profile_only else run_building(args)

@@ -4,8 +4,9 @@
 photons and evaluates the texel objective (Alg. 1, Eq. 6); its backward pass
 replays the same photon paths from their random-number counters and returns
 dO/dp (Alg. 2, Eq. 11). Nothing about the paths is stored between the two
-passes: the adjoint recomputes them, which keeps memory independent of the
-photon count (the paper's per-path adjoint states, Sec. 4.3). If another
+passes: the adjoint recomputes them (the paper's per-path adjoint states,
+Sec. 4.3); within the adjoint pass each photon leaves a 16-byte record (its
+adjoint state and first hit) for the gradient kernel. If another
 forward pass ran in between (an L-BFGS line search does this), the backward
 pass first re-runs forward and loss for its own parameters.
 
@@ -17,7 +18,9 @@ evaluation).
 from __future__ import annotations
 
 import dataclasses
+import json
 import os
+import time
 
 import numpy as np
 import torch
@@ -29,29 +32,42 @@ class LightRig(torch.nn.Module):
     """Luminaire parameters [L, 8] (float64) with the light types fixed.
 
     ``optimize`` names the parameter columns that change; the others keep
-    their values (their gradients are zeroed)."""
+    their values (their gradients are zeroed). ``scale`` (8 values, default
+    ones) sets the unit of each column for the optimiser: ``params`` holds
+    the parameters divided by it, so a step of a given size in ``params`` is
+    a step of scale times that size in metres or radians (a learning rate in
+    scaled units)."""
 
-    def __init__(self, lights, optimize=("x", "y", "z", "yaw", "pitch", "p_int", "theta_in")):
+    def __init__(self, lights, optimize=("x", "y", "z", "yaw", "pitch", "p_int", "theta_in"), scale=None):
         super().__init__()
         arr = np.asarray(lights, np.float64).reshape(-1, 9)
         self.register_buffer("types", torch.tensor(arr[:, 0]))
-        self.params = torch.nn.Parameter(torch.tensor(arr[:, 1:9].copy()))
+        sc = torch.ones(8, dtype=torch.float64) if scale is None else torch.tensor(scale, dtype=torch.float64)
+        if sc.shape != (8,) or not bool(torch.all(sc > 0)):
+            raise ValueError("scale needs 8 positive values")
+        self.register_buffer("scale", sc)
+        self.params = torch.nn.Parameter(torch.tensor(arr[:, 1:9] / sc.numpy()))
         mask = torch.zeros(8, dtype=torch.bool)
         for name in optimize:
             mask[PARAM_NAMES.index(name)] = True
         self.register_buffer("mask", mask)
 
+    def physical(self) -> torch.Tensor:
+        """The parameters in metres / radians / p_int (differentiable)."""
+        return self.params * self.scale
+
     def lights(self) -> np.ndarray:
         """[L, 9] rows (type, x, y, z, yaw, pitch, p_int, theta_in, theta_out)."""
-        p = self.params.detach().cpu().numpy()
+        p = self.physical().detach().cpu().numpy()
         return np.ascontiguousarray(np.concatenate([self.types.cpu().numpy()[:, None], p], axis=1))
 
     @torch.no_grad()
     def project(self):
         """Keep every spot valid: 0 <= theta_in < theta_out <= pi."""
-        p = self.params
+        p = self.params * self.scale
         p[:, 7].clamp_(1e-3, np.pi)
         p[:, 6].copy_(torch.minimum(p[:, 6].clamp(min=0.0), p[:, 7] - 1e-3))
+        self.params.copy_(p / self.scale)
 
     def mask_grad(self):
         if self.params.grad is not None:
@@ -109,7 +125,7 @@ class LightingProblem:
         return np.asarray(self.tr.trace_adjoint(seed_adj, self.photons, self.hits), np.float64)
 
     def objective(self, rig: LightRig, seed_fwd: int, seed_adj: int) -> torch.Tensor:
-        return TraceObjective.apply(rig.params, rig.types, self, seed_fwd, seed_adj)
+        return TraceObjective.apply(rig.physical(), rig.types, self, seed_fwd, seed_adj)
 
 
 class TraceObjective(torch.autograd.Function):
@@ -172,12 +188,40 @@ def lbfgs(problem: LightingProblem, rig: LightRig, max_iter: int = 20, seed: int
     return trace
 
 
+class MetricsLog:
+    """Per-iteration metrics of an optimisation run as JSON lines (append
+    mode, one object per step, flushed as written): the step, its objective,
+    its seeds, the norm of the gradient of every parameter column that
+    changes, and the seconds since the log was opened. Pass it as the
+    ``callback`` of ``adam``; a run resumed from a checkpoint appends to the
+    same file."""
+
+    def __init__(self, path: str, schedule: SeedSchedule | None = None):
+        self.path, self.schedule = path, schedule
+        self.t0 = time.perf_counter()
+        self.f = open(path, "a", buffering=1)
+
+    def __call__(self, step: int, loss: float, rig: LightRig):
+        rec = {"step": int(step), "loss": float(loss), "t_s": time.perf_counter() - self.t0}
+        if self.schedule is not None:
+            rec["seeds"] = list(self.schedule.seeds(step))
+        if rig.params.grad is not None:
+            g = (rig.params.grad / rig.scale).detach().cpu().numpy()      # dO/dp in physical units
+            rec["grad_norm"] = {PARAM_NAMES[j]: float(np.linalg.norm(g[:, j]))
+                                for j in range(8) if bool(rig.mask[j])}
+        self.f.write(json.dumps(rec) + "\n")
+
+    def close(self):
+        self.f.close()
+
+
 def save_checkpoint(path: str, rig: LightRig, optimizer, step: int, schedule: SeedSchedule):
     """Parameters, optimiser state, step index and seed schedule. The seeds of
     step k depend only on (schedule, k), so a resumed run repeats the same
     random numbers as an uninterrupted one."""
     tmp = path + ".tmp"
     torch.save({"params": rig.params.detach().clone(), "types": rig.types.clone(), "mask": rig.mask.clone(),
+                "scale": rig.scale.clone(),
                 "optimizer": optimizer.state_dict(), "step": step, "schedule": dataclasses.asdict(schedule)}, tmp)
     os.replace(tmp, path)
 
@@ -185,6 +229,8 @@ def save_checkpoint(path: str, rig: LightRig, optimizer, step: int, schedule: Se
 def load_checkpoint(path: str, rig: LightRig, optimizer):
     """Restore a checkpoint into rig and optimizer; returns (step, schedule)."""
     d = torch.load(path, weights_only=False)
+    if "scale" in d and not torch.equal(d["scale"], rig.scale):
+        raise ValueError("the checkpoint was written with other parameter scales")
     with torch.no_grad():
         rig.params.copy_(d["params"])
     optimizer.load_state_dict(d["optimizer"])

@@ -112,7 +112,7 @@ class SurrogateProblem:
         return self._grad
 
     def objective(self, rig, seed_fwd: int = 0, seed_adj: int = 0):
-        return optim.TraceObjective.apply(rig.params, rig.types, self, seed_fwd, seed_adj)
+        return optim.TraceObjective.apply(rig.physical(), rig.types, self, seed_fwd, seed_adj)
 
 
 def relative_loss(tracer, lights, target, area, photons: int, hits: int, seed: int, alpha=None) -> float:
