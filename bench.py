@@ -501,12 +501,14 @@ ADAM_STEPS, ADAM_LR = 200, 0.05
 # the ground truth's perturbation of each (position 0.3 m, yaw/pitch 0.1 rad,
 # intensity parameter 15 % of its mean, inner cone 5 degrees).
 ADAM_SCALE = (0.3, 0.3, 0.3, 0.1, 0.1, None, float(np.radians(5.0)), 1.0)
+ADAM_OPTIMIZE = ("x", "y", "yaw", "pitch", "p_int", "theta_in")
 
 
 def run_adam(args):
-    """200 Adam iterations (beta 0.9/0.999, lr 0.05) on the 16 office spots
-    from the 4 x 4 grid towards the perturbed ground-truth lights, 2^24
-    photons x 5 hits per iteration, decorrelated adjoint seeds (Sec. 4.3),
+    """200 Adam iterations (beta 0.9/0.999, lr 0.05 in scaled units) on the 16
+    office spots from the 4 x 4 grid towards ground-truth lights perturbed in
+    the ceiling plane, 2^24 photons x 5 hits per iteration, decorrelated
+    adjoint seeds (Sec. 4.3),
     through optim.adam (TraceObjective: forward + objective, then adjoint
     path replay): the objective and the parameter errors along the way, and
     the wall-clock ms per optimisation iteration."""
@@ -515,7 +517,11 @@ def run_adam(args):
     from paper_2310_02043_gb300.lighttrace import Tracer
 
     torch.cuda.set_device(0)
-    sc, lights, truth = workload("office")
+    sc, lights, _ = workload("office")
+    # ground truth moved in the ceiling plane (x, y N(0, 0.3 m), yaw/pitch
+    # N(0, 0.1), intensity x U[0.7, 1.3], theta_in +- 5 deg), so that every
+    # light stays inside the room
+    truth = scenes.perturb_lights_in_plane(lights, 1)
     tr = Tracer(0)
     T = tr.upload_scene(sc)
     tr.set_lights(truth)
@@ -526,7 +532,10 @@ def run_adam(args):
     prob = optim.LightingProblem(sc, target, photons=PHOTONS, hits=HITS, tracer=tr)
     scale = list(ADAM_SCALE)
     scale[5] = 0.15 * float(np.mean(lights[:, 6]))
-    rig = optim.LightRig(lights, scale=scale)
+    # ceiling-mounted spots: z stays fixed (a spot moved through the ceiling
+    # plane lights the ceiling's top side from a centimetre away, a jump of
+    # the objective that the adjoint, with visibility frozen, does not see)
+    rig = optim.LightRig(lights, optimize=ADAM_OPTIMIZE, scale=scale)
     schedule = optim.SeedSchedule(base=11)
     truth_p = truth[:, 1:9]
     # the objective's Monte Carlo floor: the ground-truth lights themselves
@@ -538,13 +547,13 @@ def run_adam(args):
     def errors(r):
         p = r.lights()[:, 1:9]
         cosang = np.clip(np.sum(axis(p) * axis(truth_p), axis=1), -1.0, 1.0)
-        return {"position_m": float(np.sqrt(np.mean(np.sum((p[:, 0:3] - truth_p[:, 0:3]) ** 2, axis=1)))),
+        return {"position_xy_m": float(np.sqrt(np.mean(np.sum((p[:, 0:2] - truth_p[:, 0:2]) ** 2, axis=1)))),
                 "axis_rad": float(np.sqrt(np.mean(np.arccos(cosang) ** 2))),
                 "p_int_rel": float(np.sqrt(np.mean(((p[:, 5] - truth_p[:, 5]) / truth_p[:, 5]) ** 2))),
                 "theta_in_rad": float(np.sqrt(np.mean((p[:, 6] - truth_p[:, 6]) ** 2)))}
 
     start_err = errors(rig)
-    warm = optim.LightRig(lights, scale=scale)
+    warm = optim.LightRig(lights, optimize=ADAM_OPTIMIZE, scale=scale)
     optim.adam(prob, warm, max(args.warmup, 1), lr=ADAM_LR, schedule=optim.SeedSchedule(base=5))
     history = []
 
@@ -566,7 +575,8 @@ def run_adam(args):
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(config_of(sc, lights, 1, "office"),
                            workload=f"procedural office ({sc.n_tri} tris, {T} texels at 2 cm), 16 spots from the "
-                                    "4x4 grid towards perturbed ground-truth spots (target traced at 2^26), "
+                                    "4x4 grid towards ground-truth spots perturbed in the ceiling plane (target "
+                                    "traced at 2^26); x, y, yaw, pitch, p_int, theta_in optimised, z fixed; "
                                     f"{ADAM_STEPS} Adam iterations, lr {ADAM_LR} in scaled units, 2^24 photons x 5 "
                                     "hits each, decorrelated adjoint seeds",
                            l2="not flushed (end-to-end optimisation timing)"),

@@ -348,7 +348,8 @@ int upload_lights(Ctx *c, uint64_t n_photons) {
 int launch_shape(Ctx *c, bool adjoint, int *grid, int *threads, size_t *smem, int32_t *n_staged) {
     const bool staged = (int64_t)c->n_nodes * (int64_t)sizeof(Node) <= (int64_t)c->smem_node_bytes;
     *n_staged = staged ? c->n_nodes : 0;
-    *smem = (size_t)(*n_staged) * sizeof(Node);
+    // staged nodes, then their parent links (int32, rounded up to 16 bytes)
+    *smem = (size_t)(*n_staged) * sizeof(Node) + ((size_t)(*n_staged) + 3) / 4 * 16;
     const int bound = trace_kernel_max_threads(staged);
     *threads = c->threads > 0 ? c->threads : bound;
     if (*threads > bound)
