@@ -281,8 +281,8 @@ LT_API int lt_get_stats(void *ctx, lt_stats *out);
 
 /* Forward pass exactly as lt_trace_forward (same texel sums) through a
  * counting variant of the kernel, for work accounting: writes
- * counts_out[0] = segments traced, [1] = BVH node visits (including the
- * re-tests on the way back up), [2] = ray/triangle tests, [3] = photons. */
+ * counts_out[0] = segments traced, [1] = BVH node visits, [2] =
+ * ray/triangle tests, [3] = photons. */
 LT_API int lt_count_work(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
                   uint64_t photon_end, uint64_t *counts_out);
 
