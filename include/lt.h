@@ -104,9 +104,11 @@ typedef struct {
     double fixed_point_scale;    /* S of the last forward pass (single or batch): a texel accumulates round(Phi * S) */
     int32_t grid_blocks;         /* launch shape of the last forward pass (single or batch) */
     int32_t block_threads;
+    int32_t staged_triangles;    /* triangles held in shared memory per block (last forward pass) */
+    int32_t reserved;
 } lt_stats;
 
-/* Library ABI version (this header: 1). */
+/* Library ABI version (this header: 2). */
 LT_API int lt_version(void);
 
 /* Create a context on CUDA device `device`; work goes to `cuda_stream`
@@ -389,6 +391,15 @@ LT_API int lt_loss_static(int device, void *cuda_stream, const int64_t *q, doubl
  * nothing. A negative argument keeps the current value. The defaults are the
  * kernel's bound, as many blocks as fit, 72 KiB. */
 LT_API int lt_set_launch(void *ctx, int32_t threads_per_block, int32_t blocks_per_sm, int32_t smem_node_bytes);
+
+/* Shared-memory budget for staging the triangles with the nodes: when the
+ * whole BVH is staged (lt_set_launch) and the nodes, their parent links and
+ * all triangles (48 bytes each) take at most max_bytes, every block copies
+ * the triangles to shared memory too, and the leaf tests read them there.
+ * max_bytes in [0, 220 KiB]; 0 = never; default 200 KiB. Results do not
+ * depend on it (the same tests on the same values). Takes effect at the next
+ * trace; a captured batch graph is rebuilt. */
+LT_API int lt_set_tri_staging(void *ctx, int32_t max_bytes);
 
 /* Give-up limit of the tracing kernels: BVH node visits one ray may make
  * before the kernel ends that ray as a miss, records the give-up in the

@@ -70,6 +70,7 @@ struct Ctx {
     double *h_pinned = nullptr;            // small pinned staging area
     // launch
     int threads = 0, blocks_per_sm = 0, smem_node_bytes = 72 * 1024;   // threads 0: the kernel's bound
+    int smem_tri_bytes = 200 * 1024;       // triangles staged when nodes + parent links + triangles fit this
     int32_t max_steps = 0;                 // node visits per ray before giving up; 0: 16 x nodes + 64
     lt_stats stats{};
     // host copy of the uploaded charts (texel centres)
@@ -343,13 +344,19 @@ int upload_lights(Ctx *c, uint64_t n_photons) {
 }
 
 // Launch shape of a tracing kernel. The whole BVH is staged in shared memory
-// when it fits the budget, otherwise no node is (nodes then come through L1).
+// when it fits the budget, otherwise no node is (nodes then come through L1);
+// with the nodes staged, the triangles follow them when nodes and triangles
+// together fit the triangle budget. Sets p->n_staged and p->n_tris_staged.
 // The block is the requested size, else the bound of the kernel chosen.
-int launch_shape(Ctx *c, bool adjoint, int *grid, int *threads, size_t *smem, int32_t *n_staged) {
+int launch_shape(Ctx *c, bool adjoint, int *grid, int *threads, size_t *smem, TraceParams *p) {
     const bool staged = (int64_t)c->n_nodes * (int64_t)sizeof(Node) <= (int64_t)c->smem_node_bytes;
-    *n_staged = staged ? c->n_nodes : 0;
+    p->n_staged = staged ? c->n_nodes : 0;
     // staged nodes, then their parent links (int32, rounded up to 16 bytes)
-    *smem = (size_t)(*n_staged) * sizeof(Node) + ((size_t)(*n_staged) + 3) / 4 * 16;
+    *smem = (size_t)p->n_staged * sizeof(Node) + ((size_t)p->n_staged + 3) / 4 * 16;
+    const size_t tri_bytes = (size_t)c->n_tri * sizeof(Tri);
+    const bool tris = staged && *smem + tri_bytes <= (size_t)c->smem_tri_bytes;
+    p->n_tris_staged = tris ? c->n_tri : 0;
+    if (tris) *smem += tri_bytes;
     const int bound = trace_kernel_max_threads(staged);
     *threads = c->threads > 0 ? c->threads : bound;
     if (*threads > bound)
@@ -357,7 +364,7 @@ int launch_shape(Ctx *c, bool adjoint, int *grid, int *threads, size_t *smem, in
                                        std::to_string(bound) + " of the kernel for this BVH");
     int bps = c->blocks_per_sm;
     if (bps <= 0) {
-        cudaError_t e = trace_occupancy(adjoint, staged, c->depth, *threads, *smem, &bps);
+        cudaError_t e = trace_occupancy(adjoint, staged, tris, c->depth, *threads, *smem, &bps);
         if (e != cudaSuccess) return cuda_fail(c, e, "occupancy query");
         if (bps < 1) return fail(c, LT_ERR_ARG, "launch shape does not fit on an SM");
     }
@@ -456,7 +463,7 @@ int batch_prepare(Ctx *c, BatchLaunch *bl) {
     bl->fwd.hdr = hdr;
     bl->fwd.q = b.d_q;
     bl->fwd.segments = reinterpret_cast<unsigned long long *>(b.d_grad + (size_t)b.n_lights * 8);
-    if ((rc = launch_shape(c, false, &bl->grid_f, &bl->threads_f, &bl->smem_f, &bl->fwd.n_staged))) return rc;
+    if ((rc = launch_shape(c, false, &bl->grid_f, &bl->threads_f, &bl->smem_f, &bl->fwd))) return rc;
     bl->fwd.chunk = photon_chunk(n_total, bl->grid_f, bl->threads_f);
     bl->fwd.max_iters = step_limit(bl->fwd);
     bl->adj = bl->fwd;
@@ -464,7 +471,7 @@ int batch_prepare(Ctx *c, BatchLaunch *bl) {
     bl->adj.w = b.d_w;
     bl->adj.wmax = b.d_wmax;
     bl->adj.segments = bl->fwd.segments + 1;
-    if ((rc = launch_shape(c, true, &bl->grid_a, &bl->threads_a, &bl->smem_a, &bl->adj.n_staged))) return rc;
+    if ((rc = launch_shape(c, true, &bl->grid_a, &bl->threads_a, &bl->smem_a, &bl->adj))) return rc;
     bl->adj.chunk = photon_chunk(n_total, bl->grid_a, bl->threads_a);
     bl->adj.max_iters = step_limit(bl->adj);
     int32_t max_count = 1, min_count = INT32_MAX;
@@ -534,7 +541,7 @@ int batch_check_device(Ctx *c) {
 
 extern "C" {
 
-int lt_version(void) { return 1; }
+int lt_version(void) { return 2; }
 
 static_assert(sizeof(lt_bvh_node) == sizeof(Node), "lt_bvh_node mirrors lt::Node");
 static_assert(offsetof(lt_bvh_node, hi_z) == offsetof(Node, hiz) && offsetof(lt_bvh_node, child) == offsetof(Node, child) &&
@@ -812,7 +819,7 @@ static int forward_pass(Ctx *c, uint64_t seed, uint64_t n_photons, int32_t max_h
     p.segments = c->d_seg;
     int grid, threads;
     size_t smem;
-    if ((rc = launch_shape(c, false, &grid, &threads, &smem, &p.n_staged))) return rc;
+    if ((rc = launch_shape(c, false, &grid, &threads, &smem, &p))) return rc;
     p.chunk = photon_chunk(photon_end - photon_begin, grid, threads);
     p.max_iters = step_limit(p);
     LT_CUDA(c, cudaMemsetAsync(c->d_q, 0, (size_t)c->n_texels * sizeof(unsigned long long), c->stream));
@@ -828,6 +835,7 @@ static int forward_pass(Ctx *c, uint64_t seed, uint64_t n_photons, int32_t max_h
     c->seg_single = true;
     c->stats.photons_forward = photon_end - photon_begin;
     c->stats.staged_nodes = p.n_staged;
+    c->stats.staged_triangles = p.n_tris_staged;
     c->stats.fixed_point_scale = S;
     c->stats.grid_blocks = grid;
     c->stats.block_threads = threads;
@@ -983,7 +991,7 @@ int lt_trace_adjoint(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_h
     p.segments = c->d_seg + 1;
     int grid, threads;
     size_t smem;
-    if ((rc = launch_shape(c, true, &grid, &threads, &smem, &p.n_staged))) return rc;
+    if ((rc = launch_shape(c, true, &grid, &threads, &smem, &p))) return rc;
     p.chunk = photon_chunk(photon_end - photon_begin, grid, threads);
     p.max_iters = step_limit(p);
     if ((rc = grow(c, c->d_rec, c->rec_bytes, (size_t)(photon_end - photon_begin) * sizeof(PhotonAdj), c->stream)))
@@ -1224,6 +1232,7 @@ int lt_batch_step(void *ctx, uint64_t seed_fwd, uint64_t seed_adj, double *loss_
     c->stats.grid_blocks = bl.grid_f;
     c->stats.block_threads = bl.threads_f;
     c->stats.staged_nodes = bl.fwd.n_staged;
+    c->stats.staged_triangles = bl.fwd.n_tris_staged;
     c->seg_single = false;
     return LT_OK;
     LT_CATCH(ctx)
@@ -1336,6 +1345,17 @@ int lt_set_launch(void *ctx, int32_t threads_per_block, int32_t blocks_per_sm, i
     if (threads_per_block >= 0) c->threads = threads_per_block;
     if (blocks_per_sm >= 0) c->blocks_per_sm = blocks_per_sm;
     if (smem_node_bytes >= 0) c->smem_node_bytes = smem_node_bytes;
+    batch_drop_graph(c);     // a captured batch step holds the old launch shape
+    return LT_OK;
+    LT_CATCH(ctx)
+}
+
+int lt_set_tri_staging(void *ctx, int32_t max_bytes) {
+    LT_TRY
+    Ctx *c = static_cast<Ctx *>(ctx);
+    if (!c) return LT_ERR_ARG;
+    if (max_bytes < 0 || max_bytes > 220 * 1024) return fail(c, LT_ERR_ARG, "max_bytes must be in [0, 220 KiB]");
+    c->smem_tri_bytes = max_bytes;
     batch_drop_graph(c);     // a captured batch step holds the old launch shape
     return LT_OK;
     LT_CATCH(ctx)

@@ -115,6 +115,7 @@ struct TraceParams {
     const int32_t *parent;
     int32_t n_nodes;
     int32_t n_staged;           // nodes copied to shared memory by every block
+    int32_t n_tris_staged;      // triangles copied there after the nodes (0: none; only with n_staged > 0)
     int32_t depth;              // levels of wide nodes (1..kMaxDepth)
     const Tri *tris;
     const TriHit *hits;
@@ -192,7 +193,8 @@ cudaError_t launch_weight_range(const float *w, int64_t n, uint32_t *wmax, cudaS
 cudaError_t launch_grad_photons(const TraceParams &p, cudaStream_t s);
 constexpr uint64_t kGradPhotonsPerThread = 64;
 int trace_kernel_max_threads(bool staged);   // block bound of the staged / L1-node kernels
-cudaError_t trace_occupancy(bool adjoint, bool staged, int depth, int block, size_t smem, int *blocks_per_sm);
+cudaError_t trace_occupancy(bool adjoint, bool staged, bool tris, int depth, int block, size_t smem,
+                            int *blocks_per_sm);
 
 // Wide-BVH builder (lt_bvh.cpp).
 struct BvhBuild {

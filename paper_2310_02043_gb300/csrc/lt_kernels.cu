@@ -129,15 +129,10 @@ struct TriTest {
     float t, U, V, W, det;
 };
 
-__device__ __forceinline__ bool tri_intersect(const Ray &r, const float4 a, const float4 b, const float4 c,
-                                              TriTest &out) {
-    const float Ax0 = __fsub_rn(a.x, r.ox), Ay0 = __fsub_rn(a.y, r.oy), Az0 = __fsub_rn(a.z, r.oz);
-    const float Bx0 = __fsub_rn(b.x, r.ox), By0 = __fsub_rn(b.y, r.oy), Bz0 = __fsub_rn(b.z, r.oz);
-    const float Cx0 = __fsub_rn(c.x, r.ox), Cy0 = __fsub_rn(c.y, r.oy), Cz0 = __fsub_rn(c.z, r.oz);
-    const int kx = r.axes & 3, ky = (r.axes >> 2) & 3, kz = r.axes >> 4;
-    const float Akx = sel3(Ax0, Ay0, Az0, kx), Aky = sel3(Ax0, Ay0, Az0, ky), Akz = sel3(Ax0, Ay0, Az0, kz);
-    const float Bkx = sel3(Bx0, By0, Bz0, kx), Bky = sel3(Bx0, By0, Bz0, ky), Bkz = sel3(Bx0, By0, Bz0, kz);
-    const float Ckx = sel3(Cx0, Cy0, Cz0, kx), Cky = sel3(Cx0, Cy0, Cz0, ky), Ckz = sel3(Cx0, Cy0, Cz0, kz);
+// The test proper, on the vertices relative to the ray origin with their
+// coordinates already in the ray's shear order (kx, ky, kz).
+__device__ __forceinline__ bool tri_sheared(const Ray &r, float Akx, float Aky, float Akz, float Bkx, float Bky,
+                                            float Bkz, float Ckx, float Cky, float Ckz, TriTest &out) {
     const float Ax = __fsub_rn(Akx, __fmul_rn(r.Sx, Akz)), Ay = __fsub_rn(Aky, __fmul_rn(r.Sy, Akz));
     const float Bx = __fsub_rn(Bkx, __fmul_rn(r.Sx, Bkz)), By = __fsub_rn(Bky, __fmul_rn(r.Sy, Bkz));
     const float Cx = __fsub_rn(Ckx, __fmul_rn(r.Sx, Ckz)), Cy = __fsub_rn(Cky, __fmul_rn(r.Sy, Ckz));
@@ -159,6 +154,17 @@ __device__ __forceinline__ bool tri_intersect(const Ray &r, const float4 a, cons
     out.t = __fdiv_rn(T, det);
     out.U = U; out.V = V; out.W = W; out.det = det;
     return true;
+}
+
+__device__ __forceinline__ bool tri_intersect(const Ray &r, const float4 a, const float4 b, const float4 c,
+                                              TriTest &out) {
+    const float Ax0 = __fsub_rn(a.x, r.ox), Ay0 = __fsub_rn(a.y, r.oy), Az0 = __fsub_rn(a.z, r.oz);
+    const float Bx0 = __fsub_rn(b.x, r.ox), By0 = __fsub_rn(b.y, r.oy), Bz0 = __fsub_rn(b.z, r.oz);
+    const float Cx0 = __fsub_rn(c.x, r.ox), Cy0 = __fsub_rn(c.y, r.oy), Cz0 = __fsub_rn(c.z, r.oz);
+    const int kx = r.axes & 3, ky = (r.axes >> 2) & 3, kz = r.axes >> 4;
+    return tri_sheared(r, sel3(Ax0, Ay0, Az0, kx), sel3(Ax0, Ay0, Az0, ky), sel3(Ax0, Ay0, Az0, kz),
+                       sel3(Bx0, By0, Bz0, kx), sel3(Bx0, By0, Bz0, ky), sel3(Bx0, By0, Bz0, kz),
+                       sel3(Cx0, Cy0, Cz0, kx), sel3(Cx0, Cy0, Cz0, ky), sel3(Cx0, Cy0, Cz0, kz), out);
 }
 
 // ---------------------------------------------------------------------------
@@ -242,6 +248,12 @@ __device__ __forceinline__ void trav_init(Trav<kDeep> &s, Hit &h) {
 // path.
 __device__ __forceinline__ const int32_t *staged_parent(const TraceParams &P, const float4 *smem) {
     return reinterpret_cast<const int32_t *>(smem + P.n_staged * kNodeVec);
+}
+
+// Triangles staged after the nodes and their parent links (three 16-byte
+// vectors each, leaf order), when the launch stages them too.
+__device__ __forceinline__ const float4 *staged_tris(const TraceParams &P, const float4 *smem) {
+    return smem + P.n_staged * kNodeVec + (P.n_staged + 3) / 4;
 }
 
 template <bool kSmem>
@@ -375,7 +387,7 @@ __device__ __forceinline__ void node_step(const TraceParams &P, const float4 *sm
 
 // Test the triangles of one pending leaf child. Ties in t go to the lower
 // uploaded triangle index.
-template <bool kCount, bool kSmem, bool kDeep>
+template <bool kCount, bool kSmem, bool kTriSmem, bool kDeep>
 __device__ __forceinline__ void leaf_step(const TraceParams &P, const float4 *smem, const Ray &r, Trav<kDeep> &s, Hit &h,
                                           int32_t skip_tile, Work &work) {
     const int k = __ffs(s.leaves) - 1;
@@ -383,6 +395,26 @@ __device__ __forceinline__ void leaf_step(const TraceParams &P, const float4 *sm
     const int32_t code = -1 - child_word<kSmem>(P, smem, s.leaf_node, k);
     if (kSmem && s.leaves == 0 && s.leaves2 != 0) { s.leaf_node = s.leaf_node2; s.leaves = s.leaves2; s.leaves2 = 0; }
     const int32_t first = code >> 2, count = (code & 3) + 1;
+    if (kTriSmem) {
+        // staged triangles: each vertex coordinate is loaded in the ray's
+        // shear order by its own address, so no selects are needed
+        const int kx = r.axes & 3, ky = (r.axes >> 2) & 3, kz = r.axes >> 4;
+        const float okx = sel3(r.ox, r.oy, r.oz, kx), oky = sel3(r.ox, r.oy, r.oz, ky), okz = sel3(r.ox, r.oy, r.oz, kz);
+        for (int32_t i = first; i < first + count; ++i) {
+            const float *t = reinterpret_cast<const float *>(staged_tris(P, smem) + 3 * i);
+            if (__float_as_int(t[7]) == skip_tile) continue;
+            if (kCount) work.tris += 1;
+            const float *tx = t + kx, *ty = t + ky, *tz = t + kz;
+            TriTest tt;
+            if (!tri_sheared(r, __fsub_rn(tx[0], okx), __fsub_rn(ty[0], oky), __fsub_rn(tz[0], okz),
+                             __fsub_rn(tx[4], okx), __fsub_rn(ty[4], oky), __fsub_rn(tz[4], okz),
+                             __fsub_rn(tx[8], okx), __fsub_rn(ty[8], oky), __fsub_rn(tz[8], okz), tt))
+                continue;
+            const int32_t prim = __float_as_int(t[3]);
+            if (tt.t < h.t || (tt.t == h.t && prim < h.prim)) take_hit(h, i, prim, tt);
+        }
+        return;
+    }
     for (int32_t i = first; i < first + count; ++i) {
         const float4 *tp = reinterpret_cast<const float4 *>(P.tris + i);
         const float4 a = __ldg(tp), b = __ldg(tp + 1), c = __ldg(tp + 2);
@@ -403,7 +435,7 @@ __device__ Hit closest_hit(const TraceParams &P, const float4 *smem, const Ray &
     Work work;
     trav_init(s, h);
     while (true) {
-        if (s.leaves) leaf_step<false, false, true>(P, smem, r, s, h, skip_tile, work);
+        if (s.leaves) leaf_step<false, false, false, true>(P, smem, r, s, h, skip_tile, work);
         else if (s.node >= 0) node_step<false, false, true>(P, smem, r, s, h, work);
         else return h;
     }
@@ -721,13 +753,20 @@ __device__ __forceinline__ uint64_t thread_end(const TraceParams &P) {
     return P.photon_begin + min((thread_index() + 1) * P.chunk, P.photon_end - P.photon_begin);
 }
 
-// Every node and its parent link into shared memory (the caller syncs).
+// Every node and its parent link into shared memory, then (kTriSmem) every
+// triangle; the caller syncs.
+template <bool kTriSmem>
 __device__ __forceinline__ void stage_nodes(const TraceParams &P, float4 *smem) {
     const int n = P.n_staged * kNodeVec;
     const float4 *src = reinterpret_cast<const float4 *>(P.nodes);
     for (int i = threadIdx.x; i < n; i += blockDim.x) smem[i] = __ldg(src + i);
     int32_t *parent = reinterpret_cast<int32_t *>(smem + n);
     for (int i = threadIdx.x; i < P.n_staged; i += blockDim.x) parent[i] = __ldg(P.parent + i);
+    if (kTriSmem) {
+        float4 *dst = const_cast<float4 *>(staged_tris(P, smem));
+        const float4 *tsrc = reinterpret_cast<const float4 *>(P.tris);
+        for (int i = threadIdx.x; i < 3 * P.n_tris_staged; i += blockDim.x) dst[i] = __ldg(tsrc + i);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -738,12 +777,13 @@ __device__ __forceinline__ void stage_nodes(const TraceParams &P, float4 *smem) 
 // iteration the warp votes and runs the kind of step most of its lanes are
 // waiting for, so lanes never idle until a neighbour's path ends.
 // ---------------------------------------------------------------------------
-template <bool kAdjoint, bool kCount, bool kSmem, bool kDeep>
+template <bool kAdjoint, bool kCount, bool kSmem, bool kTriSmem, bool kDeep>
 __global__ void __launch_bounds__(kSmem ? kThreadsStaged : kThreadsL1, kTraceMinBlocks)
     trace_kernel(const TraceParams P) {
+    static_assert(kSmem || !kTriSmem, "triangles are staged only with the nodes");
     extern __shared__ float4 smem[];
     fill_order_table();
-    if (kSmem) stage_nodes(P, smem);
+    if (kSmem) stage_nodes<kTriSmem>(P, smem);
     __syncthreads();
     // The thread's photons are [begin + tid chunk, begin + (tid + 1) chunk)
     // clipped to the range; the end and the first photon's light are
@@ -811,7 +851,7 @@ __global__ void __launch_bounds__(kSmem ? kThreadsStaged : kThreadsL1, kTraceMin
         if (kind == 0) {
             if (can_node) node_step<kCount, kSmem, kDeep>(P, smem, r, s, h, work);
         } else if (kind == 1) {
-            if (can_leaf) leaf_step<kCount, kSmem, kDeep>(P, smem, r, s, h, skip, work);
+            if (can_leaf) leaf_step<kCount, kSmem, kTriSmem, kDeep>(P, smem, r, s, h, skip, work);
         } else if (fin) {
             // Finish the segment (one traced ray, hit or miss), then start the
             // next ray: a bounce from the hit or the next photon's emission.
@@ -834,10 +874,10 @@ __global__ void __launch_bounds__(kSmem ? kThreadsStaged : kThreadsL1, kTraceMin
                     g += __ldg(P.w + tb + texel) * beta;                                          // Eq. 12
                 }
                 if (seg < P.max_hits) {
-                    const float rho = albedo_of(P, h.tri);
+                    const float rho = kTriSmem ? staged_tris(P, smem)[3 * h.tri + 2].w : albedo_of(P, h.tri);
                     phi *= rho;                                                                 // Eq. 7
                     beta *= rho;
-                    skip = tile_of(P, h.tri);
+                    skip = kTriSmem ? __float_as_int(staged_tris(P, smem)[3 * h.tri + 1].w) : tile_of(P, h.tri);
                     bounce = true;
                 }
             }
@@ -1151,26 +1191,33 @@ using TraceFn = void (*)(TraceParams);
 int trace_kernel_max_threads(bool staged) { return staged ? kThreadsStaged : kThreadsL1; }
 
 // The kernel instantiation for a launch: all nodes in shared memory when the
-// launch stages the whole BVH, otherwise none; one word of pending masks
-// when the tree has at most kShallowDepth levels, otherwise two.
+// launch stages the whole BVH, otherwise none, and the triangles too when
+// the launch stages them; one word of pending masks when the tree has at
+// most kShallowDepth levels, otherwise two.
+template <bool kAdjoint, bool kCount, bool kDeep>
+TraceFn trace_fn_depth(bool staged, bool tris) {
+    if (!staged) return trace_kernel<kAdjoint, kCount, false, false, kDeep>;
+    return tris ? trace_kernel<kAdjoint, kCount, true, true, kDeep> : trace_kernel<kAdjoint, kCount, true, false, kDeep>;
+}
+
 template <bool kAdjoint, bool kCount>
-TraceFn trace_fn(bool staged, bool deep) {
-    if (deep) return staged ? trace_kernel<kAdjoint, kCount, true, true> : trace_kernel<kAdjoint, kCount, false, true>;
-    return staged ? trace_kernel<kAdjoint, kCount, true, false> : trace_kernel<kAdjoint, kCount, false, false>;
+TraceFn trace_fn(bool staged, bool tris, bool deep) {
+    return deep ? trace_fn_depth<kAdjoint, kCount, true>(staged, tris) : trace_fn_depth<kAdjoint, kCount, false>(staged, tris);
 }
 
 template <bool kAdjoint, bool kCount>
 cudaError_t launch_trace(const TraceParams &p, int grid, int block, size_t smem, cudaStream_t s) {
-    const TraceFn fn = trace_fn<kAdjoint, kCount>(p.n_staged > 0, p.depth > kShallowDepth);
+    const TraceFn fn = trace_fn<kAdjoint, kCount>(p.n_staged > 0, p.n_tris_staged > 0, p.depth > kShallowDepth);
     cudaError_t e = allow_smem(fn, smem);
     if (e != cudaSuccess) return e;
     fn<<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
 }
 
-cudaError_t trace_occupancy(bool adjoint, bool staged, int depth, int block, size_t smem, int *blocks_per_sm) {
+cudaError_t trace_occupancy(bool adjoint, bool staged, bool tris, int depth, int block, size_t smem,
+                            int *blocks_per_sm) {
     const bool deep = depth > kShallowDepth;
-    const TraceFn fn = adjoint ? trace_fn<true, false>(staged, deep) : trace_fn<false, false>(staged, deep);
+    const TraceFn fn = adjoint ? trace_fn<true, false>(staged, tris, deep) : trace_fn<false, false>(staged, tris, deep);
     cudaError_t e = allow_smem(fn, smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem);
@@ -1191,6 +1238,7 @@ cudaError_t launch_adjoint(const TraceParams &p, int grid, int block, size_t sme
 cudaError_t launch_paths(const TraceParams &p, uint64_t count, cudaStream_t s) {
     TraceParams q = p;
     q.n_staged = 0;
+    q.n_tris_staged = 0;
     const unsigned blocks = (unsigned)((count + 127) / 128);
     paths_kernel<<<blocks, 128, 0, s>>>(q, count);
     return cudaGetLastError();

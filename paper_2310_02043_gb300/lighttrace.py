@@ -31,7 +31,7 @@ EXPORTED = ("lt_version", "lt_create", "lt_destroy", "lt_set_stream", "lt_last_e
             "lt_get_stats", "lt_set_launch", "lt_count_work", "lt_loss_static", "lt_set_design", "lt_batch_setup",
             "lt_batch_set_lights", "lt_batch_step", "lt_batch_texel_sums", "lt_batch_irradiance",
             "lt_batch_stream", "lt_texel_centres", "lt_build_bvh", "lt_set_step_limit",
-            "lt_probe_l2_read", "lt_gradient_fixed")
+            "lt_probe_l2_read", "lt_gradient_fixed", "lt_set_tri_staging")
 
 
 class LtError(RuntimeError):
@@ -52,7 +52,7 @@ class lt_stats(ctypes.Structure):
                 ("n_texels", ctypes.c_int64), ("n_triangles", ctypes.c_int32), ("n_nodes", ctypes.c_int32),
                 ("bvh_depth", ctypes.c_int32), ("staged_nodes", ctypes.c_int32),
                 ("fixed_point_scale", ctypes.c_double), ("grid_blocks", ctypes.c_int32),
-                ("block_threads", ctypes.c_int32)]
+                ("block_threads", ctypes.c_int32), ("staged_triangles", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class lt_bvh_node(ctypes.Structure):
@@ -105,6 +105,7 @@ def _declare(lib):
         "lt_debug_paths": [vp, u64, u64, i32, u64, u64, vp, vp, vp],
         "lt_get_stats": [vp, ctypes.POINTER(lt_stats)],
         "lt_set_launch": [vp, i32, i32, i32],
+        "lt_set_tri_staging": [vp, i32],
         "lt_count_work": [vp, u64, u64, i32, u64, u64, vp],
         "lt_loss_static": [ci, vp, vp, ctypes.c_double, vp, vp, vp, i64, vp, vp, vp],
         "lt_set_design": [vp, ctypes.c_uint32],
@@ -436,6 +437,11 @@ class Tracer:
         bound, 1024 staged / 768 through L1 / as many blocks as fit / no
         staged nodes; negative: keep)."""
         self._check(self.lib.lt_set_launch(self.h, threads_per_block, blocks_per_sm, smem_node_bytes))
+
+    def set_tri_staging(self, max_bytes: int):
+        """Shared-memory budget under which the triangles are staged with
+        the nodes (0: never; default 200 KiB)."""
+        self._check(self.lib.lt_set_tri_staging(self.h, max_bytes))
 
     def set_step_limit(self, max_steps: int = 0):
         """Node visits per ray before the tracing kernels give up on it (0:

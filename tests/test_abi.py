@@ -3,6 +3,7 @@ declares (no compute calls: this runs without a GPU)."""
 import ctypes
 import os
 import re
+import subprocess
 
 import pytest
 
@@ -46,15 +47,38 @@ def test_every_header_is_checked():
 
 
 def test_version_and_argument_checks(lib):
-    assert lib.lt_version() == 1
+    assert lib.lt_version() == 2
     assert lib.lt_create(None, 0, None) == lighttrace.LT_ERR_ARG
     assert lib.lt_destroy(None) == lighttrace.LT_OK
     assert lib.lt_last_error(None) == b"null context"
 
 
-def test_struct_layouts_match_the_header():
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structures have the size and field offsets the C
+    compiler gives the header's structs."""
+    structs = {"lt_light": lighttrace.lt_light, "lt_stats": lighttrace.lt_stats, "lt_bvh_node": lighttrace.lt_bvh_node}
+    lines = ['#include "lt.h"', "#include <stdio.h>", "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    seen = 0
+    for line in out:
+        if not line:
+            continue
+        name, key, value = line.split()
+        cls = structs[name]
+        want = ctypes.sizeof(cls) if key == "size" else getattr(cls, key).offset
+        assert int(value) == want, (name, key, value, want)
+        seen += 1
+    assert seen == sum(len(c._fields_) + 1 for c in structs.values())
     assert ctypes.sizeof(lighttrace.lt_light) == 36
-    assert ctypes.sizeof(lighttrace.lt_stats) == 8 * 5 + 4 * 4 + 8 + 4 * 2
 
 
 def test_every_declaration_is_documented():

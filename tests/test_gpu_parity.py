@@ -168,16 +168,25 @@ def test_fixed_point_sums_identical_across_launch_shapes(tr):
     tr.upload_scene(sc)
     tr.set_lights(L)
     ref = None
-    for threads, bps, smem in [(256, 0, 48 * 1024), (128, 0, 224), (64, 1, 16 * 1024), (256, 2, 100 * 1024),
-                               (32, 3, 224 * 7)]:
+    kinds = set()
+    # nodes through L1 (the office BVH takes 55 KiB), nodes staged, nodes and
+    # triangles staged
+    for threads, bps, smem, tris in [(256, 0, 48 * 1024, 0), (128, 0, 224, 0), (64, 1, 16 * 1024, 0),
+                                     (256, 2, 100 * 1024, 0), (256, 2, 100 * 1024, 200 * 1024),
+                                     (0, 0, 72 * 1024, 200 * 1024), (0, 0, 72 * 1024, 0), (32, 3, 224 * 7, 0)]:
         tr.set_launch(threads, bps, smem)
+        tr.set_tri_staging(tris)
         tr.trace_forward(5, 1 << 16, 5)
+        st = tr.stats()
+        kinds.add((st["staged_nodes"] > 0, st["staged_triangles"] > 0))
         q = tr.texel_sums()
         if ref is None:
             ref = q
             assert q.sum() > 0
         else:
-            assert np.array_equal(q, ref), (threads, bps, smem)
+            assert np.array_equal(q, ref), (threads, bps, smem, tris)
+    assert kinds == {(False, False), (True, False), (True, True)}
+    tr.set_tri_staging(200 * 1024)
     tr.set_launch(256, 0, 48 * 1024)
     tr.trace_forward(5, 1 << 16, 5)
     assert np.array_equal(tr.texel_sums(), ref)
@@ -194,15 +203,18 @@ def test_gradients_identical_across_launch_shapes(tr):
     w = scenes.random_weights(sc.n_texels, seed=8)
     tr.set_adjoint_weights(w)
     ref = None
-    for threads, bps, smem in [(0, 0, 72 * 1024), (256, 0, 48 * 1024), (128, 0, 224), (64, 1, 16 * 1024),
-                               (256, 2, 100 * 1024), (32, 3, 224 * 7)]:
+    for threads, bps, smem, tris in [(0, 0, 72 * 1024, 200 * 1024), (0, 0, 72 * 1024, 0), (256, 0, 48 * 1024, 0),
+                                     (128, 0, 224, 0), (64, 1, 16 * 1024, 0), (256, 2, 100 * 1024, 200 * 1024),
+                                     (32, 3, 224 * 7, 0)]:
         tr.set_launch(threads, bps, smem)
+        tr.set_tri_staging(tris)
         g = tr.trace_adjoint(7, 1 << 16, 5)
         if ref is None:
             ref = g
             assert np.all(np.abs(g) > 0)
         else:
-            assert np.array_equal(g, ref), (threads, bps, smem)
+            assert np.array_equal(g, ref), (threads, bps, smem, tris)
+    tr.set_tri_staging(200 * 1024)
     f, G = tr.gradient_fixed()
     assert np.array_equal(gradient_from_fixed(f, G), ref)
     sizes = parity.light_sizes(1 << 16, L.shape[0])
@@ -235,6 +247,19 @@ def test_launch_shape_arguments(tr):
     tr.set_launch(0, 0, -1)
     g, t, staged = shape()
     assert t == 1024 and g % sms == 0 and staged > 0
+    # the triangles follow the staged nodes while both fit the budget
+    n_tri = tr.stats()["n_triangles"]
+    assert tr.stats()["staged_triangles"] == n_tri
+    need = staged * 240 + (staged + 3) // 4 * 16 + n_tri * 48
+    tr.set_tri_staging(need - 16)
+    assert shape() == (g, t, staged) and tr.stats()["staged_triangles"] == 0
+    tr.set_tri_staging(need)
+    assert shape() == (g, t, staged) and tr.stats()["staged_triangles"] == n_tri
+    with pytest.raises(RuntimeError, match="max_bytes"):
+        tr.set_tri_staging(221 * 1024)
+    with pytest.raises(RuntimeError, match="max_bytes"):
+        tr.set_tri_staging(-1)
+    tr.set_tri_staging(200 * 1024)
     tr.set_launch(0, 0, 0)
     g, t, staged = shape()
     assert t == 768 and g % sms == 0 and staged == 0
