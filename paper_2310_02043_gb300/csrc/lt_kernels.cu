@@ -156,17 +156,6 @@ __device__ __forceinline__ bool tri_sheared(const Ray &r, float Akx, float Aky, 
     return true;
 }
 
-__device__ __forceinline__ bool tri_intersect(const Ray &r, const float4 a, const float4 b, const float4 c,
-                                              TriTest &out) {
-    const float Ax0 = __fsub_rn(a.x, r.ox), Ay0 = __fsub_rn(a.y, r.oy), Az0 = __fsub_rn(a.z, r.oz);
-    const float Bx0 = __fsub_rn(b.x, r.ox), By0 = __fsub_rn(b.y, r.oy), Bz0 = __fsub_rn(b.z, r.oz);
-    const float Cx0 = __fsub_rn(c.x, r.ox), Cy0 = __fsub_rn(c.y, r.oy), Cz0 = __fsub_rn(c.z, r.oz);
-    const int kx = r.axes & 3, ky = (r.axes >> 2) & 3, kz = r.axes >> 4;
-    return tri_sheared(r, sel3(Ax0, Ay0, Az0, kx), sel3(Ax0, Ay0, Az0, ky), sel3(Ax0, Ay0, Az0, kz),
-                       sel3(Bx0, By0, Bz0, kx), sel3(Bx0, By0, Bz0, ky), sel3(Bx0, By0, Bz0, kz),
-                       sel3(Cx0, Cy0, Cz0, kx), sel3(Cx0, Cy0, Cz0, ky), sel3(Cx0, Cy0, Cz0, kz), out);
-}
-
 // ---------------------------------------------------------------------------
 // Wide-BVH traversal without a stack. The pending children of every level
 // are an 8-bit mask packed into 64-bit registers (in the ray's visiting
@@ -395,9 +384,11 @@ __device__ __forceinline__ void leaf_step(const TraceParams &P, const float4 *sm
     const int32_t code = -1 - child_word<kSmem>(P, smem, s.leaf_node, k);
     if (kSmem && s.leaves == 0 && s.leaves2 != 0) { s.leaf_node = s.leaf_node2; s.leaves = s.leaves2; s.leaves2 = 0; }
     const int32_t first = code >> 2, count = (code & 3) + 1;
+    // Each vertex coordinate is loaded by its own address in the ray's shear
+    // order (kx, ky, kz), so the watertight test needs no selects to permute
+    // the axes (office -6 % with the triangles staged, building -2 % through
+    // L1, against three 16-byte loads per triangle and selects).
     if (kTriSmem) {
-        // staged triangles: each vertex coordinate is loaded in the ray's
-        // shear order by its own address, so no selects are needed
         const int kx = r.axes & 3, ky = (r.axes >> 2) & 3, kz = r.axes >> 4;
         const float okx = sel3(r.ox, r.oy, r.oz, kx), oky = sel3(r.ox, r.oy, r.oz, ky), okz = sel3(r.ox, r.oy, r.oz, kz);
         for (int32_t i = first; i < first + count; ++i) {
@@ -415,14 +406,19 @@ __device__ __forceinline__ void leaf_step(const TraceParams &P, const float4 *sm
         }
         return;
     }
+    const int kx = r.axes & 3, ky = (r.axes >> 2) & 3, kz = r.axes >> 4;
+    const float okx = sel3(r.ox, r.oy, r.oz, kx), oky = sel3(r.ox, r.oy, r.oz, ky), okz = sel3(r.ox, r.oy, r.oz, kz);
     for (int32_t i = first; i < first + count; ++i) {
-        const float4 *tp = reinterpret_cast<const float4 *>(P.tris + i);
-        const float4 a = __ldg(tp), b = __ldg(tp + 1), c = __ldg(tp + 2);
-        if (__float_as_int(b.w) == skip_tile) continue;
+        const float *t = reinterpret_cast<const float *>(P.tris + i);
+        if (__float_as_int(__ldg(t + 7)) == skip_tile) continue;
         if (kCount) work.tris += 1;
+        const float *tx = t + kx, *ty = t + ky, *tz = t + kz;
         TriTest tt;
-        if (!tri_intersect(r, a, b, c, tt)) continue;
-        const int32_t prim = __float_as_int(a.w);
+        if (!tri_sheared(r, __fsub_rn(__ldg(tx), okx), __fsub_rn(__ldg(ty), oky), __fsub_rn(__ldg(tz), okz),
+                         __fsub_rn(__ldg(tx + 4), okx), __fsub_rn(__ldg(ty + 4), oky), __fsub_rn(__ldg(tz + 4), okz),
+                         __fsub_rn(__ldg(tx + 8), okx), __fsub_rn(__ldg(ty + 8), oky), __fsub_rn(__ldg(tz + 8), okz), tt))
+            continue;
+        const int32_t prim = __float_as_int(__ldg(t + 3));
         if (tt.t < h.t || (tt.t == h.t && prim < h.prim)) take_hit(h, i, prim, tt);
     }
 }
