@@ -291,11 +291,13 @@ __device__ __forceinline__ uint32_t test4(const TraceParams &P, const float4 *sm
         if (kSmem) {
             tn = max3f(fmaf(a_nx[k], r.ix, qx), fmaf(a_ny[k], r.iy, qy), fmaxf(fmaf(a_nz[k], r.iz, qz), 0.0f));
             tf = min3f(fmaf(a_fx[k], r.ix, qx), fmaf(a_fy[k], r.iy, qy), fmaf(a_fz[k], r.iz, qz)) * kFarScale;
+            tf = fminf(tf, tbest);
         } else {   // nodes through L1: the two-rounding form keeps fewer values live
             tn = max3f((a_nx[k] - r.ox) * r.ix, (a_ny[k] - r.oy) * r.iy, fmaxf((a_nz[k] - r.oz) * r.iz, 0.0f));
             tf = min3f((a_fx[k] - r.ox) * r.ix, (a_fy[k] - r.oy) * r.iy, (a_fz[k] - r.oz) * r.iz) * kFarScale;
+            tf = fminf(tf, tbest);
         }
-        hit |= (tn <= tf && tn <= tbest ? 1u : 0u) << k;
+        hit |= (tn <= tf ? 1u : 0u) << k;     // tn <= exit and tn <= tbest in one comparison
     }
     return hit;
 }
