@@ -394,8 +394,10 @@ LT_API int lt_set_launch(void *ctx, int32_t threads_per_block, int32_t blocks_pe
 
 /* Shared-memory budget for staging the triangles with the nodes: when the
  * whole BVH is staged (lt_set_launch) and the nodes, their parent links and
- * all triangles (48 bytes each) take at most max_bytes, every block copies
- * the triangles to shared memory too, and the leaf tests read them there.
+ * all triangles (48 bytes each) take at most max_bytes, and the extra
+ * shared memory leaves as many blocks resident per SM as without it (the
+ * requested blocks_per_sm, else as many as fit), every block copies the
+ * triangles to shared memory too, and the leaf tests read them there.
  * max_bytes in [0, 220 KiB]; 0 = never; default 200 KiB. Results do not
  * depend on it (the same tests on the same values). Takes effect at the next
  * trace; a captured batch graph is rebuilt. */

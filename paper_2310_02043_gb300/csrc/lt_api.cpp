@@ -346,22 +346,32 @@ int upload_lights(Ctx *c, uint64_t n_photons) {
 // Launch shape of a tracing kernel. The whole BVH is staged in shared memory
 // when it fits the budget, otherwise no node is (nodes then come through L1);
 // with the nodes staged, the triangles follow them when nodes and triangles
-// together fit the triangle budget. Sets p->n_staged and p->n_tris_staged.
-// The block is the requested size, else the bound of the kernel chosen.
+// together fit the triangle budget and the extra shared memory costs no
+// resident block (the requested blocks per SM, else as many as fit without
+// the triangles). Sets p->n_staged and p->n_tris_staged. The block is the
+// requested size, else the bound of the kernel chosen.
 int launch_shape(Ctx *c, bool adjoint, int *grid, int *threads, size_t *smem, TraceParams *p) {
     const bool staged = (int64_t)c->n_nodes * (int64_t)sizeof(Node) <= (int64_t)c->smem_node_bytes;
     p->n_staged = staged ? c->n_nodes : 0;
     // staged nodes, then their parent links (int32, rounded up to 16 bytes)
     *smem = (size_t)p->n_staged * sizeof(Node) + ((size_t)p->n_staged + 3) / 4 * 16;
-    const size_t tri_bytes = (size_t)c->n_tri * sizeof(Tri);
-    const bool tris = staged && *smem + tri_bytes <= (size_t)c->smem_tri_bytes;
-    p->n_tris_staged = tris ? c->n_tri : 0;
-    if (tris) *smem += tri_bytes;
     const int bound = trace_kernel_max_threads(staged);
     *threads = c->threads > 0 ? c->threads : bound;
     if (*threads > bound)
         return fail(c, LT_ERR_ARG, "threads_per_block " + std::to_string(*threads) + " exceeds the bound " +
                                        std::to_string(bound) + " of the kernel for this BVH");
+    const size_t tri_bytes = (size_t)c->n_tri * sizeof(Tri);
+    bool tris = staged && *smem + tri_bytes <= (size_t)c->smem_tri_bytes;
+    if (tris) {
+        int with = 0, without = 0;
+        cudaError_t e = trace_occupancy(adjoint, true, true, c->depth, *threads, *smem + tri_bytes, &with);
+        if (e == cudaSuccess) e = trace_occupancy(adjoint, true, false, c->depth, *threads, *smem, &without);
+        if (e != cudaSuccess) return cuda_fail(c, e, "occupancy query");
+        const int want = c->blocks_per_sm > 0 ? std::min(c->blocks_per_sm, without) : without;
+        tris = with >= std::max(want, 1);
+    }
+    p->n_tris_staged = tris ? c->n_tri : 0;
+    if (tris) *smem += tri_bytes;
     int bps = c->blocks_per_sm;
     if (bps <= 0) {
         cudaError_t e = trace_occupancy(adjoint, staged, tris, c->depth, *threads, *smem, &bps);

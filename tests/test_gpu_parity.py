@@ -255,6 +255,14 @@ def test_launch_shape_arguments(tr):
     assert shape() == (g, t, staged) and tr.stats()["staged_triangles"] == 0
     tr.set_tri_staging(need)
     assert shape() == (g, t, staged) and tr.stats()["staged_triangles"] == n_tri
+    # smaller blocks: the triangles would cost resident blocks, so only the
+    # nodes are staged
+    tr.set_launch(256, 0, -1)
+    g2, t2, staged2 = shape()
+    assert t2 == 256 and staged2 == staged and g2 >= 2 * sms and tr.stats()["staged_triangles"] == 0
+    tr.set_launch(256, 1, -1)
+    assert shape() == (sms, 256, staged) and tr.stats()["staged_triangles"] == n_tri
+    tr.set_launch(0, 0, -1)
     with pytest.raises(RuntimeError, match="max_bytes"):
         tr.set_tri_staging(221 * 1024)
     with pytest.raises(RuntimeError, match="max_bytes"):
