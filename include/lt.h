@@ -394,7 +394,7 @@ LT_API int lt_set_launch(void *ctx, int32_t threads_per_block, int32_t blocks_pe
 
 /* Shared-memory budget for staging the triangles with the nodes: when the
  * whole BVH is staged (lt_set_launch) and the nodes, their parent links and
- * all triangles (48 bytes each) take at most max_bytes, and the extra
+ * all triangles (52 bytes each there) take at most max_bytes, and the extra
  * shared memory leaves as many blocks resident per SM as without it (the
  * requested blocks_per_sm, else as many as fit), every block copies the
  * triangles to shared memory too, and the leaf tests read them there.

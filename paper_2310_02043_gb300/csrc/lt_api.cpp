@@ -360,7 +360,7 @@ int launch_shape(Ctx *c, bool adjoint, int *grid, int *threads, size_t *smem, Tr
     if (*threads > bound)
         return fail(c, LT_ERR_ARG, "threads_per_block " + std::to_string(*threads) + " exceeds the bound " +
                                        std::to_string(bound) + " of the kernel for this BVH");
-    const size_t tri_bytes = (size_t)c->n_tri * sizeof(Tri);
+    const size_t tri_bytes = ((size_t)c->n_tri * kStagedTriBytes + 15) / 16 * 16;
     bool tris = staged && *smem + tri_bytes <= (size_t)c->smem_tri_bytes;
     if (tris) {
         int with = 0, without = 0;

@@ -46,6 +46,7 @@ struct alignas(16) Tri {
     float albedo;
 };
 static_assert(sizeof(Tri) == 48, "tri layout");
+constexpr int kStagedTriBytes = 52;   // shared-memory stride of a staged triangle (13 words)
 
 // What a hit needs besides the vertices: chart coordinates and texel range.
 struct alignas(16) TriHit {

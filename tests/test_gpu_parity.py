@@ -250,7 +250,7 @@ def test_launch_shape_arguments(tr):
     # the triangles follow the staged nodes while both fit the budget
     n_tri = tr.stats()["n_triangles"]
     assert tr.stats()["staged_triangles"] == n_tri
-    need = staged * 240 + (staged + 3) // 4 * 16 + n_tri * 48
+    need = staged * 240 + (staged + 3) // 4 * 16 + (n_tri * 52 + 15) // 16 * 16
     tr.set_tri_staging(need - 16)
     assert shape() == (g, t, staged) and tr.stats()["staged_triangles"] == 0
     tr.set_tri_staging(need)
