@@ -180,6 +180,28 @@ typedef struct {
 LT_API int lt_build_bvh(const float *tri_xyz, int32_t n_tri, lt_bvh_node *nodes_out, int32_t nodes_cap,
                         int32_t *order_out, int32_t *n_nodes_out, int32_t *depth_out);
 
+/* Compressed 8-wide node (96 bytes), the form the tracing kernels read when
+ * the BVH is not staged in shared memory (quantised child boxes). Per axis a
+ * (x, y, z): a float origin origin[a] and a step 2^e_a, where byte a of meta
+ * holds e_a + 142; child k's box along a is
+ * [origin[a] + q[a][k] 2^e_a, origin[a] + q[a][8 + k] 2^e_a]. Every box
+ * contains the float node's box widened by 2^-14 of the node's extent
+ * along a (the rounding of the kernel's decode); empty slots hold
+ * q lo = 255, q hi = 0. Byte 3 of meta is the inner mask; child[] is the
+ * float node's. */
+typedef struct {
+    float origin[3];
+    uint32_t meta;
+    uint8_t q[3][16];
+    int32_t child[8];
+} lt_bvh_cnode;
+
+/* Compress n_nodes nodes of lt_build_bvh into out[n_nodes] (host only, the
+ * conversion lt_upload_scene runs). LT_ERR_ARG for null pointers, a
+ * non-positive count, a non-empty slot with a non-finite or inverted box, or
+ * coordinates beyond the exponent range (about 2^110). */
+LT_API int lt_compress_bvh(const lt_bvh_node *nodes, int32_t n_nodes, lt_bvh_cnode *out);
+
 /* Target irradiance E*_t and weights alpha_t of the objective (Eq. 6),
  * [n_texels] floats each; alpha may be NULL (all ones). */
 LT_API int lt_set_target(void *ctx, const float *E_target, const float *alpha, int is_device);

@@ -29,6 +29,7 @@ struct Ctx {
     std::string err;
     // scene
     Node *d_nodes = nullptr;
+    CNode *d_cnodes = nullptr;             // the same nodes compressed (kernels reading nodes through L1)
     int32_t *d_parent = nullptr;
     Tri *d_tris = nullptr;
     TriHit *d_hits = nullptr;
@@ -400,6 +401,7 @@ TraceParams base_params(Ctx *c, uint64_t seed, int32_t max_hits, uint64_t begin,
     TraceParams p;
     std::memset(&p, 0, sizeof(p));
     p.nodes = c->d_nodes;
+    p.cnodes = c->d_cnodes;
     p.parent = c->d_parent;
     p.n_nodes = c->n_nodes;
     p.depth = c->depth;
@@ -580,6 +582,26 @@ int lt_build_bvh(const float *tri_xyz, int32_t n_tri, lt_bvh_node *nodes_out, in
     LT_CATCH(nullptr)
 }
 
+static_assert(sizeof(lt_bvh_cnode) == sizeof(CNode), "lt_bvh_cnode mirrors lt::CNode");
+static_assert(offsetof(lt_bvh_cnode, meta) == offsetof(CNode, meta) && offsetof(lt_bvh_cnode, q) == offsetof(CNode, q) &&
+                  offsetof(lt_bvh_cnode, child) == offsetof(CNode, child),
+              "lt_bvh_cnode field offsets");
+
+int lt_compress_bvh(const lt_bvh_node *nodes, int32_t n_nodes, lt_bvh_cnode *out) {
+    LT_TRY
+    if (!nodes || !out || n_nodes <= 0) return LT_ERR_ARG;
+    const Node *in = reinterpret_cast<const Node *>(nodes);
+    for (int32_t i = 0; i < n_nodes; ++i)
+        for (int k = 0; k < kWide; ++k)
+            if (in[i].child[k] != kEmptyChild &&
+                !(std::isfinite(in[i].lox[k]) && std::isfinite(in[i].hix[k]) && std::isfinite(in[i].loy[k]) &&
+                  std::isfinite(in[i].hiy[k]) && std::isfinite(in[i].loz[k]) && std::isfinite(in[i].hiz[k]) &&
+                  in[i].lox[k] <= in[i].hix[k] && in[i].loy[k] <= in[i].hiy[k] && in[i].loz[k] <= in[i].hiz[k]))
+                return LT_ERR_ARG;
+    return compress_nodes(in, n_nodes, reinterpret_cast<CNode *>(out)) ? LT_OK : LT_ERR_ARG;
+    LT_CATCH(nullptr)
+}
+
 int lt_create(void **ctx_out, int device, void *cuda_stream) {
     LT_TRY
     if (!ctx_out) return LT_ERR_ARG;
@@ -625,7 +647,7 @@ int lt_destroy(void *ctx) {
     if (!c) return LT_OK;
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
-    dfree(c->d_nodes); dfree(c->d_parent); dfree(c->d_tris); dfree(c->d_hits); dfree(c->d_area);
+    dfree(c->d_nodes); dfree(c->d_cnodes); dfree(c->d_parent); dfree(c->d_tris); dfree(c->d_hits); dfree(c->d_area);
     dfree(c->d_target); dfree(c->d_alpha); dfree(c->d_lights); dfree(c->d_q); dfree(c->d_E); dfree(c->d_w);
     dfree(c->d_loss); dfree(c->d_partial); dfree(c->d_grad); dfree(c->d_slots); dfree(c->d_seg);
     dfree(c->d_err); dfree(c->d_gfix); dfree(c->d_gscale); dfree(c->d_wmax); dfree(c->d_gpart); dfree(c->d_rec);
@@ -679,6 +701,9 @@ int lt_upload_scene(void *ctx, const float *tri_xyz, const float *tri_uv, const 
     std::string berr;
     maybe_inject_host_oom();
     if (!build_wide_bvh(tri_xyz, n_tri, &bvh, &berr)) return fail(c, LT_ERR_ARG, berr);
+    std::vector<CNode> cnodes(bvh.nodes.size());
+    if (!compress_nodes(bvh.nodes.data(), (int32_t)bvh.nodes.size(), cnodes.data()))
+        return fail(c, LT_ERR_ARG, "scene extent beyond the compressed nodes' exponent range");
     std::vector<Tri> tris((size_t)n_tri);
     std::vector<TriHit> hits((size_t)n_tri);
     for (int32_t j = 0; j < n_tri; ++j) {
@@ -718,6 +743,7 @@ int lt_upload_scene(void *ctx, const float *tri_xyz, const float *tri_uv, const 
     LT_CUDA(c, cudaStreamSynchronize(c->stream));
     batch_free(c);     // batch buffers are sized by the old texel count
     LT_CUDA(c, dalloc(c->d_nodes, bvh.nodes.size()));
+    LT_CUDA(c, dalloc(c->d_cnodes, cnodes.size()));
     LT_CUDA(c, dalloc(c->d_parent, bvh.parent.size()));
     LT_CUDA(c, dalloc(c->d_tris, (size_t)n_tri));
     LT_CUDA(c, dalloc(c->d_hits, (size_t)n_tri));
@@ -728,6 +754,7 @@ int lt_upload_scene(void *ctx, const float *tri_xyz, const float *tri_uv, const 
     LT_CUDA(c, dalloc(c->d_target, (size_t)T));
     dfree(c->d_alpha);
     LT_CUDA(c, cudaMemcpy(c->d_nodes, bvh.nodes.data(), bvh.nodes.size() * sizeof(Node), cudaMemcpyHostToDevice));
+    LT_CUDA(c, cudaMemcpy(c->d_cnodes, cnodes.data(), cnodes.size() * sizeof(CNode), cudaMemcpyHostToDevice));
     LT_CUDA(c, cudaMemcpy(c->d_parent, bvh.parent.data(), bvh.parent.size() * sizeof(int32_t),
                           cudaMemcpyHostToDevice));
     LT_CUDA(c, cudaMemcpy(c->d_tris, tris.data(), tris.size() * sizeof(Tri), cudaMemcpyHostToDevice));

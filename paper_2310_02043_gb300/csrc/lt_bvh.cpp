@@ -396,4 +396,55 @@ bool build_wide_bvh(const float *xyz, int32_t n_tri, BvhBuild *out, std::string 
     return true;
 }
 
+// Node compression. Per axis the origin p is a float a little below the
+// lowest plane of the node's children and the step 2^e the smallest power of
+// two with 254 steps covering the planes; lo planes round down and hi planes
+// up. The kernel decodes a plane distance as fma(1 + q 2^-15, S, B) with
+// S = 2^(e+15) / d and B = (p - 2^(e+15) - o) / d, each rounded in float,
+// which moves a plane by at most about 2^-24 (6 |coordinate| + 400 extent);
+// the float node's padding covers the first term (8x over), and a margin of
+// 2^-14 of the node's extent on every side covers the second.
+bool compress_nodes(const Node *nodes, int32_t n_nodes, CNode *out) {
+    for (int32_t i = 0; i < n_nodes; ++i) {
+        const Node &nd = nodes[i];
+        CNode &cn = out[i];
+        std::memset(&cn, 0, sizeof(cn));
+        uint32_t meta = (nd.inner_mask & 0xffu) << 24;
+        const float *lo[3] = {nd.lox, nd.loy, nd.loz}, *hi[3] = {nd.hix, nd.hiy, nd.hiz};
+        for (int a = 0; a < 3; ++a) {
+            double mn = INFINITY, mx = -INFINITY;
+            for (int k = 0; k < kWide; ++k) {
+                if (nd.child[k] == kEmptyChild) continue;
+                mn = std::min(mn, (double)lo[a][k]);
+                mx = std::max(mx, (double)hi[a][k]);
+            }
+            if (!(mn <= mx)) mn = mx = 0.0;            // no child (not built): any valid origin
+            const double m = (mx - mn) * 0x1p-14;
+            float p = (float)(mn - m);
+            while ((double)p > mn - m) p = std::nextafter(p, -INFINITY);
+            const double ext = mx + m - (double)p;
+            int e = -126;
+            while (std::ldexp(254.0, e) < ext) ++e;
+            const int biased = e + 15 + 127;
+            if (biased < 1 || biased > 254) return false;
+            cn.p[a] = p;
+            meta |= (uint32_t)biased << (8 * a);
+            const double step = std::ldexp(1.0, e);
+            for (int k = 0; k < kWide; ++k) {
+                int ql = 255, qh = 0;                   // empty slot: an inverted box
+                if (nd.child[k] != kEmptyChild) {
+                    ql = (int)std::floor(((double)lo[a][k] - m - (double)p) / step);
+                    qh = (int)std::ceil(((double)hi[a][k] + m - (double)p) / step);
+                    if (ql < 0 || qh > 254 || ql > qh) return false;
+                }
+                cn.q[a][k] = (uint8_t)ql;
+                cn.q[a][8 + k] = (uint8_t)qh;
+            }
+        }
+        cn.meta = meta;
+        for (int k = 0; k < kWide; ++k) cn.child[k] = nd.child[k];
+    }
+    return true;
+}
+
 }  // namespace lt

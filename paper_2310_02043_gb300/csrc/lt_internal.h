@@ -36,6 +36,24 @@ struct alignas(16) Node {
 static_assert(sizeof(Node) == 240, "node layout");
 constexpr int kNodeVec = (int)(sizeof(Node) / 16);
 
+// Compressed 8-wide node, 96 bytes, read by the kernels whose nodes come
+// through L1 (quantised child boxes after Ylitie, Karras and Laine, HPG
+// 2017). Per axis a: a float origin p[a] and a step 2^e_a; child k's planes
+// are p[a] + q 2^e_a with the 8-bit q in q[a][k] (lo) and q[a][8 + k] (hi),
+// rounded outward from the float node's (padded) planes by a further margin
+// that covers the rounding of the kernel's decode. meta bytes 0-2 hold the
+// biased exponents of 2^(e_a + 15) (so a plane decodes as one byte permute
+// and one fma), byte 3 the inner mask. Empty slots have q lo = 255, q hi = 0,
+// an inverted box. Slots and children as in Node.
+struct alignas(16) CNode {
+    float p[3];
+    uint32_t meta;
+    uint8_t q[3][16];
+    int32_t child[kWide];
+};
+static_assert(sizeof(CNode) == 96, "compressed node layout");
+constexpr int kCNodeVec = (int)(sizeof(CNode) / 16);
+
 // Triangle in leaf order, 48 bytes (three 16-byte loads).
 struct alignas(16) Tri {
     float v0[3];
@@ -112,7 +130,8 @@ static_assert(sizeof(PhotonAdj) == 16, "photon record layout");
 enum : int32_t { kErrSteps = 1, kErrRange = 2, kErrDepth = 4 };
 
 struct TraceParams {
-    const Node *nodes;
+    const Node *nodes;          // float nodes (staged kernels)
+    const CNode *cnodes;        // the same nodes compressed (kernels that read nodes through L1)
     const int32_t *parent;
     int32_t n_nodes;
     int32_t n_staged;           // nodes copied to shared memory by every block
@@ -205,5 +224,8 @@ struct BvhBuild {
     int depth = 0;
 };
 bool build_wide_bvh(const float *xyz, int32_t n_tri, BvhBuild *out, std::string *err);
+// The compressed form of every node (false when a node's extent does not fit
+// the exponent range: coordinates beyond about 2^110).
+bool compress_nodes(const Node *nodes, int32_t n_nodes, CNode *out);
 
 }  // namespace lt

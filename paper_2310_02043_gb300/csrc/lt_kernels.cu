@@ -231,10 +231,10 @@ __device__ __forceinline__ void trav_init(Trav<kDeep> &s, Hit &h) {
     h.tri = -1; h.prim = INT32_MAX; h.t = FLT_MAX; h.b0 = h.b1 = h.b2 = 0.0f;
 }
 
-// Node loads: with kSmem every node of the BVH sits in shared memory (the
-// whole array was staged by the block, followed by the parent links);
-// otherwise every node comes from global memory through the read-only L1
-// path.
+// Node loads: with kSmem every float node of the BVH sits in shared memory
+// (the whole array was staged by the block, followed by the parent links);
+// otherwise every node comes as a compressed node (CNode) from global memory
+// through the read-only L1 path.
 __device__ __forceinline__ const int32_t *staged_parent(const TraceParams &P, const float4 *smem) {
     return reinterpret_cast<const int32_t *>(smem + P.n_staged * kNodeVec);
 }
@@ -255,69 +255,102 @@ __device__ __forceinline__ float staged_tri_word(const TraceParams &P, const flo
     return reinterpret_cast<const float *>(staged_tris(P, smem))[kTriWords * i + w];
 }
 
-template <bool kSmem>
-__device__ __forceinline__ float4 node_vec(const TraceParams &P, const float4 *smem, int32_t n, int v) {
-    if (kSmem) return smem[n * kNodeVec + v];
-    return __ldg(reinterpret_cast<const float4 *>(P.nodes + n) + v);
-}
-
-template <bool kSmem>
-__device__ __forceinline__ int32_t node_word(const TraceParams &P, const float4 *smem, int32_t n, int w) {
-    if (kSmem) return reinterpret_cast<const int32_t *>(smem + n * kNodeVec)[w];
-    return __ldg(reinterpret_cast<const int32_t *>(P.nodes + n) + w);
-}
-
+// Child word k of node n: staged float node, or compressed node through L1.
 template <bool kSmem>
 __device__ __forceinline__ int32_t child_word(const TraceParams &P, const float4 *smem, int32_t n, int k) {
-    return node_word<kSmem>(P, smem, n, 48 + k);
+    if (kSmem) return reinterpret_cast<const int32_t *>(smem + n * kNodeVec)[48 + k];
+    return __ldg(reinterpret_cast<const int32_t *>(P.cnodes + n) + 16 + k);
 }
 
 // Ize, "Robust BVH ray traversal" (JCGT 2013): scale the exit distance by
 // 1 + 2 gamma_3 so float rounding never rejects a box the ray touches.
 constexpr float kFarScale = 1.0f + 2.0f * (3.0f * 0x1p-24f) / (1.0f - 3.0f * 0x1p-24f);
 
-// Slab test of 4 children (slots 4h .. 4h+3). The ray's near plane along an
-// axis is lo when it runs towards +a and hi otherwise, so the entry and exit
-// distances need no per-axis min/max: near and far planes are picked by
-// address (lo and hi of an axis are two 16-byte vectors apart). A plane
-// distance is one fma, plane * (1/d) + q with q = -o/d rounded once per node
-// visit; the builder pads every child box by more than that rounding moves
-// a plane, and the exit distance is scaled as in Ize's test, so no box the
-// ray touches is rejected.
-template <bool kSmem>
-__device__ __forceinline__ uint32_t test4(const TraceParams &P, const float4 *smem, int32_t n, const Ray &r,
-                                          float qx, float qy, float qz, float tbest, int half) {
+// Slab test of 4 children (slots 4h .. 4h+3) of a staged float node. The
+// ray's near plane along an axis is lo when it runs towards +a and hi
+// otherwise, so the entry and exit distances need no per-axis min/max: near
+// and far planes are picked by address (lo and hi of an axis are two 16-byte
+// vectors apart). A plane distance is one fma, plane * (1/d) + q with
+// q = -o/d rounded once per node visit; the builder pads every child box by
+// more than that rounding moves a plane, and the exit distance is scaled as
+// in Ize's test, so no box the ray touches is rejected. The closest-hit
+// bound is folded into the exit distance: tn <= min(tf, tbest).
+__device__ __forceinline__ uint32_t test4(const float4 *smem, int32_t n, const Ray &r, float qx, float qy, float qz,
+                                          float tbest, int half) {
     const int xn = (r.octant & 1) << 1, yn = 4 + (r.octant & 2), zn = 8 + ((r.octant & 4) >> 1);
-    const float4 nx = node_vec<kSmem>(P, smem, n, xn + half), fx = node_vec<kSmem>(P, smem, n, (xn ^ 2) + half);
-    const float4 ny = node_vec<kSmem>(P, smem, n, yn + half), fy = node_vec<kSmem>(P, smem, n, (yn ^ 2) + half);
-    const float4 nz = node_vec<kSmem>(P, smem, n, zn + half), fz = node_vec<kSmem>(P, smem, n, (zn ^ 2) + half);
+    const float4 *v = smem + n * kNodeVec + half;
+    const float4 nx = v[xn], fx = v[xn ^ 2], ny = v[yn], fy = v[yn ^ 2], nz = v[zn], fz = v[zn ^ 2];
     const float a_nx[4] = {nx.x, nx.y, nx.z, nx.w}, a_fx[4] = {fx.x, fx.y, fx.z, fx.w};
     const float a_ny[4] = {ny.x, ny.y, ny.z, ny.w}, a_fy[4] = {fy.x, fy.y, fy.z, fy.w};
     const float a_nz[4] = {nz.x, nz.y, nz.z, nz.w}, a_fz[4] = {fz.x, fz.y, fz.z, fz.w};
     uint32_t hit = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        float tn, tf;
-        if (kSmem) {
-            tn = max3f(fmaf(a_nx[k], r.ix, qx), fmaf(a_ny[k], r.iy, qy), fmaxf(fmaf(a_nz[k], r.iz, qz), 0.0f));
-            tf = min3f(fmaf(a_fx[k], r.ix, qx), fmaf(a_fy[k], r.iy, qy), fmaf(a_fz[k], r.iz, qz)) * kFarScale;
-            tf = fminf(tf, tbest);
-        } else {   // nodes through L1: the two-rounding form keeps fewer values live
-            tn = max3f((a_nx[k] - r.ox) * r.ix, (a_ny[k] - r.oy) * r.iy, fmaxf((a_nz[k] - r.oz) * r.iz, 0.0f));
-            tf = min3f((a_fx[k] - r.ox) * r.ix, (a_fy[k] - r.oy) * r.iy, (a_fz[k] - r.oz) * r.iz) * kFarScale;
-            tf = fminf(tf, tbest);
-        }
-        hit |= (tn <= tf ? 1u : 0u) << k;     // tn <= exit and tn <= tbest in one comparison
+        const float tn = max3f(fmaf(a_nx[k], r.ix, qx), fmaf(a_ny[k], r.iy, qy), fmaxf(fmaf(a_nz[k], r.iz, qz), 0.0f));
+        float tf = min3f(fmaf(a_fx[k], r.ix, qx), fmaf(a_fy[k], r.iy, qy), fmaf(a_fz[k], r.iz, qz)) * kFarScale;
+        tf = fminf(tf, tbest);
+        hit |= (tn <= tf ? 1u : 0u) << k;
     }
     return hit;
 }
 
-// Child boxes of node n the ray enters before tbest (slot order).
+// Plane byte k (0..3) of a packed word of a compressed node, as the float
+// 1 + q 2^-15 (exact: q lands in mantissa bits 8..15).
+__device__ __forceinline__ float qplane(uint32_t word, int k) {
+    return __uint_as_float(__byte_perm(word, 0x3F800000u, 0x7604u | ((uint32_t)k << 4)));
+}
+
+// Slab test of all 8 children of a compressed node read through L1 (four
+// 16-byte loads). With E = 2^(e+15), plane p + q 2^e = p - E + (1 + q 2^-15) E,
+// so its distance is fma(1 + q 2^-15, E/d, (p - E - o)/d): one byte permute
+// and one fma per plane after three products per axis. The builder widens
+// the quantised boxes by more than the decode's rounding moves a plane.
+// Returns the hit mask (slot order) and the node's inner mask.
+__device__ __forceinline__ uint32_t test_cnode(const TraceParams &P, int32_t n, const Ray &r, float tbest,
+                                               uint32_t &inner) {
+    const uint4 *cn = reinterpret_cast<const uint4 *>(P.cnodes + n);
+    const uint4 hd = __ldg(cn);
+    inner = hd.w >> 24;
+    const uint4 vx = __ldg(cn + 1), vy = __ldg(cn + 2), vz = __ldg(cn + 3);
+    const float Ex = __uint_as_float((hd.w & 0xffu) << 23), Ey = __uint_as_float(((hd.w >> 8) & 0xffu) << 23),
+                Ez = __uint_as_float(((hd.w >> 16) & 0xffu) << 23);
+    const float Sx = Ex * r.ix, Sy = Ey * r.iy, Sz = Ez * r.iz;
+    const float Bx = ((__uint_as_float(hd.x) - Ex) - r.ox) * r.ix;
+    const float By = ((__uint_as_float(hd.y) - Ey) - r.oy) * r.iy;
+    const float Bz = ((__uint_as_float(hd.z) - Ez) - r.oz) * r.iz;
+    const bool hx = r.octant & 1, hy = r.octant & 2, hz = r.octant & 4;   // near plane is hi
+    uint32_t hit = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        // words: lo bytes of children 4h..4h+3, then their hi bytes 8 bytes on
+        const uint32_t lx = h ? vx.y : vx.x, ux = h ? vx.w : vx.z;
+        const uint32_t ly = h ? vy.y : vy.x, uy = h ? vy.w : vy.z;
+        const uint32_t lz = h ? vz.y : vz.x, uz = h ? vz.w : vz.z;
+        const uint32_t nx = hx ? ux : lx, fx = hx ? lx : ux;
+        const uint32_t ny = hy ? uy : ly, fy = hy ? ly : uy;
+        const uint32_t nz = hz ? uz : lz, fz = hz ? lz : uz;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float tn = max3f(fmaf(qplane(nx, k), Sx, Bx), fmaf(qplane(ny, k), Sy, By),
+                                   fmaxf(fmaf(qplane(nz, k), Sz, Bz), 0.0f));
+            float tf = min3f(fmaf(qplane(fx, k), Sx, Bx), fmaf(qplane(fy, k), Sy, By), fmaf(qplane(fz, k), Sz, Bz)) *
+                       kFarScale;
+            tf = fminf(tf, tbest);
+            hit |= (tn <= tf ? 1u : 0u) << (4 * h + k);
+        }
+    }
+    return hit;
+}
+
+// Child boxes of node n the ray enters before tbest (slot order), and the
+// node's inner mask.
 template <bool kSmem>
 __device__ __forceinline__ uint32_t test_node(const TraceParams &P, const float4 *smem, int32_t n, const Ray &r,
-                                              float tbest) {
-    const float qx = kSmem ? -r.ox * r.ix : 0.0f, qy = kSmem ? -r.oy * r.iy : 0.0f, qz = kSmem ? -r.oz * r.iz : 0.0f;
-    return test4<kSmem>(P, smem, n, r, qx, qy, qz, tbest, 0) | (test4<kSmem>(P, smem, n, r, qx, qy, qz, tbest, 1) << 4);
+                                              float tbest, uint32_t &inner) {
+    if (!kSmem) return test_cnode(P, n, r, tbest, inner);
+    inner = reinterpret_cast<const uint32_t *>(smem + n * kNodeVec)[56];
+    const float qx = -r.ox * r.ix, qy = -r.oy * r.iy, qz = -r.oz * r.iz;
+    return test4(smem, n, r, qx, qy, qz, tbest, 0) | (test4(smem, n, r, qx, qy, qz, tbest, 1) << 4);
 }
 
 // Mask in the ray's visiting order: slot s becomes bit s ^ octant, so the
@@ -353,8 +386,8 @@ __device__ __forceinline__ void node_step(const TraceParams &P, const float4 *sm
         s.node = -1; s.leaves = 0; s.leaves2 = 0; h.tri = -1;
         return;
     }
-    const uint32_t hit = test_node<kSmem>(P, smem, s.node, r, h.t);
-    const uint32_t inner = (uint32_t)node_word<kSmem>(P, smem, s.node, 56);
+    uint32_t inner;
+    const uint32_t hit = test_node<kSmem>(P, smem, s.node, r, h.t, inner);
     const uint32_t leaves = hit & ~inner;
     if (leaves) {   // the second slot is taken only by a speculative step (first slot busy)
         if (!kSmem || s.leaves == 0) { s.leaf_node = s.node; s.leaves = leaves; }

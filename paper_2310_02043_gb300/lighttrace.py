@@ -31,7 +31,7 @@ EXPORTED = ("lt_version", "lt_create", "lt_destroy", "lt_set_stream", "lt_last_e
             "lt_get_stats", "lt_set_launch", "lt_count_work", "lt_loss_static", "lt_set_design", "lt_batch_setup",
             "lt_batch_set_lights", "lt_batch_step", "lt_batch_texel_sums", "lt_batch_irradiance",
             "lt_batch_stream", "lt_texel_centres", "lt_build_bvh", "lt_set_step_limit",
-            "lt_probe_l2_read", "lt_gradient_fixed", "lt_set_tri_staging")
+            "lt_probe_l2_read", "lt_gradient_fixed", "lt_set_tri_staging", "lt_compress_bvh")
 
 
 class LtError(RuntimeError):
@@ -64,6 +64,14 @@ class lt_bvh_node(ctypes.Structure):
 BVH_NODE_DTYPE = np.dtype([("lo_x", "<f4", 8), ("hi_x", "<f4", 8), ("lo_y", "<f4", 8), ("hi_y", "<f4", 8),
                            ("lo_z", "<f4", 8), ("hi_z", "<f4", 8), ("child", "<i4", 8), ("inner_mask", "<u4"),
                            ("pad", "<u4", 3)])
+
+
+class lt_bvh_cnode(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_float * 3), ("meta", ctypes.c_uint32), ("q", (ctypes.c_uint8 * 16) * 3),
+                ("child", ctypes.c_int32 * 8)]
+
+
+CBVH_NODE_DTYPE = np.dtype([("origin", "<f4", 3), ("meta", "<u4"), ("q", "u1", (3, 16)), ("child", "<i4", 8)])
 
 
 _lib = None
@@ -106,6 +114,7 @@ def _declare(lib):
         "lt_get_stats": [vp, ctypes.POINTER(lt_stats)],
         "lt_set_launch": [vp, i32, i32, i32],
         "lt_set_tri_staging": [vp, i32],
+        "lt_compress_bvh": [vp, i32, vp],
         "lt_count_work": [vp, u64, u64, i32, u64, u64, vp],
         "lt_loss_static": [ci, vp, vp, ctypes.c_double, vp, vp, vp, i64, vp, vp, vp],
         "lt_set_design": [vp, ctypes.c_uint32],
@@ -232,6 +241,19 @@ def build_bvh(tri_xyz):
     if rc != LT_OK:
         raise LtError(rc, "lt_build_bvh failed")
     return nodes, order, depth.value
+
+
+def compress_bvh(nodes):
+    """lt_compress_bvh: the compressed nodes (CBVH_NODE_DTYPE) of a
+    BVH_NODE_DTYPE array from build_bvh, as the kernels read them when the
+    BVH is not staged in shared memory."""
+    lib = load_library()
+    nodes = np.ascontiguousarray(nodes, BVH_NODE_DTYPE)
+    out = np.zeros(len(nodes), CBVH_NODE_DTYPE)
+    rc = lib.lt_compress_bvh(nodes.ctypes.data_as(ctypes.c_void_p), len(nodes), out.ctypes.data_as(ctypes.c_void_p))
+    if rc != LT_OK:
+        raise LtError(rc, "lt_compress_bvh failed")
+    return out
 
 
 class Tracer:

@@ -56,7 +56,8 @@ def test_version_and_argument_checks(lib):
 def test_struct_layouts_match_the_header(tmp_path):
     """The binding's ctypes structures have the size and field offsets the C
     compiler gives the header's structs."""
-    structs = {"lt_light": lighttrace.lt_light, "lt_stats": lighttrace.lt_stats, "lt_bvh_node": lighttrace.lt_bvh_node}
+    structs = {"lt_light": lighttrace.lt_light, "lt_stats": lighttrace.lt_stats, "lt_bvh_node": lighttrace.lt_bvh_node,
+               "lt_bvh_cnode": lighttrace.lt_bvh_cnode}
     lines = ['#include "lt.h"', "#include <stdio.h>", "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')

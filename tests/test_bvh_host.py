@@ -157,3 +157,120 @@ def test_host_allocation_failure_is_a_status(lib, monkeypatch):
     monkeypatch.delenv("LT_FAULT_HOST_ALLOC")
     nodes, order, depth = lighttrace.build_bvh(xyz)
     _check_tree(xyz, nodes, order, depth)
+
+
+# ---------------------------------------------------------------------------
+# Compressed nodes (lt_compress_bvh): the form the kernels read when the BVH
+# is not staged in shared memory.
+# ---------------------------------------------------------------------------
+FAR_SCALE = np.float32(1.0 + 2.0 * (3.0 * 2.0 ** -24) / (1.0 - 3.0 * 2.0 ** -24))
+
+
+def _decode(cn):
+    """Exact (float64) planes of compressed nodes: lo, hi [n, 8, 3]."""
+    e = np.stack([(cn["meta"] >> (8 * a)) & 0xFF for a in range(3)], -1).astype(np.int64) - 142   # [n, 3]
+    step = np.ldexp(1.0, e)[:, None, :]
+    q = cn["q"].astype(np.float64)                                    # [n, 3, 16]
+    origin = cn["origin"].astype(np.float64)[:, None, :]
+    lo = origin + np.transpose(q[:, :, :8], (0, 2, 1)) * step
+    hi = origin + np.transpose(q[:, :, 8:], (0, 2, 1)) * step
+    return lo, hi, step[:, 0, :]
+
+
+@pytest.mark.parametrize("name", ["cornell", "office", "nested_shelf", "soup_5000", "building_1"])
+def test_compressed_nodes_contain_the_float_boxes(lib, name):
+    xyz = {"cornell": lambda: scenes.cornell_box(res=8).xyz,
+           "office": lambda: scenes.office().xyz,
+           "nested_shelf": lambda: scenes.nested_shelf().xyz,
+           "soup_5000": lambda: _soup(5000, 2),
+           "building_1": lambda: scenes.building(floors=1).xyz}[name]()
+    nodes, order, depth = lighttrace.build_bvh(xyz)
+    cn = lighttrace.compress_bvh(nodes)
+    assert np.array_equal(cn["child"], nodes["child"])
+    assert np.array_equal(cn["meta"] >> 24, nodes["inner_mask"])
+    flo, fhi = _boxes(nodes)
+    lo, hi, step = _decode(cn)
+    full = nodes["child"] != EMPTY
+    f64lo, f64hi = flo.astype(np.float64), fhi.astype(np.float64)
+    big = np.where(full[..., None], f64hi, -np.inf).max(1) - np.where(full[..., None], f64lo, np.inf).min(1)   # [n, 3]
+    m = big * 2.0 ** -14
+    # every box contains the float box widened by the margin, and is at most
+    # one step wider on each side
+    sel = full[..., None] & np.ones(3, bool)
+    assert np.all((lo <= f64lo - m[:, None, :])[sel]) and np.all((hi >= f64hi + m[:, None, :])[sel])
+    assert np.all((lo > f64lo - m[:, None, :] - step[:, None, :] - 1e-6 * (np.abs(f64lo) + 1))[sel])
+    assert np.all((hi < f64hi + m[:, None, :] + step[:, None, :] + 1e-6 * (np.abs(f64hi) + 1))[sel])
+    # the step is the smallest power of two whose 254 steps span the node
+    origin = cn["origin"].astype(np.float64)
+    span = np.where(full[..., None], f64hi, -np.inf).max(1) + m - origin
+    assert np.all(254 * step >= span) and np.all((127 * step < span) | (step == 2.0 ** -126))
+    # empty slots are inverted boxes
+    q = cn["q"]
+    for a in range(3):
+        assert np.all(q[:, a, :8][~full] == 255) and np.all(q[:, a, 8:][~full] == 0)
+
+
+def _fma32(a, b, c):
+    """float32 fma emulated in float64 (the product of two float32 is exact in
+    float64; the sum is rounded twice, within the tolerance used here)."""
+    return (a.astype(np.float64) * b.astype(np.float64) + c.astype(np.float64)).astype(np.float32)
+
+
+def test_compressed_slab_test_is_conservative(lib):
+    """The kernel's decode in float32 (planes as fma(1 + q 2^-15, E/d,
+    (p - E - o)/d), the exit scaled by 1 + 2 gamma_3): for rays from points of
+    the scene to points inside a child's triangle bounds, the child's box is
+    entered no later and left no earlier than the point."""
+    xyz = scenes.office().xyz
+    nodes, order, depth = lighttrace.build_bvh(xyz)
+    cn = lighttrace.compress_bvh(nodes)
+    flo, fhi = _boxes(nodes)
+    amax = float(np.abs(xyz).max())
+    pad = (amax + 1.0) * 2.0 ** -19
+    rng = np.random.default_rng(21)
+    n_idx, k_idx = np.nonzero(nodes["child"] != EMPTY)
+    pick = rng.integers(0, len(n_idx), 20000)
+    n, k = n_idx[pick], k_idx[pick]
+    # a point of the child's unpadded bounds, a ray origin anywhere in the room
+    inner_lo, inner_hi = flo[n, k].astype(np.float64) + pad, fhi[n, k].astype(np.float64) - pad
+    x = inner_lo + rng.uniform(0, 1, inner_lo.shape) * np.maximum(inner_hi - inner_lo, 0)
+    lo_s, hi_s = xyz.reshape(-1, 3).min(0), xyz.reshape(-1, 3).max(0)
+    o = rng.uniform(lo_s, hi_s, (len(n), 3)).astype(np.float32)
+    d = x - o.astype(np.float64)
+    dist = np.linalg.norm(d, axis=1)
+    d = (d / dist[:, None]).astype(np.float32)
+    d = np.where(np.abs(d) < 1e-30, np.copysign(np.float32(1e-30), d), d)
+    inv = (np.float32(1.0) / d).astype(np.float32)
+    meta, origin, q = cn["meta"][n], cn["origin"][n], cn["q"][n]
+    tn = np.zeros(len(n), np.float32)
+    tf = np.full(len(n), np.inf, np.float32)
+    for a in range(3):
+        E = np.ldexp(np.float32(1.0), ((meta >> (8 * a)) & 0xFF).astype(np.int64) - 127).astype(np.float32)
+        S = (E * inv[:, a]).astype(np.float32)
+        B = (((origin[:, a] - E).astype(np.float32) - o[:, a]).astype(np.float32) * inv[:, a]).astype(np.float32)
+        qlo = (1.0 + q[np.arange(len(n)), a, k].astype(np.float64) * 2.0 ** -15).astype(np.float32)
+        qhi = (1.0 + q[np.arange(len(n)), a, 8 + k].astype(np.float64) * 2.0 ** -15).astype(np.float32)
+        t_lo, t_hi = _fma32(qlo, S, B), _fma32(qhi, S, B)
+        near = np.where(d[:, a] < 0, t_hi, t_lo)
+        far = np.where(d[:, a] < 0, t_lo, t_hi)
+        tn = np.maximum(tn, near)
+        tf = np.minimum(tf, far)
+    tf = (tf * FAR_SCALE).astype(np.float32)
+    ok = (tn.astype(np.float64) < dist * (1 - 2.0 ** -20)) & (tf.astype(np.float64) > dist * (1 + 2.0 ** -20))
+    assert ok.all(), (np.count_nonzero(~ok), len(ok))
+
+
+def test_compress_refusals(lib):
+    nodes, order, depth = lighttrace.build_bvh(_soup(50, 4))
+    bad = nodes.copy()
+    k = int(np.nonzero(bad["child"][0] != EMPTY)[0][0])
+    bad["lo_x"][0, k] = bad["hi_x"][0, k] + 1.0                 # an inverted box in a used slot
+    with pytest.raises(lighttrace.LtError, match="LT_ERR_ARG"):
+        lighttrace.compress_bvh(bad)
+    bad = nodes.copy()
+    bad["hi_y"][0, k] = np.nan
+    with pytest.raises(lighttrace.LtError, match="LT_ERR_ARG"):
+        lighttrace.compress_bvh(bad)
+    out = np.zeros(1, lighttrace.CBVH_NODE_DTYPE)
+    assert lib.lt_compress_bvh(None, 1, out.ctypes.data_as(ctypes.c_void_p)) == lighttrace.LT_ERR_ARG
+    assert lighttrace.CBVH_NODE_DTYPE.itemsize == ctypes.sizeof(lighttrace.lt_bvh_cnode) == 96
