@@ -157,9 +157,12 @@ OPS_PER_SEGMENT = 80
 # an 8-wide node with quantised child boxes (80 B, five 16-byte loads), a
 # triangle (48 B, three 16-byte loads), and the texel access (8 B deposit in
 # the forward pass, 4 B weight gather in the adjoint); random numbers are
-# computed in registers. This build stores float nodes of 240 B, of which a
-# visit loads the ray's near and far planes (192 B) and the inner-slot mask.
-NODE_BYTES, NODE_BYTES_LOADED, TRI_BYTES = 80, 196, 48
+# computed in registers. A visit of a float node staged in shared memory (240
+# B) loads the ray's near and far planes (192 B) and the inner-slot mask; a
+# visit of a compressed node read through L1 (96 B) loads its header and
+# planes (64 B).
+NODE_BYTES, TRI_BYTES = 80, 48
+NODE_BYTES_LOADED = {True: 196, False: 64}      # staged float node / compressed node through L1
 HBM_FALLBACK_GBS = 6800.0
 
 
@@ -180,16 +183,16 @@ def hbm_peak():
     return HBM_FALLBACK_GBS, "of fallback (6.8 TB/s, one earlier GB300 measurement)"
 
 
-def traversal_roofline(work, seg_launch, kernel_ms, adjoint, l2_gbs, peak_clock, traffic_per_seg, name):
+def traversal_roofline(work, seg_launch, kernel_ms, adjoint, l2_gbs, peak_clock, traffic_per_seg, name, staged=True):
     """Roofline record of one trace launch: algorithmic bytes (per segment from
     the counting kernel, times the launch's segments) over its CUDA-event time
     against the L2 read rate; beside it the same bytes against HBM, the bytes
-    the float nodes actually load, and the FP32 operations against the issue
-    peak."""
+    the kernel's nodes actually load (staged float nodes or compressed nodes
+    through L1), and the FP32 operations against the issue peak."""
     segs = work["segments"]
     nv, tt = work["node_visits"] / segs, work["tri_tests"] / segs
     per_seg = nv * NODE_BYTES + tt * TRI_BYTES + (4 if adjoint else 8)
-    per_seg_loaded = nv * NODE_BYTES_LOADED + tt * TRI_BYTES + (4 if adjoint else 8)
+    per_seg_loaded = nv * NODE_BYTES_LOADED[staged] + tt * TRI_BYTES + (4 if adjoint else 8)
     secs = kernel_ms / 1e3
     achieved = per_seg * seg_launch / secs / 1e9
     ops_seg = nv * OPS_PER_NODE + tt * OPS_PER_TRI + OPS_PER_SEGMENT
@@ -203,7 +206,9 @@ def traversal_roofline(work, seg_launch, kernel_ms, adjoint, l2_gbs, peak_clock,
                           "L2-only loads), measured in this run",
             "bytes_per_segment": {"algorithmic": per_seg, "node_visits": nv, "tri_tests": tt,
                                   "node_bytes": NODE_BYTES, "tri_bytes": TRI_BYTES,
-                                  "as_loaded_from_float_nodes": per_seg_loaded},
+                                  "node_bytes_loaded": NODE_BYTES_LOADED[staged],
+                                  "nodes": "staged float nodes" if staged else "compressed nodes through L1",
+                                  "as_loaded": per_seg_loaded},
             "hbm": {"achieved": achieved, "peak": hbm, "frac": achieved / hbm, "unit": "GB/s",
                     "peak_basis": hbm_basis},
             "alu": {"achieved": ops, "peak": alu, "frac": ops / alu, "unit": "TFLOP/s",
@@ -467,10 +472,11 @@ def run_ours(args):
     peak_clock = clocks["sm_max_mhz"] if clocks and clocks.get("sm_max_mhz") else 2070.0
     traffic = stored_traffic(f"trace_kernel_{dom}") if name == "office" else None
     l2 = l2_read_gbs()
+    staged = tr.stats()["staged_nodes"] > 0
     roofline = traversal_roofline(work, seg_a if adjoint_dominant else seg_f, dom_ms, adjoint_dominant, l2,
-                                  peak_clock, traffic, name)
+                                  peak_clock, traffic, name, staged)
     other = traversal_roofline(work, seg_f if adjoint_dominant else seg_a, fwd_ms if adjoint_dominant else adj_ms,
-                               not adjoint_dominant, l2, peak_clock, None, name)
+                               not adjoint_dominant, l2, peak_clock, None, name, staged)
     roofline["other_trace_kernel"] = {"kernel": other["kernel"], "achieved": other["achieved"], "frac": other["frac"],
                                       "alu_frac": other["alu"]["frac"]}
     cpu = None
@@ -712,7 +718,7 @@ def run_batch(args):
     step_ms = total_ms / args.steps
     peak_clock = clocks["sm_max_mhz"] if clocks and clocks.get("sm_max_mhz") else 2070.0
     roofline = traversal_roofline(acc, seg_step, step_ms, False, l2_read_gbs(), peak_clock, None,
-                                  "whole batch step: forward + adjoint of 64 designs")
+                                  "whole batch step: forward + adjoint of 64 designs", tr.stats()["staged_nodes"] > 0)
     line = {"metric": METRIC, "value": value, "unit": "Msegments/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": batch_config(sc, counts, shape),
@@ -944,7 +950,7 @@ def run_building(args):
     # the adjoint launch (its time excludes the objective, which the forward
     # interval includes)
     roofline = traversal_roofline(work, seg_adj, adj_ms, True,
-                                  l2_read_gbs(), peak_clock, traffic, "building, BVH through L1/L2")
+                                  l2_read_gbs(), peak_clock, traffic, "building, BVH through L1/L2", staged=False)
     line = {"metric": METRIC, "value": value, "unit": "Msegments/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
