@@ -302,12 +302,14 @@ int grow(Ctx *c, T *&buf, size_t &cap, size_t bytes, cudaStream_t s, bool *grown
 }
 
 // Launch parameters of the gradient kernel (Eq. 11) after an adjoint trace
-// over the photons of `p`: kGradPhotonsPerThread photons per thread, a slot
-// per light that a thread's chunk can touch (chunk / fewest photons of a
-// light + 2, at most all lights).
-TraceParams grad_params(const TraceParams &p, uint64_t min_photons_per_light, ulonglong2 *slots) {
+// over the photons of `p`: kGradPhotonsPerThread photons per thread, or fewer
+// for a pass too small to give every SM 1024 threads that way (at least 1),
+// and a slot per light that a thread's chunk can touch (chunk / fewest
+// photons of a light + 2, at most all lights).
+TraceParams grad_params(const TraceParams &p, uint64_t min_photons_per_light, ulonglong2 *slots, int sm_count) {
     TraceParams g = p;
-    g.chunk = kGradPhotonsPerThread;
+    const uint64_t n = p.photon_end - p.photon_begin, full = (uint64_t)std::max(sm_count, 1) * 1024;
+    g.chunk = n >= kGradPhotonsPerThread * full ? kGradPhotonsPerThread : std::max<uint64_t>(1, n / full);
     g.n_slots = min_photons_per_light == 0
                     ? p.n_lights
                     : (int32_t)std::min<uint64_t>((uint64_t)p.n_lights, g.chunk / min_photons_per_light + 2);
@@ -494,7 +496,7 @@ int batch_prepare(Ctx *c, BatchLaunch *bl) {
     bool grown = false;
     if ((rc = grow(c, b.d_rec, b.rec_bytes, (size_t)n_total * sizeof(PhotonAdj), b.stream, &grown))) return rc;
     bl->adj.rec_adj = b.d_rec;
-    bl->grad = grad_params(bl->adj, b.photons / (uint64_t)max_count, nullptr);
+    bl->grad = grad_params(bl->adj, b.photons / (uint64_t)max_count, nullptr, c->sm_count);
     if ((rc = grow(c, b.d_slots, b.slots_bytes, grad_slot_bytes(bl->grad), b.stream, &grown))) return rc;
     bl->grad.slots = b.d_slots;
     bl->grad_parts = grad_parts((b.photons + (uint64_t)min_count - 1) / (uint64_t)min_count, bl->grad.chunk);
@@ -1034,7 +1036,7 @@ int lt_trace_adjoint(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_h
     if ((rc = grow(c, c->d_rec, c->rec_bytes, (size_t)(photon_end - photon_begin) * sizeof(PhotonAdj), c->stream)))
         return rc;
     p.rec_adj = c->d_rec;
-    TraceParams pg = grad_params(p, n_photons / (uint64_t)L, nullptr);
+    TraceParams pg = grad_params(p, n_photons / (uint64_t)L, nullptr, c->sm_count);
     if ((rc = grow(c, c->d_slots, c->slots_bytes, grad_slot_bytes(pg), c->stream))) return rc;
     pg.slots = c->d_slots;
     const int32_t parts = grad_parts((n_photons + (uint64_t)L - 1) / (uint64_t)L, pg.chunk);
