@@ -142,7 +142,11 @@ LT_API const char *lt_last_error(const void *ctx);
  * tile_area / (res_u res_v) (the box basis standing in for the per-vertex
  * hat basis of Eq. 4; mass-lumped projection, Eq. S.6). Writes the texel
  * count to *n_texels_out. Invalidates targets, weights and pass results.
- * An argument error or a failed BVH build leaves the previous scene in place. */
+ * The BVH is kept as float nodes (staged in shared memory when it fits) and
+ * as compressed nodes (lt_compress_bvh, read through L1 otherwise); a scene
+ * whose BVH has a node wider than about 2e6 along an axis is refused
+ * (LT_ERR_ARG). An argument error or a failed BVH build leaves the previous
+ * scene in place. */
 LT_API int lt_upload_scene(void *ctx, const float *tri_xyz, const float *tri_uv, const int32_t *tri_tile,
                     const float *tri_albedo, int32_t n_tri, const int32_t *tile_res, const double *tile_area,
                     int32_t n_tiles, int64_t *n_texels_out);
@@ -199,7 +203,8 @@ typedef struct {
 /* Compress n_nodes nodes of lt_build_bvh into out[n_nodes] (host only, the
  * conversion lt_upload_scene runs). LT_ERR_ARG for null pointers, a
  * non-positive count, a non-empty slot with a non-finite or inverted box, or
- * coordinates beyond the exponent range (about 2^110). */
+ * a node wider than about 2e6 along an axis (the range of the kernels'
+ * decode; lt_upload_scene refuses such a scene the same way). */
 LT_API int lt_compress_bvh(const lt_bvh_node *nodes, int32_t n_nodes, lt_bvh_cnode *out);
 
 /* Target irradiance E*_t and weights alpha_t of the objective (Eq. 6),

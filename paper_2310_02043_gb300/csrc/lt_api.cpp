@@ -705,7 +705,7 @@ int lt_upload_scene(void *ctx, const float *tri_xyz, const float *tri_uv, const 
     if (!build_wide_bvh(tri_xyz, n_tri, &bvh, &berr)) return fail(c, LT_ERR_ARG, berr);
     std::vector<CNode> cnodes(bvh.nodes.size());
     if (!compress_nodes(bvh.nodes.data(), (int32_t)bvh.nodes.size(), cnodes.data()))
-        return fail(c, LT_ERR_ARG, "scene extent beyond the compressed nodes' exponent range");
+        return fail(c, LT_ERR_ARG, "a BVH node wider than about 2e6: beyond the range of the compressed nodes");
     std::vector<Tri> tris((size_t)n_tri);
     std::vector<TriHit> hits((size_t)n_tri);
     for (int32_t j = 0; j < n_tri; ++j) {

@@ -425,8 +425,11 @@ bool compress_nodes(const Node *nodes, int32_t n_nodes, CNode *out) {
             const double ext = mx + m - (double)p;
             int e = -126;
             while (std::ldexp(254.0, e) < ext) ++e;
+            // E = 2^(e+15) at most 2^28, so that E / d stays finite for the
+            // 1e30 reciprocal of an axis-parallel ray (node extents up to
+            // 254 x 2^13, about 2e6)
             const int biased = e + 15 + 127;
-            if (biased < 1 || biased > 254) return false;
+            if (biased < 1 || biased > 127 + 28) return false;
             cn.p[a] = p;
             meta |= (uint32_t)biased << (8 * a);
             const double step = std::ldexp(1.0, e);

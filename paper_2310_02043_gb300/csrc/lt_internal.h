@@ -224,8 +224,8 @@ struct BvhBuild {
     int depth = 0;
 };
 bool build_wide_bvh(const float *xyz, int32_t n_tri, BvhBuild *out, std::string *err);
-// The compressed form of every node (false when a node's extent does not fit
-// the exponent range: coordinates beyond about 2^110).
+// The compressed form of every node (false when a node is wider than about
+// 2e6 along an axis, beyond the range of the kernels' decode).
 bool compress_nodes(const Node *nodes, int32_t n_nodes, CNode *out);
 
 }  // namespace lt

@@ -273,4 +273,12 @@ def test_compress_refusals(lib):
         lighttrace.compress_bvh(bad)
     out = np.zeros(1, lighttrace.CBVH_NODE_DTYPE)
     assert lib.lt_compress_bvh(None, 1, out.ctypes.data_as(ctypes.c_void_p)) == lighttrace.LT_ERR_ARG
+    # nodes wider than the decode's range (about 2e6) are refused; 1e6 is fine
+    for extent, ok in ((1.0e6, True), (4.0e6, False)):
+        huge, _, _ = lighttrace.build_bvh(_soup(50, 4) * np.float32(extent / 5.0))
+        if ok:
+            lighttrace.compress_bvh(huge)
+        else:
+            with pytest.raises(lighttrace.LtError, match="LT_ERR_ARG"):
+                lighttrace.compress_bvh(huge)
     assert lighttrace.CBVH_NODE_DTYPE.itemsize == ctypes.sizeof(lighttrace.lt_bvh_cnode) == 96
