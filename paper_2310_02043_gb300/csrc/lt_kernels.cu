@@ -165,14 +165,19 @@ __device__ __forceinline__ bool tri_sheared(const Ray &r, float Akx, float Aky, 
 // cull is culled one level lower, by its own children's boxes, and CPU
 // emulation of primary and bounce rays on the office and building BVHs
 // shows that this visits 10-12 % fewer nodes than re-testing the parent.
-// Trees of at most kShallowDepth levels keep the masks in one 32-bit word
-// (levels 0-3: the deepest level's nodes have leaf children only; 2 % faster
-// forward on the office than a 64-bit word), deeper ones (up to kMaxDepth)
-// in two 64-bit words.
+// The pending masks of levels 0 .. depth - 2 (the deepest level's nodes
+// have leaf children only) sit in one 32-bit word for trees of up to 5
+// levels, in one 64-bit word for up to 9 and in two for up to kMaxDepth (the
+// kTrail = 0, 1, 2 instantiations). Narrower words measured faster: 32 bits
+// instead of 64 for the office's 5 levels -2 % forward time, one 64-bit word
+// instead of two for the building's 9 levels -3 to -4 %.
 // ---------------------------------------------------------------------------
-constexpr int kShallowDepth = 5;
+// most levels of a tree each trail holds
+__host__ __device__ constexpr int trail_levels(int kind) { return kind == 0 ? 5 : (kind == 1 ? 9 : kMaxDepth); }
 
-template <bool kDeep>
+__host__ __device__ constexpr int trail_kind(int depth) { return depth <= trail_levels(0) ? 0 : (depth <= trail_levels(1) ? 1 : 2); }
+
+template <int kTrail>
 struct Trail {
     uint64_t w0 = 0, w1 = 0;
     __device__ __forceinline__ uint32_t get(int lvl) const {
@@ -188,8 +193,18 @@ struct Trail {
 };
 
 template <>
-struct Trail<false> {
-    uint32_t w0 = 0;     // levels 0 .. kShallowDepth - 2
+struct Trail<1> {
+    uint64_t w0 = 0;     // levels 0-7
+    __device__ __forceinline__ uint32_t get(int lvl) const { return (uint32_t)(w0 >> (lvl * 8)) & 0xffu; }
+    __device__ __forceinline__ void set(int lvl, uint32_t m) {
+        const int sh = lvl * 8;
+        w0 = (w0 & ~(0xffull << sh)) | ((uint64_t)m << sh);
+    }
+};
+
+template <>
+struct Trail<0> {
+    uint32_t w0 = 0;     // levels 0-3
     __device__ __forceinline__ uint32_t get(int lvl) const { return (w0 >> (lvl * 8)) & 0xffu; }
     __device__ __forceinline__ void set(int lvl, uint32_t m) {
         const int sh = lvl * 8;
@@ -214,7 +229,7 @@ struct Work {
     uint32_t nodes = 0, tris = 0;   // node visits and triangle tests
 };
 
-template <bool kDeep>
+template <int kTrail>
 struct Trav {
     int32_t node;       // node to test next, -1 when the traversal has no node left
     int32_t lvl;
@@ -223,13 +238,13 @@ struct Trav {
     uint32_t leaves;    // pending leaf children of leaf_node (slot order)
     int32_t leaf_node2; // a second node with pending leaves (speculative node steps only)
     uint32_t leaves2;
-    Trail<kDeep> trail;
+    Trail<kTrail> trail;
 };
 
-template <bool kDeep>
-__device__ __forceinline__ void trav_init(Trav<kDeep> &s, Hit &h) {
+template <int kTrail>
+__device__ __forceinline__ void trav_init(Trav<kTrail> &s, Hit &h) {
     s.node = 0; s.lvl = 0; s.steps = 0; s.leaf_node = 0; s.leaves = 0; s.leaf_node2 = 0; s.leaves2 = 0;
-    s.trail = Trail<kDeep>();
+    s.trail = Trail<kTrail>();
     h.tri = -1; h.prim = INT32_MAX; h.t = FLT_MAX; h.b0 = h.b1 = h.b2 = 0.0f;
 }
 
@@ -379,8 +394,8 @@ __device__ __forceinline__ uint32_t order_mask(uint32_t m, int oct) { return g_o
 // Test the children of s.node; note hit leaves; descend to the first hit
 // inner child in visiting order, or climb to the nearest level with pending
 // children and descend into the first of them.
-template <bool kCount, bool kSmem, bool kDeep>
-__device__ __forceinline__ void node_step(const TraceParams &P, const float4 *smem, const Ray &r, Trav<kDeep> &s, Hit &h,
+template <bool kCount, bool kSmem, int kTrail>
+__device__ __forceinline__ void node_step(const TraceParams &P, const float4 *smem, const Ray &r, Trav<kTrail> &s, Hit &h,
                                           Work &work) {
     if (kCount) work.nodes += 1;
     if (++s.steps > P.max_steps) {
@@ -397,7 +412,7 @@ __device__ __forceinline__ void node_step(const TraceParams &P, const float4 *sm
     }
     const uint32_t cand = order_mask(hit & inner, r.octant);
     if (cand) {
-        if (s.lvl + 1 >= (kDeep ? kMaxDepth : kShallowDepth)) {   // deeper than the trail holds
+        if (s.lvl + 1 >= trail_levels(kTrail)) {   // deeper than the trail holds
             atomicOr(P.err, kErrDepth);
             s.node = -1; s.leaves = 0; s.leaves2 = 0; h.tri = -1;
             return;
@@ -425,8 +440,8 @@ __device__ __forceinline__ void node_step(const TraceParams &P, const float4 *sm
 
 // Test the triangles of one pending leaf child. Ties in t go to the lower
 // uploaded triangle index.
-template <bool kCount, bool kSmem, bool kTriSmem, bool kDeep>
-__device__ __forceinline__ void leaf_step(const TraceParams &P, const float4 *smem, const Ray &r, Trav<kDeep> &s, Hit &h,
+template <bool kCount, bool kSmem, bool kTriSmem, int kTrail>
+__device__ __forceinline__ void leaf_step(const TraceParams &P, const float4 *smem, const Ray &r, Trav<kTrail> &s, Hit &h,
                                           int32_t skip_tile, Work &work) {
     const int k = __ffs(s.leaves) - 1;
     s.leaves &= s.leaves - 1;
@@ -475,13 +490,13 @@ __device__ __forceinline__ void leaf_step(const TraceParams &P, const float4 *sm
 // Closest hit excluding triangles of tile `skip_tile`, one ray at a time
 // (path record); the same steps as the tracing kernels, so the same hits.
 __device__ Hit closest_hit(const TraceParams &P, const float4 *smem, const Ray &r, int32_t skip_tile) {
-    Trav<true> s;
+    Trav<2> s;
     Hit h;
     Work work;
     trav_init(s, h);
     while (true) {
-        if (s.leaves) leaf_step<false, false, false, true>(P, smem, r, s, h, skip_tile, work);
-        else if (s.node >= 0) node_step<false, false, true>(P, smem, r, s, h, work);
+        if (s.leaves) leaf_step<false, false, false, 2>(P, smem, r, s, h, skip_tile, work);
+        else if (s.node >= 0) node_step<false, false, 2>(P, smem, r, s, h, work);
         else return h;
     }
 }
@@ -823,7 +838,7 @@ __device__ __forceinline__ void stage_nodes(const TraceParams &P, float4 *smem) 
 // iteration the warp votes and runs the kind of step most of its lanes are
 // waiting for, so lanes never idle until a neighbour's path ends.
 // ---------------------------------------------------------------------------
-template <bool kAdjoint, bool kCount, bool kSmem, bool kTriSmem, bool kDeep>
+template <bool kAdjoint, bool kCount, bool kSmem, bool kTriSmem, int kTrail>
 __global__ void __launch_bounds__(kSmem ? kThreadsStaged : kThreadsL1, kTraceMinBlocks)
     trace_kernel(const TraceParams P) {
     static_assert(kSmem || !kTriSmem, "triangles are staged only with the nodes");
@@ -843,7 +858,7 @@ __global__ void __launch_bounds__(kSmem ? kThreadsStaged : kThreadsL1, kTraceMin
     float t_first = 0.0f;
     int32_t n1code = -1;
     Ray r;
-    Trav<kDeep> s;
+    Trav<kTrail> s;
     Hit h;
     Work work;
     unsigned long long segs = 0;
@@ -895,9 +910,9 @@ __global__ void __launch_bounds__(kSmem ? kThreadsStaged : kThreadsL1, kTraceMin
         else if (nf > 0) kind = 2;
         else kind = nn > 0 ? 0 : 1;
         if (kind == 0) {
-            if (can_node) node_step<kCount, kSmem, kDeep>(P, smem, r, s, h, work);
+            if (can_node) node_step<kCount, kSmem, kTrail>(P, smem, r, s, h, work);
         } else if (kind == 1) {
-            if (can_leaf) leaf_step<kCount, kSmem, kTriSmem, kDeep>(P, smem, r, s, h, skip, work);
+            if (can_leaf) leaf_step<kCount, kSmem, kTriSmem, kTrail>(P, smem, r, s, h, skip, work);
         } else if (fin) {
             // Finish the segment (one traced ray, hit or miss), then start the
             // next ray: a bounce from the hit or the next photon's emission.
@@ -1238,22 +1253,26 @@ int trace_kernel_max_threads(bool staged) { return staged ? kThreadsStaged : kTh
 
 // The kernel instantiation for a launch: all nodes in shared memory when the
 // launch stages the whole BVH, otherwise none, and the triangles too when
-// the launch stages them; pending masks in one 32-bit word when the tree has
-// at most kShallowDepth levels, otherwise in two 64-bit words.
-template <bool kAdjoint, bool kCount, bool kDeep>
-TraceFn trace_fn_depth(bool staged, bool tris) {
-    if (!staged) return trace_kernel<kAdjoint, kCount, false, false, kDeep>;
-    return tris ? trace_kernel<kAdjoint, kCount, true, true, kDeep> : trace_kernel<kAdjoint, kCount, true, false, kDeep>;
+// the launch stages them; the narrowest trail of pending masks that holds
+// the tree's levels.
+template <bool kAdjoint, bool kCount, int kTrail>
+TraceFn trace_fn_trail(bool staged, bool tris) {
+    if (!staged) return trace_kernel<kAdjoint, kCount, false, false, kTrail>;
+    return tris ? trace_kernel<kAdjoint, kCount, true, true, kTrail> : trace_kernel<kAdjoint, kCount, true, false, kTrail>;
 }
 
 template <bool kAdjoint, bool kCount>
-TraceFn trace_fn(bool staged, bool tris, bool deep) {
-    return deep ? trace_fn_depth<kAdjoint, kCount, true>(staged, tris) : trace_fn_depth<kAdjoint, kCount, false>(staged, tris);
+TraceFn trace_fn(bool staged, bool tris, int depth) {
+    switch (trail_kind(depth)) {
+        case 0: return trace_fn_trail<kAdjoint, kCount, 0>(staged, tris);
+        case 1: return trace_fn_trail<kAdjoint, kCount, 1>(staged, tris);
+        default: return trace_fn_trail<kAdjoint, kCount, 2>(staged, tris);
+    }
 }
 
 template <bool kAdjoint, bool kCount>
 cudaError_t launch_trace(const TraceParams &p, int grid, int block, size_t smem, cudaStream_t s) {
-    const TraceFn fn = trace_fn<kAdjoint, kCount>(p.n_staged > 0, p.n_tris_staged > 0, p.depth > kShallowDepth);
+    const TraceFn fn = trace_fn<kAdjoint, kCount>(p.n_staged > 0, p.n_tris_staged > 0, p.depth);
     cudaError_t e = allow_smem(fn, smem);
     if (e != cudaSuccess) return e;
     fn<<<grid, block, smem, s>>>(p);
@@ -1262,8 +1281,7 @@ cudaError_t launch_trace(const TraceParams &p, int grid, int block, size_t smem,
 
 cudaError_t trace_occupancy(bool adjoint, bool staged, bool tris, int depth, int block, size_t smem,
                             int *blocks_per_sm) {
-    const bool deep = depth > kShallowDepth;
-    const TraceFn fn = adjoint ? trace_fn<true, false>(staged, tris, deep) : trace_fn<false, false>(staged, tris, deep);
+    const TraceFn fn = adjoint ? trace_fn<true, false>(staged, tris, depth) : trace_fn<false, false>(staged, tris, depth);
     cudaError_t e = allow_smem(fn, smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem);
