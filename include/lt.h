@@ -409,10 +409,11 @@ LT_API int lt_loss_static(int device, void *cuda_stream, const int64_t *q, doubl
                           float *E_out, double *loss_out);
 
 /* Launch shape of the tracing kernels. threads_per_block: a multiple of 32
- * up to 1024, 0 = the bound of the kernel the BVH selects (1024 when the
- * whole BVH is staged in shared memory, 768 when nodes are read through L1);
- * a trace whose BVH selects a kernel with a smaller bound than the request
- * fails with LT_ERR_ARG. blocks_per_sm: resident blocks per SM, 0 = as many
+ * up to 1024, 0 = the bound of the kernel the BVH selects (1024, both for
+ * the kernels that stage the BVH in shared memory and for those that read
+ * nodes through L1; the bounds are build-time constants); a trace whose BVH
+ * selects a kernel with a smaller bound than the request fails with
+ * LT_ERR_ARG. blocks_per_sm: resident blocks per SM, 0 = as many
  * as fit. smem_node_bytes: shared-memory budget for staged BVH nodes in
  * [0, 200 KiB] (the whole BVH is staged when it fits, else none), 0 = stage
  * nothing. A negative argument keeps the current value. The defaults are the

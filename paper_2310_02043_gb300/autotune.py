@@ -13,7 +13,7 @@ import os
 import statistics
 
 # (threads per block (0: the bound of the kernel the BVH selects, 1024 when it
-# is staged, 768 when nodes come through L1), blocks per SM (0: as many as
+# is staged and when nodes come through L1), blocks per SM (0: as many as
 # fit), shared-memory node budget in bytes (0: nodes through L1; the library
 # stages the triangles with the nodes where that costs no resident block));
 # every field is set explicitly.

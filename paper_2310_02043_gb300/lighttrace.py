@@ -456,7 +456,7 @@ class Tracer:
 
     def set_launch(self, threads_per_block: int = -1, blocks_per_sm: int = -1, smem_node_bytes: int = -1):
         """Launch shape of the tracing kernels (0: the kernel's own block
-        bound, 1024 staged / 768 through L1 / as many blocks as fit / no
+        bound, 1024 staged and through L1 / as many blocks as fit / no
         staged nodes; negative: keep)."""
         self._check(self.lib.lt_set_launch(self.h, threads_per_block, blocks_per_sm, smem_node_bytes))
 

@@ -227,7 +227,7 @@ def test_gradients_identical_across_launch_shapes(tr):
 
 def test_launch_shape_arguments(tr):
     # 0 selects the default (the bound of the kernel the BVH selects: 1024
-    # threads when the BVH is staged, 768 through L1 / as many blocks as fit /
+    # threads, staged or through L1 / as many blocks as fit /
     # no staged nodes), a negative argument keeps the current value
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
@@ -270,12 +270,14 @@ def test_launch_shape_arguments(tr):
     tr.set_tri_staging(200 * 1024)
     tr.set_launch(0, 0, 0)
     g, t, staged = shape()
-    assert t == 768 and g % sms == 0 and staged == 0
-    # a block above the bound of the kernel the BVH selects is refused on the
+    assert t == 1024 and g % sms == 0 and staged == 0
+    # blocks beyond 1024 threads or not a multiple of 32 are refused on the
     # host, before any launch
-    tr.set_launch(1024, 0, 0)
-    with pytest.raises(RuntimeError, match="exceeds the bound"):
-        tr.trace_forward(5, 1 << 14, 5)
+    for bad in (1056, 100):
+        with pytest.raises(RuntimeError, match="multiple of 32"):
+            tr.set_launch(bad, 0, 0)
+    tr.set_launch(512, 0, 0)
+    assert shape()[1:] == (512, 0)
     tr.set_launch(1024, 0, 200 * 1024)
     assert shape() == (sms, 1024, tr.stats()["n_nodes"])
     tr.set_launch(256, 0, 48 * 1024)
@@ -373,7 +375,7 @@ def test_deep_bvh_staged_and_through_l1(tr):
     tr.set_launch(0, 0, 0)
     tr.trace_forward(seed, n, hits)
     st = tr.stats()
-    assert st["staged_nodes"] == 0 and st["block_threads"] == 768
+    assert st["staged_nodes"] == 0 and st["block_threads"] == 1024
     assert np.array_equal(tr.texel_sums(), q_staged)
     tr.set_launch(0, 0, 72 * 1024)
     Lt = L.copy()
