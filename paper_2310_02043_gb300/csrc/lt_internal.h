@@ -114,14 +114,15 @@ struct alignas(16) StepHeader {
     float pad[3];
 };
 
-// What the adjoint trace keeps of one photon for the gradient kernel: its
-// adjoint state dO/dPhi_r = sum_i w_{t_i} beta_i (Eq. 12), the distance to
-// its first hit along the emitted ray, and 2 x first-hit triangle + 1 if the
-// normal was flipped towards the light (-1: no hit).
+// What the adjoint trace keeps of one photon for the gradient kernel: the
+// distance to its first hit along the emitted ray and 2 x first-hit
+// triangle + 1 if the normal was flipped towards the light (-1: no hit),
+// stored at the first hit, and its adjoint state dO/dPhi_r =
+// sum_i w_{t_i} beta_i (Eq. 12), stored at the end of the path.
 struct alignas(16) PhotonAdj {
-    float g;
     float t_first;
     int32_t n1code;
+    float g;
     uint32_t pad;
 };
 static_assert(sizeof(PhotonAdj) == 16, "photon record layout");

@@ -855,10 +855,6 @@ __global__ void __launch_bounds__(kSmem ? kThreadsStaged : kThreadsL1, kTraceMin
 
     int32_t l = 0, seg = 0, skip = -1;
     float phi = 0.0f, g = 0.0f, beta = 1.0f;
-    // adjoint: distance to the first hit along the emitted ray and 2 x
-    // first-hit triangle + 1 if its normal was flipped (the photon's record)
-    float t_first = 0.0f;
-    int32_t n1code = -1;
     Ray r;
     Trav<kTrail> s;
     Hit h;
@@ -929,10 +925,11 @@ __global__ void __launch_bounds__(kSmem ? kThreadsStaged : kThreadsL1, kTraceMin
                 if (!kAdjoint) {
                     deposit(P.q + tb, texel, (unsigned long long)__float2ll_rn(phi * launch_scale(P)));   // Eq. 8
                 } else {
-                    if (seg == 1) {
-                        t_first = h.t;
-                        n1code = 2 * h.tri + (nrm.x != __ldg(P.hits[h.tri].n) || nrm.y != __ldg(P.hits[h.tri].n + 1) ||
+                    if (seg == 1) {   // the first hit: distance and 2 x triangle + flip bit
+                        const int32_t n1code = 2 * h.tri + (nrm.x != __ldg(P.hits[h.tri].n) || nrm.y != __ldg(P.hits[h.tri].n + 1) ||
                                               nrm.z != __ldg(P.hits[h.tri].n + 2) ? 1 : 0);
+                        *reinterpret_cast<float2 *>(&P.rec_adj[photon - P.photon_begin]) =
+                            make_float2(h.t, __int_as_float(n1code));
                     }
                     g += __ldg(P.w + tb + texel) * beta;                                          // Eq. 12
                 }
@@ -946,14 +943,12 @@ __global__ void __launch_bounds__(kSmem ? kThreadsStaged : kThreadsL1, kTraceMin
             }
             if (!bounce) {
                 if (kAdjoint) {
-                    // the photon's adjoint state dO/dPhi_r (Eq. 12) and first hit,
-                    // for the gradient kernel (Eq. 11)
-                    PhotonAdj rec;
-                    rec.g = g;
-                    rec.t_first = t_first;
-                    rec.n1code = n1code;
-                    rec.pad = 0;
-                    P.rec_adj[photon - P.photon_begin] = rec;
+                    // the photon's record for the gradient kernel (Eq. 11): its
+                    // adjoint state dO/dPhi_r (Eq. 12) now; the first hit went
+                    // in when it was found (two registers fewer along the path)
+                    float2 *rp = reinterpret_cast<float2 *>(&P.rec_adj[photon - P.photon_begin]);
+                    if (seg == 1 && h.tri < 0) rp[0] = make_float2(0.0f, __int_as_float(-1));   // no first hit
+                    rp[1] = make_float2(g, 0.0f);
                 }
                 ++photon;
                 if (photon >= thread_end(P)) active = false;
@@ -978,7 +973,6 @@ __global__ void __launch_bounds__(kSmem ? kThreadsStaged : kThreadsL1, kTraceMin
                     skip = -1;
                     g = 0.0f;
                     beta = 1.0f;
-                    n1code = -1;
                 }
                 const float3 w = frame_dir(c, sn, u.y, t1, t2, axis);
                 ray_init(r, org.x, org.y, org.z, w.x, w.y, w.z);
