@@ -224,7 +224,10 @@ LT_API int lt_set_lights(void *ctx, const lt_light *lights, int32_t n_lights);
  * Philox4x32-10 with counter (photon lo, photon hi, segment, 0) and key
  * (seed lo, seed hi). Clears and then fills the texel accumulator, a
  * [n_texels] int64 fixed-point array (value round(Phi * S)); the result is
- * bit-reproducible for any launch configuration. */
+ * bit-reproducible for any launch configuration. A pass covers at most
+ * 2^32 - 1 photons (photon_end - photon_begin; larger ranges are
+ * LT_ERR_ARG: split them, the integer sums add up exactly); the same holds
+ * for lt_trace_adjoint, lt_count_work and lt_debug_paths. */
 LT_API int lt_trace_forward(void *ctx, uint64_t seed, uint64_t n_photons, int32_t max_hits, uint64_t photon_begin,
                      uint64_t photon_end);
 
@@ -341,8 +344,10 @@ LT_API int lt_set_design(void *ctx, uint32_t design);
 
 /* Allocate a batch: n_designs designs with lights_per_design[d] >= 1 lights
  * each (at most LT_MAX_BATCH_LIGHTS in total), photons_per_design photons and
- * max_hits hits per photon. Needs an uploaded scene; replaces a previous
- * batch. Device memory: n_designs x n_texels x 16 bytes plus small buffers. */
+ * max_hits hits per photon; n_designs x photons_per_design at most
+ * 2^32 - 1 (LT_ERR_ARG otherwise). Needs an uploaded scene; replaces a
+ * previous batch. Device memory: n_designs x n_texels x 16 bytes plus small
+ * buffers. */
 LT_API int lt_batch_setup(void *ctx, int32_t n_designs, const int32_t *lights_per_design,
                           uint64_t photons_per_design, int32_t max_hits);
 

@@ -428,6 +428,7 @@ int check_trace_args(Ctx *c, uint64_t n_photons, int32_t max_hits, uint64_t begi
     if (n_photons == 0) return fail(c, LT_ERR_ARG, "n_photons must be positive");
     if (max_hits < 1 || max_hits > 64) return fail(c, LT_ERR_ARG, "max_hits must be in [1, 64]");
     if (begin > end || end > n_photons) return fail(c, LT_ERR_ARG, "photon range outside [0, n_photons]");
+    if (end - begin > kMaxPassPhotons) return fail(c, LT_ERR_ARG, "a pass covers at most 2^32 - 1 photons");
     return LT_OK;
 }
 
@@ -1148,6 +1149,8 @@ int lt_batch_setup(void *ctx, int32_t n_designs, const int32_t *lights_per_desig
     if (!c->d_nodes) return fail(c, LT_ERR_STATE, "no scene uploaded");
     if (n_designs < 1 || !lights_per_design) return fail(c, LT_ERR_ARG, "need at least one design");
     if (photons_per_design == 0) return fail(c, LT_ERR_ARG, "photons_per_design must be positive");
+    if (photons_per_design > kMaxPassPhotons / (uint64_t)n_designs)
+        return fail(c, LT_ERR_ARG, "a batch pass covers at most 2^32 - 1 photons (designs x photons per design)");
     if (max_hits < 1 || max_hits > 64) return fail(c, LT_ERR_ARG, "max_hits must be in [1, 64]");
     int64_t total = 0;
     for (int32_t d = 0; d < n_designs; ++d) {

@@ -212,6 +212,9 @@ inline int32_t grad_parts(uint64_t max_nl, uint64_t chunk) {
 cudaError_t launch_weight_range(const float *w, int64_t n, uint32_t *wmax, cudaStream_t s);
 // The gradient kernel: p.chunk photons per thread, p.n_slots slots each.
 cudaError_t launch_grad_photons(const TraceParams &p, cudaStream_t s);
+// Photons of one tracing pass at most: the kernels index a pass's photons
+// and count a thread's segments and loop iterations in 32 bits.
+constexpr uint64_t kMaxPassPhotons = 0xffffffffull;
 constexpr uint64_t kGradPhotonsPerThread = 64;   // fewer for small passes (grad_params)
 int trace_kernel_max_threads(bool staged);   // block bound of the staged / L1-node kernels
 cudaError_t trace_occupancy(bool adjoint, bool staged, bool tris, int depth, int block, size_t smem,

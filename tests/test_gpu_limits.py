@@ -81,6 +81,15 @@ def test_limits_are_rejected(tr):
     for bad in (0, 65):
         with pytest.raises(LtError):
             tr.trace_forward(1, 1000, bad)
+    # a pass covers at most 2^32 - 1 photons (the kernels count a pass's
+    # photons in 32 bits); larger ranges are refused before any launch, and a
+    # small range far into a larger budget is fine
+    with pytest.raises(LtError, match="2\\^32"):
+        tr.trace_forward(1, 1 << 33, 3, 0, 1 << 32)
+    with pytest.raises(LtError, match="2\\^32"):
+        tr.batch_setup([2, 1], 1 << 31, 3)
+    tr.trace_forward(1, 1 << 33, 3, (1 << 33) - 4096, 1 << 33)
+    assert tr.stats()["segments_forward"] > 0
 
 
 def test_power_beyond_the_fixed_point_range(tr):
