@@ -220,8 +220,10 @@ struct Hit {
     float t, b0, b1, b2;   // distance and barycentric weights of the three vertices
 };
 
+template <bool kHoldPrim>
 __device__ __forceinline__ void take_hit(Hit &h, int32_t tri, int32_t prim, const TriTest &tt) {
-    h.tri = tri; h.prim = prim; h.t = tt.t;
+    h.tri = tri; h.t = tt.t;
+    if (kHoldPrim) h.prim = prim;
     h.b0 = __fdiv_rn(tt.U, tt.det);
     h.b1 = __fdiv_rn(tt.V, tt.det);
     h.b2 = __fdiv_rn(tt.W, tt.det);
@@ -442,7 +444,11 @@ __device__ __forceinline__ void node_step(const TraceParams &P, const float4 *sm
 
 // Test the triangles of one pending leaf child. Ties in t go to the lower
 // uploaded triangle index.
-template <bool kCount, bool kSmem, bool kTriSmem, int kTrail>
+// kHoldPrim: keep the closest hit's uploaded index in a register for ties in
+// t; otherwise read it back on a tie (rare), which frees a register (the
+// forward kernels: building forward -2 %; the adjoint kernels keep it,
+// where the freed register made the office 1 % slower).
+template <bool kCount, bool kSmem, bool kTriSmem, int kTrail, bool kHoldPrim>
 __device__ __forceinline__ void leaf_step(const TraceParams &P, const float4 *smem, const Ray &r, Trav<kTrail> &s, Hit &h,
                                           int32_t skip_tile, Work &work) {
     const int k = __ffs(s.leaves) - 1;
@@ -468,7 +474,9 @@ __device__ __forceinline__ void leaf_step(const TraceParams &P, const float4 *sm
                              __fsub_rn(tx[8], okx), __fsub_rn(ty[8], oky), __fsub_rn(tz[8], okz), tt))
                 continue;
             const int32_t prim = __float_as_int(t[3]);
-            if (tt.t < h.t || (tt.t == h.t && prim < h.prim)) take_hit(h, i, prim, tt);
+            if (tt.t < h.t || (tt.t == h.t && (kHoldPrim ? prim < h.prim
+                                                      : (h.tri < 0 || prim < __float_as_int(staged_tri_word(P, smem, h.tri, 3))))))
+                take_hit<kHoldPrim>(h, i, prim, tt);
         }
         return;
     }
@@ -485,7 +493,10 @@ __device__ __forceinline__ void leaf_step(const TraceParams &P, const float4 *sm
                          __fsub_rn(__ldg(tx + 8), okx), __fsub_rn(__ldg(ty + 8), oky), __fsub_rn(__ldg(tz + 8), okz), tt))
             continue;
         const int32_t prim = __float_as_int(__ldg(t + 3));
-        if (tt.t < h.t || (tt.t == h.t && prim < h.prim)) take_hit(h, i, prim, tt);
+        if (tt.t < h.t ||
+            (tt.t == h.t && (kHoldPrim ? prim < h.prim
+                                       : (h.tri < 0 || prim < __float_as_int(__ldg(reinterpret_cast<const float *>(P.tris + h.tri) + 3))))))
+            take_hit<kHoldPrim>(h, i, prim, tt);
     }
 }
 
@@ -497,7 +508,7 @@ __device__ Hit closest_hit(const TraceParams &P, const float4 *smem, const Ray &
     Work work;
     trav_init(s, h);
     while (true) {
-        if (s.leaves) leaf_step<false, false, false, 2>(P, smem, r, s, h, skip_tile, work);
+        if (s.leaves) leaf_step<false, false, false, 2, true>(P, smem, r, s, h, skip_tile, work);
         else if (s.node >= 0) node_step<false, false, 2>(P, smem, r, s, h, work);
         else return h;
     }
@@ -915,7 +926,7 @@ __global__ void __launch_bounds__(kSmem ? kThreadsStaged : kThreadsL1, kTraceMin
         if (kind == 0) {
             if (can_node) node_step<kCount, kSmem, kTrail>(P, smem, r, s, h, work);
         } else if (kind == 1) {
-            if (can_leaf) leaf_step<kCount, kSmem, kTriSmem, kTrail>(P, smem, r, s, h, skip, work);
+            if (can_leaf) leaf_step<kCount, kSmem, kTriSmem, kTrail, kAdjoint>(P, smem, r, s, h, skip, work);
         } else if (fin) {
             // Finish the segment (one traced ray, hit or miss), then start the
             // next ray: a bounce from the hit or the next photon's emission.
