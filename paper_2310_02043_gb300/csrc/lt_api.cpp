@@ -303,13 +303,18 @@ int grow(Ctx *c, T *&buf, size_t &cap, size_t bytes, cudaStream_t s, bool *grown
 
 // Launch parameters of the gradient kernel (Eq. 11) after an adjoint trace
 // over the photons of `p`: kGradPhotonsPerThread photons per thread, or fewer
-// for a pass too small to give every SM 1024 threads that way (at least 1),
-// and a slot per light that a thread's chunk can touch (chunk / fewest
-// photons of a light + 2, at most all lights).
+// for a pass too small to give every SM 1024 threads that way, but at least
+// kGradMinPhotonsPerThread: every thread writes 128 bytes of 128-bit sums per
+// slot, which at one photon per thread outweigh the 16-byte photon records
+// (Cornell box, 2^18 photons, adjoint with 1, 3, 6 and 13 photons per
+// thread: 0.129, 0.123, 0.125 and 0.135 ms); and a slot per light that a
+// thread's chunk can touch (chunk / fewest photons of a light + 2, at most
+// all lights).
 TraceParams grad_params(const TraceParams &p, uint64_t min_photons_per_light, ulonglong2 *slots, int sm_count) {
     TraceParams g = p;
     const uint64_t n = p.photon_end - p.photon_begin, full = (uint64_t)std::max(sm_count, 1) * 1024;
-    g.chunk = n >= kGradPhotonsPerThread * full ? kGradPhotonsPerThread : std::max<uint64_t>(1, n / full);
+    g.chunk = n >= kGradPhotonsPerThread * full ? kGradPhotonsPerThread
+                                                : std::max<uint64_t>(kGradMinPhotonsPerThread, n / full);
     g.n_slots = min_photons_per_light == 0
                     ? p.n_lights
                     : (int32_t)std::min<uint64_t>((uint64_t)p.n_lights, g.chunk / min_photons_per_light + 2);

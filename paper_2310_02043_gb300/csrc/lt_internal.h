@@ -201,13 +201,16 @@ cudaError_t launch_resolve(const unsigned long long *q, const float *area, doubl
 // ([n_lights][parts][8]), then one conversion per light.
 cudaError_t launch_grad_finalize(const TraceParams &p, ulonglong2 *partial, int32_t parts, double *out,
                                  ulonglong2 *fixed_out, double *scale_out, cudaStream_t s);
-// Partial sums per light: one per 4096 threads covering the light's photons
+// Partial sums per light: one per 1024 threads covering the light's photons
 // (a light of max_nl photons in chunks of `chunk` spans up to
-// ceil(max_nl / chunk) + 1 threads), at least 1, at most 64.
+// ceil(max_nl / chunk) + 1 threads), at least 1, at most 256, so that a
+// thread of the 256-thread partial blocks adds about four slots (one per
+// 4096 threads, at most 64, left each thread a chain of 16 dependent slot
+// loads: 24 us of a 0.22 ms Cornell box step).
 inline int32_t grad_parts(uint64_t max_nl, uint64_t chunk) {
     const uint64_t threads = (max_nl + chunk - 1) / chunk + 1;
-    const uint64_t parts = (threads + 4095) / 4096;
-    return (int32_t)(parts < 1 ? 1 : (parts > 64 ? 64 : parts));
+    const uint64_t parts = (threads + 1023) / 1024;
+    return (int32_t)(parts < 1 ? 1 : (parts > 256 ? 256 : parts));
 }
 cudaError_t launch_weight_range(const float *w, int64_t n, uint32_t *wmax, cudaStream_t s);
 // The gradient kernel: p.chunk photons per thread, p.n_slots slots each.
@@ -216,6 +219,7 @@ cudaError_t launch_grad_photons(const TraceParams &p, cudaStream_t s);
 // and count a thread's segments and loop iterations in 32 bits.
 constexpr uint64_t kMaxPassPhotons = 0xffffffffull;
 constexpr uint64_t kGradPhotonsPerThread = 64;   // fewer for small passes (grad_params)
+constexpr uint64_t kGradMinPhotonsPerThread = 3;
 int trace_kernel_max_threads(bool staged);   // block bound of the staged / L1-node kernels
 cudaError_t trace_occupancy(bool adjoint, bool staged, bool tris, int depth, int block, size_t smem,
                             int *blocks_per_sm);

@@ -1218,25 +1218,25 @@ __global__ void __launch_bounds__(256) grad_partial_kernel(const TraceParams P, 
     }
 }
 
-__global__ void __launch_bounds__(32) grad_finalize_kernel(const TraceParams P, const ulonglong2 *partial,
-                                                           int32_t parts, double *out, ulonglong2 *fixed_out,
-                                                           double *scale_out) {
+// One block of 8 warps per light, warp k summing component k.
+__global__ void __launch_bounds__(256) grad_finalize_kernel(const TraceParams P, const ulonglong2 *partial,
+                                                            int32_t parts, double *out, ulonglong2 *fixed_out,
+                                                            double *scale_out) {
     const int32_t l = blockIdx.x;
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const double unit = 0x1p-64 / (double)grad_scale(P);          // a power of two: exact
-    for (int k = 0; k < 8; ++k) {
-        ulonglong2 x = make_ulonglong2(0, 0);
-        for (int32_t p = threadIdx.x; p < parts; p += 32) add128(x, partial[((uint64_t)l * parts + p) * 8 + k]);
+    ulonglong2 x = make_ulonglong2(0, 0);
+    for (int32_t p = lane; p < parts; p += 32) add128(x, partial[((uint64_t)l * parts + p) * 8 + k]);
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            ulonglong2 y;
-            y.x = __shfl_xor_sync(kFull, x.x, off);
-            y.y = __shfl_xor_sync(kFull, x.y, off);
-            add128(x, y);
-        }
-        if (threadIdx.x == 0) {
-            fixed_out[l * 8 + k] = x;
-            out[l * 8 + k] = int128_to_double(x) * unit;
-        }
+    for (int off = 16; off > 0; off >>= 1) {
+        ulonglong2 y;
+        y.x = __shfl_xor_sync(kFull, x.x, off);
+        y.y = __shfl_xor_sync(kFull, x.y, off);
+        add128(x, y);
+    }
+    if (lane == 0) {
+        fixed_out[l * 8 + k] = x;
+        out[l * 8 + k] = int128_to_double(x) * unit;
     }
     if (l == 0 && threadIdx.x == 0) scale_out[0] = (double)grad_scale(P);
 }
@@ -1336,7 +1336,7 @@ cudaError_t launch_resolve(const unsigned long long *q, const float *area, doubl
 cudaError_t launch_grad_finalize(const TraceParams &p, ulonglong2 *partial, int32_t parts, double *out,
                                  ulonglong2 *fixed_out, double *scale_out, cudaStream_t s) {
     grad_partial_kernel<<<dim3(p.n_lights, parts), 256, 0, s>>>(p, partial);
-    grad_finalize_kernel<<<p.n_lights, 32, 0, s>>>(p, partial, parts, out, fixed_out, scale_out);
+    grad_finalize_kernel<<<p.n_lights, 256, 0, s>>>(p, partial, parts, out, fixed_out, scale_out);
     return cudaGetLastError();
 }
 
