@@ -1174,8 +1174,9 @@ __global__ void resolve_kernel(const unsigned long long *q, const float *area, d
 // chunk of photons starts at begin + t * chunk and its slot s holds light
 // (light of its first photon) + s. Step 1: block (l, p) of a grid of
 // n_lights x P blocks sums every P-th group of 256 of the threads that cover
-// light l into partial[l][p]. Step 2: one warp per light sums the P partials
-// and writes the 128-bit sums (fixed_out), their value dO/dp = sum 2^-64 / G as
+// light l into partial[l][p]. Step 2: one block per light, warp k summing
+// component k of the P partials, writes the 128-bit sums (fixed_out), their
+// value dO/dp = sum 2^-64 / G as
 // doubles (out) and G (scale_out). Integer sums are exact, so neither the
 // split nor the order of the additions changes a bit.
 __global__ void __launch_bounds__(256) grad_partial_kernel(const TraceParams P, ulonglong2 *partial) {
