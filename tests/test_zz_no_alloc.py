@@ -5,7 +5,8 @@ capture, or on a device at its memory budget cannot call cudaMalloc; it gets
 the objective and the adjoint weights from buffers it owns through
 lt_loss_static, whose only scratch is a fixed array inside the library. This
 file checks two calls in a row against lt_loss (the entry point that
-allocates), on different targets, so a stale scratch array would show."""
+allocates), on different targets, so a stale scratch array would show, and
+that a call leaves the device's free memory unchanged."""
 import numpy as np
 import pytest
 
@@ -54,6 +55,15 @@ def test_static_loss_matches_lt_loss_on_two_calls():
             # identical weights give the identical (deterministic) adjoint
             tr.set_adjoint_weights(w)
             assert np.array_equal(tr.trace_adjoint(4, N, HITS), g_ref)
+        # with its kernels loaded and its scratch array found by the calls
+        # above, a call allocates no device memory: the device's free memory
+        # and torch's allocation count are the same before and after it
+        torch.cuda.synchronize()
+        free0, alloc0 = torch.cuda.mem_get_info(0)[0], torch.cuda.memory_allocated(0)
+        lighttrace.loss_static(0, stream, q_ptr, scale, area, target, w, O, alpha=alpha, E_out=E)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info(0)[0] == free0
+        assert torch.cuda.memory_allocated(0) == alloc0
         # a shorter prefix after a full-length call: every block partial it
         # reads must be its own, not one left by the longer call; checked
         # against a float64 sum on the host over the same prefix
