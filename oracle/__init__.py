@@ -26,15 +26,21 @@ _lock = threading.Lock()
 _lib = None
 
 
+def compile_source(src: str, out: str) -> None:
+    """Compile one C source of the oracle into the shared library `out`
+    (gcc, OpenMP, no floating-point contraction)."""
+    cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-Wall", "-Wno-unknown-pragmas", src, "-o", out, "-lm"]
+    subprocess.run(cmd, check=True)
+
+
 def build(force: bool = False) -> str:
-    """Compile oracle.c into oracle/_lib/liboracle.so (gcc, OpenMP)."""
+    """Compile oracle.c into oracle/_lib/liboracle.so."""
     os.makedirs(_OUT_DIR, exist_ok=True)
     if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
         return _SO
     tmp = _SO + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-           "-Wall", "-Wno-unknown-pragmas", _SRC, "-o", tmp, "-lm"]
-    subprocess.run(cmd, check=True)
+    compile_source(_SRC, tmp)
     os.replace(tmp, _SO)
     return _SO
 
