@@ -13,10 +13,12 @@ import types
 import pytest
 
 import oracle
+from oracle import surrogate as S
 from tests import test_oracle_area as T_area
 from tests import test_oracle_geometry as T_geo
 from tests import test_oracle_gradient as T_grad
 from tests import test_oracle_rng as T_rng
+from tests import test_oracle_surrogate as T_sg
 from tests import test_oracle_transport as T_tr
 
 
@@ -42,23 +44,28 @@ def planted_c(old, new):
 
 
 @contextlib.contextmanager
-def planted_py(name, old, new):
-    """oracle.<name> taken from a copy of the module's source with `old`
-    replaced by `new`."""
-    src = open(oracle.__file__).read()
+def planted_py(module, old, new):
+    """Every name of `module` taken from a copy of its source with `old`
+    replaced by `new`, so that whatever the pin calls runs the copy."""
+    src = open(module.__file__).read()
     assert src.count(old) == 1, f"the text to replace must occur once: {old!r}"
-    mod = types.ModuleType("oracle_planted")
-    mod.__file__ = oracle.__file__
-    exec(compile(src.replace(old, new), oracle.__file__, "exec"), mod.__dict__)
-    saved = getattr(oracle, name)
-    setattr(oracle, name, getattr(mod, name))
+    copy = types.ModuleType(module.__name__ + "_planted")
+    copy.__file__ = module.__file__
+    exec(compile(src.replace(old, new), module.__file__, "exec"), copy.__dict__)
+    saved = {}
+    for name, value in copy.__dict__.items():
+        if not name.startswith("__") and hasattr(module, name):
+            saved[name] = getattr(module, name)
+            setattr(module, name, value)
     try:
         yield
     finally:
-        setattr(oracle, name, saved)
+        for name, value in saved.items():
+            setattr(module, name, value)
 
 
-# (id, where, text in the oracle, planted text, the pin that must catch it)
+# (id, where: "c" for oracle.c or the Python module, text in the oracle,
+#  planted text, the pin that must catch it)
 CASES = [
     ("philox-multiplier", "c",
      "uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;",
@@ -110,17 +117,42 @@ CASES = [
      "g += io->w[t] * beta;",
      "g += io->w[t];",
      T_grad.test_fd_exact_intensity_matches_adjoint_point_cornell),
-    ("objective-area-weight-dropped", "py",
+    ("objective-area-weight-dropped", oracle,
      "O = 0.5 * float(np.sum(A * a * r * r))",
      "O = 0.5 * float(np.sum(a * r * r))",
      T_grad.test_loss_on_a_hand_computed_case),
+    # the surrogate's oracle (oracle/surrogate.py)
+    ("hash-prime", S,
+     "PRIMES = (1, 2654435761, 805459861)",
+     "PRIMES = (1, 2654435761, 805459863)",
+     T_sg.test_hash_at_hand_computed_vertices),
+    ("trilinear-weights-swapped", S,
+     "w[..., c] *= f[..., a] if CORNERS[c, a] else 1.0 - f[..., a]",
+     "w[..., c] *= 1.0 - f[..., a] if CORNERS[c, a] else f[..., a]",
+     T_sg.test_encoding_reproduces_linear_fields_on_dense_levels),
+    ("relu-dropped", S,
+     "a.append(_round(np.maximum(z, 0.0), rounding))",
+     "a.append(_round(z, rounding))",
+     T_sg.test_network_matches_torch_autograd),
+    ("relu-mask-dropped-in-backward", S,
+     "dz = _round(da * (a[k] > 0.0), rounding)",
+     "dz = _round(da, rounding)",
+     T_sg.test_network_matches_torch_autograd),
+    ("bf16-round-half-up", S,
+     "b = (b + np.uint64(0x7FFF) + lsb) >> np.uint64(16) << np.uint64(16)",
+     "b = (b + np.uint64(0x8000)) >> np.uint64(16) << np.uint64(16)",
+     T_sg.test_bf16_matches_torch_and_ties_to_even),
+    ("adam-bias-correction-dropped", S,
+     "vh = v / (1 - beta2 ** step)",
+     "vh = v",
+     T_sg.test_adam_matches_torch),
 ]
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 def test_planted_mistake_fails_its_pin(case):
     _, where, old, new, pin = case
-    ctx = planted_c(old, new) if where == "c" else planted_py("loss", old, new)
+    ctx = planted_c(old, new) if where == "c" else planted_py(where, old, new)
     with ctx:
         with pytest.raises(AssertionError):
             pin()
@@ -136,5 +168,9 @@ def test_an_unmodified_copy_passes_every_pin():
     with planted_c(same, same):
         for pin in pins:
             pin()
-    with planted_py("loss", "O = 0.5 * float(np.sum(A * a * r * r))", "O = 0.5 * float(np.sum(A * a * r * r))"):
-        T_grad.test_loss_on_a_hand_computed_case()
+    for module in (oracle, S):
+        keep = "O = 0.5 * float(np.sum(A * a * r * r))" if module is oracle else "vh = v / (1 - beta2 ** step)"
+        with planted_py(module, keep, keep):
+            for c in CASES:
+                if c[1] is module:
+                    c[4]()
