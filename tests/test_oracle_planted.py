@@ -117,6 +117,34 @@ CASES = [
      "g += io->w[t] * beta;",
      "g += io->w[t];",
      T_grad.test_fd_exact_intensity_matches_adjoint_point_cornell),
+    ("point-emission-hemisphere", "c",
+     "double c = 1.0 - 2.0 * u1;",
+     "double c = 1.0 - u1;",
+     T_tr.test_point_emission_is_uniform_on_the_sphere),
+    ("area-emission-cosine-lobe", "c",
+     "        double c = 1.0 - u1;\n",
+     "        double c = sqrt(1.0 - u1);\n",
+     T_area.test_emission_samples_the_rectangle_and_the_hemisphere),
+    ("spot-solid-angle-of-the-inner-cone", "c",
+     "o->omega = 2.0 * OR_PI * (1.0 - o->co);",
+     "o->omega = 2.0 * OR_PI * (1.0 - o->ci);",
+     T_tr.test_energy_closed_cube_spot_matches_cone_integral),
+    ("intensity-not-halved", "c",
+     "o->I = 0.5 * o->p * o->p;",
+     "o->I = o->p * o->p;",
+     T_tr.test_point_light_irradiance_on_plane_is_inverse_square),
+    ("texel-area-of-one-axis", "c",
+     "double a = tile_area[k] / ((double)res[2 * k] * (double)res[2 * k + 1]);",
+     "double a = tile_area[k] / (double)res[2 * k];",
+     T_tr.test_point_light_irradiance_on_plane_is_inverse_square),
+    ("one-sided-triangles", "c",
+     "if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return 0;",
+     "if (U < 0.0f || V < 0.0f || W < 0.0f) return 0;",
+     T_geo.test_closest_hit_matches_fp64_brute_force),
+    ("skip-tile-ignored", "c",
+     "        if (s->tile[i] == skip_tile) continue;",
+     "        if (0 && s->tile[i] == skip_tile) continue;",
+     T_geo.test_skip_tile_excludes_the_tile_left),
     ("objective-area-weight-dropped", oracle,
      "O = 0.5 * float(np.sum(A * a * r * r))",
      "O = 0.5 * float(np.sum(a * r * r))",
