@@ -380,8 +380,8 @@ LT_API int lt_batch_irradiance(void *ctx, int32_t design, float *E_out, int is_d
  * lt_loss.
  *
  * Some callers must not call cudaMalloc: code running inside a memory pool
- * that another framework owns (its allocator would not see the block), code
- * inside a CUDA-graph capture, or a device already at its memory budget.
+ * that another framework owns (its allocator would not see the block), or a
+ * device already at its memory budget.
  * This call allocates nothing. The caller passes every input and output as
  * device pointers on `device`; the only scratch, one double per block of
  * 4096 texels, lives in a fixed 32 KiB array compiled into the library, which
@@ -397,8 +397,7 @@ LT_API int lt_batch_irradiance(void *ctx, int32_t design, float *E_out, int is_d
  * LT_ERR_ARG (use lt_loss). Work is queued on cuda_stream, nothing is
  * synchronised; the calling thread's current device is restored. The first
  * call on a device looks up the array's device address
- * (cudaGetSymbolAddress): make that first call before any stream capture.
- * The address is kept for the life of the process: after cudaDeviceReset
+ * (cudaGetSymbolAddress). The address is kept for the life of the process: after cudaDeviceReset
  * (or anything else that replaces the device's primary context) this call
  * must not be used on that device again. If a CUDA error from earlier work
  * is pending on the calling thread, the call returns LT_ERR_STATE without

@@ -3,8 +3,7 @@
 //
 // Some callers must not call cudaMalloc at all: code running inside a
 // memory pool that another framework owns (its allocator would not see the
-// block and could not account for it), inside a CUDA-graph capture where a
-// fresh allocation is not allowed, or on a device already filled to its
+// block and could not account for it), or on a device already filled to its
 // budget. lt_loss_static computes the same objective as lt_loss from buffers
 // the caller owns, and keeps its only scratch -- one partial sum per block --
 // in a fixed array compiled into this library.

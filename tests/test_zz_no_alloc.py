@@ -1,9 +1,9 @@
 """lt_loss_static: the objective for callers that cannot allocate device memory.
 
-Code that runs inside another framework's memory pool, inside a CUDA-graph
-capture, or on a device at its memory budget cannot call cudaMalloc; it gets
-the objective and the adjoint weights from buffers it owns through
-lt_loss_static, whose only scratch is a fixed array inside the library. This
+Code that runs inside another framework's memory pool, or on a device at its
+memory budget, cannot call cudaMalloc; it gets the objective and the adjoint
+weights from buffers it owns through lt_loss_static, whose only scratch is a
+fixed array inside the library. This
 file checks two calls in a row against lt_loss (the entry point that
 allocates), on different targets, so a stale scratch array would show, and
 that a call leaves the device's free memory unchanged."""
