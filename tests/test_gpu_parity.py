@@ -163,6 +163,35 @@ def test_all_photons_escape(tr):
     assert np.all(E == 0) and st["segments_forward"] == 4096
 
 
+def test_single_triangle_scene_staged_and_through_l1(tr):
+    # The smallest scene: one triangle, so the BVH is one node whose only
+    # child is a leaf. Both node paths (staged and through L1) trace it; the
+    # texel and the gradient match the oracle, and the two paths give the
+    # same integer sums.
+    b = scenes._Builder()
+    b.triangle([-1.0, -1.0, 0.0], [1.5, -1.0, 0.0], [-1.0, 1.5, 0.0], 0.6)
+    sc = b.build("one triangle")
+    L = scenes.make_lights([scenes.point_light((0.0, 0.0, 0.7), 1.0)])
+    n, hits, seed = 1 << 16, 3, 6
+    E, st = _forward(tr, sc, L, seed, n, hits)
+    assert st["n_nodes"] == 1 and st["bvh_depth"] == 1 and st["staged_nodes"] == 1, st
+    q_staged = tr.texel_sums()
+    info = _every_texel(tr, sc, L, seed, n, hits)
+    assert info["lit"] == 1 and info["diverged"] <= 1e-3 * n, info
+    ref = oracle.forward(sc, L, seed, n, hits, counts=True)
+    assert st["segments_forward"] == ref["segments"]
+    tr.set_launch(0, 0, 0)
+    try:
+        tr.trace_forward(seed, n, hits)
+        assert tr.stats()["staged_nodes"] == 0
+        assert np.array_equal(tr.texel_sums(), q_staged)
+        target = np.full(sc.n_texels, 0.5 * float(E[0]), np.float32)
+        g = _adjoint_case(tr, sc, L, target, n, hits, seed + 1)
+        assert np.all(np.abs(g[0, [0, 1, 2, 5]]) > 0)
+    finally:
+        tr.set_launch(0, 0, 72 * 1024)
+
+
 def test_fixed_point_sums_identical_across_launch_shapes(tr):
     sc, L = scenes.office(seed=0, pitch=0.1), scenes.office_lights(0)
     tr.upload_scene(sc)
