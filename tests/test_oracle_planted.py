@@ -170,6 +170,22 @@ CASES = [
      "b = (b + np.uint64(0x7FFF) + lsb) >> np.uint64(16) << np.uint64(16)",
      "b = (b + np.uint64(0x8000)) >> np.uint64(16) << np.uint64(16)",
      T_sg.test_bf16_matches_torch_and_ties_to_even),
+    ("direct-term-inverse-cube-factor", S,
+     "dD[:, 0:3] += (-2.0 * a * np.abs(cr) / r ** 3)[:, None] * u",
+     "dD[:, 0:3] += (-3.0 * a * np.abs(cr) / r ** 3)[:, None] * u",
+     T_sg.test_geometry_derivatives_against_central_differences),
+    ("direction-derivative-sign", S,
+     "P = (np.eye(3)[None] - u[:, :, None] * u[:, None, :]) / r[:, None, None]",
+     "P = (np.eye(3)[None] + u[:, :, None] * u[:, None, :]) / r[:, None, None]",
+     T_sg.test_geometry_derivatives_against_central_differences),
+    ("surrogate-soft-edge-derivative-factor", S,
+     "da_dcos = np.where(soft, 2.0 * s / (ci - co), 0.0)",
+     "da_dcos = np.where(soft, s / (ci - co), 0.0)",
+     T_sg.test_geometry_derivatives_against_central_differences),
+    ("head-sigmoid-derivative", S,
+     "return K, v * (1.0 - v) * D, R_SCALE * sigmoid(o[:, 1]), v",
+     "return K, v * D, R_SCALE * sigmoid(o[:, 1]), v",
+     T_sg.test_head_derivatives),
     ("adam-bias-correction-dropped", S,
      "vh = v / (1 - beta2 ** step)",
      "vh = v",
